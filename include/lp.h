@@ -1,0 +1,223 @@
+/*
+ * lp.h - C ABI of the GB300 (sm_103a) Lagrangian-particle granular-flow step.
+ *
+ * The library implements, on one GPU, the per-time-step particle hot path of
+ * the Lagrangian particle (LP) method with mu(I) rheology of Zepeda & Samulyak,
+ * "Computational Model for Granular Flows based on the Lagrangian Particle
+ * Method" (arXiv 2206.14061):
+ *   neighbour search and stencils          (Sec. 3.1 items 4-6)
+ *   GFD least-squares derivative fits      (Sec. 3.1 item 7)
+ *   strain-rate norm and mu(I) closure     (Sec. 2.2, 2.3)
+ *   stress-divergence update of V, u, x    (Sec. 3.1 items 8, 10)
+ *   floor mirror particles                 (Sec. 3.1 item 9, solid boundary)
+ * plus a hand-written adjoint of the step (not in the paper).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an lp_status. LP_OK is 0.
+ *   - Particle arrays are CALLER-OWNED DEVICE pointers, FP64, structure of
+ *     arrays, length n, in the caller's particle order. The library never
+ *     frees them and never keeps them beyond the call.
+ *   - The library owns its workspace through an opaque lp_ctx (one context
+ *     per device; not thread-safe: serialise calls on one context).
+ *   - Work is enqueued on the given CUDA stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream) and returns before it
+ *     finishes, except where a call says it synchronises.
+ *   - Null pointers, negative sizes and sizes beyond the context's capacity
+ *     fail on the host with LP_ERR_INVALID_ARG and enqueue nothing.
+ *   - Errors detected on the device (stencil overflow, non-finite values,
+ *     bounded-wait timeouts) are accumulated in the context and reported by
+ *     lp_ctx_sync(), which returns the first such error and clears them.
+ *
+ * Neighbour encoding: an entry j (0 <= j < 2^31) is particle j; j | 2^31 is
+ * the floor mirror of particle j, located at (x_j, y_j, 2 floor_z - z_j).
+ */
+#ifndef LP_H
+#define LP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lp_status;
+#define LP_OK 0
+#define LP_ERR_INVALID_ARG 1
+#define LP_ERR_STENCIL_OVERFLOW 2
+#define LP_ERR_NONFINITE 3
+#define LP_ERR_TIMEOUT 4
+#define LP_ERR_CUDA 5
+#define LP_ERR_OOM 6
+#define LP_ERR_UNIMPLEMENTED 7
+
+/* arithmetic of the least-squares fits */
+#define LP_FP64 0  /* FP64 moments, Cholesky and solve (QR fallback in FP64)   */
+#define LP_MIXED 1 /* FP32 moments and Cholesky + one FP64 refinement step     */
+
+/* floor mirror particles (Sec. 3.1 item 9) */
+#define LP_MIRROR_NONE 0
+#define LP_MIRROR_NOSLIP 1   /* mirror velocity -u (all components)            */
+#define LP_MIRROR_FREESLIP 2 /* mirror velocity (u, v, -w): normal component flipped */
+
+/* bits of lp_diag.flags */
+#define LP_FLAG_OVERFLOW 0x1u  /* a stencil had more neighbours than cap       */
+#define LP_FLAG_NONFINITE 0x2u /* a new state value was NaN or infinite        */
+#define LP_FLAG_TIMEOUT 0x4u   /* a bounded device wait gave up                */
+#define LP_FLAG_BELOW_FLOOR 0x8u /* a particle ended below the floor           */
+
+#define LP_MAX_CAP 64 /* largest stencil capacity */
+
+typedef struct lp_ctx lp_ctx;
+
+typedef struct {
+  int32_t device;        /* CUDA device ordinal the context lives on          */
+  int32_t max_columns;   /* largest number of independent columns per call    */
+  int64_t max_particles; /* largest n of any call on this context             */
+  int32_t cap;           /* stencil capacity (1..LP_MAX_CAP) used by lp_step  */
+  int32_t pad;
+} lp_ctx_desc;
+
+/* A set of particles. Columns are independent problems (their particles never
+ * neighbour each other); column c holds particles
+ * [column_offsets[c], column_offsets[c+1]). */
+typedef struct {
+  double *x, *y, *z;    /* positions (m)                                      */
+  double *u, *v, *w;    /* velocity (m/s)                                      */
+  double *V;            /* specific volume V = 1/phi (dimensionless)           */
+  int64_t n;
+  const int32_t* column_offsets; /* HOST array of ncolumns+1 ints, or NULL for one column */
+  int32_t ncolumns;              /* >= 1                                        */
+  int32_t pad;
+} lp_particles;
+
+/* mu(I) law (Sec. 2.2): mu(I) = mu_s + (mu_2 - mu_s)/(I0/I + 1), grain
+ * diameter d (m), grain density rho_s = phi_s (kg/m^3). */
+typedef struct {
+  double mu_s, mu_2, I0, d, rho_s;
+} lp_mui;
+
+/* pressure law (Sec. 2.2.1): P = 0 for phi <= phi_min; Bagnold-type inertial
+ * pressure for phi_min < phi <= phi_max; phi_s (alpha + beta phi) above. */
+typedef struct {
+  double phi_c, phi_min, phi_max, alpha, beta;
+} lp_eos;
+
+typedef struct {
+  double h;           /* lattice spacing: offsets are scaled by 1/h in the fits */
+  double radius;      /* stencil radius: all neighbours with d <= radius        */
+  double gx, gy, gz;  /* body force (m/s^2)                                     */
+  double floor_z;     /* height of the floor plane for mirrors                  */
+  int32_t mirror_mode;   /* LP_MIRROR_*                                         */
+  int32_t precision;     /* LP_FP64 or LP_MIXED                                 */
+  int32_t rebuild_every; /* rebuild stencils every k steps (1 = every step)     */
+  int32_t use_graph;     /* 1: replay the step as a captured CUDA graph         */
+} lp_params;
+
+/* Stencils produced by lp_build_neighbors: library-owned device memory, valid
+ * until the next lp_build_neighbors / lp_step / lp_step_adjoint call on the
+ * same context. nbr is k-major: nbr[k*n + i], k < min(cnt[i], cap), in
+ * caller indices with the mirror bit. */
+typedef struct {
+  const int32_t* nbr;
+  const int32_t* cnt;
+  int64_t n;
+  int32_t cap;
+  int32_t pad;
+} lp_neighbors;
+
+typedef struct {
+  uint32_t flags;        /* LP_FLAG_* seen since the last lp_ctx_sync            */
+  int32_t min_stencil, max_stencil;
+  int32_t pad;
+  int64_t n_overflow;    /* particle-steps whose stencil exceeded cap            */
+  int64_t n_fallback;    /* fits that used the pivoted-QR path                   */
+  int64_t n_gas, n_quasistatic, n_over_c; /* particle-steps per regime (phi > phi_c) */
+  int64_t n_nonfinite, n_below_floor;
+} lp_diag;
+
+/* Version string of the library build. Never fails. */
+const char* lp_version(void);
+/* Human-readable name of a status code. Never fails. */
+const char* lp_status_string(lp_status s);
+
+/* Create a context on desc->device: allocates the workspace for
+ * desc->max_particles particles (about 1 kB each). Makes desc->device current
+ * for the calling thread. LP_ERR_OOM if the allocation fails. */
+lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out);
+/* Free the workspace. Waits for all work of the context to finish. */
+lp_status lp_ctx_destroy(lp_ctx* ctx);
+/* Wait for `stream`, copy the device diagnostics into *diag (may be NULL),
+ * clear them, and return the first device-detected error (overflow ->
+ * LP_ERR_STENCIL_OVERFLOW, non-finite -> LP_ERR_NONFINITE, timeout ->
+ * LP_ERR_TIMEOUT) or LP_OK. Synchronises. */
+lp_status lp_ctx_sync(lp_ctx* ctx, void* stream, lp_diag* diag);
+
+/* Neighbour search (Sec. 3.1 items 5-6, mirrors item 9). For every particle i:
+ * all j != i of the same column with ((dx*dx)+(dy*dy))+(dz*dz) <= r_i*r_i in
+ * FP64 without contraction (d = x_j - x_i), and, if mirror_mode != NONE, every
+ * mirror j* (including i*) passing the same test. r_i = radius[i] if radius
+ * (device, length n) is non-NULL, else r_const. If keep_nearest != 0, only
+ * the min(cap, m_i) nearest are kept (ties by index, real before mirror) and
+ * cnt[i] is that number; otherwise cnt[i] is the full count and stencils
+ * longer than cap set LP_FLAG_OVERFLOW. Order within a stencil is
+ * unspecified. Result in *out (library-owned). */
+lp_status lp_build_neighbors(lp_ctx* ctx, const lp_particles* p, const double* radius,
+                             double r_const, int32_t mirror_mode, double floor_z, int32_t cap,
+                             int32_t keep_nearest, lp_neighbors* out, void* stream);
+
+/* Copy stencils to host in canonical order: host_nbr is n x cap row-major,
+ * real neighbours first then mirrors, each ascending; host_cnt[i] =
+ * min(cnt[i], cap). Synchronises. */
+lp_status lp_neighbors_export(lp_ctx* ctx, const lp_neighbors* nb, int32_t* host_nbr,
+                              int32_t* host_cnt, void* stream);
+
+/* GFD least-squares derivatives (Sec. 3.1 item 7) of nf fields on the given
+ * stencils. fields: HOST array of nf DEVICE pointers (length n each);
+ * mirror_sign: HOST array of nf factors applied to a field at a floor mirror
+ * (+1 even, -1 odd, 0 zero). Rows: offsets d = (x_k - x_i)/h, columns
+ * [dx, dy, dz, dx^2/2, dy^2/2, dz^2/2, dx dy, dx dz, dy dz], right-hand side
+ * s_k - s_i. coeffs (device, n*nf*9 doubles, row-major [i][f][c]) receives
+ * d/dx, d/dy, d/dz, d2/dx2, d2/dy2, d2/dz2, d2/dxdy, d2/dxdz, d2/dydz.
+ * precision: LP_FP64 or LP_MIXED. 1 <= nf <= 16. */
+lp_status lp_fit_derivatives(lp_ctx* ctx, const lp_particles* p, const lp_neighbors* nb,
+                             const double* const* fields, const double* mirror_sign, int32_t nf,
+                             double h, double floor_z, double* coeffs, int32_t precision,
+                             void* stream);
+
+/* Pointwise mu(I) stress (Sec. 2.2, 2.2.1) from V and the velocity gradient
+ * grad_u (device, n x 9 row-major, grad_u[9i + 3a + b] = d u_a / d x_b):
+ * gdot = D - (div u / 3) I as (xx, yy, zz, xy, xz, yz) (device, n x 6),
+ * |gdot| = sqrt(gdot:gdot / 2), pressure P, effective viscosity eta
+ * (tau = eta gdot) and regime (0 gas, 1 inertial, 2 quasi-static) chosen
+ * from phi = 1/V. Any output pointer may be NULL. */
+lp_status lp_mui_stress(lp_ctx* ctx, const lp_mui* mui, const lp_eos* eos, int64_t n,
+                        const double* V, const double* grad_u, double* gdot, double* gdot_norm,
+                        double* P, double* eta, int8_t* regime, void* stream);
+
+/* nsteps explicit LP steps in place (Sec. 3.1 items 4-10). mui points to
+ * p->ncolumns entries (HOST), one per column. Per step: stencils from the
+ * current positions (every params->rebuild_every steps), pass 1 fits u, v, w
+ * and gives gdot, |gdot|, div u, (1/2) Lap u + (1/6) grad div u and
+ * V^{n+1} = V^n + dt V^n div u^n; pass 2 fits |gdot| and V^{n+1} and gives the
+ * acceleration from the pressure law and mu(I) stress at phi^{n+1}; then
+ * u^{n+1} = u^n + dt a and x^{n+1} = x^n + dt (u^n + u^{n+1})/2. */
+lp_status lp_step(lp_ctx* ctx, lp_particles* p, const lp_mui* mui, const lp_eos* eos,
+                  const lp_params* params, double dt, int32_t nsteps, void* stream);
+
+/* Adjoint of nsteps lp_step steps (FP64) from `initial` (not modified). The
+ * forward run being differentiated rebuilds stencils only at the start of each
+ * segment of checkpoint_every steps and holds them fixed within it; regimes
+ * are frozen at their forward values and d|gdot|/d gdot is taken as 0 where
+ * |gdot| = 0. seed holds dL/d(final x, y, z, u, v, w, V) (device). On return
+ * dL_dmui (device, 3 doubles) holds dL/d(mu_s, mu_2, I0) summed over all
+ * columns, and if dL_dinitial is non-NULL its arrays receive dL/d(initial
+ * state). Synchronises. Requires p->ncolumns == 1 in this version. */
+lp_status lp_step_adjoint(lp_ctx* ctx, const lp_particles* initial, const lp_mui* mui,
+                          const lp_eos* eos, const lp_params* params, double dt, int32_t nsteps,
+                          int32_t checkpoint_every, const lp_particles* seed, double* dL_dmui,
+                          lp_particles* dL_dinitial, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LP_H */

@@ -1,0 +1,639 @@
+// C ABI of the LP step library: context, workspace, argument checks and the
+// host-side orchestration of the kernels in neighbors.cu and fit.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+namespace lp {
+// neighbors.cu
+void launch_fill_colid(int n, const int32_t* offs, int ncol, int32_t* colid, cudaStream_t st);
+void launch_bbox(int ncol, const double* x, const double* y, const double* z, const double* radius,
+                 const int32_t* offs, double* out, cudaStream_t st);
+void launch_keys(int n, const double* x, const double* y, const double* z, const int32_t* colid,
+                 const GridCol* grids, int64_t ncell, uint32_t* key, uint32_t* count,
+                 cudaStream_t st);
+void exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* tile_sum, int64_t n,
+                    cudaStream_t st);
+int64_t scan_tiles(int64_t n);
+void launch_scatter(int n, const uint32_t* key, const uint32_t* start, uint32_t* fill,
+                    int32_t* tmp, cudaStream_t st);
+void launch_cell_sort(int64_t ncell, const uint32_t* start, int32_t* tmp, const int32_t* ids,
+                      cudaStream_t st);
+void launch_gather(int n, const int32_t* tmp, const double* const* src, double* const* dst,
+                   int nsrc, const int32_t* ids_in, int32_t* ids_out, const int32_t* col_in,
+                   int32_t* col_out, const GridCol* grids, float4* pf, cudaStream_t st);
+void launch_neighbors(bool keep, int n, const double* x, const double* y, const double* z,
+                      const float4* pf, const int32_t* colid, const int32_t* ids,
+                      const GridCol* grids, const uint32_t* start, const double* radius,
+                      double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
+                      int32_t* cnt, DevDiag* dg, cudaStream_t st);
+void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
+                          const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st);
+// fit.cu
+void launch_pass1(int prec, const StepArgs& A, cudaStream_t st);
+void launch_pass2(int prec, const StepArgs& A, cudaStream_t st);
+void launch_fit(int prec, const FitArgs& F, cudaStream_t st);
+void launch_mui_stress(int64_t n, const ColMui& m, const lp_eos& e, const double* V,
+                       const double* gu, double* gdot, double* gnorm, double* P, double* eta,
+                       int8_t* regime, cudaStream_t st);
+// misc.cu
+void launch_iota(int n, int32_t* a, cudaStream_t st);
+void launch_scatter_state(int n, const int32_t* ids, const double* const* src,
+                          double* const* dst, int nf, cudaStream_t st);
+}  // namespace lp
+
+using namespace lp;
+
+// gather tables: [direction][kind][field]; kind 0 = step state
+// (x,y,z,u,v,w,V), kind 1 = search (x,y,z,radius)
+enum { kTabFields = 8 };
+
+struct lp_ctx {
+  int device = 0;
+  int64_t cap_n = 0;
+  int cap_cols = 0;
+  int cap = 0;
+  double* X[2][kTabFields] = {};  // state fields 0..6 and radius (7)
+  int32_t* ids[2] = {};
+  int32_t* colid[2] = {};
+  float4* pf = nullptr;
+  uint32_t* key = nullptr;
+  int32_t* tmp = nullptr;
+  int32_t* nbr = nullptr;
+  int32_t* cnt = nullptr;
+  int32_t* nbr_o = nullptr;
+  int32_t* cnt_o = nullptr;
+  double* p1 = nullptr;
+  double* fac = nullptr;
+  float* facf = nullptr;
+  int32_t* fbslot = nullptr;
+  int32_t* fb_list = nullptr;
+  int32_t* fb_count = nullptr;
+  double* fbgrad = nullptr;
+  int fb_cap = 0;
+  uint32_t* cells = nullptr;  // count | fill | start, cell_capacity entries each
+  uint32_t* tile = nullptr;
+  int64_t cell_capacity = 0;
+  GridCol* d_grids = nullptr;
+  ColMui* d_mui = nullptr;
+  int32_t* d_offs = nullptr;
+  double* d_bbox = nullptr;
+  double* h_bbox = nullptr;
+  DevDiag* dg = nullptr;
+  DevDiag* h_dg = nullptr;
+  double** d_tab = nullptr;  // [2 dir][2 kind][2 src/dst][8]
+  double** d_ptr = nullptr;  // caller pointers for the final scatter
+  double** h_ptr = nullptr;  // pinned staging of d_ptr
+  int cx = 0, ci = 0;
+  int64_t ncell = 0;
+  std::vector<GridCol> h_grids;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+const char* kVersion = "lp-gb300 0.1 (sm_103a)";
+
+template <typename T>
+lp_status dalloc(lp_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_OOM;
+  }
+  c->allocs.push_back(q);
+  *p = (T*)q;
+  return LP_OK;
+}
+
+lp_status cuda_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+#define LP_TRY(expr)                 \
+  do {                               \
+    lp_status _s = (expr);           \
+    if (_s != LP_OK) return _s;      \
+  } while (0)
+
+lp_status reset_diag(lp_ctx* c, cudaStream_t st) {
+  DevDiag z{};
+  z.min_stencil = INT32_MAX;
+  *c->h_dg = z;
+  if (cudaMemcpyAsync(c->dg, c->h_dg, sizeof(DevDiag), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return LP_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+lp_status ensure_cells(lp_ctx* c, int64_t ncell) {
+  if (ncell + 2 <= c->cell_capacity) return LP_OK;
+  int64_t want = std::max<int64_t>(ncell + 2, c->cell_capacity * 2);
+  if (c->cells) {
+    cudaFree(c->cells);
+    cudaFree(c->tile);
+    c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), (void*)c->cells), c->allocs.end());
+    c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), (void*)c->tile), c->allocs.end());
+    c->cells = nullptr;
+    c->tile = nullptr;
+  }
+  LP_TRY(dalloc(c, &c->cells, (size_t)want * 3));
+  LP_TRY(dalloc(c, &c->tile, (size_t)scan_tiles(want) + 1));
+  c->cell_capacity = want;
+  return LP_OK;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Per-column grids from the bounding boxes (host), uploaded to the device.
+lp_status setup_grids(lp_ctx* c, int ncol, double rmax, cudaStream_t st) {
+  const int margin = 4;
+  const double base = rmax * (1.0 + 0x1p-20);
+  const int64_t budget = std::max<int64_t>(4 * c->cap_n, (int64_t)1 << 20);
+  c->h_grids.resize(ncol);
+  int64_t total = 0;
+  double cell = base;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    total = 0;
+    for (int k = 0; k < ncol; ++k) {
+      const double* b = c->h_bbox + 7 * k;
+      GridCol g{};
+      double lo[3], ext[3];
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::isfinite(b[a]) ? b[a] : 0.0;
+        ext[a] = (std::isfinite(b[a]) && std::isfinite(b[3 + a])) ? b[3 + a] - b[a] : 0.0;
+      }
+      int dims[3];
+      for (int a = 0; a < 3; ++a) {
+        double d = std::floor(ext[a] / cell) + 1 + 2 * margin;
+        dims[a] = (int)std::min(1024.0, std::max(1.0, d));
+      }
+      g.ox = lo[0] - margin * cell;
+      g.oy = lo[1] - margin * cell;
+      g.oz = lo[2] - margin * cell;
+      g.inv_c = 1.0 / cell;
+      g.cf = (float)cell;
+      g.nx = dims[0]; g.ny = dims[1]; g.nz = dims[2];
+      g.cell_off = total;
+      total += (int64_t)dims[0] * dims[1] * dims[2];
+      c->h_grids[k] = g;
+    }
+    if (total <= budget) break;
+    cell *= 1.25;  // coarser cells keep the grid within budget (still >= rmax)
+  }
+  if (total > ((int64_t)1 << 31) - 2) return LP_ERR_INVALID_ARG;
+  LP_TRY(ensure_cells(c, total));
+  c->ncell = total;
+  if (cudaMemcpyAsync(c->d_grids, c->h_grids.data(), sizeof(GridCol) * ncol,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return LP_ERR_CUDA;
+  return LP_OK;
+}
+
+// Upload offsets and column ids; compute the bounding boxes (synchronises).
+lp_status begin_columns(lp_ctx* c, const lp_particles* p, const double* radius_dev, int buf,
+                        std::vector<int32_t>& offs, cudaStream_t st) {
+  const int ncol = p->ncolumns;
+  if (cudaMemcpyAsync(c->d_offs, offs.data(), sizeof(int32_t) * (ncol + 1), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return LP_ERR_CUDA;
+  launch_fill_colid((int)p->n, c->d_offs, ncol, c->colid[c->ci], st);
+  launch_bbox(ncol, c->X[buf][0], c->X[buf][1], c->X[buf][2], radius_dev, c->d_offs, c->d_bbox, st);
+  if (cudaMemcpyAsync(c->h_bbox, c->d_bbox, sizeof(double) * 7 * ncol, cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess)
+    return LP_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LP_ERR_CUDA;
+  return cuda_status();
+}
+
+lp_status check_particles(const lp_ctx* c, const lp_particles* p, std::vector<int32_t>& offs,
+                          bool need_state) {
+  if (!p || p->n < 0 || p->n > c->cap_n || p->ncolumns < 1 || p->ncolumns > c->cap_cols)
+    return LP_ERR_INVALID_ARG;
+  if (!p->x || !p->y || !p->z) return LP_ERR_INVALID_ARG;
+  if (need_state && (!p->u || !p->v || !p->w || !p->V)) return LP_ERR_INVALID_ARG;
+  offs.assign(p->ncolumns + 1, 0);
+  if (p->column_offsets) {
+    for (int k = 0; k <= p->ncolumns; ++k) offs[k] = p->column_offsets[k];
+    if (offs[0] != 0 || offs[p->ncolumns] != p->n) return LP_ERR_INVALID_ARG;
+    for (int k = 0; k < p->ncolumns; ++k)
+      if (offs[k + 1] < offs[k]) return LP_ERR_INVALID_ARG;
+  } else {
+    if (p->ncolumns != 1) return LP_ERR_INVALID_ARG;
+    offs[1] = (int32_t)p->n;
+  }
+  return LP_OK;
+}
+
+// Counting sort by cell (stable by original index) from buffer c->cx into
+// the other buffer; nsrc fields of table `kind`.
+void sort_particles(lp_ctx* c, int n, int kind, int nsrc, cudaStream_t st) {
+  const int d = c->cx;
+  uint32_t* count = c->cells;
+  uint32_t* fill = c->cells + c->cell_capacity;
+  uint32_t* start = c->cells + 2 * c->cell_capacity;
+  cudaMemsetAsync(c->cells, 0, sizeof(uint32_t) * 2 * c->cell_capacity, st);
+  launch_keys(n, c->X[d][0], c->X[d][1], c->X[d][2], c->colid[c->ci], c->d_grids, c->ncell,
+              c->key, count, st);
+  // cells 0..ncell-1, the bucket of non-finite particles (ncell), the total
+  exclusive_scan(count, start, c->tile, c->ncell + 2, st);
+  launch_scatter(n, c->key, start, fill, c->tmp, st);
+  launch_cell_sort(c->ncell, start, c->tmp, c->ids[c->ci], st);
+  const double* const* src = (const double* const*)(c->d_tab + ((d * 2 + kind) * 2 + 0) * kTabFields);
+  double* const* dst = c->d_tab + ((d * 2 + kind) * 2 + 1) * kTabFields;
+  launch_gather(n, c->tmp, src, dst, nsrc, c->ids[c->ci], c->ids[1 - c->ci], c->colid[c->ci],
+                c->colid[1 - c->ci], c->d_grids, c->pf, st);
+  c->cx ^= 1;
+  c->ci ^= 1;
+}
+
+StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
+  StepArgs A{};
+  A.n = n;
+  A.cap = c->cap;
+  const int d = c->cx;
+  A.x = c->X[d][0]; A.y = c->X[d][1]; A.z = c->X[d][2];
+  A.u = c->X[d][3]; A.v = c->X[d][4]; A.w = c->X[d][5]; A.V = c->X[d][6];
+  A.xo = c->X[1 - d][0]; A.yo = c->X[1 - d][1]; A.zo = c->X[1 - d][2];
+  A.uo = c->X[1 - d][3]; A.vo = c->X[1 - d][4]; A.wo = c->X[1 - d][5]; A.Vo = c->X[1 - d][6];
+  A.nbr = c->nbr; A.cnt = c->cnt; A.colid = c->colid[c->ci];
+  A.mui = c->d_mui;
+  A.fac = c->fac; A.facf = c->facf;
+  A.fbslot = c->fbslot; A.fb_list = c->fb_list; A.fb_count = c->fb_count; A.fb_cap = c->fb_cap;
+  A.p1 = c->p1; A.fbgrad = c->fbgrad; A.dg = c->dg;
+  A.K = K;
+  return A;
+}
+
+// One LP step on the context's internal (sorted) state.
+void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cudaStream_t st) {
+  if (rebuild) {
+    sort_particles(c, n, 0, 7, st);
+    launch_neighbors(false, n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->pf,
+                     c->colid[c->ci], c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity,
+                     nullptr, K.radius, K.mirror_mode, K.floor_z, c->cap, c->nbr, c->cnt, c->dg,
+                     st);
+  }
+  cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
+  StepArgs A = step_args(c, n, K);
+  launch_pass1(prec, A, st);
+  launch_pass2(prec, A, st);
+  c->cx ^= 1;
+}
+
+bool valid_params(const lp_params* q, const lp_eos* e, double dt) {
+  if (!q || !e) return false;
+  if (!finite_pos(q->h) || !finite_pos(q->radius) || !std::isfinite(dt) || dt < 0) return false;
+  if (q->mirror_mode < 0 || q->mirror_mode > 2) return false;
+  if (q->precision != LP_FP64 && q->precision != LP_MIXED) return false;
+  if (q->rebuild_every < 1) return false;
+  if (!(e->phi_min < e->phi_max && e->phi_max < e->phi_c)) return false;
+  return true;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+
+extern "C" {
+
+const char* lp_version(void) { return kVersion; }
+
+const char* lp_status_string(lp_status s) {
+  switch (s) {
+    case LP_OK: return "ok";
+    case LP_ERR_INVALID_ARG: return "invalid argument";
+    case LP_ERR_STENCIL_OVERFLOW: return "stencil overflow";
+    case LP_ERR_NONFINITE: return "non-finite value";
+    case LP_ERR_TIMEOUT: return "device wait timed out";
+    case LP_ERR_CUDA: return "CUDA error";
+    case LP_ERR_OOM: return "out of device memory";
+    case LP_ERR_UNIMPLEMENTED: return "not implemented";
+    default: return "unknown status";
+  }
+}
+
+lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
+  if (!desc || !out || desc->max_particles < 1 || desc->max_particles > ((int64_t)1 << 30) ||
+      desc->cap < 1 || desc->cap > LP_MAX_CAP || desc->max_columns < 1 ||
+      desc->max_columns > kMaxColumns)
+    return LP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(desc->device) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  lp_ctx* c = new lp_ctx();
+  c->device = desc->device;
+  c->cap_n = desc->max_particles;
+  c->cap_cols = desc->max_columns;
+  c->cap = desc->cap;
+  const size_t n = (size_t)c->cap_n;
+  lp_status s = LP_OK;
+  for (int d = 0; d < 2 && s == LP_OK; ++d) {
+    for (int f = 0; f < kTabFields && s == LP_OK; ++f) s = dalloc(c, &c->X[d][f], n);
+    if (s == LP_OK) s = dalloc(c, &c->ids[d], n);
+    if (s == LP_OK) s = dalloc(c, &c->colid[d], n);
+  }
+  c->fb_cap = (int)std::min<int64_t>(c->cap_n, 1 << 20);
+  if (s == LP_OK) s = dalloc(c, &c->pf, n);
+  if (s == LP_OK) s = dalloc(c, &c->key, n);
+  if (s == LP_OK) s = dalloc(c, &c->tmp, n);
+  if (s == LP_OK) s = dalloc(c, &c->nbr, n * c->cap);
+  if (s == LP_OK) s = dalloc(c, &c->cnt, n);
+  if (s == LP_OK) s = dalloc(c, &c->p1, n * P1_N);
+  if (s == LP_OK) s = dalloc(c, &c->fac, n * kTri);
+  if (s == LP_OK) s = dalloc(c, &c->facf, n * kTri);
+  if (s == LP_OK) s = dalloc(c, &c->fbslot, n);
+  if (s == LP_OK) s = dalloc(c, &c->fb_list, (size_t)c->fb_cap);
+  if (s == LP_OK) s = dalloc(c, &c->fb_count, 1);
+  if (s == LP_OK) s = dalloc(c, &c->fbgrad, (size_t)c->fb_cap * 6);
+  if (s == LP_OK) s = dalloc(c, &c->d_grids, (size_t)c->cap_cols);
+  if (s == LP_OK) s = dalloc(c, &c->d_mui, (size_t)c->cap_cols);
+  if (s == LP_OK) s = dalloc(c, &c->d_offs, (size_t)c->cap_cols + 1);
+  if (s == LP_OK) s = dalloc(c, &c->d_bbox, (size_t)c->cap_cols * 7);
+  if (s == LP_OK) s = dalloc(c, &c->dg, 1);
+  if (s == LP_OK) s = dalloc(c, &c->d_tab, 2 * 2 * 2 * kTabFields);
+  if (s == LP_OK) s = dalloc(c, &c->d_ptr, kTabFields);
+  if (s == LP_OK) s = ensure_cells(c, 1 << 16);
+  if (s == LP_OK) {
+    if (cudaMallocHost(&c->h_bbox, sizeof(double) * 7 * c->cap_cols) != cudaSuccess ||
+        cudaMallocHost(&c->h_dg, sizeof(DevDiag)) != cudaSuccess ||
+        cudaMallocHost(&c->h_ptr, sizeof(double*) * kTabFields) != cudaSuccess) {
+      cudaGetLastError();
+      s = LP_ERR_OOM;
+    }
+  }
+  if (s == LP_OK) {
+    // gather tables: kind 0 gathers the 7 state fields, kind 1 x, y, z, radius
+    double* tab[2 * 2 * 2 * kTabFields] = {};
+    const int order[2][kTabFields] = {{0, 1, 2, 3, 4, 5, 6, 7}, {0, 1, 2, 7, 3, 4, 5, 6}};
+    for (int d = 0; d < 2; ++d)
+      for (int kind = 0; kind < 2; ++kind)
+        for (int f = 0; f < kTabFields; ++f) {
+          tab[((d * 2 + kind) * 2 + 0) * kTabFields + f] = c->X[d][order[kind][f]];
+          tab[((d * 2 + kind) * 2 + 1) * kTabFields + f] = c->X[1 - d][order[kind][f]];
+        }
+    if (cudaMemcpy(c->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice) != cudaSuccess) s = LP_ERR_CUDA;
+  }
+  if (s == LP_OK) s = reset_diag(c, 0);
+  if (s != LP_OK) {
+    lp_ctx_destroy(c);
+    return s;
+  }
+  *out = c;
+  return LP_OK;
+}
+
+lp_status lp_ctx_destroy(lp_ctx* c) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_bbox) cudaFreeHost(c->h_bbox);
+  if (c->h_dg) cudaFreeHost(c->h_dg);
+  if (c->h_ptr) cudaFreeHost(c->h_ptr);
+  delete c;
+  return cuda_status();
+}
+
+lp_status lp_ctx_sync(lp_ctx* c, void* stream, lp_diag* diag) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(c->device);
+  if (cudaMemcpyAsync(c->h_dg, c->dg, sizeof(DevDiag), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  const DevDiag d = *c->h_dg;
+  if (diag) {
+    std::memset(diag, 0, sizeof(*diag));
+    diag->flags = d.flags;
+    diag->min_stencil = d.min_stencil == INT32_MAX ? 0 : d.min_stencil;
+    diag->max_stencil = d.max_stencil;
+    diag->n_overflow = (int64_t)d.n_overflow;
+    diag->n_fallback = (int64_t)d.n_fallback;
+    diag->n_gas = (int64_t)d.n_gas;
+    diag->n_quasistatic = (int64_t)d.n_quasistatic;
+    diag->n_over_c = (int64_t)d.n_over_c;
+    diag->n_nonfinite = (int64_t)d.n_nonfinite;
+    diag->n_below_floor = (int64_t)d.n_below_floor;
+  }
+  LP_TRY(reset_diag(c, st));
+  if (d.flags & LP_FLAG_TIMEOUT) return LP_ERR_TIMEOUT;
+  if (d.flags & LP_FLAG_OVERFLOW) return LP_ERR_STENCIL_OVERFLOW;
+  if (d.flags & LP_FLAG_NONFINITE) return LP_ERR_NONFINITE;
+  return LP_OK;
+}
+
+lp_status lp_build_neighbors(lp_ctx* c, const lp_particles* p, const double* radius,
+                             double r_const, int32_t mirror_mode, double floor_z, int32_t cap,
+                             int32_t keep_nearest, lp_neighbors* out, void* stream) {
+  if (!c || !out) return LP_ERR_INVALID_ARG;
+  std::vector<int32_t> offs;
+  LP_TRY(check_particles(c, p, offs, false));
+  if (cap < 1 || cap > c->cap || mirror_mode < 0 || mirror_mode > 2 || !std::isfinite(floor_z))
+    return LP_ERR_INVALID_ARG;
+  if (!radius && !finite_pos(r_const)) return LP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(c->device);
+  const int n = (int)p->n;
+  if (!c->nbr_o) {
+    LP_TRY(dalloc(c, &c->nbr_o, (size_t)c->cap_n * c->cap));
+    LP_TRY(dalloc(c, &c->cnt_o, (size_t)c->cap_n));
+  }
+  out->nbr = c->nbr_o; out->cnt = c->cnt_o; out->n = n; out->cap = cap;
+  if (n == 0) return LP_OK;
+  const int d = c->cx;
+  cudaMemcpyAsync(c->X[d][0], p->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->X[d][1], p->y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->X[d][2], p->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (radius)
+    cudaMemcpyAsync(c->X[d][7], radius, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  launch_iota(n, c->ids[c->ci], st);
+  LP_TRY(begin_columns(c, p, radius ? c->X[d][7] : nullptr, d, offs, st));
+  double rmax = r_const;
+  if (radius) {
+    rmax = 0.0;
+    for (int k = 0; k < p->ncolumns; ++k) rmax = std::max(rmax, c->h_bbox[7 * k + 6]);
+    if (!finite_pos(rmax)) return LP_ERR_INVALID_ARG;
+  }
+  LP_TRY(setup_grids(c, p->ncolumns, rmax, st));
+  sort_particles(c, n, 1, radius ? 4 : 3, st);
+  const int e = c->cx;
+  launch_neighbors(keep_nearest != 0, n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf,
+                   c->colid[c->ci], c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity,
+                   radius ? c->X[e][7] : nullptr, r_const, mirror_mode, floor_z, cap, c->nbr,
+                   c->cnt, c->dg, st);
+  launch_nbr_to_caller(n, cap, c->ids[c->ci], c->nbr, c->cnt, c->nbr_o, c->cnt_o, st);
+  return cuda_status();
+}
+
+lp_status lp_neighbors_export(lp_ctx* c, const lp_neighbors* nb, int32_t* host_nbr,
+                              int32_t* host_cnt, void* stream) {
+  if (!c || !nb || !host_nbr || !host_cnt || !nb->nbr || !nb->cnt || nb->n < 0 || nb->cap < 1)
+    return LP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(c->device);
+  const int64_t n = nb->n;
+  const int cap = nb->cap;
+  std::vector<int32_t> kn((size_t)n * cap), cn((size_t)n);
+  if (n > 0) {
+    if (cudaMemcpyAsync(kn.data(), nb->nbr, sizeof(int32_t) * n * cap, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(cn.data(), nb->cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return LP_ERR_CUDA;
+    }
+  }
+  std::vector<uint32_t> row;
+  for (int64_t i = 0; i < n; ++i) {
+    const int m = std::min(cn[i], cap);
+    row.assign(m, 0);
+    for (int k = 0; k < m; ++k) row[k] = (uint32_t)kn[(size_t)k * n + i];
+    // real neighbours first, then mirrors; each ascending
+    std::sort(row.begin(), row.end(), [](uint32_t a, uint32_t b) {
+      if ((a >> 31) != (b >> 31)) return (a >> 31) < (b >> 31);
+      return (a & 0x7fffffffu) < (b & 0x7fffffffu);
+    });
+    for (int k = 0; k < cap; ++k) host_nbr[i * cap + k] = k < m ? (int32_t)row[k] : 0;
+    host_cnt[i] = m;
+  }
+  return LP_OK;
+}
+
+lp_status lp_fit_derivatives(lp_ctx* c, const lp_particles* p, const lp_neighbors* nb,
+                             const double* const* fields, const double* mirror_sign, int32_t nf,
+                             double h, double floor_z, double* coeffs, int32_t precision,
+                             void* stream) {
+  if (!c || !nb || !fields || !mirror_sign || !coeffs) return LP_ERR_INVALID_ARG;
+  std::vector<int32_t> offs;
+  LP_TRY(check_particles(c, p, offs, false));
+  if (nf < 1 || nf > kMaxFields || !finite_pos(h) || !std::isfinite(floor_z) ||
+      (precision != LP_FP64 && precision != LP_MIXED) || nb->n != p->n || !nb->nbr || !nb->cnt ||
+      nb->cap < 1 || nb->cap > LP_MAX_CAP)
+    return LP_ERR_INVALID_ARG;
+  for (int f = 0; f < nf; ++f)
+    if (!fields[f] || !std::isfinite(mirror_sign[f])) return LP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(c->device);
+  if (p->n == 0) return LP_OK;
+  FitArgs F{};
+  F.n = (int)p->n; F.cap = nb->cap; F.nf = nf;
+  F.x = p->x; F.y = p->y; F.z = p->z;
+  F.nbr = nb->nbr; F.cnt = nb->cnt;
+  for (int f = 0; f < nf; ++f) {
+    F.fields[f] = fields[f];
+    F.msign[f] = mirror_sign[f];
+  }
+  F.inv_h = 1.0 / h; F.f2 = 2.0 * floor_z;
+  F.coeffs = coeffs;
+  F.fb_list = c->fb_list; F.fb_count = c->fb_count; F.fb_cap = c->fb_cap;
+  F.dg = c->dg;
+  cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
+  launch_fit(precision, F, st);
+  return cuda_status();
+}
+
+lp_status lp_mui_stress(lp_ctx* c, const lp_mui* mui, const lp_eos* eos, int64_t n,
+                        const double* V, const double* grad_u, double* gdot, double* gdot_norm,
+                        double* P, double* eta, int8_t* regime, void* stream) {
+  if (!c || !mui || !eos || n < 0 || (n > 0 && (!V || !grad_u))) return LP_ERR_INVALID_ARG;
+  if (!(eos->phi_min < eos->phi_max && eos->phi_max < eos->phi_c)) return LP_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (n == 0) return LP_OK;
+  ColMui m{mui->mu_s, mui->mu_2, mui->I0, mui->d, mui->rho_s};
+  launch_mui_stress(n, m, *eos, V, grad_u, gdot, gdot_norm, P, eta, regime,
+                    (cudaStream_t)stream);
+  return cuda_status();
+}
+
+lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* eos,
+                  const lp_params* q, double dt, int32_t nsteps, void* stream) {
+  if (!c || !mui || nsteps < 0) return LP_ERR_INVALID_ARG;
+  std::vector<int32_t> offs;
+  LP_TRY(check_particles(c, p, offs, true));
+  if (!valid_params(q, eos, dt)) return LP_ERR_INVALID_ARG;
+  if (q->radius * (1.0 / q->h) > 64.0) return LP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(c->device);
+  const int n = (int)p->n;
+  if (n == 0 || nsteps == 0) return LP_OK;
+  std::vector<ColMui> hm(p->ncolumns);
+  for (int k = 0; k < p->ncolumns; ++k)
+    hm[k] = ColMui{mui[k].mu_s, mui[k].mu_2, mui[k].I0, mui[k].d, mui[k].rho_s};
+  if (cudaMemcpyAsync(c->d_mui, hm.data(), sizeof(ColMui) * p->ncolumns, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return LP_ERR_CUDA;
+  StepConsts K{};
+  K.phi_c = eos->phi_c; K.phi_min = eos->phi_min; K.phi_max = eos->phi_max;
+  K.alpha = eos->alpha; K.beta = eos->beta;
+  K.h = q->h; K.inv_h = 1.0 / q->h; K.radius = q->radius; K.r2 = q->radius * q->radius;
+  K.gx = q->gx; K.gy = q->gy; K.gz = q->gz; K.floor_z = q->floor_z; K.dt = dt;
+  K.mirror_mode = q->mirror_mode; K.cap = c->cap;
+  // caller state -> internal buffer, identity order
+  const int d = c->cx;
+  double* const src[7] = {p->x, p->y, p->z, p->u, p->v, p->w, p->V};
+  for (int f = 0; f < 7; ++f)
+    cudaMemcpyAsync(c->X[d][f], src[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  launch_iota(n, c->ids[c->ci], st);
+  LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
+  LP_TRY(setup_grids(c, p->ncolumns, q->radius, st));
+  const int R = q->rebuild_every;
+  int done = 0;
+  const int period = 2 * R;  // buffer toggles repeat after 2R steps
+  if (q->use_graph && st != nullptr && nsteps >= 2 * period) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return LP_ERR_CUDA;
+    const int cx0 = c->cx, ci0 = c->ci;
+    for (int k = 0; k < period; ++k) run_step(c, n, K, q->precision, k % R == 0, st);
+    if (cudaStreamEndCapture(st, &g) != cudaSuccess || c->cx != cx0 || c->ci != ci0) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return LP_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      cudaGetLastError();
+      return LP_ERR_CUDA;
+    }
+    const int reps = nsteps / period;
+    for (int r = 0; r < reps; ++r) cudaGraphLaunch(ge, st);
+    done = reps * period;
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+  }
+  for (int k = done; k < nsteps; ++k) run_step(c, n, K, q->precision, (k % R) == 0, st);
+  // internal state -> caller arrays (original order)
+  {
+    const int e = c->cx;
+    const double* const* dsrc = (const double* const*)(c->d_tab + ((e * 2 + 0) * 2 + 0) * kTabFields);
+    double* hp[7] = {p->x, p->y, p->z, p->u, p->v, p->w, p->V};
+    std::memcpy(c->h_ptr, hp, sizeof(hp));
+    cudaMemcpyAsync(c->d_ptr, c->h_ptr, sizeof(hp), cudaMemcpyHostToDevice, st);
+    launch_scatter_state(n, c->ids[c->ci], dsrc, c->d_ptr, 7, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LP_ERR_CUDA;
+  }
+  return cuda_status();
+}
+
+lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* mui,
+                          const lp_eos* eos, const lp_params* params, double dt, int32_t nsteps,
+                          int32_t checkpoint_every, const lp_particles* seed, double* dL_dmui,
+                          lp_particles* dL_dinitial, void* stream) {
+  (void)initial; (void)mui; (void)eos; (void)params; (void)dt; (void)nsteps;
+  (void)checkpoint_every; (void)seed; (void)dL_dmui; (void)dL_dinitial; (void)stream;
+  if (!c) return LP_ERR_INVALID_ARG;
+  return LP_ERR_UNIMPLEMENTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,316 @@
+// Internal device-side definitions shared by the CUDA translation units of the
+// LP step library. Nothing here is part of the C ABI (see include/lp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lp.h"
+
+namespace lp {
+
+constexpr uint32_t kMirrorBit = 0x80000000u;
+constexpr int kNB = 9;            // quadratic Taylor basis in 3D, no constant term
+constexpr int kTri = 45;          // packed lower triangle of a 9x9 matrix
+constexpr int kMaxColumns = 4096;
+constexpr int kBlock = 128;       // threads per block of the per-particle kernels
+constexpr int kMaxFields = 16;    // lp_fit_derivatives
+constexpr int kMaxCand = 128;     // candidate buffer of the keep-nearest search
+
+// Uniform cell grid of one column. Cell edge >= the largest stencil radius,
+// cell coordinates clamped into the grid (clamping keeps any two points within
+// one cell of each other per axis when they are within one cell edge).
+struct GridCol {
+  double ox, oy, oz;   // origin
+  double inv_c;        // 1 / cell edge
+  float cf;            // cell edge (FP32) for the prefilter bound
+  int nx, ny, nz;
+  int64_t cell_off;    // first global cell id of this column
+};
+
+// per-column material parameters
+struct ColMui {
+  double mu_s, mu_2, I0, d, rho_s;
+};
+
+// constants of one step
+struct StepConsts {
+  double phi_c, phi_min, phi_max, alpha, beta;
+  double h, inv_h, radius, r2;
+  double gx, gy, gz, floor_z, dt;
+  int mirror_mode;
+  int cap;
+};
+
+// device diagnostics, accumulated until lp_ctx_sync
+struct DevDiag {
+  unsigned int flags;
+  int min_stencil, max_stencil;
+  int pad;
+  unsigned long long n_overflow, n_fallback, n_gas, n_quasistatic, n_over_c, n_nonfinite,
+      n_below_floor;
+};
+
+__host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
+
+// clamped cell coordinate; NaN maps to 0 (fmax returns the non-NaN operand)
+__device__ __forceinline__ int cell_coord(double p, double o, double inv_c, int n) {
+  double t = (p - o) * inv_c;
+  t = fmin(fmax(t, 0.0), (double)(n - 1));
+  return (int)t;
+}
+
+__device__ __forceinline__ int64_t cell_id(const GridCol& g, int cx, int cy, int cz) {
+  return g.cell_off + ((int64_t)cz * g.ny + cy) * g.nx + cx;
+}
+
+// warp-aggregated counter increment (one atomic per warp)
+__device__ __forceinline__ void warp_count(unsigned long long* ctr, bool pred) {
+  unsigned int b = __ballot_sync(0xffffffffu, pred);
+  if (b && (threadIdx.x & 31) == (__ffs(b) - 1)) atomicAdd(ctr, (unsigned long long)__popc(b));
+}
+
+// indices of the per-particle pass-1 outputs in the SoA block p1[k*n + s]
+enum { P1_GD = 0, P1_GN = 6, P1_LD = 7, P1_VN = 10, P1_DIV = 11, P1_N = 12 };
+
+struct StepArgs {
+  int n, cap;
+  const double *x, *y, *z, *u, *v, *w, *V;  // state at time n (sorted order)
+  double *xo, *yo, *zo, *uo, *vo, *wo, *Vo; // state at n+1
+  const int32_t *nbr, *cnt, *colid;
+  const ColMui* mui;
+  double* fac;      // FP64 Cholesky factors, 45 * n (k-major)
+  float* facf;      // FP32 Cholesky factors, 45 * n (k-major)
+  int32_t* fbslot;  // per particle: fallback slot or -1
+  int32_t* fb_list; // fallback particles
+  int32_t* fb_count;
+  int fb_cap;
+  double* p1;       // pass-1 outputs, P1_N * n
+  double* fbgrad;   // pass-2 fallback results, 6 per slot
+  DevDiag* dg;
+  StepConsts K;
+};
+
+struct FitArgs {
+  int n, cap, nf;
+  const double *x, *y, *z;
+  const int32_t *nbr, *cnt;
+  const double* fields[kMaxFields];
+  double msign[kMaxFields];
+  double inv_h, f2;
+  double* coeffs;     // n x nf x 9
+  int32_t* fb_list;
+  int32_t* fb_count;
+  int fb_cap;
+  DevDiag* dg;
+};
+
+// ------------------------------------------------------------------ closure
+// mu(I) closure of Sec. 2.3 at solid fraction phi (inertial regime):
+//   M = -4 a^2 d^2/(phi_c-phi)^2, N = -M mu, S = dM/dphi, R = dN/dphi,
+//   mu = (a mu_s I0 + mu_2 (phi_c-phi)) / (a I0 + phi_c - phi).
+struct Closure {
+  double M, N, S, R, mu;
+};
+__device__ __forceinline__ Closure closure_at(double phi, const ColMui& m, double phi_c,
+                                              double phi_min) {
+  const double a = phi_c - phi_min;
+  const double w = phi_c - phi;
+  const double k = 4.0 * a * a * m.d * m.d;
+  Closure c;
+  const double iw = 1.0 / w;
+  c.M = -k * iw * iw;
+  const double den = a * m.I0 + w;
+  const double iden = 1.0 / den;
+  c.mu = (a * m.mu_s * m.I0 + m.mu_2 * w) * iden;
+  c.N = -c.M * c.mu;
+  c.S = -2.0 * k * iw * iw * iw;
+  const double dmu = -(a * m.I0 * (m.mu_2 - m.mu_s)) * iden * iden;
+  c.R = -c.S * c.mu - c.M * dmu;
+  return c;
+}
+
+// ---------------------------------------------------------- 9x9 Cholesky
+// In-place factorisation of a packed SPD matrix (lower triangle). On return
+// a[tri(i,j)] = L_ij for j < i and a[tri(j,j)] = 1/L_jj. Returns false if a
+// pivot falls below rel_tol times the original diagonal entry (then the
+// caller falls back to pivoted QR).
+template <typename T>
+__device__ __forceinline__ bool chol9(T* a, T rel_tol) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < kNB; ++j) {
+    T d = a[tri(j, j)];
+    const T d0 = d;
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= a[tri(j, k)] * a[tri(j, k)];
+    const bool good = d > rel_tol * d0;
+    ok = ok && good;
+    const T inv = good ? T(1) / sqrt(d) : T(0);
+    a[tri(j, j)] = inv;
+#pragma unroll
+    for (int i = j + 1; i < kNB; ++i) {
+      T s = a[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= a[tri(i, k)] * a[tri(j, k)];
+      a[tri(i, j)] = s * inv;
+    }
+  }
+  return ok;
+}
+
+// Solve L L^T c = b with a factor from chol9 (b overwritten by c).
+template <typename T, typename TB>
+__device__ __forceinline__ void chol9_solve(const T* L, TB* b) {
+#pragma unroll
+  for (int i = 0; i < kNB; ++i) {
+    TB s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= TB(L[tri(i, k)]) * b[k];
+    b[i] = s * TB(L[tri(i, i)]);
+  }
+#pragma unroll
+  for (int i = kNB - 1; i >= 0; --i) {
+    TB s = b[i];
+#pragma unroll
+    for (int k = i + 1; k < kNB; ++k) s -= TB(L[tri(k, i)]) * b[k];
+    b[i] = s * TB(L[tri(i, i)]);
+  }
+}
+
+// Taylor-row moments of one stencil: the 31 distinct moments of the 9x9 Gram
+// matrix (degree 2, 3 and 4 in the scaled offsets).
+template <typename T>
+struct Moments {
+  T xx, yy, zz, xy, xz, yz;                                 // degree 2
+  T xxx, yyy, zzz, xxy, xxz, xyy, yyz, xzz, yzz, xyz;      // degree 3
+  T xxxx, yyyy, zzzz, xxxy, xxxz, xyyy, yyyz, xzzz, yzzz,  // degree 4
+      xxyy, xxzz, yyzz, xxyz, xyyz, xyzz;
+  __device__ __forceinline__ void zero() {
+    xx = yy = zz = xy = xz = yz = T(0);
+    xxx = yyy = zzz = xxy = xxz = xyy = yyz = xzz = yzz = xyz = T(0);
+    xxxx = yyyy = zzzz = xxxy = xxxz = xyyy = yyyz = xzzz = yzzz = T(0);
+    xxyy = xxzz = yyzz = xxyz = xyyz = xyzz = T(0);
+  }
+  __device__ __forceinline__ void add(T dx, T dy, T dz) {
+    const T qxx = dx * dx, qyy = dy * dy, qzz = dz * dz;
+    const T qxy = dx * dy, qxz = dx * dz, qyz = dy * dz;
+    xx += qxx; yy += qyy; zz += qzz; xy += qxy; xz += qxz; yz += qyz;
+    xxx += dx * qxx; yyy += dy * qyy; zzz += dz * qzz;
+    xxy += dy * qxx; xxz += dz * qxx; xyy += dx * qyy;
+    yyz += dz * qyy; xzz += dx * qzz; yzz += dy * qzz; xyz += dz * qxy;
+    xxxx += qxx * qxx; yyyy += qyy * qyy; zzzz += qzz * qzz;
+    xxxy += qxx * qxy; xxxz += qxx * qxz; xyyy += qyy * qxy;
+    yyyz += qyy * qyz; xzzz += qzz * qxz; yzzz += qzz * qyz;
+    xxyy += qxx * qyy; xxzz += qxx * qzz; yyzz += qyy * qzz;
+    xxyz += qxx * qyz; xyyz += qyy * qxz; xyzz += qzz * qxy;
+  }
+  // Gram matrix of the columns [dx, dy, dz, dx^2/2, dy^2/2, dz^2/2, dx dy,
+  // dx dz, dy dz], packed lower triangle.
+  __device__ __forceinline__ void gram(T* g) const {
+    const T h = T(0.5), q = T(0.25);
+    g[tri(0, 0)] = xx;
+    g[tri(1, 0)] = xy;       g[tri(1, 1)] = yy;
+    g[tri(2, 0)] = xz;       g[tri(2, 1)] = yz;       g[tri(2, 2)] = zz;
+    g[tri(3, 0)] = h * xxx;  g[tri(3, 1)] = h * xxy;  g[tri(3, 2)] = h * xxz;
+    g[tri(3, 3)] = q * xxxx;
+    g[tri(4, 0)] = h * xyy;  g[tri(4, 1)] = h * yyy;  g[tri(4, 2)] = h * yyz;
+    g[tri(4, 3)] = q * xxyy; g[tri(4, 4)] = q * yyyy;
+    g[tri(5, 0)] = h * xzz;  g[tri(5, 1)] = h * yzz;  g[tri(5, 2)] = h * zzz;
+    g[tri(5, 3)] = q * xxzz; g[tri(5, 4)] = q * yyzz; g[tri(5, 5)] = q * zzzz;
+    g[tri(6, 0)] = xxy;      g[tri(6, 1)] = xyy;      g[tri(6, 2)] = xyz;
+    g[tri(6, 3)] = h * xxxy; g[tri(6, 4)] = h * xyyy; g[tri(6, 5)] = h * xyzz;
+    g[tri(6, 6)] = xxyy;
+    g[tri(7, 0)] = xxz;      g[tri(7, 1)] = xyz;      g[tri(7, 2)] = xzz;
+    g[tri(7, 3)] = h * xxxz; g[tri(7, 4)] = h * xyyz; g[tri(7, 5)] = h * xzzz;
+    g[tri(7, 6)] = xxyz;     g[tri(7, 7)] = xxzz;
+    g[tri(8, 0)] = xyz;      g[tri(8, 1)] = yyz;      g[tri(8, 2)] = yzz;
+    g[tri(8, 3)] = h * xxyz; g[tri(8, 4)] = h * yyyz; g[tri(8, 5)] = h * yzzz;
+    g[tri(8, 6)] = xyyz;     g[tri(8, 7)] = xyzz;     g[tri(8, 8)] = yyzz;
+  }
+};
+
+// Taylor row of a scaled offset.
+template <typename T>
+__device__ __forceinline__ void taylor_row(T dx, T dy, T dz, T* a) {
+  a[0] = dx; a[1] = dy; a[2] = dz;
+  a[3] = T(0.5) * dx * dx; a[4] = T(0.5) * dy * dy; a[5] = T(0.5) * dz * dz;
+  a[6] = dx * dy; a[7] = dx * dz; a[8] = dy * dz;
+}
+
+// ------------------------------------------------ pivoted Householder QR
+// Least-squares solve of A c = B by Householder QR with column pivoting
+// (largest remaining column norm, ties to the lower column), rank =
+// #{|R_kk| > 1e-8 |R_00|}, basic solution (coefficients beyond the rank are
+// zero). A: m x 9 row-major, B: m x nf row-major (both overwritten), C: nf x 9.
+__device__ inline int qr_pivoted_solve(int m, double* A, int nf, double* B, double* C) {
+  int perm[kNB];
+  double rdiag[kNB];
+  for (int j = 0; j < kNB; ++j) perm[j] = j;
+  const int kmax = m < kNB ? m : kNB;
+  int steps = 0;
+  for (int k = 0; k < kmax; ++k) {
+    int best = k;
+    double bestn = -1.0;
+    for (int j = k; j < kNB; ++j) {
+      double s = 0.0;
+      for (int i = k; i < m; ++i) s += A[i * kNB + j] * A[i * kNB + j];
+      if (s > bestn) { bestn = s; best = j; }
+    }
+    if (best != k) {
+      for (int i = 0; i < m; ++i) {
+        double t = A[i * kNB + k]; A[i * kNB + k] = A[i * kNB + best]; A[i * kNB + best] = t;
+      }
+      int t = perm[k]; perm[k] = perm[best]; perm[best] = t;
+    }
+    double ss = 0.0;
+    for (int i = k; i < m; ++i) ss += A[i * kNB + k] * A[i * kNB + k];
+    const double alpha = sqrt(ss);
+    if (alpha == 0.0) break;
+    const double sgn = A[k * kNB + k] >= 0.0 ? 1.0 : -1.0;
+    // Householder vector v = x + sgn |x| e_1 kept in column k, rows k..m-1
+    const double v0 = A[k * kNB + k] + sgn * alpha;
+    double vtv = v0 * v0;
+    for (int i = k + 1; i < m; ++i) vtv += A[i * kNB + k] * A[i * kNB + k];
+    for (int j = k + 1; j < kNB; ++j) {
+      double s = v0 * A[k * kNB + j];
+      for (int i = k + 1; i < m; ++i) s += A[i * kNB + k] * A[i * kNB + j];
+      const double f = 2.0 * s / vtv;
+      A[k * kNB + j] -= f * v0;
+      for (int i = k + 1; i < m; ++i) A[i * kNB + j] -= f * A[i * kNB + k];
+    }
+    for (int q = 0; q < nf; ++q) {
+      double s = v0 * B[k * nf + q];
+      for (int i = k + 1; i < m; ++i) s += A[i * kNB + k] * B[i * nf + q];
+      const double f = 2.0 * s / vtv;
+      B[k * nf + q] -= f * v0;
+      for (int i = k + 1; i < m; ++i) B[i * nf + q] -= f * A[i * kNB + k];
+    }
+    rdiag[k] = -sgn * alpha;
+    A[k * kNB + k] = rdiag[k];
+    steps = k + 1;
+  }
+  int rank = 0;
+  if (steps > 0) {
+    const double r0 = fabs(rdiag[0]);
+    for (int k = 0; k < steps; ++k) {
+      if (fabs(rdiag[k]) > 1e-8 * r0) rank = k + 1;
+      else break;
+    }
+  }
+  for (int q = 0; q < nf; ++q) {
+    double y[kNB];
+    for (int k = rank - 1; k >= 0; --k) {
+      double s = B[k * nf + q];
+      for (int j = k + 1; j < rank; ++j) s -= A[k * kNB + j] * y[j];
+      y[k] = s / rdiag[k];
+    }
+    for (int j = 0; j < kNB; ++j) C[q * kNB + j] = 0.0;
+    for (int k = 0; k < rank; ++k) C[q * kNB + perm[k]] = y[k];
+  }
+  return rank;
+}
+
+}  // namespace lp

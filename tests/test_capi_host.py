@@ -1,0 +1,62 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and
+exports every function declared in include/lp.h; argument checks that happen
+before any CUDA call report LP_ERR_INVALID_ARG."""
+import ctypes
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2206_14061_gb300 import build, capi
+    build.build()
+    return capi.lib()
+
+
+def test_exports_every_header_function(L):
+    from paper_2206_14061_gb300 import capi
+    names = capi.header_functions()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(capi._SIGS)
+
+
+def test_version_and_status_strings(L):
+    assert b"sm_103a" in L.lp_version()
+    for s in range(8):
+        assert L.lp_status_string(s)
+    assert L.lp_status_string(0) == b"ok"
+    assert L.lp_status_string(99) == b"unknown status"
+
+
+def test_invalid_arguments_fail_on_host(L):
+    from paper_2206_14061_gb300 import capi
+    h = ctypes.c_void_p()
+    bad = [capi.LpCtxDesc(0, 1, 0, 64, 0),       # no particles
+           capi.LpCtxDesc(0, 1, 1000, 0, 0),     # cap 0
+           capi.LpCtxDesc(0, 1, 1000, 65, 0),    # cap above LP_MAX_CAP
+           capi.LpCtxDesc(0, 0, 1000, 64, 0)]    # no columns
+    for d in bad:
+        assert L.lp_ctx_create(ctypes.byref(d), ctypes.byref(h)) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_ctx_create(None, ctypes.byref(h)) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_ctx_destroy(None) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_ctx_sync(None, None, None) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_step(None, None, None, None, None, 1e-5, 1, None) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_build_neighbors(None, None, None, 0.0, 0, 0.0, 1, 0, None,
+                                None) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_fit_derivatives(None, None, None, None, None, 0, 1.0, 0.0, None, 0,
+                                None) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_mui_stress(None, None, None, 0, None, None, None, None, None, None, None,
+                           None) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_step_adjoint(None, None, None, None, None, 1e-5, 1, 1, None, None, None,
+                             None) == capi.LP_ERR_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """The binding raises instead of falling back when liblp.so is absent."""
+    from paper_2206_14061_gb300 import build, capi
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(capi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.lib()

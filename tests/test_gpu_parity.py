@@ -1,0 +1,338 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.
+
+Bars: neighbour sets bit-exact (canonical sorted order); FP64 derivatives
+within 1e-11 relative per coefficient class (max |diff| / max |oracle|);
+state after 50 FP64 steps within 1e-9 relative (displacement, velocity and
+change of V each normalised by the oracle's largest value). The mixed-precision
+path is held to the bounds stated in each test.
+"""
+import numpy as np
+import pytest
+
+from paper_2206_14061_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_14061_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def capi(dev):
+    from paper_2206_14061_gb300 import capi as C
+    C.lib()
+    return C
+
+
+def T(a, dev):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+
+
+def _dicts(pd):
+    mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
+    eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max", "alpha", "beta")}
+    return mui, eos
+
+
+def _prm(pd, **kw):
+    q = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
+             floor_z=pd["floor_z"], mirror_mode=pd["mirror_mode"], precision=0, rebuild_every=1,
+             use_graph=0)
+    q.update(kw)
+    return q
+
+
+# ------------------------------------------------------------ neighbours ---
+
+def test_neighbors_bitexact_cube_with_mirrors(dev, capi, orc):
+    wl = W.cube(20)
+    x, y, z = (wl.state[k] for k in "xyz")
+    ref, rcnt, over = orc.neighbors(x, y, z, r_const=wl.radius, mirror_mode=1, cap=64, brute=True)
+    assert over == 0
+    ctx = capi.Context(wl.n, cap=64)
+    nb = capi.lp_build_neighbors(ctx, T(x, dev), T(y, dev), T(z, dev), r_const=wl.radius,
+                                 mirror_mode=1, cap=64)
+    d = ctx.sync()
+    got, gcnt = nb.export()
+    assert np.array_equal(gcnt, rcnt)
+    assert np.array_equal(got, ref[:, :64])
+    assert d["min_stencil"] == rcnt.min() and d["max_stencil"] == rcnt.max()
+
+
+def test_neighbors_keep_nearest_per_particle_radius(dev, capi, orc):
+    x, y, z, rad, _, _ = W.sweep_lattice(n_side=18, nfields=1)
+    ref, rcnt, _ = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, cap=48, keep_nearest=True)
+    ctx = capi.Context(x.size, cap=64)
+    nb = capi.lp_build_neighbors(ctx, T(x, dev), T(y, dev), T(z, dev), radius=T(rad, dev),
+                                 mirror_mode=1, cap=48, keep_nearest=True)
+    ctx.sync()
+    got, gcnt = nb.export()
+    assert np.array_equal(gcnt, rcnt)
+    assert np.array_equal(got, ref[:, :48])
+    assert gcnt.max() == 48 and gcnt.min() >= 9
+
+
+def test_neighbors_stay_within_columns(dev, capi, orc):
+    wl = W.columns(ncol=5, n_lo=300, n_hi=1500, only=[0, 1, 2, 3, 4])
+    x, y, z = (wl.state[k] for k in "xyz")
+    offs = wl.column_offsets
+    ctx = capi.Context(wl.n, max_columns=8, cap=64)
+    nb = capi.lp_build_neighbors(ctx, T(x, dev), T(y, dev), T(z, dev), r_const=wl.radius,
+                                 mirror_mode=1, cap=64, column_offsets=offs)
+    ctx.sync()
+    got, gcnt = nb.export()
+    for c in range(len(offs) - 1):
+        b, e = offs[c], offs[c + 1]
+        ref, rcnt, _ = orc.neighbors(x[b:e], y[b:e], z[b:e], r_const=wl.radius, mirror_mode=1,
+                                     cap=64)
+        assert np.array_equal(gcnt[b:e], rcnt)
+        g = got[b:e].astype(np.int64) & 0xFFFFFFFF
+        r = ref[:, :64].astype(np.int64) & 0xFFFFFFFF
+        mask = np.arange(64)[None, :] < rcnt[:, None]
+        gi = np.where(mask, (g & 0x7FFFFFFF) - b, 0)
+        ri = np.where(mask, r & 0x7FFFFFFF, 0)
+        assert np.array_equal(gi, ri)
+        assert np.array_equal(np.where(mask, g >> 31, 0), np.where(mask, r >> 31, 0))
+
+
+def test_neighbor_overflow_is_reported(dev, capi):
+    wl = W.cube(8)
+    ctx = capi.Context(wl.n, cap=64)
+    capi.lp_build_neighbors(ctx, *(T(wl.state[k], dev) for k in "xyz"), r_const=wl.radius,
+                            mirror_mode=1, cap=8)
+    with pytest.raises(capi.LpError) as e:
+        ctx.sync()
+    assert e.value.status == capi.LP_ERR_STENCIL_OVERFLOW
+    assert ctx.sync()["status"] == 0  # cleared
+
+
+# ------------------------------------------------------------------ fits ---
+
+def _class_err(got, ref):
+    """max |diff| / max |ref| per field and class (first / second derivatives)."""
+    out = []
+    for f in range(ref.shape[1]):
+        for sl in (slice(0, 3), slice(3, 9)):
+            r = ref[:, f, sl]
+            out.append(np.abs(got[:, f, sl] - r).max() / np.abs(r).max())
+    return max(out)
+
+
+@pytest.fixture(scope="module")
+def sweep(dev, capi, orc):
+    x, y, z, rad, fields, spec = W.sweep_lattice(n_side=24)
+    ctx = capi.Context(x.size, cap=64)
+    X = [T(a, dev) for a in (x, y, z)]
+    nb = capi.lp_build_neighbors(ctx, *X, radius=T(rad, dev), mirror_mode=0, cap=48,
+                                 keep_nearest=True)
+    ctx.sync()
+    nbr, cnt = nb.export()
+    ref, rank = orc.fit(x, y, z, nbr, cnt, fields, [1.0] * 4, 1e-3)
+    return dict(x=x, y=y, z=z, fields=fields, ctx=ctx, X=X, nb=nb, ref=ref, rank=rank, nbr=nbr,
+                cnt=cnt)
+
+
+def test_fit_fp64_parity(dev, capi, sweep):
+    F = [T(f, dev) for f in sweep["fields"]]
+    got = capi.lp_fit_derivatives(sweep["ctx"], *sweep["X"], sweep["nb"], F, [1.0] * 4, 1e-3,
+                                  precision=capi.LP_FP64)
+    sweep["ctx"].sync()
+    err = _class_err(got.cpu().numpy(), sweep["ref"])
+    assert err <= 1e-11, err
+
+
+def test_fit_mixed_error_bound(dev, capi, sweep):
+    F = [T(f, dev) for f in sweep["fields"]]
+    got = capi.lp_fit_derivatives(sweep["ctx"], *sweep["X"], sweep["nb"], F, [1.0] * 4, 1e-3,
+                                  precision=capi.LP_MIXED)
+    sweep["ctx"].sync()
+    err = _class_err(got.cpu().numpy(), sweep["ref"])
+    print(f"mixed-precision fit: max class error vs FP64 oracle = {err:.3e}")
+    assert err <= 1e-6, err
+
+
+def test_fit_fallback_matches_oracle_projection(dev, capi, orc):
+    """Sparse clouds (m < 9) and planar stencils take the pivoted-QR path; the
+    fitted values A c (unique even when the basic solution is not) match."""
+    rng = np.random.default_rng(21)
+    n = 600
+    x = rng.uniform(0, 0.03, n)
+    y = rng.uniform(0, 0.03, n)
+    z = np.where(rng.uniform(size=n) < 0.5, 0.005, rng.uniform(0, 0.03, n))
+    f = np.stack([np.sin(100 * x) + y * 50, np.cos(70 * y) * z * 30])
+    r = 0.0042
+    ctx = capi.Context(n, cap=64)
+    X = [T(a, dev) for a in (x, y, z)]
+    nb = capi.lp_build_neighbors(ctx, *X, r_const=r, mirror_mode=0, cap=64)
+    ctx.sync()
+    nbr, cnt = nb.export()
+    assert (cnt < 9).any()
+    got = capi.lp_fit_derivatives(ctx, *X, nb, [T(a, dev) for a in f], [1, 1], 1e-3).cpu().numpy()
+    d = ctx.sync()
+    assert d["n_fallback"] > 0
+    ref, rank = orc.fit(x, y, z, nbr, cnt, f, [1, 1], 1e-3)
+    h = 1e-3
+    for i in range(n):
+        m = cnt[i]
+        if m == 0:
+            continue
+        j = nbr[i, :m]
+        dx, dy, dz = (x[j] - x[i]) / h, (y[j] - y[i]) / h, (z[j] - z[i]) / h
+        A = np.stack([dx, dy, dz, dx * dx / 2, dy * dy / 2, dz * dz / 2, dx * dy, dx * dz,
+                      dy * dz], 1)
+        sc = np.array([h] * 3 + [h * h] * 6)
+        for q in range(2):
+            fa = A @ (got[i, q] * sc)
+            fb = A @ (ref[i, q] * sc)
+            b = f[q, j] - f[q, i]
+            assert np.abs(fa - fb).max() <= 1e-9 * (np.abs(b).max() + 1e-30), (i, q)
+
+
+# ----------------------------------------------------------------- mu(I) ---
+
+def test_mui_stress_parity(dev, capi, orc):
+    rng = np.random.default_rng(5)
+    n = 5000
+    phi = rng.uniform(0.3, 0.62, n)
+    G = rng.standard_normal((n, 9)) * 20
+    pd = W.param_dict(W.cube(4))
+    mui, eos = _dicts(pd)
+    ctx = capi.Context(16)
+    out = capi.lp_mui_stress(ctx, mui, eos, T(1 / phi, dev), T(G, dev))
+    ctx.sync()
+    gd, gn, P, eta, reg = orc.mui_stress(1 / phi, G, orc.params(**pd))
+    assert np.array_equal(out["regime"].cpu().numpy(), reg)
+    for a, b in ((out["gdot"], gd), (out["gdot_norm"], gn), (out["P"], P), (out["eta"], eta)):
+        a = a.cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+
+
+# ------------------------------------------------------------------ step ---
+
+def _state_err(got, ref, s0):
+    e = {}
+    for k in "xyz":
+        d = ref[k] - s0[k]
+        e[k] = np.abs((got[k] - s0[k]) - d).max() / np.abs(d).max()
+    for k in "uvw":
+        e[k] = np.abs(got[k] - ref[k]).max() / max(np.abs(ref[k]).max(), 1e-300)
+    dV = ref["V"] - s0["V"]
+    e["V"] = np.abs((got["V"] - s0["V"]) - dV).max() / np.abs(dV).max()
+    return e
+
+
+def _run_gpu(capi, dev, wl, pd, nsteps, prec=0, offsets=None, mui=None, stream=None, **kw):
+    ctx = capi.Context(wl.n, max_columns=1 if offsets is None else len(offsets) - 1, cap=64)
+    st = {k: T(wl.state[k], dev) for k in capi.FIELDS}
+    m, eos = _dicts(pd)
+    capi.lp_step(ctx, st, mui if mui is not None else m, eos, _prm(pd, precision=prec, **kw),
+                 pd["dt"], nsteps, column_offsets=offsets, stream=stream)
+    d = ctx.sync(stream)
+    return {k: st[k].cpu().numpy() for k in capi.FIELDS}, d
+
+
+def test_step_fp64_parity_50_steps(dev, capi, orc):
+    wl = W.cube(20)
+    pd = W.param_dict(wl)
+    ref, rd = orc.step(wl.state, orc.params(**pd), 50, brute=False)
+    got, d = _run_gpu(capi, dev, wl, pd, 50)
+    e = _state_err(got, ref, wl.state)
+    print("FP64 50-step errors:", {k: f"{v:.2e}" for k, v in e.items()})
+    assert max(e.values()) <= 1e-9, e
+    assert d["n_nonfinite"] == 0 and d["n_overflow"] == 0
+
+
+def test_step_mixed_error_bound(dev, capi, orc):
+    wl = W.cube(20)
+    pd = W.param_dict(wl)
+    ref, _ = orc.step(wl.state, orc.params(**pd), 50, brute=False)
+    got, d = _run_gpu(capi, dev, wl, pd, 50, prec=1)
+    e = _state_err(got, ref, wl.state)
+    print("MIXED 50-step errors:", {k: f"{v:.2e}" for k, v in e.items()})
+    assert max(e.values()) <= 1e-6, e
+
+
+def test_step_graph_replay_is_bitwise_identical(dev, capi):
+    wl = W.cube(12)
+    pd = W.param_dict(wl)
+    s = torch.cuda.Stream()
+    a, _ = _run_gpu(capi, dev, wl, pd, 12, stream=s, use_graph=0)
+    b, _ = _run_gpu(capi, dev, wl, pd, 12, stream=s, use_graph=1)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_step_rebuild_period_matches_oracle(dev, capi, orc):
+    wl = W.cube(10)
+    pd = W.param_dict(wl)
+    for R, steps in ((3, 10), (5, 10)):
+        ref, _ = orc.step(wl.state, orc.params(**pd), steps, rebuild_every=R)
+        got, _ = _run_gpu(capi, dev, wl, pd, steps, rebuild_every=R)
+        e = _state_err(got, ref, wl.state)
+        assert max(e.values()) <= 1e-9, (R, e)
+
+
+def test_step_columns_match_oracle_per_column(dev, capi, orc):
+    wl = W.columns(ncol=4, n_lo=400, n_hi=2500, only=[0, 1, 2, 3])
+    pd = W.param_dict(wl)
+    mui_c = [dict(_dicts(pd)[0], mu_s=float(m)) for m in wl.mu_s_col]
+    got, _ = _run_gpu(capi, dev, wl, pd, 10, offsets=wl.column_offsets, mui=mui_c)
+    offs = wl.column_offsets
+    for c in range(len(offs) - 1):
+        b, e = offs[c], offs[c + 1]
+        sc = {k: v[b:e] for k, v in wl.state.items()}
+        ref, _ = orc.step(sc, orc.params(**dict(pd, mu_s=float(wl.mu_s_col[c]))), 10)
+        err = _state_err({k: got[k][b:e] for k in got}, ref, sc)
+        assert max(err.values()) <= 1e-9, (c, err)
+
+
+def test_step_edge_cases(dev, capi, orc):
+    pd = W.param_dict(W.cube(2))
+    # empty set: no work, no error
+    ctx = capi.Context(8)
+    empty = {k: torch.zeros(0, dtype=torch.float64, device=dev) for k in capi.FIELDS}
+    m, eos = _dicts(pd)
+    capi.lp_step(ctx, empty, m, eos, _prm(pd), pd["dt"], 3)
+    ctx.sync()
+    # one particle near the floor: only its own mirror (m = 1 < 9, QR path)
+    one = dict(x=np.array([0.0]), y=np.array([0.0]), z=np.array([0.4e-3]),
+               u=np.array([0.01]), v=np.array([0.0]), w=np.array([-0.02]),
+               V=np.array([1 / 0.585]))
+    wl1 = W.Workload("one", pd["h"], pd["radius"], pd["dt"], one)
+    ref, _ = orc.step(one, orc.params(**pd), 5)
+    got, d = _run_gpu(capi, dev, wl1, pd, 5)
+    assert d["n_fallback"] > 0
+    for k in capi.FIELDS:
+        assert np.allclose(got[k], ref[k], rtol=1e-12, atol=1e-18), k
+    # invalid arguments are rejected on the host
+    with pytest.raises(capi.LpError) as e:
+        capi.lp_step(ctx, {k: T(one[k], dev) for k in capi.FIELDS}, m, eos,
+                     _prm(pd, rebuild_every=0), pd["dt"], 1)
+    assert e.value.status == capi.LP_ERR_INVALID_ARG
+
+
+@pytest.mark.slow
+def test_step_full_size_cylinder_one_step(dev, capi, orc):
+    """The column of radius 0.02 m at spacing R/50 (785k particles), one FP64
+    step in the launch configuration the benchmark uses, against the oracle on
+    every particle."""
+    wl = W.cylinder()
+    pd = W.param_dict(wl)
+    ref, _ = orc.step(wl.state, orc.params(**pd), 1, brute=False)
+    got, d = _run_gpu(capi, dev, wl, pd, 1)
+    e = _state_err(got, ref, wl.state)
+    print("cylinder one-step FP64 errors:", {k: f"{v:.2e}" for k, v in e.items()})
+    assert max(e.values()) <= 1e-9, e
+    gotm, _ = _run_gpu(capi, dev, wl, pd, 1, prec=1)
+    em = _state_err(gotm, ref, wl.state)
+    print("cylinder one-step MIXED errors:", {k: f"{v:.2e}" for k, v in em.items()})
+    assert max(em.values()) <= 1e-6, em
