@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the LP granular-flow step on GB300: particle-updates/s.
+
+Default workload: the single cylindrical column collapse (radius 0.02 m,
+height 2R, lattice spacing R/50 with +-0.05h jitter, 785,398 particles,
+mu(I) parameters of the benchmark set, dt 1e-5 s), mixed-precision fits, the
+step replayed as a captured CUDA graph. One "step" is one full LP step: cell
+sort, neighbour search with floor mirrors, pass-1 fits, pass-2 fits with the
+mu(I) closure and the update of V, u and x.
+
+Every `restart_every` steps the state is reset to the initial column (a
+device copy inside the timed region): without the free-surface ghost
+particles the explicit scheme develops a growing surface mode after a few
+tens of steps at this spacing, and timing a blown-up state would time a
+different workload.
+
+Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s per GB300 (full LP mu(I) step) & % HBM roofline; mixed vs FP64"
+UNIT = "particle-updates/s"
+B_ALG = 128.0  # algorithmic bytes per particle update: read+write x,u,V (112) + |gdot| (16)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--restart-every", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- our path
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _traffic(kernel_key: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))[kernel_key]
+    except (OSError, ValueError, KeyError):
+        return None
+    src = os.path.join(ROOT, "paper_2206_14061_gb300", "csrc", "fit.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if t.get("fit_cu_sha256_16") != h:
+        return None
+    return t.get("bytes_per_launch_full")
+
+
+def pass1_flops(prec: str, rows: float, n: int) -> float:
+    """Algorithmic FP64 flops of one pass-1 launch (FMA = 2 flops).
+
+    FP64: per stencil row 6 (offsets) + 6 (quadratic terms) + 62 (31 moments)
+    + 3 (differences) + 54 (3 right-hand sides x 9) = 131; per particle about
+    1000 (9x9 Cholesky, three solves, derived quantities).
+    MIXED (FP64 part only; the FP32 moments run on the FP32 pipe): per row 6 +
+    9 + 3 + 54 (residual) + 54 (A^T r) = 126; per particle about 550."""
+    if prec == "fp64":
+        return 131.0 * rows + 1000.0 * n
+    return 126.0 * rows + 550.0 * n
+
+
+def our_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2206_14061_gb300 import capi, workloads as W
+
+    rank, world, local = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    capi.lib(build_if_missing=True)
+
+    wl = W.cylinder()
+    pd = W.param_dict(wl)
+    n = wl.n
+    mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
+    eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max", "alpha", "beta")}
+    init = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
+    st = {k: v.clone() for k, v in init.items()}
+    ctx = capi.Context(n, cap=64)
+    stream = torch.cuda.Stream(device=dev)
+    R = max(1, args.restart_every)
+
+    def params(prec, graph=1):
+        return dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
+                    floor_z=0.0, mirror_mode=1,
+                    precision=capi.LP_MIXED if prec == "mixed" else capi.LP_FP64,
+                    rebuild_every=1, use_graph=graph)
+
+    def run(nsteps, prec, graph=1):
+        done = 0
+        with torch.cuda.stream(stream):
+            while done < nsteps:
+                k = min(R, nsteps - done)
+                for f in capi.FIELDS:
+                    st[f].copy_(init[f])
+                capi.lp_step(ctx, st, mui, eos, params(prec, graph), pd["dt"], k, stream=stream)
+                done += k
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def timed(nsteps, prec, graph=1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        run(nsteps, prec, graph)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    def bench(prec):
+        run(args.warmup, prec)
+        ctx.sync(stream)
+        ctx.phase_times(stream)  # reset counters
+        clocks = ClockSampler(local)
+        clocks.start()
+        ms = timed(args.steps, prec)
+        ck = clocks.stop()
+        pt = ctx.phase_times(stream)
+        diag = ctx.sync(stream, raise_on_error=False)
+        # per-kernel durations, measured with events on the launch stream
+        ctx.profile(True)
+        prof_steps = min(args.steps, R)
+        run(prof_steps, prec, graph=0)
+        prof = ctx.phase_times(stream)
+        ctx.profile(False)
+        ctx.sync(stream, raise_on_error=False)
+        return ms, ck, pt, diag, prof, prof_steps
+
+    ms, clocks, pt, diag, prof, prof_steps = bench(args.precision)
+    updates = n * args.steps * world
+    value = updates / (ms / 1e3)
+    mean_m = diag["n_stencil_rows"] / max(diag["n_stencils"], 1)
+
+    peaks = _peaks()
+    per_phase = {k: v / max(prof["steps"], 1) for k, v in prof["ms"].items()}
+    dom = max(per_phase, key=per_phase.get)
+    fp64_peak_tflops = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)
+    roof = {"kernel": {"pass1": "k_pass1", "pass2": "k_pass2", "neighbors": "k_neighbors",
+                       "sort": "sort kernels"}[dom]}
+    if dom == "pass1":
+        flops = pass1_flops(args.precision, mean_m * n, n)
+        ach = flops / (per_phase["pass1"] / 1e3) / 1e12
+        roof.update(bound="alu", achieved=ach, peak=fp64_peak_tflops, unit="TFLOP/s (FP64)",
+                    frac=ach / fp64_peak_tflops, peak_source="nominal FP64 rate (fallback)",
+                    flops_per_launch=flops, ms_per_launch=per_phase["pass1"],
+                    traffic=_traffic(f"k_pass1_{args.precision}"))
+    else:
+        roof.update(bound="alu", achieved=None, peak=fp64_peak_tflops, unit="TFLOP/s (FP64)",
+                    frac=None, ms_per_launch=per_phase[dom], traffic=None)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_ach = value / world * B_ALG / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic (seeded jittered lattice column)",
+        "config": {
+            "workload": "cylindrical column collapse R=0.02 m H=2R h=R/50 jitter 0.05h "
+                        f"({n} particles), mu_s 0.38 mu_2 0.64 I0 0.28 d 5e-4 rho 2500, "
+                        "dt 1e-5, stencil radius 2.2h, no-slip floor mirrors",
+            "precision": args.precision, "graph": True, "restart_every": R,
+            "mean_stencil": mean_m, "parallelism": f"replicas x{world}",
+            "l2": "per-step working set (state, stencils, factors) is larger than L2",
+        },
+        "roofline": roof,
+        "hbm": {"bytes_per_update": B_ALG, "achieved_gbs": hbm_ach, "peak_gbs": hbm_peak,
+                "frac": hbm_ach / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "phase_ms_per_step": per_phase,
+        "gpu_launches": pt["launches"],
+        "clocks": clocks,
+        "diag": {k: diag[k] for k in ("n_fallback", "n_gas", "n_quasistatic", "n_nonfinite",
+                                      "min_stencil", "max_stencil")},
+    }
+
+    if not args.no_fp64 and args.precision == "mixed":
+        ms64, _, _, d64, prof64, _ = bench("fp64")
+        ph64 = {k: v / max(prof64["steps"], 1) for k, v in prof64["ms"].items()}
+        v64 = n * args.steps * world / (ms64 / 1e3)
+        fl64 = pass1_flops("fp64", mean_m * n, n)
+        line["fp64"] = {"value": v64, "ms_per_step": ms64 / args.steps, "phase_ms_per_step": ph64,
+                        "pass1_tflops": fl64 / (ph64["pass1"] / 1e3) / 1e12}
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, pd, budget_s=20.0)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world):
+    """The same metric through the public API with HOST buffers: every step
+    copies the state from pinned host memory, runs lp_step and reads the new
+    state back."""
+    import torch
+
+    from paper_2206_14061_gb300 import capi
+
+    n = wl.n
+    host0 = {k: torch.tensor(wl.state[k]).pin_memory() for k in capi.FIELDS}
+    host = {k: v.clone().pin_memory() for k, v in host0.items()}
+    dst = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in capi.FIELDS}
+    R = max(1, args.restart_every)
+
+    def one(i):
+        if i % R == 0:
+            for k in capi.FIELDS:
+                host[k].copy_(host0[k])
+        with torch.cuda.stream(stream):
+            for k in capi.FIELDS:
+                dst[k].copy_(host[k], non_blocking=True)
+            capi.lp_step(ctx, dst, mui, eos, params(args.precision, graph=0), pd["dt"], 1,
+                         stream=stream)
+            for k in capi.FIELDS:
+                host[k].copy_(dst[k], non_blocking=True)
+        stream.synchronize()
+
+    for i in range(args.warmup):
+        one(i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        one(i)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    ctx.sync(stream, raise_on_error=False)
+    return {"value": n * args.steps * world / dt, "unit": UNIT,
+            "h2d_bytes_per_step": 7 * 8 * n, "d2h_bytes_per_step": 7 * 8 * n,
+            "ms_per_step": dt * 1e3 / args.steps}
+
+
+def cpu_baseline(wl, pd, budget_s=20.0, steps=None):
+    """The oracle, as it stands, on the host cores: full LP steps of the same
+    workload from the initial state, run until about budget_s of wall time."""
+    from oracle import oracle as O
+
+    O.build()
+    p = O.params(**pd)
+    cores = O.max_threads()
+    done, t0 = 0, time.perf_counter()
+    while True:
+        O.step(wl.state, p, 1, brute=False)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and el >= budget_s):
+            break
+    return {"value": wl.n * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} full LP step(s) of the {wl.n}-particle column from its initial "
+                      f"state, grid neighbour search, OpenMP over particles ({el:.1f} s)"}
+
+
+# -------------------------------------------------------------- reference
+
+def reference_arm(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from paper_2206_14061_gb300 import workloads as W
+
+    wl = W.cylinder()
+    pd = W.param_dict(wl)
+    from oracle import oracle as O
+    O.build()
+    p = O.params(**pd)
+    # warm-up steps (from the initial state), then the timed sample
+    t_w = time.perf_counter()
+    for _ in range(max(args.warmup, 0)):
+        O.step(wl.state, p, 1, brute=False)
+    t_step = (time.perf_counter() - t_w) / max(args.warmup, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(wl.state, p, 1, brute=False)
+    el = time.perf_counter() - t0
+    value = wl.n * args.steps / el
+    cores = O.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded jittered lattice column)",
+            "config": {"workload": "cylindrical column collapse R=0.02 m H=2R h=R/50 "
+                                   f"({wl.n} particles), FP64 CPU oracle",
+                       "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full LP steps of the {wl.n}-particle column "
+                                       f"from its initial state ({t_step:.2f} s per step)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -67,6 +67,13 @@ typedef int32_t lp_status;
 
 #define LP_MAX_CAP 64 /* largest stencil capacity */
 
+/* phases timed by lp_ctx_phase_times */
+#define LP_PHASE_SORT 0      /* cell keys, scan, scatter, in-cell sort, gather   */
+#define LP_PHASE_NEIGHBORS 1 /* stencil search                                   */
+#define LP_PHASE_PASS1 2     /* fits of u, v, w (+ QR fallback kernel)           */
+#define LP_PHASE_PASS2 3     /* fits of |gdot|, V^{n+1}; acceleration; update    */
+#define LP_NPHASES 4
+
 typedef struct lp_ctx lp_ctx;
 
 typedef struct {
@@ -133,6 +140,8 @@ typedef struct {
   int64_t n_fallback;    /* fits that used the pivoted-QR path                   */
   int64_t n_gas, n_quasistatic, n_over_c; /* particle-steps per regime (phi > phi_c) */
   int64_t n_nonfinite, n_below_floor;
+  int64_t n_stencil_rows;  /* sum of stencil sizes over all stencils built     */
+  int64_t n_stencils;      /* number of stencils built                          */
 } lp_diag;
 
 /* Version string of the library build. Never fails. */
@@ -151,6 +160,18 @@ lp_status lp_ctx_destroy(lp_ctx* ctx);
  * LP_ERR_STENCIL_OVERFLOW, non-finite -> LP_ERR_NONFINITE, timeout ->
  * LP_ERR_TIMEOUT) or LP_OK. Synchronises. */
 lp_status lp_ctx_sync(lp_ctx* ctx, void* stream, lp_diag* diag);
+
+/* Per-phase timing (profiling aid, not in the paper). While enabled, lp_step
+ * records a CUDA event pair around each phase of every step and does not use
+ * graph replay. */
+lp_status lp_ctx_profile(lp_ctx* ctx, int32_t enable);
+/* Wait for `stream`; ms[LP_NPHASES] receives the device time of each phase
+ * accumulated since the last call (0 where profiling was off); *launches
+ * (may be NULL) the number of kernels the library launched since the last
+ * call, *steps (may be NULL) the number of LP steps. Resets all three.
+ * Synchronises. */
+lp_status lp_ctx_phase_times(lp_ctx* ctx, void* stream, double* ms, int64_t* launches,
+                             int64_t* steps);
 
 /* Neighbour search (Sec. 3.1 items 5-6, mirrors item 9). For every particle i:
  * all j != i of the same column with ((dx*dx)+(dy*dy))+(dz*dz) <= r_i*r_i in

@@ -68,7 +68,8 @@ class LpDiag(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("min_stencil", ctypes.c_int32),
                 ("max_stencil", ctypes.c_int32), ("pad", ctypes.c_int32)] + [
         (k, ctypes.c_int64) for k in ("n_overflow", "n_fallback", "n_gas", "n_quasistatic",
-                                      "n_over_c", "n_nonfinite", "n_below_floor")]
+                                      "n_over_c", "n_nonfinite", "n_below_floor",
+                                      "n_stencil_rows", "n_stencils")]
 
 
 class LpError(RuntimeError):
@@ -87,6 +88,9 @@ _SIGS = {
     "lp_ctx_create": ([_P(LpCtxDesc), _P(_vp)], ctypes.c_int32),
     "lp_ctx_destroy": ([_vp], ctypes.c_int32),
     "lp_ctx_sync": ([_vp, _vp, _P(LpDiag)], ctypes.c_int32),
+    "lp_ctx_profile": ([_vp, ctypes.c_int32], ctypes.c_int32),
+    "lp_ctx_phase_times": ([_vp, _vp, _P(ctypes.c_double), _P(ctypes.c_int64),
+                            _P(ctypes.c_int64)], ctypes.c_int32),
     "lp_build_neighbors": ([_vp, _P(LpParticles), _vp, ctypes.c_double, ctypes.c_int32,
                             ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _P(LpNeighbors), _vp],
                            ctypes.c_int32),
@@ -213,6 +217,19 @@ class Context:
         if raise_on_error:
             _check(st, "lp_ctx_sync")
         return out
+
+    def profile(self, enable: bool = True):
+        _check(lib().lp_ctx_profile(self.handle, int(bool(enable))), "lp_ctx_profile")
+
+    def phase_times(self, stream=None) -> dict:
+        """Device ms per phase (sort, neighbors, pass1, pass2), kernel launches
+        and steps since the last call."""
+        ms = (ctypes.c_double * 4)()
+        la, stp = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().lp_ctx_phase_times(self.handle, _stream(stream), ms, ctypes.byref(la),
+                                        ctypes.byref(stp)), "lp_ctx_phase_times")
+        return dict(ms=dict(zip(("sort", "neighbors", "pass1", "pass2"), list(ms))),
+                    launches=la.value, steps=stp.value)
 
     def close(self):
         if getattr(self, "handle", None):

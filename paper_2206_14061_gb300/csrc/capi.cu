@@ -91,6 +91,13 @@ struct lp_ctx {
   int64_t ncell = 0;
   std::vector<GridCol> h_grids;
   std::vector<void*> allocs;
+  // profiling: event pairs per phase, launch and step counters
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_phase;  // phase of each recorded pair
+  int64_t launches = 0;
+  int64_t steps = 0;
 };
 
 namespace {
@@ -214,8 +221,8 @@ lp_status check_particles(const lp_ctx* c, const lp_particles* p, std::vector<in
                           bool need_state) {
   if (!p || p->n < 0 || p->n > c->cap_n || p->ncolumns < 1 || p->ncolumns > c->cap_cols)
     return LP_ERR_INVALID_ARG;
-  if (!p->x || !p->y || !p->z) return LP_ERR_INVALID_ARG;
-  if (need_state && (!p->u || !p->v || !p->w || !p->V)) return LP_ERR_INVALID_ARG;
+  if (p->n > 0 && (!p->x || !p->y || !p->z)) return LP_ERR_INVALID_ARG;
+  if (p->n > 0 && need_state && (!p->u || !p->v || !p->w || !p->V)) return LP_ERR_INVALID_ARG;
   offs.assign(p->ncolumns + 1, 0);
   if (p->column_offsets) {
     for (int k = 0; k <= p->ncolumns; ++k) offs[k] = p->column_offsets[k];
@@ -227,6 +234,18 @@ lp_status check_particles(const lp_ctx* c, const lp_particles* p, std::vector<in
     offs[1] = (int32_t)p->n;
   }
   return LP_OK;
+}
+
+// Record the start or end event of a phase (profiling only).
+void phase_mark(lp_ctx* c, int phase, bool start, cudaStream_t st) {
+  if (!c->profile) return;
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  cudaEventRecord(c->ev_pool[c->ev_used++], st);
+  if (start) c->ev_phase.push_back(phase);
 }
 
 // Counting sort by cell (stable by original index) from buffer c->cx into
@@ -249,6 +268,7 @@ void sort_particles(lp_ctx* c, int n, int kind, int nsrc, cudaStream_t st) {
                 c->colid[1 - c->ci], c->d_grids, c->pf, st);
   c->cx ^= 1;
   c->ci ^= 1;
+  c->launches += 7;
 }
 
 StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
@@ -272,16 +292,27 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
 // One LP step on the context's internal (sorted) state.
 void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cudaStream_t st) {
   if (rebuild) {
+    phase_mark(c, LP_PHASE_SORT, true, st);
     sort_particles(c, n, 0, 7, st);
+    phase_mark(c, LP_PHASE_SORT, false, st);
+    phase_mark(c, LP_PHASE_NEIGHBORS, true, st);
     launch_neighbors(false, n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->pf,
                      c->colid[c->ci], c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity,
                      nullptr, K.radius, K.mirror_mode, K.floor_z, c->cap, c->nbr, c->cnt, c->dg,
                      st);
+    phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
+    c->launches += 1;
   }
   cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
   StepArgs A = step_args(c, n, K);
+  phase_mark(c, LP_PHASE_PASS1, true, st);
   launch_pass1(prec, A, st);
+  phase_mark(c, LP_PHASE_PASS1, false, st);
+  phase_mark(c, LP_PHASE_PASS2, true, st);
   launch_pass2(prec, A, st);
+  phase_mark(c, LP_PHASE_PASS2, false, st);
+  c->launches += 4;
+  c->steps += 1;
   c->cx ^= 1;
 }
 
@@ -394,6 +425,7 @@ lp_status lp_ctx_destroy(lp_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->h_bbox) cudaFreeHost(c->h_bbox);
   if (c->h_dg) cudaFreeHost(c->h_dg);
   if (c->h_ptr) cudaFreeHost(c->h_ptr);
@@ -423,11 +455,43 @@ lp_status lp_ctx_sync(lp_ctx* c, void* stream, lp_diag* diag) {
     diag->n_over_c = (int64_t)d.n_over_c;
     diag->n_nonfinite = (int64_t)d.n_nonfinite;
     diag->n_below_floor = (int64_t)d.n_below_floor;
+    diag->n_stencil_rows = (int64_t)d.n_stencil_rows;
+    diag->n_stencils = (int64_t)d.n_stencils;
   }
   LP_TRY(reset_diag(c, st));
   if (d.flags & LP_FLAG_TIMEOUT) return LP_ERR_TIMEOUT;
   if (d.flags & LP_FLAG_OVERFLOW) return LP_ERR_STENCIL_OVERFLOW;
   if (d.flags & LP_FLAG_NONFINITE) return LP_ERR_NONFINITE;
+  return LP_OK;
+}
+
+lp_status lp_ctx_profile(lp_ctx* c, int32_t enable) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  c->profile = enable != 0;
+  return LP_OK;
+}
+
+lp_status lp_ctx_phase_times(lp_ctx* c, void* stream, double* ms, int64_t* launches,
+                             int64_t* steps) {
+  if (!c || !ms) return LP_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  for (int k = 0; k < LP_NPHASES; ++k) ms[k] = 0.0;
+  for (size_t r = 0; r < c->ev_phase.size(); ++r) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->ev_pool[2 * r], c->ev_pool[2 * r + 1]) == cudaSuccess)
+      ms[c->ev_phase[r]] += t;
+  }
+  cudaGetLastError();
+  c->ev_phase.clear();
+  c->ev_used = 0;
+  if (launches) *launches = c->launches;
+  if (steps) *steps = c->steps;
+  c->launches = 0;
+  c->steps = 0;
   return LP_OK;
 }
 
@@ -589,12 +653,15 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   const int R = q->rebuild_every;
   int done = 0;
   const int period = 2 * R;  // buffer toggles repeat after 2R steps
-  if (q->use_graph && st != nullptr && nsteps >= 2 * period) {
+  if (q->use_graph && !c->profile && st != nullptr && nsteps >= 2 * period) {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return LP_ERR_CUDA;
     const int cx0 = c->cx, ci0 = c->ci;
+    const int64_t launches0 = c->launches, steps0 = c->steps;
+    c->launches = 0;
+    c->steps = 0;
     for (int k = 0; k < period; ++k) run_step(c, n, K, q->precision, k % R == 0, st);
     if (cudaStreamEndCapture(st, &g) != cudaSuccess || c->cx != cx0 || c->ci != ci0) {
       if (g) cudaGraphDestroy(g);
@@ -607,7 +674,11 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
       return LP_ERR_CUDA;
     }
     const int reps = nsteps / period;
+    // the capture counted one period of launches and steps
+    const int64_t per_launch = c->launches, per_steps = c->steps;
     for (int r = 0; r < reps; ++r) cudaGraphLaunch(ge, st);
+    c->launches = launches0 + per_launch * reps;
+    c->steps = steps0 + per_steps * reps;
     done = reps * period;
     cudaGraphExecDestroy(ge);
     cudaGraphDestroy(g);
@@ -621,6 +692,7 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
     std::memcpy(c->h_ptr, hp, sizeof(hp));
     cudaMemcpyAsync(c->d_ptr, c->h_ptr, sizeof(hp), cudaMemcpyHostToDevice, st);
     launch_scatter_state(n, c->ids[c->ci], dsrc, c->d_ptr, 7, st);
+    c->launches += 4;  // fill_colid, bbox, iota, scatter_state
     if (cudaStreamSynchronize(st) != cudaSuccess) return LP_ERR_CUDA;
   }
   return cuda_status();

@@ -50,7 +50,7 @@ struct DevDiag {
   int min_stencil, max_stencil;
   int pad;
   unsigned long long n_overflow, n_fallback, n_gas, n_quasistatic, n_over_c, n_nonfinite,
-      n_below_floor;
+      n_below_floor, n_stencil_rows, n_stencils;
 };
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }

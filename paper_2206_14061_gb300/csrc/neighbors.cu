@@ -341,6 +341,16 @@ k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
     cnt[s] = c;
   }
   warp_count(&dg->n_overflow, live && over);
+  {
+    // total stencil rows and stencils (warp-reduced)
+    unsigned long long rows = live ? (unsigned long long)min(c, cap) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) rows += __shfl_xor_sync(0xffffffffu, rows, o);
+    const unsigned live_n = __popc(__ballot_sync(0xffffffffu, live));
+    if ((threadIdx.x & 31) == 0 && live_n) {
+      atomicAdd(&dg->n_stencil_rows, rows);
+      atomicAdd(&dg->n_stencils, (unsigned long long)live_n);
+    }
+  }
   if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
   // stencil size range (warp-reduced)
   int mn = live ? c : INT32_MAX, mx = live ? c : 0;
