@@ -98,6 +98,9 @@ _SIGS = {
     "lp_fit_derivatives": ([_vp, _P(LpParticles), _P(LpNeighbors), _P(_vp), _P(ctypes.c_double),
                             ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int32,
                             _vp], ctypes.c_int32),
+    "lp_fit_derivatives_noalloc": ([ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32,
+                                    _P(_vp), _P(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                    ctypes.c_double, _vp, ctypes.c_int32, _vp], ctypes.c_int32),
     "lp_mui_stress": ([_vp, _P(LpMui), _P(LpEos), ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp,
                        _vp, _vp], ctypes.c_int32),
     "lp_step": ([_vp, _P(LpParticles), _P(LpMui), _P(LpEos), _P(LpParams), ctypes.c_double,
@@ -288,6 +291,32 @@ def lp_fit_derivatives(ctx: Context, x, y, z, nb: Neighbors, fields, mirror_sign
     _check(lib().lp_fit_derivatives(ctx.handle, ctypes.byref(p), ctypes.byref(nb.s), fp, ms, nf,
                                     float(h), float(floor_z), _ptr(out), int(precision),
                                     _stream(stream)), "lp_fit_derivatives")
+    return out
+
+
+NOALLOC_MAX_PARTICLES = 1 << 20
+
+
+def lp_fit_derivatives_noalloc(x, y, z, nbr, cnt, cap, fields, mirror_sign, h, out,
+                               floor_z=0.0, precision=LP_FP64, stream=None) -> torch.Tensor:
+    """The fit without a context and without any device allocation by the
+    library: stencils nbr (int32, k-major [cap, n] or flat) and cnt (int32, n)
+    and the output `out` ([n, nf, 9] float64) are all supplied by the caller."""
+    n = x.numel()
+    for t, nm in ((x, "x"), (y, "y"), (z, "z")):
+        _dev(t, nm)
+    _dev(nbr, "nbr", torch.int32)
+    _dev(cnt, "cnt", torch.int32)
+    _dev(out, "out")
+    nf = len(fields)
+    for i, f in enumerate(fields):
+        _dev(f, f"fields[{i}]")
+    fp = (_vp * nf)(*[f.data_ptr() for f in fields])
+    ms = (ctypes.c_double * nf)(*[float(v) for v in mirror_sign])
+    _check(lib().lp_fit_derivatives_noalloc(n, _ptr(x), _ptr(y), _ptr(z), _ptr(nbr), _ptr(cnt),
+                                            int(cap), fp, ms, nf, float(h), float(floor_z),
+                                            _ptr(out), int(precision), _stream(stream)),
+           "lp_fit_derivatives_noalloc")
     return out
 
 
