@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-columns line")
     return ap.parse_args()
 
 
@@ -173,7 +174,7 @@ def our_arm(args):
         return dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
                     floor_z=0.0, mirror_mode=1,
                     precision=capi.LP_MIXED if prec == "mixed" else capi.LP_FP64,
-                    rebuild_every=1, use_graph=graph)
+                    rebuild_every=1, launch_mode=graph)
 
     def run(nsteps, prec, graph=1):
         done = 0
@@ -282,14 +283,88 @@ def our_arm(args):
     if not args.no_e2e:
         line["e2e"] = e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world)
 
+    if not args.no_batched and world == 1:
+        ctx.close()
+        line["batched"] = batched(args, dev, stream)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, pd, budget_s=20.0)
 
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched(args, dev, stream):
+    """256 independent columns (log-uniform 2k-64k particles, aspect 0.5-6,
+    mu_s 0.3-0.45) advanced together in one lp_step call per window, with the
+    autotuned launch configuration, against 256 sequential per-column lp_step
+    calls over the same steps."""
+    import torch
+
+    from paper_2206_14061_gb300 import capi, workloads as W
+
+    wl = W.columns()
+    pd = W.param_dict(wl)
+    offs = wl.column_offsets
+    ncol = len(offs) - 1
+    base = {k: pd[k] for k in ("mu_2", "I0", "d", "rho_s")}
+    mui_c = [dict(base, mu_s=float(m)) for m in wl.mu_s_col]
+    eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max", "alpha", "beta")}
+    init = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
+    st = {k: v.clone() for k, v in init.items()}
+    prm = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
+               floor_z=0.0, mirror_mode=1, precision=capi.LP_MIXED, rebuild_every=1,
+               launch_mode=capi.LP_LAUNCH_GRAPH)
+    ctx = capi.Context(wl.n, max_columns=ncol, cap=64)
+    tune = capi.lp_autotune(ctx, init, mui_c, eos, prm, pd["dt"], 3, column_offsets=offs,
+                            stream=stream)
+    steps = max(1, min(args.steps, args.restart_every))
+
+    def reset():
+        for k in capi.FIELDS:
+            st[k].copy_(init[k])
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            reset()
+            fn()  # warm-up
+            reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    modes = {}
+    for name, mode in (("graph", capi.LP_LAUNCH_GRAPH), ("persistent", capi.LP_LAUNCH_PERSISTENT)):
+        p = dict(prm, launch_mode=mode)
+        modes[name] = timed(lambda: capi.lp_step(ctx, st, mui_c, eos, p, pd["dt"], steps,
+                                                 column_offsets=offs, stream=stream))
+    chosen = "persistent" if tune["launch_mode"] == capi.LP_LAUNCH_PERSISTENT else "graph"
+    ms_b = modes[chosen]
+
+    def per_column():
+        p = dict(prm, launch_mode=capi.LP_LAUNCH_GRAPH)
+        for c in range(ncol):
+            sl = {k: st[k][offs[c]:offs[c + 1]] for k in capi.FIELDS}
+            capi.lp_step(ctx, sl, mui_c[c], eos, p, pd["dt"], steps, stream=stream)
+
+    ms_c = timed(per_column)
+    ctx.sync(stream, raise_on_error=False)
+    ctx.close()
+    upd = wl.n * steps
+    return {"workload": f"{ncol} columns, {wl.n} particles, mixed precision, {steps} steps",
+            "value": upd / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / steps,
+            "launch": chosen, "tuning": tune,
+            "graph_ms_per_step": modes["graph"] / steps,
+            "persistent_ms_per_step": modes["persistent"] / steps,
+            "per_column_value": upd / (ms_c / 1e3), "per_column_ms_per_step": ms_c / steps,
+            "speedup_vs_per_column": ms_c / ms_b}
 
 
 def e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world):

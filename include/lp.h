@@ -59,6 +59,12 @@ typedef int32_t lp_status;
 #define LP_MIRROR_NOSLIP 1   /* mirror velocity -u (all components)            */
 #define LP_MIRROR_FREESLIP 2 /* mirror velocity (u, v, -w): normal component flipped */
 
+/* how lp_step issues a step */
+#define LP_LAUNCH_KERNELS 0    /* one kernel per phase                               */
+#define LP_LAUNCH_GRAPH 1      /* the per-phase kernels replayed as a CUDA graph     */
+#define LP_LAUNCH_PERSISTENT 2 /* one cooperative persistent launch per step, phases */
+                               /* separated by a bounded grid barrier               */
+
 /* bits of lp_diag.flags */
 #define LP_FLAG_OVERFLOW 0x1u  /* a stencil had more neighbours than cap       */
 #define LP_FLAG_NONFINITE 0x2u /* a new state value was NaN or infinite        */
@@ -117,7 +123,7 @@ typedef struct {
   int32_t mirror_mode;   /* LP_MIRROR_*                                         */
   int32_t precision;     /* LP_FP64 or LP_MIXED                                 */
   int32_t rebuild_every; /* rebuild stencils every k steps (1 = every step)     */
-  int32_t use_graph;     /* 1: replay the step as a captured CUDA graph         */
+  int32_t launch_mode;   /* LP_LAUNCH_*                                         */
 } lp_params;
 
 /* Stencils produced by lp_build_neighbors: library-owned device memory, valid
@@ -249,6 +255,33 @@ lp_status lp_mui_stress(lp_ctx* ctx, const lp_mui* mui, const lp_eos* eos, int64
  * u^{n+1} = u^n + dt a and x^{n+1} = x^n + dt (u^n + u^{n+1})/2. */
 lp_status lp_step(lp_ctx* ctx, lp_particles* p, const lp_mui* mui, const lp_eos* eos,
                   const lp_params* params, double dt, int32_t nsteps, void* stream);
+
+/* Launch configuration of lp_step (not in the paper). Block sizes are threads
+ * per block of the neighbour search and of the two fit passes (64, 128 or
+ * 256); launch_mode is the faster of LP_LAUNCH_GRAPH and LP_LAUNCH_PERSISTENT
+ * for the tuned workload, for the caller to pass in lp_params. */
+typedef struct {
+  int32_t block_neighbors, block_pass1, block_pass2;
+  int32_t launch_mode;
+  double ms_per_step;  /* step time measured with this configuration          */
+  int32_t from_table;  /* 1: read from the table, 0: measured by this call     */
+  int32_t pad;
+} lp_tuning;
+
+/* Apply a launch configuration to the context. */
+lp_status lp_ctx_set_tuning(lp_ctx* ctx, const lp_tuning* tuning);
+
+/* Autotuner (not in the paper): times steps_per_trial steps of the given
+ * workload (from the caller's particles, which are not modified) for each
+ * candidate block size, keeps the fastest per phase, then times graph replay
+ * against the persistent launch. The choice is applied to the context and
+ * returned in *out. If table_path is non-NULL, a table line keyed by device
+ * name, log2 n, log2 columns, precision and radius/h is looked up first
+ * (then nothing is measured) and a new measurement is appended to it.
+ * Synchronises. */
+lp_status lp_autotune(lp_ctx* ctx, const lp_particles* p, const lp_mui* mui, const lp_eos* eos,
+                      const lp_params* params, double dt, int32_t steps_per_trial,
+                      const char* table_path, lp_tuning* out, void* stream);
 
 /* Adjoint of nsteps lp_step steps (FP64) from `initial` (not modified). The
  * forward run being differentiated rebuilds stencils only at the start of each

@@ -30,6 +30,9 @@ LP_MIRROR_NONE = 0
 LP_MIRROR_NOSLIP = 1
 LP_MIRROR_FREESLIP = 2
 LP_MAX_CAP = 64
+LP_LAUNCH_KERNELS = 0
+LP_LAUNCH_GRAPH = 1
+LP_LAUNCH_PERSISTENT = 2
 MIRROR_BIT = 0x80000000
 
 _vp = ctypes.c_void_p
@@ -56,7 +59,7 @@ class LpEos(ctypes.Structure):
 
 class LpParams(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("h", "radius", "gx", "gy", "gz", "floor_z")] + [
-        (k, ctypes.c_int32) for k in ("mirror_mode", "precision", "rebuild_every", "use_graph")]
+        (k, ctypes.c_int32) for k in ("mirror_mode", "precision", "rebuild_every", "launch_mode")]
 
 
 class LpNeighbors(ctypes.Structure):
@@ -70,6 +73,13 @@ class LpDiag(ctypes.Structure):
         (k, ctypes.c_int64) for k in ("n_overflow", "n_fallback", "n_gas", "n_quasistatic",
                                       "n_over_c", "n_nonfinite", "n_below_floor",
                                       "n_stencil_rows", "n_stencils")]
+
+
+class LpTuning(ctypes.Structure):
+    _fields_ = [("block_neighbors", ctypes.c_int32), ("block_pass1", ctypes.c_int32),
+                ("block_pass2", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
+                ("ms_per_step", ctypes.c_double), ("from_table", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class LpError(RuntimeError):
@@ -91,6 +101,9 @@ _SIGS = {
     "lp_ctx_profile": ([_vp, ctypes.c_int32], ctypes.c_int32),
     "lp_ctx_phase_times": ([_vp, _vp, _P(ctypes.c_double), _P(ctypes.c_int64),
                             _P(ctypes.c_int64)], ctypes.c_int32),
+    "lp_ctx_set_tuning": ([_vp, _P(LpTuning)], ctypes.c_int32),
+    "lp_autotune": ([_vp, _P(LpParticles), _P(LpMui), _P(LpEos), _P(LpParams), ctypes.c_double,
+                     ctypes.c_int32, ctypes.c_char_p, _P(LpTuning), _vp], ctypes.c_int32),
     "lp_build_neighbors": ([_vp, _P(LpParticles), _vp, ctypes.c_double, ctypes.c_int32,
                             ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _P(LpNeighbors), _vp],
                            ctypes.c_int32),
@@ -194,7 +207,7 @@ def params_struct(q) -> LpParams:
     return LpParams(float(q["h"]), float(q["radius"]), float(q["gx"]), float(q["gy"]),
                     float(q["gz"]), float(q.get("floor_z", 0.0)), int(q.get("mirror_mode", 1)),
                     int(q.get("precision", LP_FP64)), int(q.get("rebuild_every", 1)),
-                    int(q.get("use_graph", 0)))
+                    int(q.get("launch_mode", LP_LAUNCH_KERNELS)))
 
 
 class Context:
@@ -354,6 +367,28 @@ def lp_step(ctx: Context, state: dict, mui, eos: dict, params: dict, dt: float, 
     e, q = eos_struct(eos), params_struct(params)
     _check(lib().lp_step(ctx.handle, ctypes.byref(p), ma, ctypes.byref(e), ctypes.byref(q),
                          float(dt), int(nsteps), _stream(stream)), "lp_step")
+
+
+def lp_autotune(ctx: Context, state: dict, mui, eos: dict, params: dict, dt: float,
+                steps_per_trial: int = 5, table_path: str | None = None, column_offsets=None,
+                stream=None) -> dict:
+    """Pick block sizes and the launch mode for this workload (applied to ctx)."""
+    p, keep = _particles(state, column_offsets)
+    ma = _mui_array(mui, p.ncolumns)
+    e, q = eos_struct(eos), params_struct(params)
+    t = LpTuning()
+    _check(lib().lp_autotune(ctx.handle, ctypes.byref(p), ma, ctypes.byref(e), ctypes.byref(q),
+                             float(dt), int(steps_per_trial),
+                             table_path.encode() if table_path else None, ctypes.byref(t),
+                             _stream(stream)), "lp_autotune")
+    return {k: getattr(t, k) for k, _ in LpTuning._fields_ if k != "pad"}
+
+
+def lp_ctx_set_tuning(ctx: Context, block_neighbors=128, block_pass1=128, block_pass2=128,
+                      launch_mode=LP_LAUNCH_GRAPH):
+    t = LpTuning(int(block_neighbors), int(block_pass1), int(block_pass2), int(launch_mode), 0.0,
+                 0, 0)
+    _check(lib().lp_ctx_set_tuning(ctx.handle, ctypes.byref(t)), "lp_ctx_set_tuning")
 
 
 def lp_step_adjoint(ctx: Context, initial: dict, mui, eos: dict, params: dict, dt: float,

@@ -1,0 +1,404 @@
+// Hand-written adjoint (reverse mode) of one FP64 LP step with frozen stencils.
+//
+// Forward step of particle i (stencil rows k, scaled offsets d_k, Taylor rows
+// a_k, Gram matrix G = sum a_k a_k^T):
+//   pass 1:  c_f = G^{-1} sum_k a_k b_fk,  b_fk = s_f u_f(j_k) - u_f(i)  (f = u,v,w)
+//            -> velocity gradient, Hessians, div u, gdot, |gdot|,
+//               ld = (1/2) Lap u + (1/6) grad div u,  V^{n+1} = V + dt V div u
+//   pass 2:  c_g = G^{-1} A^T b_g (b_g from |gdot|, 0 at mirrors),
+//            c_V = G^{-1} A^T b_V (b_V from V^{n+1})
+//   accel:   pressure law / mu(I) stress at phi^{n+1} = 1/V^{n+1} (Sec. 2.3)
+//   update:  u' = u + dt a,  x' = x + dt (u + u')/2,  V' = V^{n+1}
+// Least-squares adjoint, for c = G^{-1} A^T b with residual r = b - A c:
+//   z = G^{-1} cbar,  bbar = A z,  Abar = r z^T - (A z) c^T,
+// and Abar reaches the positions through the offsets d_k = (p_k - p_i)/h.
+// Regimes are frozen at their forward values; d|gdot|/dgdot is 0 where
+// |gdot| = 0. Parameter gradients w.r.t. (mu_s, mu_2, I0) enter through N and
+// R only. Stencils that took the pivoted-QR path in the forward step are
+// full rank in all but degenerate cases; their least-squares solution is then
+// G^{-1} A^T b as well, and the adjoint refactors G for them without the
+// forward path's conditioning threshold. Rank-deficient stencils (fewer than
+// 9 rows, or a non-positive pivot) carry no fit adjoint and are counted in
+// n_fallback.
+#include "lp_internal.cuh"
+
+namespace lp {
+
+// Closure of Sec. 2.3 with the derivatives the adjoint needs.
+struct ClosureD {
+  double M, N, S, R, dS, dR;  // dS = dS/dphi, dR = dR/dphi (dM/dphi = S, dN/dphi = R)
+  double dN_dth[3], dR_dth[3];
+};
+__device__ __forceinline__ ClosureD closure_d(double phi, const ColMui& m, double phi_c,
+                                              double phi_min) {
+  const double a = phi_c - phi_min;
+  const double w = phi_c - phi;
+  const double k = 4.0 * a * a * m.d * m.d;
+  const double iw = 1.0 / w;
+  ClosureD c;
+  c.M = -k * iw * iw;
+  c.S = -2.0 * k * iw * iw * iw;
+  c.dS = -6.0 * k * iw * iw * iw * iw;
+  const double den = a * m.I0 + w, iden = 1.0 / den;
+  const double mu = (a * m.mu_s * m.I0 + m.mu_2 * w) * iden;
+  const double dmu = m.mu_2 - m.mu_s;
+  const double q = -a * m.I0 * dmu * iden * iden;          // dmu/dphi
+  const double dq = -2.0 * a * m.I0 * dmu * iden * iden * iden;  // d2mu/dphi2
+  c.N = -c.M * mu;
+  c.R = -c.S * mu - c.M * q;
+  c.dR = -c.dS * mu - 2.0 * c.S * q - c.M * dq;
+  const double dmu_dth[3] = {a * m.I0 * iden, w * iden, a * w * (m.mu_s - m.mu_2) * iden * iden};
+  const double dq_dth[3] = {a * m.I0 * iden * iden, -a * m.I0 * iden * iden,
+                            -a * dmu * (w - a * m.I0) * iden * iden * iden};
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    c.dN_dth[t] = -c.M * dmu_dth[t];
+    c.dR_dth[t] = -c.S * dmu_dth[t] - c.M * dq_dth[t];
+  }
+  return c;
+}
+
+__device__ __forceinline__ double usign_adj(int mode, int a) {
+  return mode == LP_MIRROR_NOSLIP ? -1.0 : (mode == LP_MIRROR_FREESLIP && a == 2 ? -1.0 : 1.0);
+}
+
+// adjoint of the Taylor row: dbar = J^T abar
+__device__ __forceinline__ void row_adjoint(double dx, double dy, double dz, const double* ab,
+                                            double* db) {
+  db[0] = ab[0] + dx * ab[3] + dy * ab[6] + dz * ab[7];
+  db[1] = ab[1] + dy * ab[4] + dx * ab[6] + dz * ab[8];
+  db[2] = ab[2] + dz * ab[5] + dx * ab[7] + dy * ab[8];
+}
+
+// ---------------------------------------------------------------- R0
+// which stencils carry a fit adjoint; FP64 factors for the QR-path ones
+__global__ void __launch_bounds__(kBlock) k_adj_prepare(const AdjArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = s < A.n;
+  bool skipped = false;
+  if (live) {
+    const int n = A.n;
+    if (A.fbslot[s] == -1) {
+      A.ok[s] = 1;
+    } else {
+      const int m = min(A.cnt[s], A.cap);
+      const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
+      const double ih = A.K.inv_h, f2 = 2.0 * A.K.floor_z;
+      Moments<double> M;
+      M.zero();
+      for (int k = 0; k < m; ++k) {
+        const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
+        const int j = code & ~kMirrorBit;
+        const double zj = (code >> 31) ? f2 - A.z[j] : A.z[j];
+        M.add((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih);
+      }
+      double L[kTri];
+      M.gram(L);
+      const bool good = m >= kNB && chol9(L, 1e-15);
+      A.ok[s] = good ? 1 : 0;
+      skipped = !good;
+      if (good)
+        for (int k = 0; k < kTri; ++k) A.facx[(int64_t)k * n + s] = L[k];
+    }
+  }
+  warp_count(&A.dg->n_fallback, live && skipped);
+}
+
+__device__ __forceinline__ const double* factor_of(const AdjArgs& A, int s) {
+  return A.fbslot[s] == -1 ? A.fac : A.facx;
+}
+
+// ---------------------------------------------------------------- R1
+// update and acceleration adjoints; solves for the pass-2 z vectors
+__global__ void __launch_bounds__(kBlock) k_adj_accel(const AdjArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double th[3] = {0.0, 0.0, 0.0};
+  if (s < A.n) {
+    const int n = A.n;
+    const double dt = A.K.dt, ih = A.K.inv_h;
+    double lu1t[3], la[3];
+    for (int c = 0; c < 3; ++c) {
+      lu1t[c] = A.l1[3 + c][s] + 0.5 * dt * A.l1[c][s];
+      la[c] = dt * lu1t[c];
+      A.l0[c][s] = A.l1[c][s];                           // x' = x + ...
+      A.l0[3 + c][s] = lu1t[c] + 0.5 * dt * A.l1[c][s];  // u' = u + dt a, x' has u/2
+    }
+    double lVn = A.l1[6][s];  // V' = V^{n+1}
+    const double Vn = A.p1[P1_VN * n + s];
+    const double Gn = A.p1[P1_GN * n + s];
+    const double phi = 1.0 / Vn;
+    const int slot = A.fbslot[s];
+    const bool ok = A.ok[s];
+    double gg[3], gV[3];
+    if (slot == -1 || slot >= 0) {
+      for (int q = 0; q < 3; ++q) {
+        gg[q] = A.coef2[(int64_t)q * n + s] * ih;
+        gV[q] = A.coef2[(int64_t)(kNB + q) * n + s] * ih;
+      }
+    } else {
+      for (int q = 0; q < 3; ++q) gg[q] = gV[q] = 0.0;
+    }
+    double lgg[3] = {0, 0, 0}, lgV[3] = {0, 0, 0}, lld[3] = {0, 0, 0}, lGam[3][3] = {};
+    double lGn = 0.0;
+    if (phi <= A.K.phi_min) {
+      // gas: a = g, no dependence on the state
+    } else if (phi <= A.K.phi_max) {
+      const ClosureD cl = closure_d(phi, A.mui[A.colid[s]], A.K.phi_c, A.K.phi_min);
+      const double* p = A.p1;
+      const double g00 = p[(P1_GD + 0) * n + s], g11 = p[(P1_GD + 1) * n + s];
+      const double g22 = p[(P1_GD + 2) * n + s], g01 = p[(P1_GD + 3) * n + s];
+      const double g02 = p[(P1_GD + 4) * n + s], g12 = p[(P1_GD + 5) * n + s];
+      const double Gm[3][3] = {{g00, g01, g02}, {g01, g11, g12}, {g02, g12, g22}};
+      double ld[3];
+      for (int c = 0; c < 3; ++c) ld[c] = p[(P1_LD + c) * n + s];
+      const double A1 = Gn / (Vn * Vn);
+      double lM = 0, lN = 0, lS = 0, lR = 0;
+      for (int c = 0; c < 3; ++c) {
+        const double gV_c = (Gm[c][0] * gV[0] + Gm[c][1] * gV[1]) + Gm[c][2] * gV[2];
+        const double gg_c = (Gm[c][0] * gg[0] + Gm[c][1] * gg[1]) + Gm[c][2] * gg[2];
+        const double T1 = -A1 * (cl.S * Gn * gV[c] + cl.R * gV_c);
+        const double T2 = 2.0 * cl.M * Gn * gg[c];
+        const double T3 = cl.N * gg_c;
+        const double T4 = cl.N * Gn * ld[c];
+        const double B = ((T1 + T2) + T3) + T4;
+        lVn += la[c] * B;  // a = V^{n+1} B + g
+        const double lB = Vn * la[c];
+        lS += -A1 * Gn * gV[c] * lB;
+        lR += -A1 * gV_c * lB;
+        lM += 2.0 * Gn * gg[c] * lB;
+        lN += (gg_c + Gn * ld[c]) * lB;
+        lgV[c] += -A1 * cl.S * Gn * lB;
+        lgg[c] += 2.0 * cl.M * Gn * lB;
+        for (int d = 0; d < 3; ++d) {
+          lgV[d] += -A1 * cl.R * Gm[c][d] * lB;
+          lgg[d] += cl.N * Gm[c][d] * lB;
+          lGam[c][d] += (-A1 * cl.R * gV[d] + cl.N * gg[d]) * lB;
+        }
+        lld[c] += cl.N * Gn * lB;
+        lGn += (-(2.0 * cl.S * Gn * gV[c] + cl.R * gV_c) / (Vn * Vn) + 2.0 * cl.M * gg[c] +
+                cl.N * ld[c]) * lB;
+        lVn += 2.0 * (Gn / (Vn * Vn * Vn)) * (cl.S * Gn * gV[c] + cl.R * gV_c) * lB;
+      }
+      // closure through phi = 1/V^{n+1}
+      const double lphi = lM * cl.S + lN * cl.R + lS * cl.dS + lR * cl.dR;
+      lVn += -lphi / (Vn * Vn);
+      for (int t = 0; t < 3; ++t) th[t] = lN * cl.dN_dth[t] + lR * cl.dR_dth[t];
+    } else {
+      // quasi-static: a = beta grad V / V + g
+      for (int c = 0; c < 3; ++c) {
+        lgV[c] += A.K.beta * la[c] / Vn;
+        lVn += -A.K.beta * gV[c] * la[c] / (Vn * Vn);
+      }
+    }
+    A.lGn[s] = lGn;
+    A.lVn[s] = lVn;
+    A.lG6[0 * n + s] = lGam[0][0];
+    A.lG6[1 * n + s] = lGam[1][1];
+    A.lG6[2 * n + s] = lGam[2][2];
+    A.lG6[3 * n + s] = lGam[0][1] + lGam[1][0];
+    A.lG6[4 * n + s] = lGam[0][2] + lGam[2][0];
+    A.lG6[5 * n + s] = lGam[1][2] + lGam[2][1];
+    for (int c = 0; c < 3; ++c) A.lld[c * n + s] = lld[c];
+    // pass-2 least-squares adjoint: z = G^{-1} cbar
+    double zg[kNB], zV[kNB];
+    for (int q = 0; q < kNB; ++q) zg[q] = zV[q] = 0.0;
+    if (ok) {
+      for (int q = 0; q < 3; ++q) {
+        zg[q] = lgg[q] * ih;
+        zV[q] = lgV[q] * ih;
+      }
+      const double* F = factor_of(A, s);
+      double L[kTri];
+#pragma unroll
+      for (int k = 0; k < kTri; ++k) L[k] = F[(int64_t)k * n + s];
+      chol9_solve(L, zg);
+      chol9_solve(L, zV);
+    }
+    for (int q = 0; q < kNB; ++q) {
+      A.zz[(int64_t)q * n + s] = zg[q];
+      A.zz[(int64_t)(kNB + q) * n + s] = zV[q];
+    }
+  }
+  // parameter gradient: warp reduction, one atomic per warp and parameter
+  for (int t = 0; t < 3; ++t) {
+    double v = th[t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&A.dtheta[t], v);
+  }
+}
+
+// ---------------------------------------------------------------- R2
+// rows of the pass-2 adjoint: to the neighbours' |gdot| and V^{n+1}, and to
+// the positions
+__global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= A.n || !A.ok[s]) return;
+  const int n = A.n;
+  double zg[kNB], zV[kNB], cg[kNB], cV[kNB];
+  bool any = false;
+  for (int q = 0; q < kNB; ++q) {
+    zg[q] = A.zz[(int64_t)q * n + s];
+    zV[q] = A.zz[(int64_t)(kNB + q) * n + s];
+    cg[q] = A.coef2[(int64_t)q * n + s];
+    cV[q] = A.coef2[(int64_t)(kNB + q) * n + s];
+    any = any || zg[q] != 0.0 || zV[q] != 0.0;
+  }
+  if (!any) return;
+  const double ih = A.K.inv_h, f2 = 2.0 * A.K.floor_z;
+  const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
+  const double* Gn = A.p1 + P1_GN * n;
+  const double* Vn = A.p1 + P1_VN * n;
+  const double gni = Gn[s], Vi = Vn[s];
+  const int m = min(A.cnt[s], A.cap);
+  double sg = 0.0, sV = 0.0, sp[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < m; ++k) {
+    const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
+    const int j = code & ~kMirrorBit;
+    const bool mir = code >> 31;
+    const double zj = mir ? f2 - A.z[j] : A.z[j];
+    const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+    double a[kNB];
+    taylor_row(dx, dy, dz, a);
+    double rg = (mir ? 0.0 : Gn[j]) - gni, rV = Vn[j] - Vi, bg = 0.0, bV = 0.0;
+    for (int q = 0; q < kNB; ++q) {
+      rg -= a[q] * cg[q];
+      rV -= a[q] * cV[q];
+      bg += a[q] * zg[q];
+      bV += a[q] * zV[q];
+    }
+    if (!mir) atomicAdd(&A.lGn[j], bg);
+    sg += bg;
+    atomicAdd(&A.lVn[j], bV);  // the mirror of j carries V^{n+1}_j
+    sV += bV;
+    double ab[kNB], db[3];
+    for (int q = 0; q < kNB; ++q) ab[q] = rg * zg[q] - bg * cg[q] + rV * zV[q] - bV * cV[q];
+    row_adjoint(dx, dy, dz, ab, db);
+    atomicAdd(&A.l0[0][j], db[0] * ih);
+    atomicAdd(&A.l0[1][j], db[1] * ih);
+    atomicAdd(&A.l0[2][j], (mir ? -db[2] : db[2]) * ih);
+    for (int c = 0; c < 3; ++c) sp[c] += db[c] * ih;
+  }
+  atomicAdd(&A.lGn[s], -sg);
+  atomicAdd(&A.lVn[s], -sV);
+  for (int c = 0; c < 3; ++c) atomicAdd(&A.l0[c][s], -sp[c]);
+}
+
+// ---------------------------------------------------------------- R3
+// pass-1 adjoint: |gdot| and ld to the velocity gradient and Hessians, then
+// the least-squares rows to the neighbours' velocities and the positions
+__global__ void __launch_bounds__(kBlock) k_adj_pass1(const AdjArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= A.n) return;
+  const int n = A.n;
+  const double dt = A.K.dt, ih = A.K.inv_h, ih2 = ih * ih;
+  const double lVn = A.lVn[s];
+  const double div = A.p1[P1_DIV * n + s];
+  const double Vi = A.V[s];
+  A.l0[6][s] = lVn * (1.0 + dt * div);  // V^{n+1} = V + dt V div
+  if (!A.ok[s]) return;
+  const double ldiv = lVn * dt * Vi;
+  const double Gn = A.p1[P1_GN * n + s];
+  double lg[6];
+  for (int q = 0; q < 6; ++q) lg[q] = A.lG6[q * n + s];
+  const double lGn = A.lGn[s];
+  if (Gn > 0.0 && lGn != 0.0) {
+    const double h2 = lGn / (2.0 * Gn);
+    for (int q = 0; q < 3; ++q) lg[q] += h2 * A.p1[(P1_GD + q) * n + s];
+    for (int q = 3; q < 6; ++q) lg[q] += 2.0 * h2 * A.p1[(P1_GD + q) * n + s];
+  }
+  // gdot = sym(grad u) - div/3 I ; div = trace(grad u)
+  const double tr3 = (lg[0] + lg[1] + lg[2]) * (1.0 / 3.0);
+  double lc[3][kNB];
+  lc[0][0] = (lg[0] - tr3 + ldiv) * ih;
+  lc[1][1] = (lg[1] - tr3 + ldiv) * ih;
+  lc[2][2] = (lg[2] - tr3 + ldiv) * ih;
+  lc[0][1] = lc[1][0] = 0.5 * lg[3] * ih;
+  lc[0][2] = lc[2][0] = 0.5 * lg[4] * ih;
+  lc[1][2] = lc[2][1] = 0.5 * lg[5] * ih;
+  // ld_a = (1/2) Lap u_a + (1/6) d_a div u; columns 3 xx, 4 yy, 5 zz, 6 xy, 7 xz, 8 yz
+  const double lx = A.lld[0 * n + s] * ih2, ly = A.lld[1 * n + s] * ih2,
+               lz = A.lld[2 * n + s] * ih2;
+  const double h6 = 1.0 / 6.0;
+  lc[0][3] = (0.5 + h6) * lx; lc[0][4] = 0.5 * lx; lc[0][5] = 0.5 * lx;
+  lc[0][6] = h6 * ly;         lc[0][7] = h6 * lz;  lc[0][8] = 0.0;
+  lc[1][3] = 0.5 * ly; lc[1][4] = (0.5 + h6) * ly; lc[1][5] = 0.5 * ly;
+  lc[1][6] = h6 * lx;  lc[1][7] = 0.0;             lc[1][8] = h6 * lz;
+  lc[2][3] = 0.5 * lz; lc[2][4] = 0.5 * lz; lc[2][5] = (0.5 + h6) * lz;
+  lc[2][6] = 0.0;      lc[2][7] = h6 * lx;  lc[2][8] = h6 * ly;
+  bool any = false;
+  for (int f = 0; f < 3; ++f)
+    for (int q = 0; q < kNB; ++q) any = any || lc[f][q] != 0.0;
+  if (!any) return;
+  const double* F = factor_of(A, s);
+  double L[kTri];
+#pragma unroll
+  for (int k = 0; k < kTri; ++k) L[k] = F[(int64_t)k * n + s];
+  double c[3][kNB];
+  for (int f = 0; f < 3; ++f) {
+    chol9_solve(L, lc[f]);  // lc becomes z_f
+    for (int q = 0; q < kNB; ++q) c[f][q] = A.coef1[(int64_t)(f * kNB + q) * n + s];
+  }
+  const double f2 = 2.0 * A.K.floor_z;
+  const int mm = A.K.mirror_mode;
+  const double sgn[3] = {usign_adj(mm, 0), usign_adj(mm, 1), usign_adj(mm, 2)};
+  const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
+  const double* uf[3] = {A.u, A.v, A.w};
+  double ui[3] = {A.u[s], A.v[s], A.w[s]};
+  const int m = min(A.cnt[s], A.cap);
+  double su[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
+  for (int k = 0; k < m; ++k) {
+    const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
+    const int j = code & ~kMirrorBit;
+    const bool mir = code >> 31;
+    const double zj = mir ? f2 - A.z[j] : A.z[j];
+    const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+    double a[kNB];
+    taylor_row(dx, dy, dz, a);
+    double ab[kNB];
+    for (int q = 0; q < kNB; ++q) ab[q] = 0.0;
+    for (int f = 0; f < 3; ++f) {
+      const double sj = mir ? sgn[f] : 1.0;
+      double r = sj * uf[f][j] - ui[f], b = 0.0;
+      for (int q = 0; q < kNB; ++q) {
+        r -= a[q] * c[f][q];
+        b += a[q] * lc[f][q];
+      }
+      atomicAdd(&A.l0[3 + f][j], sj * b);
+      su[f] += b;
+      for (int q = 0; q < kNB; ++q) ab[q] += r * lc[f][q] - b * c[f][q];
+    }
+    double db[3];
+    row_adjoint(dx, dy, dz, ab, db);
+    atomicAdd(&A.l0[0][j], db[0] * ih);
+    atomicAdd(&A.l0[1][j], db[1] * ih);
+    atomicAdd(&A.l0[2][j], (mir ? -db[2] : db[2]) * ih);
+    for (int q = 0; q < 3; ++q) sp[q] += db[q] * ih;
+  }
+  for (int f = 0; f < 3; ++f) atomicAdd(&A.l0[3 + f][s], -su[f]);
+  for (int q = 0; q < 3; ++q) atomicAdd(&A.l0[q][s], -sp[q]);
+}
+
+// dst[f][s] = src[f][idx[s]] (caller order to sorted order)
+__global__ void k_gather_fields(int n, const int32_t* __restrict__ idx,
+                                const double* const* __restrict__ src,
+                                double* const* __restrict__ dst, int nf) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int o = idx[s];
+  for (int f = 0; f < nf; ++f) dst[f][s] = src[f][o];
+}
+
+void launch_gather_fields(int n, const int32_t* idx, const double* const* src, double* const* dst,
+                          int nf, cudaStream_t st) {
+  k_gather_fields<<<(n + 255) / 256, 256, 0, st>>>(n, idx, src, dst, nf);
+}
+
+void launch_adjoint_step(const AdjArgs& A, cudaStream_t st) {
+  const int nb = (A.n + kBlock - 1) / kBlock;
+  k_adj_prepare<<<nb, kBlock, 0, st>>>(A);
+  k_adj_accel<<<nb, kBlock, 0, st>>>(A);
+  k_adj_pass2<<<nb, kBlock, 0, st>>>(A);
+  k_adj_pass1<<<nb, kBlock, 0, st>>>(A);
+}
+
+}  // namespace lp

@@ -2,7 +2,9 @@
 // host-side orchestration of the kernels in neighbors.cu and fit.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "lp_internal.cuh"
@@ -10,8 +12,9 @@
 namespace lp {
 // neighbors.cu
 void launch_fill_colid(int n, const int32_t* offs, int ncol, int32_t* colid, cudaStream_t st);
-void launch_bbox(int ncol, const double* x, const double* y, const double* z, const double* radius,
-                 const int32_t* offs, double* out, cudaStream_t st);
+void launch_bbox(int n, int ncol, const double* x, const double* y, const double* z,
+                 const double* radius, const int32_t* colid, unsigned long long* out,
+                 cudaStream_t st);
 void launch_keys(int n, const double* x, const double* y, const double* z, const int32_t* colid,
                  const GridCol* grids, int64_t ncell, uint32_t* key, uint32_t* count,
                  cudaStream_t st);
@@ -29,16 +32,23 @@ void launch_neighbors(bool keep, int n, const double* x, const double* y, const 
                       const float4* pf, const int32_t* colid, const int32_t* ids,
                       const GridCol* grids, const uint32_t* start, const double* radius,
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
-                      int32_t* cnt, DevDiag* dg, cudaStream_t st);
+                      int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs = kBlock);
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st);
 // fit.cu
-void launch_pass1(int prec, const StepArgs& A, cudaStream_t st);
-void launch_pass2(int prec, const StepArgs& A, cudaStream_t st);
+void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs = kBlock);
+void launch_pass2(int prec, const StepArgs& A, cudaStream_t st, int bs = kBlock);
 void launch_fit(int prec, const FitArgs& F, cudaStream_t st);
 void launch_mui_stress(int64_t n, const ColMui& m, const lp_eos& e, const double* V,
                        const double* gu, double* gdot, double* gnorm, double* P, double* eta,
                        int8_t* regime, cudaStream_t st);
+// adjoint.cu
+void launch_adjoint_step(const AdjArgs& A, cudaStream_t st);
+void launch_gather_fields(int n, const int32_t* idx, const double* const* src, double* const* dst,
+                          int nf, cudaStream_t st);
+// persistent.cu
+cudaError_t launch_persistent(int prec, const PersistArgs& P, cudaStream_t st);
+int64_t persistent_scan_tiles(int64_t len);
 // misc.cu
 void launch_iota(int n, int32_t* a, cudaStream_t st);
 void launch_scatter_state(int n, const int32_t* ids, const double* const* src,
@@ -87,6 +97,7 @@ struct lp_ctx {
   double** d_tab = nullptr;  // [2 dir][2 kind][2 src/dst][8]
   double** d_ptr = nullptr;  // caller pointers for the final scatter
   double** h_ptr = nullptr;  // pinned staging of d_ptr
+  unsigned* bar = nullptr;   // grid barrier of the persistent kernel
   int cx = 0, ci = 0;
   int64_t ncell = 0;
   std::vector<GridCol> h_grids;
@@ -98,6 +109,8 @@ struct lp_ctx {
   std::vector<int> ev_phase;  // phase of each recorded pair
   int64_t launches = 0;
   int64_t steps = 0;
+  // launch configuration (lp_ctx_set_tuning / lp_autotune)
+  int bs_nbr = kBlock, bs_p1 = kBlock, bs_p2 = kBlock;
 };
 
 namespace {
@@ -149,7 +162,8 @@ lp_status ensure_cells(lp_ctx* c, int64_t ncell) {
     c->tile = nullptr;
   }
   LP_TRY(dalloc(c, &c->cells, (size_t)want * 3));
-  LP_TRY(dalloc(c, &c->tile, (size_t)scan_tiles(want) + 1));
+  LP_TRY(dalloc(c, &c->tile,
+                (size_t)std::max(scan_tiles(want), persistent_scan_tiles(want)) + 1));
   c->cell_capacity = want;
   return LP_OK;
 }
@@ -209,11 +223,24 @@ lp_status begin_columns(lp_ctx* c, const lp_particles* p, const double* radius_d
                       st) != cudaSuccess)
     return LP_ERR_CUDA;
   launch_fill_colid((int)p->n, c->d_offs, ncol, c->colid[c->ci], st);
-  launch_bbox(ncol, c->X[buf][0], c->X[buf][1], c->X[buf][2], radius_dev, c->d_offs, c->d_bbox, st);
+  launch_bbox((int)p->n, ncol, c->X[buf][0], c->X[buf][1], c->X[buf][2], radius_dev,
+              c->colid[c->ci], (unsigned long long*)c->d_bbox, st);
   if (cudaMemcpyAsync(c->h_bbox, c->d_bbox, sizeof(double) * 7 * ncol, cudaMemcpyDeviceToHost,
                       st) != cudaSuccess)
     return LP_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return LP_ERR_CUDA;
+  // decode the order-preserving keys; empty columns keep +-inf
+  for (int k = 0; k < 7 * ncol; ++k) {
+    unsigned long long u;
+    std::memcpy(&u, &c->h_bbox[k], 8);
+    const bool empty = (k % 7) < 3 ? u == ~0ull : u == 0ull;
+    if (empty) {
+      c->h_bbox[k] = (k % 7) < 3 ? INFINITY : ((k % 7) == 6 ? 0.0 : -INFINITY);
+      continue;
+    }
+    const unsigned long long b = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+    std::memcpy(&c->h_bbox[k], &b, 8);
+  }
   return cuda_status();
 }
 
@@ -299,21 +326,112 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
     launch_neighbors(false, n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->pf,
                      c->colid[c->ci], c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity,
                      nullptr, K.radius, K.mirror_mode, K.floor_z, c->cap, c->nbr, c->cnt, c->dg,
-                     st);
+                     st, c->bs_nbr);
     phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
     c->launches += 1;
   }
   cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
   StepArgs A = step_args(c, n, K);
   phase_mark(c, LP_PHASE_PASS1, true, st);
-  launch_pass1(prec, A, st);
+  launch_pass1(prec, A, st, c->bs_p1);
   phase_mark(c, LP_PHASE_PASS1, false, st);
   phase_mark(c, LP_PHASE_PASS2, true, st);
-  launch_pass2(prec, A, st);
+  launch_pass2(prec, A, st, c->bs_p2);
   phase_mark(c, LP_PHASE_PASS2, false, st);
   c->launches += 4;
   c->steps += 1;
   c->cx ^= 1;
+}
+
+// One LP step as a single persistent cooperative launch (same buffers and
+// toggles as run_step).
+lp_status run_step_persistent(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild,
+                              cudaStream_t st) {
+  PersistArgs P{};
+  P.n = n;
+  P.rebuild = rebuild ? 1 : 0;
+  P.ncell = c->ncell;
+  const int d = c->cx;
+  if (rebuild) {
+    P.xs = c->X[d][0]; P.ys = c->X[d][1]; P.zs = c->X[d][2];
+    P.colid_in = c->colid[c->ci]; P.ids_in = c->ids[c->ci];
+    P.colid_out = c->colid[1 - c->ci]; P.ids_out = c->ids[1 - c->ci];
+    P.grids = c->d_grids;
+    P.key = c->key;
+    P.count = c->cells;
+    P.fill = c->cells + c->cell_capacity;
+    P.start = c->cells + 2 * c->cell_capacity;
+    P.tile = c->tile;
+    P.ntiles = (int)persistent_scan_tiles(c->ncell + 2);
+    P.tmp = c->tmp;
+    P.src = (const double* const*)(c->d_tab + ((d * 2 + 0) * 2 + 0) * kTabFields);
+    P.dst = c->d_tab + ((d * 2 + 0) * 2 + 1) * kTabFields;
+    P.nsrc = 7;
+    P.pf = c->pf;
+    P.radius = K.radius; P.floor_z = K.floor_z; P.mirror_mode = K.mirror_mode; P.cap = c->cap;
+    P.nbr = c->nbr; P.cnt = c->cnt;
+    c->cx ^= 1;  // the gather fills the other buffer
+    c->ci ^= 1;
+  }
+  P.S = step_args(c, n, K);
+  P.bar = c->bar;
+  P.max_spins = 1ull << 25;  // about 2 s of __nanosleep(64)
+  cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st);
+  if (launch_persistent(prec, P, st) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  c->launches += 1;
+  c->steps += 1;
+  c->cx ^= 1;
+  return LP_OK;
+}
+
+// nsteps steps on the internal state with the given launch mode (the loop of
+// lp_step; also timed by lp_autotune).
+lp_status run_steps(lp_ctx* c, int n, const StepConsts& K, int prec, int R, int launch_mode,
+                    int nsteps, cudaStream_t st) {
+  int done = 0;
+  const int period = 2 * R;  // buffer toggles repeat after 2R steps
+  if (launch_mode == LP_LAUNCH_PERSISTENT) {
+    for (int k = 0; k < nsteps; ++k) {
+      const lp_status r = run_step_persistent(c, n, K, prec, (k % R) == 0, st);
+      if (r != LP_OK) return r;
+    }
+    done = nsteps;
+  } else if (launch_mode == LP_LAUNCH_GRAPH && !c->profile && st != nullptr &&
+             nsteps >= 2 * period) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return LP_ERR_CUDA;
+    const int cx0 = c->cx, ci0 = c->ci;
+    const int64_t launches0 = c->launches, steps0 = c->steps;
+    c->launches = 0;
+    c->steps = 0;
+    for (int k = 0; k < period; ++k) run_step(c, n, K, prec, k % R == 0, st);
+    if (cudaStreamEndCapture(st, &g) != cudaSuccess || c->cx != cx0 || c->ci != ci0) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return LP_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      cudaGetLastError();
+      return LP_ERR_CUDA;
+    }
+    const int reps = nsteps / period;
+    // the capture counted one period of launches and steps
+    const int64_t per_launch = c->launches, per_steps = c->steps;
+    for (int r = 0; r < reps; ++r) cudaGraphLaunch(ge, st);
+    c->launches = launches0 + per_launch * reps;
+    c->steps = steps0 + per_steps * reps;
+    done = reps * period;
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+  }
+  for (int k = done; k < nsteps; ++k) run_step(c, n, K, prec, (k % R) == 0, st);
+  return LP_OK;
 }
 
 bool valid_params(const lp_params* q, const lp_eos* e, double dt) {
@@ -322,6 +440,7 @@ bool valid_params(const lp_params* q, const lp_eos* e, double dt) {
   if (q->mirror_mode < 0 || q->mirror_mode > 2) return false;
   if (q->precision != LP_FP64 && q->precision != LP_MIXED) return false;
   if (q->rebuild_every < 1) return false;
+  if (q->launch_mode < LP_LAUNCH_KERNELS || q->launch_mode > LP_LAUNCH_PERSISTENT) return false;
   if (!(e->phi_min < e->phi_max && e->phi_max < e->phi_c)) return false;
   return true;
 }
@@ -390,6 +509,8 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->dg, 1);
   if (s == LP_OK) s = dalloc(c, &c->d_tab, 2 * 2 * 2 * kTabFields);
   if (s == LP_OK) s = dalloc(c, &c->d_ptr, kTabFields);
+  if (s == LP_OK) s = dalloc(c, &c->bar, 2);
+  if (s == LP_OK && cudaMemset(c->bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) s = LP_ERR_CUDA;
   if (s == LP_OK) s = ensure_cells(c, 1 << 16);
   if (s == LP_OK) {
     if (cudaMallocHost(&c->h_bbox, sizeof(double) * 7 * c->cap_cols) != cudaSuccess ||
@@ -619,6 +740,42 @@ lp_status lp_mui_stress(lp_ctx* c, const lp_mui* mui, const lp_eos* eos, int64_t
   return cuda_status();
 }
 
+namespace {
+StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap) {
+  StepConsts K{};
+  K.phi_c = eos->phi_c; K.phi_min = eos->phi_min; K.phi_max = eos->phi_max;
+  K.alpha = eos->alpha; K.beta = eos->beta;
+  K.h = q->h; K.inv_h = 1.0 / q->h; K.radius = q->radius; K.r2 = q->radius * q->radius;
+  K.gx = q->gx; K.gy = q->gy; K.gz = q->gz; K.floor_z = q->floor_z; K.dt = dt;
+  K.mirror_mode = q->mirror_mode; K.cap = cap;
+  return K;
+}
+
+// caller state -> internal buffer in caller order; per-column mu(I) upload
+lp_status load_state(lp_ctx* c, const lp_particles* p, const lp_mui* mui, cudaStream_t st) {
+  const int n = (int)p->n;
+  std::vector<ColMui> hm(p->ncolumns);
+  for (int k = 0; k < p->ncolumns; ++k)
+    hm[k] = ColMui{mui[k].mu_s, mui[k].mu_2, mui[k].I0, mui[k].d, mui[k].rho_s};
+  if (cudaMemcpyAsync(c->d_mui, hm.data(), sizeof(ColMui) * p->ncolumns, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return LP_ERR_CUDA;
+  const int d = c->cx;
+  double* const src[7] = {p->x, p->y, p->z, p->u, p->v, p->w, p->V};
+  for (int f = 0; f < 7; ++f)
+    cudaMemcpyAsync(c->X[d][f], src[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  launch_iota(n, c->ids[c->ci], st);
+  // mu(I) parameters are read back from pageable memory only once the copy ran
+  return cudaStreamSynchronize(st) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+int log2_bucket(int64_t v) {
+  int b = 0;
+  while (v > 1) { v >>= 1; ++b; }
+  return b;
+}
+}  // namespace
+
 lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* eos,
                   const lp_params* q, double dt, int32_t nsteps, void* stream) {
   if (!c || !mui || nsteps < 0) return LP_ERR_INVALID_ARG;
@@ -630,60 +787,12 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   cudaSetDevice(c->device);
   const int n = (int)p->n;
   if (n == 0 || nsteps == 0) return LP_OK;
-  std::vector<ColMui> hm(p->ncolumns);
-  for (int k = 0; k < p->ncolumns; ++k)
-    hm[k] = ColMui{mui[k].mu_s, mui[k].mu_2, mui[k].I0, mui[k].d, mui[k].rho_s};
-  if (cudaMemcpyAsync(c->d_mui, hm.data(), sizeof(ColMui) * p->ncolumns, cudaMemcpyHostToDevice,
-                      st) != cudaSuccess)
-    return LP_ERR_CUDA;
-  StepConsts K{};
-  K.phi_c = eos->phi_c; K.phi_min = eos->phi_min; K.phi_max = eos->phi_max;
-  K.alpha = eos->alpha; K.beta = eos->beta;
-  K.h = q->h; K.inv_h = 1.0 / q->h; K.radius = q->radius; K.r2 = q->radius * q->radius;
-  K.gx = q->gx; K.gy = q->gy; K.gz = q->gz; K.floor_z = q->floor_z; K.dt = dt;
-  K.mirror_mode = q->mirror_mode; K.cap = c->cap;
-  // caller state -> internal buffer, identity order
+  const StepConsts K = step_consts(eos, q, dt, c->cap);
+  LP_TRY(load_state(c, p, mui, st));
   const int d = c->cx;
-  double* const src[7] = {p->x, p->y, p->z, p->u, p->v, p->w, p->V};
-  for (int f = 0; f < 7; ++f)
-    cudaMemcpyAsync(c->X[d][f], src[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-  launch_iota(n, c->ids[c->ci], st);
   LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
   LP_TRY(setup_grids(c, p->ncolumns, q->radius, st));
-  const int R = q->rebuild_every;
-  int done = 0;
-  const int period = 2 * R;  // buffer toggles repeat after 2R steps
-  if (q->use_graph && !c->profile && st != nullptr && nsteps >= 2 * period) {
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-      return LP_ERR_CUDA;
-    const int cx0 = c->cx, ci0 = c->ci;
-    const int64_t launches0 = c->launches, steps0 = c->steps;
-    c->launches = 0;
-    c->steps = 0;
-    for (int k = 0; k < period; ++k) run_step(c, n, K, q->precision, k % R == 0, st);
-    if (cudaStreamEndCapture(st, &g) != cudaSuccess || c->cx != cx0 || c->ci != ci0) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      return LP_ERR_CUDA;
-    }
-    if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
-      cudaGraphDestroy(g);
-      cudaGetLastError();
-      return LP_ERR_CUDA;
-    }
-    const int reps = nsteps / period;
-    // the capture counted one period of launches and steps
-    const int64_t per_launch = c->launches, per_steps = c->steps;
-    for (int r = 0; r < reps; ++r) cudaGraphLaunch(ge, st);
-    c->launches = launches0 + per_launch * reps;
-    c->steps = steps0 + per_steps * reps;
-    done = reps * period;
-    cudaGraphExecDestroy(ge);
-    cudaGraphDestroy(g);
-  }
-  for (int k = done; k < nsteps; ++k) run_step(c, n, K, q->precision, (k % R) == 0, st);
+  LP_TRY(run_steps(c, n, K, q->precision, q->rebuild_every, q->launch_mode, nsteps, st));
   // internal state -> caller arrays (original order)
   {
     const int e = c->cx;
@@ -698,14 +807,340 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   return cuda_status();
 }
 
+lp_status lp_ctx_set_tuning(lp_ctx* c, const lp_tuning* t) {
+  if (!c || !t) return LP_ERR_INVALID_ARG;
+  for (int b : {t->block_neighbors, t->block_pass1, t->block_pass2})
+    if (b != 64 && b != 128 && b != 256) return LP_ERR_INVALID_ARG;
+  c->bs_nbr = t->block_neighbors;
+  c->bs_p1 = t->block_pass1;
+  c->bs_p2 = t->block_pass2;
+  return LP_OK;
+}
+
+lp_status lp_autotune(lp_ctx* c, const lp_particles* p, const lp_mui* mui, const lp_eos* eos,
+                      const lp_params* q, double dt, int32_t steps_per_trial,
+                      const char* table_path, lp_tuning* out, void* stream) {
+  if (!c || !mui || !out || steps_per_trial < 1 || steps_per_trial > 1000)
+    return LP_ERR_INVALID_ARG;
+  std::vector<int32_t> offs;
+  LP_TRY(check_particles(c, p, offs, true));
+  if (!valid_params(q, eos, dt) || p->n < 1) return LP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(c->device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return LP_ERR_CUDA;
+  // table key: device, log2 n, log2 columns, precision, stencil radius in h/10
+  std::string dev = prop.name;
+  for (char& ch : dev)
+    if (ch == ' ' || ch == '|') ch = '_';
+  char key[256];
+  std::snprintf(key, sizeof(key), "%s|n2^%d|c2^%d|p%d|r%d", dev.c_str(), log2_bucket(p->n),
+                log2_bucket(p->ncolumns), q->precision, (int)std::lround(10.0 * q->radius / q->h));
+  if (table_path) {
+    if (FILE* fp = std::fopen(table_path, "r")) {
+      char line[512];
+      while (std::fgets(line, sizeof(line), fp)) {
+        char k[256];
+        lp_tuning t{};
+        if (std::sscanf(line, "%255s %d %d %d %d %lf", k, &t.block_neighbors, &t.block_pass1,
+                        &t.block_pass2, &t.launch_mode, &t.ms_per_step) == 6 &&
+            std::strcmp(k, key) == 0) {
+          std::fclose(fp);
+          t.from_table = 1;
+          LP_TRY(lp_ctx_set_tuning(c, &t));
+          *out = t;
+          return LP_OK;
+        }
+      }
+      std::fclose(fp);
+    }
+  }
+  const int n = (int)p->n;
+  const StepConsts K = step_consts(eos, q, dt, c->cap);
+  const int R = q->rebuild_every;
+  // every trial starts from the caller's state (which is never modified)
+  auto restart = [&]() -> lp_status {
+    LP_TRY(load_state(c, p, mui, st));
+    launch_fill_colid(n, c->d_offs, p->ncolumns, c->colid[c->ci], st);
+    return LP_OK;
+  };
+  LP_TRY(load_state(c, p, mui, st));
+  LP_TRY(begin_columns(c, p, nullptr, c->cx, offs, st));
+  LP_TRY(setup_grids(c, p->ncolumns, q->radius, st));
+  // block sizes: per-phase device time of each candidate
+  const int cand[3] = {64, 128, 256};
+  double best_ms[LP_NPHASES];
+  int best_bs[LP_NPHASES];
+  for (int k = 0; k < LP_NPHASES; ++k) {
+    best_ms[k] = 1e300;
+    best_bs[k] = kBlock;
+  }
+  const bool prof0 = c->profile;
+  double ms[LP_NPHASES];
+  for (int bs : cand) {
+    LP_TRY(restart());
+    c->bs_nbr = c->bs_p1 = c->bs_p2 = bs;
+    lp_ctx_phase_times(c, st, ms, nullptr, nullptr);  // reset
+    c->profile = true;
+    const lp_status r = run_steps(c, n, K, q->precision, R, LP_LAUNCH_KERNELS, steps_per_trial, st);
+    c->profile = prof0;
+    LP_TRY(r);
+    LP_TRY(lp_ctx_phase_times(c, st, ms, nullptr, nullptr));
+    for (int k = 0; k < LP_NPHASES; ++k)
+      if (ms[k] < best_ms[k]) {
+        best_ms[k] = ms[k];
+        best_bs[k] = bs;
+      }
+  }
+  lp_tuning t{};
+  t.block_neighbors = best_bs[LP_PHASE_NEIGHBORS];
+  t.block_pass1 = best_bs[LP_PHASE_PASS1];
+  t.block_pass2 = best_bs[LP_PHASE_PASS2];
+  LP_TRY(lp_ctx_set_tuning(c, &t));
+  // launch mode: whole-step time of graph replay vs one persistent launch
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int modes[2] = {LP_LAUNCH_GRAPH, LP_LAUNCH_PERSISTENT};
+  double mode_ms[2] = {1e300, 1e300};
+  const int steps = std::max(steps_per_trial, 4 * R);
+  for (int m = 0; m < 2; ++m) {
+    if (modes[m] == LP_LAUNCH_GRAPH && st == nullptr) continue;
+    LP_TRY(restart());
+    cudaEventRecord(e0, st);
+    const lp_status r = run_steps(c, n, K, q->precision, R, modes[m], steps, st);
+    cudaEventRecord(e1, st);
+    if (r != LP_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float el = 0.f;
+    cudaEventElapsedTime(&el, e0, e1);
+    mode_ms[m] = el / steps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int pick = mode_ms[1] < mode_ms[0] ? 1 : 0;
+  if (mode_ms[pick] >= 1e299) return LP_ERR_CUDA;
+  t.launch_mode = modes[pick];
+  t.ms_per_step = mode_ms[pick];
+  t.from_table = 0;
+  lp_diag dummy;
+  lp_ctx_sync(c, st, &dummy);  // trial steps may flag a blow-up; not the caller's state
+  if (table_path) {
+    if (FILE* fp = std::fopen(table_path, "a")) {
+      std::fprintf(fp, "%s %d %d %d %d %.6f\n", key, t.block_neighbors, t.block_pass1,
+                   t.block_pass2, t.launch_mode, t.ms_per_step);
+      std::fclose(fp);
+    }
+  }
+  *out = t;
+  return LP_OK;
+}
+
 lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* mui,
-                          const lp_eos* eos, const lp_params* params, double dt, int32_t nsteps,
+                          const lp_eos* eos, const lp_params* q, double dt, int32_t nsteps,
                           int32_t checkpoint_every, const lp_particles* seed, double* dL_dmui,
                           lp_particles* dL_dinitial, void* stream) {
-  (void)initial; (void)mui; (void)eos; (void)params; (void)dt; (void)nsteps;
-  (void)checkpoint_every; (void)seed; (void)dL_dmui; (void)dL_dinitial; (void)stream;
-  if (!c) return LP_ERR_INVALID_ARG;
-  return LP_ERR_UNIMPLEMENTED;
+  if (!c || !mui || !seed || !dL_dmui || nsteps < 0 || checkpoint_every < 1)
+    return LP_ERR_INVALID_ARG;
+  std::vector<int32_t> offs;
+  LP_TRY(check_particles(c, initial, offs, true));
+  if (!valid_params(q, eos, dt) || q->precision != LP_FP64) return LP_ERR_INVALID_ARG;
+  if (seed->n != initial->n || (initial->n > 0 && (!seed->x || !seed->y || !seed->z || !seed->u ||
+                                                   !seed->v || !seed->w || !seed->V)))
+    return LP_ERR_INVALID_ARG;
+  if (dL_dinitial && (dL_dinitial->n != initial->n ||
+                      (initial->n > 0 && (!dL_dinitial->x || !dL_dinitial->y || !dL_dinitial->z ||
+                                          !dL_dinitial->u || !dL_dinitial->v || !dL_dinitial->w ||
+                                          !dL_dinitial->V))))
+    return LP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(c->device);
+  const int n = (int)initial->n;
+  cudaMemsetAsync(dL_dmui, 0, 3 * sizeof(double), st);
+  if (n == 0 || nsteps == 0) {
+    if (dL_dinitial && n > 0) {
+      double* const dst[7] = {dL_dinitial->x, dL_dinitial->y, dL_dinitial->z, dL_dinitial->u,
+                              dL_dinitial->v, dL_dinitial->w, dL_dinitial->V};
+      const double* const src[7] = {seed->x, seed->y, seed->z, seed->u, seed->v, seed->w, seed->V};
+      for (int f = 0; f < 7; ++f)
+        cudaMemcpyAsync(dst[f], src[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    }
+    return cuda_status();
+  }
+  const int C = checkpoint_every;
+  const int nseg = (nsteps + C - 1) / C;
+  std::vector<ColMui> hm(initial->ncolumns);
+  for (int k = 0; k < initial->ncolumns; ++k)
+    hm[k] = ColMui{mui[k].mu_s, mui[k].mu_2, mui[k].I0, mui[k].d, mui[k].rho_s};
+  if (cudaMemcpyAsync(c->d_mui, hm.data(), sizeof(ColMui) * initial->ncolumns,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return LP_ERR_CUDA;
+  StepConsts K{};
+  K.phi_c = eos->phi_c; K.phi_min = eos->phi_min; K.phi_max = eos->phi_max;
+  K.alpha = eos->alpha; K.beta = eos->beta;
+  K.h = q->h; K.inv_h = 1.0 / q->h; K.radius = q->radius; K.r2 = q->radius * q->radius;
+  K.gx = q->gx; K.gy = q->gy; K.gz = q->gz; K.floor_z = q->floor_z; K.dt = dt;
+  K.mirror_mode = q->mirror_mode; K.cap = c->cap;
+
+  // workspace of this call: checkpoints, segment states, coefficients, adjoints
+  const size_t N = (size_t)n;
+  const size_t nd =
+      N * (7 * (size_t)nseg + 7 * (size_t)(C + 1) + 27 + 18 + 14 + 2 + 6 + 3 + 18 + 7 + 45 + 1) + 3;
+  double* W = nullptr;
+  if (cudaMalloc(&W, nd * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_OOM;
+  }
+  double* p = W;
+  auto take = [&](size_t k) { double* r = p; p += k; return r; };
+  double* ckpt = take(7 * N * nseg);
+  double* seg = take(7 * N * (C + 1));
+  double* coef1 = take(27 * N);
+  double* coef2 = take(18 * N);
+  double* lam[2] = {take(7 * N), take(7 * N)};
+  double* lGn = take(N);
+  double* lVn = take(N);
+  double* lG6 = take(6 * N);
+  double* lld = take(3 * N);
+  double* zz = take(18 * N);
+  double* scratch = take(7 * N);
+  double* facx = take(45 * N);
+  uint8_t* okf = (uint8_t*)take(N);  // N bytes used of N doubles
+  double* dth = take(3);
+  // device pointer tables: checkpoints (nseg x 7), segment states ((C+1) x 7),
+  // lam[0], lam[1], seed, caller initial, dL_dinitial, internal X[0], X[1]
+  const int ntab = 7 * nseg + 7 * (C + 1) + 7 * 7;
+  std::vector<double*> tab(ntab);
+  for (int s2 = 0; s2 < nseg; ++s2)
+    for (int f = 0; f < 7; ++f) tab[7 * s2 + f] = ckpt + (size_t)(7 * s2 + f) * N;
+  const int tseg = 7 * nseg;
+  for (int k = 0; k <= C; ++k)
+    for (int f = 0; f < 7; ++f) tab[tseg + 7 * k + f] = seg + (size_t)(7 * k + f) * N;
+  const int tlam = tseg + 7 * (C + 1);
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < 7; ++f) tab[tlam + 7 * b + f] = lam[b] + (size_t)f * N;
+  const int tseed = tlam + 14;
+  double* const sd[7] = {seed->x, seed->y, seed->z, seed->u, seed->v, seed->w, seed->V};
+  for (int f = 0; f < 7; ++f) tab[tseed + f] = sd[f];
+  const int tinit = tseed + 7;
+  double* const in[7] = {initial->x, initial->y, initial->z, initial->u, initial->v, initial->w,
+                         initial->V};
+  for (int f = 0; f < 7; ++f) tab[tinit + f] = in[f];
+  const int tout = tinit + 7;
+  for (int f = 0; f < 7; ++f) tab[tout + f] = dL_dinitial ? (&dL_dinitial->x)[f] : lam[0];
+  const int tX = tout + 7;
+  for (int d = 0; d < 2; ++d)
+    for (int f = 0; f < 7; ++f) tab[tX + 7 * d + f] = c->X[d][f];
+  double** dtab = nullptr;
+  if (cudaMalloc(&dtab, sizeof(double*) * ntab) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(W);
+    return LP_ERR_OOM;
+  }
+  lp_status rs = LP_OK;
+  do {
+    if (cudaMemcpy(dtab, tab.data(), sizeof(double*) * ntab, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      rs = LP_ERR_CUDA;
+      break;
+    }
+    cudaMemsetAsync(dth, 0, 3 * sizeof(double), st);
+    // ---- forward sweep: checkpoints at segment starts (caller order)
+    for (int f = 0; f < 7; ++f) {
+      cudaMemcpyAsync(c->X[c->cx][f], in[f], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(tab[f], in[f], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    }
+    launch_iota(n, c->ids[c->ci], st);
+    rs = begin_columns(c, initial, nullptr, c->cx, offs, st);
+    if (rs != LP_OK) break;
+    rs = setup_grids(c, initial->ncolumns, q->radius, st);
+    if (rs != LP_OK) break;
+    for (int k = 0; k < nsteps; ++k) {
+      if (k > 0 && k % C == 0)
+        launch_scatter_state(n, c->ids[c->ci], (const double* const*)(dtab + tX + 7 * c->cx),
+                             dtab + 7 * (k / C), 7, st);
+      run_step(c, n, K, LP_FP64, k % C == 0, st);
+    }
+    // ---- reverse sweep
+    int cur = 0;  // lam[cur] holds the adjoint (caller order between segments)
+    for (int f = 0; f < 7; ++f)
+      cudaMemcpyAsync(lam[cur] + f * N, sd[f], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    for (int s2 = nseg - 1; s2 >= 0; --s2) {
+      const int steps = std::min(C, nsteps - s2 * C);
+      // restore the checkpoint, rebuild the stencils exactly as the forward run did
+      for (int f = 0; f < 7; ++f)
+        cudaMemcpyAsync(c->X[c->cx][f], tab[7 * s2 + f], sizeof(double) * N,
+                        cudaMemcpyDeviceToDevice, st);
+      launch_iota(n, c->ids[c->ci], st);
+      launch_fill_colid(n, c->d_offs, initial->ncolumns, c->colid[c->ci], st);
+      sort_particles(c, n, 0, 7, st);
+      launch_neighbors(false, n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->pf,
+                       c->colid[c->ci], c->ids[c->ci], c->d_grids,
+                       c->cells + 2 * c->cell_capacity, nullptr, K.radius, K.mirror_mode,
+                       K.floor_z, c->cap, c->nbr, c->cnt, c->dg, st);
+      for (int f = 0; f < 7; ++f)
+        cudaMemcpyAsync(tab[tseg + f], c->X[c->cx][f], sizeof(double) * N,
+                        cudaMemcpyDeviceToDevice, st);
+      // re-run the segment, keeping every step's state
+      StepArgs S = step_args(c, n, K);
+      for (int k = 0; k < steps; ++k) {
+        double* const* sk = &tab[tseg + 7 * k];
+        double* const* sk1 = &tab[tseg + 7 * (k + 1)];
+        S.x = sk[0]; S.y = sk[1]; S.z = sk[2]; S.u = sk[3]; S.v = sk[4]; S.w = sk[5]; S.V = sk[6];
+        S.xo = sk1[0]; S.yo = sk1[1]; S.zo = sk1[2]; S.uo = sk1[3]; S.vo = sk1[4]; S.wo = sk1[5];
+        S.Vo = sk1[6];
+        cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
+        launch_pass1(LP_FP64, S, st);
+        launch_pass2(LP_FP64, S, st);
+      }
+      // adjoint to the sorted order of this segment
+      launch_gather_fields(n, c->ids[c->ci], (const double* const*)(dtab + tlam + 7 * cur),
+                           dtab + tlam + 7 * (1 - cur), 7, st);
+      cur = 1 - cur;
+      for (int k = steps - 1; k >= 0; --k) {
+        double* const* sk = &tab[tseg + 7 * k];
+        S.x = sk[0]; S.y = sk[1]; S.z = sk[2]; S.u = sk[3]; S.v = sk[4]; S.w = sk[5]; S.V = sk[6];
+        S.xo = scratch; S.yo = scratch + N; S.zo = scratch + 2 * N; S.uo = scratch + 3 * N;
+        S.vo = scratch + 4 * N; S.wo = scratch + 5 * N; S.Vo = scratch + 6 * N;
+        S.coef1 = coef1;
+        S.coef2 = coef2;
+        cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
+        launch_pass1(LP_FP64, S, st);
+        launch_pass2(LP_FP64, S, st);
+        S.coef1 = S.coef2 = nullptr;
+        AdjArgs J{};
+        J.n = n; J.cap = c->cap;
+        J.x = S.x; J.y = S.y; J.z = S.z; J.u = S.u; J.v = S.v; J.w = S.w; J.V = S.V;
+        J.nbr = c->nbr; J.cnt = c->cnt; J.colid = c->colid[c->ci]; J.fbslot = c->fbslot;
+        J.mui = c->d_mui; J.fac = c->fac; J.p1 = c->p1; J.coef1 = coef1; J.coef2 = coef2;
+        J.fbgrad = c->fbgrad; J.K = K;
+        for (int f = 0; f < 7; ++f) {
+          J.l1[f] = lam[cur] + f * N;
+          J.l0[f] = lam[1 - cur] + f * N;
+        }
+        J.lGn = lGn; J.lVn = lVn; J.lG6 = lG6; J.lld = lld; J.zz = zz; J.dtheta = dth;
+        J.dg = c->dg; J.ok = okf; J.facx = facx;
+        launch_adjoint_step(J, st);
+        cur = 1 - cur;
+      }
+      // back to caller order
+      launch_scatter_state(n, c->ids[c->ci], (const double* const*)(dtab + tlam + 7 * cur),
+                           dtab + tlam + 7 * (1 - cur), 7, st);
+      cur = 1 - cur;
+    }
+    if (dL_dinitial)
+      for (int f = 0; f < 7; ++f)
+        cudaMemcpyAsync(tab[tout + f], lam[cur] + f * N, sizeof(double) * N,
+                        cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(dL_dmui, dth, 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) rs = LP_ERR_CUDA;
+    if (rs == LP_OK) rs = cuda_status();
+  } while (0);
+  cudaFree(dtab);
+  cudaFree(W);
+  return rs;
 }
 
 }  // extern "C"

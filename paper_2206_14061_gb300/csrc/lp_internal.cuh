@@ -15,7 +15,8 @@ constexpr uint32_t kMirrorBit = 0x80000000u;
 constexpr int kNB = 9;            // quadratic Taylor basis in 3D, no constant term
 constexpr int kTri = 45;          // packed lower triangle of a 9x9 matrix
 constexpr int kMaxColumns = 4096;
-constexpr int kBlock = 128;       // threads per block of the per-particle kernels
+constexpr int kBlock = 128;       // default threads per block of the per-particle kernels
+constexpr int kMaxBlock = 256;    // largest block size the tuner may pick
 constexpr int kMaxFields = 16;    // lp_fit_derivatives
 constexpr int kMaxCand = 128;     // candidate buffer of the keep-nearest search
 
@@ -91,6 +92,8 @@ struct StepArgs {
   double* fbgrad;   // pass-2 fallback results, 6 per slot
   DevDiag* dg;
   StepConsts K;
+  double* coef1;    // optional (FP64 only): pass-1 coefficients, 27 * n (k-major)
+  double* coef2;    // optional (FP64 only): pass-2 coefficients of |gdot|, V^{n+1}, 18 * n
 };
 
 struct FitArgs {
@@ -105,6 +108,58 @@ struct FitArgs {
   int32_t* fb_count;
   int fb_cap;
   DevDiag* dg;
+};
+
+// arguments of the persistent step kernel (persistent.cu)
+struct PersistArgs {
+  StepArgs S;  // pass 1 / pass 2 (state pointers of the sorted order)
+  int n;
+  int rebuild;
+  int64_t ncell;
+  // sort phases
+  const double *xs, *ys, *zs;  // positions before the sort
+  const int32_t *colid_in, *ids_in;
+  int32_t *colid_out, *ids_out;
+  const GridCol* grids;
+  uint32_t *key, *count, *fill, *start, *tile;
+  int ntiles;
+  int32_t* tmp;
+  const double* const* src;
+  double* const* dst;
+  int nsrc;
+  float4* pf;
+  // neighbour phase
+  double radius, floor_z;
+  int mirror_mode, cap;
+  int32_t *nbr, *cnt;
+  // barrier: [0] arrivals, [1] generation
+  unsigned* bar;
+  unsigned long long max_spins;
+};
+
+// arguments of the adjoint kernels (adjoint.cu)
+struct AdjArgs {
+  int n, cap;
+  const double *x, *y, *z, *u, *v, *w, *V;  // forward state at step n (sorted order)
+  const int32_t *nbr, *cnt, *colid, *fbslot;
+  const ColMui* mui;
+  const double* fac;     // FP64 Cholesky factors, 45 * n
+  const double* p1;      // pass-1 outputs (P1_*)
+  const double* coef1;   // pass-1 coefficients, 27 * n
+  const double* coef2;   // pass-2 coefficients, 18 * n
+  const double* fbgrad;  // pass-2 gradients of QR-path stencils, 6 per slot
+  StepConsts K;
+  const double* l1[7];   // adjoint of the state at n+1: x, y, z, u, v, w, V
+  double* l0[7];         // adjoint of the state at n (output)
+  double* lGn;           // adjoint of |gdot|^n (accumulated)
+  double* lVn;           // adjoint of V^{n+1} (accumulated)
+  double* lG6;           // adjoint of gdot from the acceleration, 6 * n
+  double* lld;           // adjoint of ld, 3 * n
+  double* zz;            // G^{-1} cbar of pass 2 (|gdot|, V^{n+1}), 18 * n
+  double* dtheta;        // dL/d(mu_s, mu_2, I0), accumulated
+  DevDiag* dg;
+  uint8_t* ok;           // per particle: 1 if the fit adjoint is available
+  double* facx;          // FP64 factors of the QR-path stencils, 45 * n
 };
 
 // ------------------------------------------------------------------ closure

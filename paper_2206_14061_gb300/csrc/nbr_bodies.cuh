@@ -1,0 +1,248 @@
+// Device bodies of the cell sort and the neighbour search, shared by the
+// per-phase kernels (neighbors.cu) and the persistent step kernel
+// (persistent.cu). See neighbors.cu for the method.
+#pragma once
+
+#include "lp_internal.cuh"
+
+namespace lp {
+
+// Cell key of every particle; particles with a non-finite coordinate go to
+// the extra bucket `ncell`, which no search visits.
+__device__ __forceinline__ void keys_body(int s, const double* __restrict__ x,
+                                          const double* __restrict__ y,
+                                          const double* __restrict__ z,
+                                          const int32_t* __restrict__ colid,
+                                          const GridCol* __restrict__ grids, uint32_t ncell,
+                                          uint32_t* __restrict__ key,
+                                          uint32_t* __restrict__ count) {
+  if (!(isfinite(x[s]) && isfinite(y[s]) && isfinite(z[s]))) {
+    key[s] = ncell;
+    atomicAdd(&count[ncell], 1u);
+    return;
+  }
+  const GridCol g = grids[colid[s]];
+  const int cx = cell_coord(x[s], g.ox, g.inv_c, g.nx);
+  const int cy = cell_coord(y[s], g.oy, g.inv_c, g.ny);
+  const int cz = cell_coord(z[s], g.oz, g.inv_c, g.nz);
+  const uint32_t k = (uint32_t)cell_id(g, cx, cy, cz);
+  key[s] = k;
+  atomicAdd(&count[k], 1u);
+}
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) ws[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    ws[lane] = wi - w;  // exclusive prefix of each warp
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  const uint32_t r = ws[wid] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void scatter_body(int s, const uint32_t* __restrict__ key,
+                                             const uint32_t* __restrict__ start,
+                                             uint32_t* __restrict__ fill,
+                                             int32_t* __restrict__ tmp) {
+  const uint32_t k = key[s];
+  const uint32_t pos = start[k] + atomicAdd(&fill[k], 1u);
+  tmp[pos] = s;
+}
+
+// Order each cell's particles by original index (insertion sort; cells hold
+// about (cell edge / h)^3 particles). A cell crowded beyond kSortCap (only
+// after a blow-up) keeps its arrival order: the stencils stay exact, only the
+// row order inside them loses its determinism.
+constexpr uint32_t kSortCap = 1024;
+__device__ __forceinline__ void cell_sort_body(int64_t c, const uint32_t* __restrict__ start,
+                                               int32_t* __restrict__ tmp,
+                                               const int32_t* __restrict__ ids) {
+  const uint32_t b = start[c], e = start[c + 1];
+  if (e - b > kSortCap) return;
+  for (uint32_t i = b + 1; i < e; ++i) {
+    const int32_t v = tmp[i];
+    const int32_t kv = ids[v];
+    uint32_t j = i;
+    while (j > b && ids[tmp[j - 1]] > kv) {
+      tmp[j] = tmp[j - 1];
+      --j;
+    }
+    tmp[j] = v;
+  }
+}
+
+// Gather the state into the new order; FP32 origin-relative positions for the
+// prefilter.
+__device__ __forceinline__ void gather_body(int t, const int32_t* __restrict__ tmp,
+                                            const double* const* __restrict__ src,
+                                            double* const* __restrict__ dst, int nsrc,
+                                            const int32_t* __restrict__ ids_in,
+                                            int32_t* __restrict__ ids_out,
+                                            const int32_t* __restrict__ col_in,
+                                            int32_t* __restrict__ col_out,
+                                            const GridCol* __restrict__ grids,
+                                            float4* __restrict__ pf) {
+  const int s = tmp[t];
+  for (int f = 0; f < nsrc; ++f) dst[f][t] = src[f][s];
+  ids_out[t] = ids_in[s];
+  const int c = col_in[s];
+  col_out[t] = c;
+  const GridCol g = grids[c];
+  pf[t] = make_float4(__double2float_rn(src[0][s] - g.ox), __double2float_rn(src[1][s] - g.oy),
+                      __double2float_rn(src[2][s] - g.oz), 0.f);
+}
+
+__device__ __forceinline__ bool exact_in(double xi, double yi, double zi, double xj, double yj,
+                                         double zj, double r2, double* d2out) {
+  const double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  *d2out = d2;
+  return d2 <= r2;
+}
+
+// ordering of keep-nearest candidates: nearest first, then original index,
+// then real before mirror
+__device__ __forceinline__ bool cand_less(double da, uint32_t ka, double db, uint32_t kb) {
+  if (da != db) return da < db;
+  return ka < kb;  // ka = (orig id << 1) | mirror
+}
+
+// Stencil of particle s; every lane of the warp must call it (live or not).
+template <bool KEEP>
+__device__ __forceinline__ void neighbors_body(
+    int s, bool live, int n, const double* __restrict__ x, const double* __restrict__ y,
+    const double* __restrict__ z, const float4* __restrict__ pf,
+    const int32_t* __restrict__ colid, const int32_t* __restrict__ ids,
+    const GridCol* __restrict__ grids, const uint32_t* __restrict__ start,
+    const double* __restrict__ radius, double r_const, int mirror_mode, double floor_z, int cap,
+    int32_t* __restrict__ nbr, int32_t* __restrict__ cnt, DevDiag* __restrict__ dg) {
+  int c = 0;
+  bool over = false;
+  if (live) {
+    const GridCol g = grids[colid[s]];
+    const double xi = x[s], yi = y[s], zi = z[s];
+    const double r = radius ? radius[s] : r_const;
+    const double r2 = r * r;
+    const float r2f = __double2float_rn(r2);
+    const float lo = r2f * (1.0f - 0.015625f), hi = r2f * (1.0f + 0.015625f);
+    const float4 pi = pf[s];
+    const float lim = 4096.0f * __double2float_rn(r);
+    const bool exact_only = !(fabsf(pi.x) <= lim && fabsf(pi.y) <= lim && fabsf(pi.z) <= lim);
+    const float fz2 = __double2float_rn(2.0 * (floor_z - g.oz));
+    double cd2[KEEP ? kMaxCand : 1];
+    uint32_t cj[KEEP ? kMaxCand : 1];
+    const int ncx = g.nx, ncy = g.ny, ncz = g.nz;
+    const int cx = cell_coord(xi, g.ox, g.inv_c, ncx);
+    const int cy = cell_coord(yi, g.oy, g.inv_c, ncy);
+    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, ncx - 1);
+    const int y0 = max(cy - 1, 0), y1 = min(cy + 1, ncy - 1);
+    for (int pass = 0; pass < (mirror_mode ? 2 : 1); ++pass) {
+      const double qz = pass == 0 ? zi : 2.0 * floor_z - zi;
+      const int cz = cell_coord(qz, g.oz, g.inv_c, ncz);
+      const int z0 = max(cz - 1, 0), z1 = min(cz + 1, ncz - 1);
+      for (int kz = z0; kz <= z1; ++kz)
+        for (int ky = y0; ky <= y1; ++ky) {
+          // cells kx = x0..x1 are contiguous in the cell table
+          const int64_t c0 = cell_id(g, x0, ky, kz), c1 = cell_id(g, x1, ky, kz);
+          const uint32_t b = start[c0], e = start[c1 + 1];
+          for (uint32_t j = b; j < e; ++j) {
+            if (pass == 0 && (int)j == s) continue;
+            const float4 pj = pf[j];
+            const float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
+            const float dzf = (pass == 0 ? pj.z : fz2 - pj.z) - pi.z;
+            const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+            if (!exact_only && d2f > hi) continue;
+            double d2 = 0.0;
+            bool in;
+            if (!exact_only && d2f < lo && !KEEP) {
+              in = true;
+            } else {
+              const double zj = pass == 0 ? z[j] : __dsub_rn(2.0 * floor_z, z[j]);
+              in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2);
+            }
+            if (!in) continue;
+            const uint32_t code = j | (pass ? kMirrorBit : 0u);
+            if (KEEP) {
+              if (c < kMaxCand) {
+                cd2[c] = d2;
+                cj[c] = code;
+              } else {
+                over = true;
+              }
+            } else if (c < cap) {
+              nbr[(int64_t)c * n + s] = (int32_t)code;
+            }
+            ++c;
+          }
+        }
+    }
+    if (KEEP) {
+      int m = c < kMaxCand ? c : kMaxCand;
+      if (m > cap) {
+        // partial selection sort: the cap nearest to the front
+        for (int t = 0; t < cap; ++t) {
+          int best = t;
+          uint32_t kb = ((uint32_t)ids[cj[t] & ~kMirrorBit] << 1) | (cj[t] >> 31);
+          for (int u = t + 1; u < m; ++u) {
+            const uint32_t ku = ((uint32_t)ids[cj[u] & ~kMirrorBit] << 1) | (cj[u] >> 31);
+            if (cand_less(cd2[u], ku, cd2[best], kb)) { best = u; kb = ku; }
+          }
+          const double td = cd2[t]; cd2[t] = cd2[best]; cd2[best] = td;
+          const uint32_t tj = cj[t]; cj[t] = cj[best]; cj[best] = tj;
+        }
+        m = cap;
+      }
+      for (int t = 0; t < m; ++t) nbr[(int64_t)t * n + s] = (int32_t)cj[t];
+      c = m;
+    } else {
+      over = c > cap;
+    }
+    cnt[s] = c;
+  }
+  warp_count(&dg->n_overflow, live && over);
+  {
+    // total stencil rows and stencils (warp-reduced)
+    unsigned long long rows = live ? (unsigned long long)min(c, cap) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) rows += __shfl_xor_sync(0xffffffffu, rows, o);
+    const unsigned live_n = __popc(__ballot_sync(0xffffffffu, live));
+    if ((threadIdx.x & 31) == 0 && live_n) {
+      atomicAdd(&dg->n_stencil_rows, rows);
+      atomicAdd(&dg->n_stencils, (unsigned long long)live_n);
+    }
+  }
+  if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
+  // stencil size range (warp-reduced)
+  int mn = live ? c : INT32_MAX, mx = live ? c : 0;
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mn != INT32_MAX) atomicMin(&dg->min_stencil, mn);
+    atomicMax(&dg->max_stencil, mx);
+  }
+}
+
+}  // namespace lp

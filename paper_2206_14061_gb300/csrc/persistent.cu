@@ -1,0 +1,173 @@
+// One LP step as a single persistent, cooperative launch over all particles
+// of all columns: cell sort, neighbour search, pass 1 and pass 2 run as
+// phases of one kernel, separated by a grid barrier. The same device bodies
+// as the per-phase kernels are used, so results are identical.
+//
+// The barrier is a generation counter in global memory. A block that waits
+// longer than the spin limit sets LP_FLAG_TIMEOUT and leaves the kernel, so
+// the launch always ends; the host reads the flag with lp_ctx_sync. The
+// launch is cooperative, so all blocks are resident and the limit is never
+// reached by a correct run.
+#include "fit_bodies.cuh"
+#include "nbr_bodies.cuh"
+
+namespace lp {
+
+constexpr int kPTile = kBlock * kScanItems;  // scan tile of one persistent block
+
+int64_t persistent_scan_tiles(int64_t len) { return (len + kPTile - 1) / kPTile; }
+
+// Grid barrier with a bounded wait. Returns false if this block gave up.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long max_spins,
+                                          DevDiag* dg) {
+  __shared__ int gave_up;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gave_up = 0;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > max_spins) {
+          gave_up = 1;
+          atomicOr(&dg->flags, (unsigned)LP_FLAG_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return !gave_up;
+}
+
+#define LP_SYNC_OR_LEAVE()                                  \
+  do {                                                      \
+    if (!grid_sync(P.bar, P.max_spins, P.S.dg)) return;    \
+  } while (0)
+
+template <int PREC>
+__global__ void __launch_bounds__(kBlock) k_step_persistent(const PersistArgs P) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const int n = P.n;
+  const StepArgs& S = P.S;
+  if (P.rebuild) {
+    // cell counts and fill counters start at zero
+    for (int64_t i = tid; i < 2 * (P.ncell + 2); i += nth) {
+      if (i < P.ncell + 2) P.count[i] = 0u;
+      else P.fill[i - (P.ncell + 2)] = 0u;
+    }
+    LP_SYNC_OR_LEAVE();
+    for (int s = tid; s < n; s += nth)
+      keys_body(s, P.xs, P.ys, P.zs, P.colid_in, P.grids, (uint32_t)P.ncell, P.key, P.count);
+    LP_SYNC_OR_LEAVE();
+    // exclusive scan of ncell + 2 counts: tiles of kPTile, tile sums, add
+    {
+      __shared__ uint32_t tot;
+      const int64_t len = P.ncell + 2;
+      for (int tl = blockIdx.x; tl < P.ntiles; tl += gridDim.x) {
+        const int64_t base = (int64_t)tl * kPTile + (int64_t)threadIdx.x * kScanItems;
+        uint32_t v[kScanItems];
+        uint32_t t = 0;
+        for (int k = 0; k < kScanItems; ++k) {
+          v[k] = (base + k < len) ? P.count[base + k] : 0u;
+          t += v[k];
+        }
+        uint32_t ex = block_exclusive_scan(t, &tot);
+        for (int k = 0; k < kScanItems; ++k) {
+          if (base + k < len) P.start[base + k] = ex;
+          ex += v[k];
+        }
+        if (threadIdx.x == 0) P.tile[tl] = tot;
+      }
+      LP_SYNC_OR_LEAVE();
+      if (blockIdx.x == 0) {
+        uint32_t carry = 0;
+        for (int b = 0; b < P.ntiles; b += blockDim.x) {
+          const int i = b + threadIdx.x;
+          const uint32_t v = i < P.ntiles ? P.tile[i] : 0u;
+          const uint32_t ex = block_exclusive_scan(v, &tot);
+          if (i < P.ntiles) P.tile[i] = ex + carry;
+          carry += tot;
+          __syncthreads();
+        }
+      }
+      LP_SYNC_OR_LEAVE();
+      for (int tl = blockIdx.x; tl < P.ntiles; tl += gridDim.x) {
+        const int64_t base = (int64_t)tl * kPTile;
+        const uint32_t add = P.tile[tl];
+        for (int k = threadIdx.x; k < kPTile; k += blockDim.x)
+          if (base + k < len) P.start[base + k] += add;
+      }
+    }
+    LP_SYNC_OR_LEAVE();
+    for (int s = tid; s < n; s += nth) scatter_body(s, P.key, P.start, P.fill, P.tmp);
+    LP_SYNC_OR_LEAVE();
+    for (int64_t c = tid; c < P.ncell; c += nth) cell_sort_body(c, P.start, P.tmp, P.ids_in);
+    LP_SYNC_OR_LEAVE();
+    for (int t = tid; t < n; t += nth)
+      gather_body(t, P.tmp, P.src, P.dst, P.nsrc, P.ids_in, P.ids_out, P.colid_in, P.colid_out,
+                  P.grids, P.pf);
+    LP_SYNC_OR_LEAVE();
+    // every lane of a warp runs the same number of rounds (warp-wide reductions)
+    for (int base = 0; base < n; base += nth) {
+      const int s = base + tid;
+      neighbors_body<false>(s, s < n, n, S.x, S.y, S.z, P.pf, S.colid, P.ids_out, P.grids,
+                            P.start, nullptr, P.radius, P.mirror_mode, P.floor_z, P.cap, P.nbr,
+                            P.cnt, S.dg);
+    }
+  }
+  if (tid == 0) *S.fb_count = 0;
+  LP_SYNC_OR_LEAVE();
+  for (int s = tid; s < n; s += nth) pass1_body<PREC>(S, s);
+  LP_SYNC_OR_LEAVE();
+  const int nfb = min(*S.fb_count, S.fb_cap);
+  for (int t = tid; t < nfb; t += nth) pass1_fallback_item(S, t);
+  if (tid == 0 && nfb > 0) atomicAdd(&S.dg->n_fallback, (unsigned long long)nfb);
+  LP_SYNC_OR_LEAVE();
+  for (int t = tid; t < nfb; t += nth) pass2_fallback_item(S, t);
+  LP_SYNC_OR_LEAVE();
+  for (int base = 0; base < n; base += nth) {
+    const int s = base + tid;
+    pass2_body<PREC>(S, s, s < n);
+  }
+}
+
+// Largest co-resident grid for the persistent kernel (cached per precision).
+int persistent_blocks(int prec) {
+  static int cached[2] = {0, 0};
+  const int k = prec == LP_FP64 ? 0 : 1;
+  if (!cached[k]) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (prec == LP_FP64)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_persistent<LP_FP64>, kBlock, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_persistent<LP_MIXED>, kBlock, 0);
+    cached[k] = per > 0 ? per * sms : 0;
+  }
+  return cached[k];
+}
+
+cudaError_t launch_persistent(int prec, const PersistArgs& P, cudaStream_t st) {
+  const int nb = persistent_blocks(prec);
+  if (nb <= 0) return cudaErrorLaunchFailure;
+  void* args[] = {(void*)&P};
+  if (prec == LP_FP64)
+    return cudaLaunchCooperativeKernel((void*)k_step_persistent<LP_FP64>, dim3(nb), dim3(kBlock),
+                                       args, 0, st);
+  return cudaLaunchCooperativeKernel((void*)k_step_persistent<LP_MIXED>, dim3(nb), dim3(kBlock),
+                                     args, 0, st);
+}
+
+}  // namespace lp

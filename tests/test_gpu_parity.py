@@ -46,7 +46,7 @@ def _dicts(pd):
 def _prm(pd, **kw):
     q = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
              floor_z=pd["floor_z"], mirror_mode=pd["mirror_mode"], precision=0, rebuild_every=1,
-             use_graph=0)
+             launch_mode=0)
     q.update(kw)
     return q
 
@@ -274,10 +274,68 @@ def test_step_graph_replay_is_bitwise_identical(dev, capi):
     wl = W.cube(12)
     pd = W.param_dict(wl)
     s = torch.cuda.Stream()
-    a, _ = _run_gpu(capi, dev, wl, pd, 12, stream=s, use_graph=0)
-    b, _ = _run_gpu(capi, dev, wl, pd, 12, stream=s, use_graph=1)
+    a, _ = _run_gpu(capi, dev, wl, pd, 12, stream=s, launch_mode=0)
+    b, _ = _run_gpu(capi, dev, wl, pd, 12, stream=s, launch_mode=1)
     for k in a:
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_step_persistent_launch_is_bitwise_identical(dev, capi):
+    """One cooperative persistent launch per step (phases separated by a grid
+    barrier) gives exactly the per-phase kernels' result, for one column and
+    for a batch of columns."""
+    wl = W.cube(12)
+    pd = W.param_dict(wl)
+    a, _ = _run_gpu(capi, dev, wl, pd, 6, launch_mode=0)
+    b, d = _run_gpu(capi, dev, wl, pd, 6, launch_mode=2)
+    assert d["status"] == 0 and d["flags"] == 0
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    wc = W.columns(ncol=6, n_lo=300, n_hi=3000, only=list(range(6)))
+    pc = W.param_dict(wc)
+    mui_c = [dict(_dicts(pc)[0], mu_s=float(m)) for m in wc.mu_s_col]
+    for prec in (0, 1):
+        a, _ = _run_gpu(capi, dev, wc, pc, 5, prec=prec, offsets=wc.column_offsets, mui=mui_c,
+                        launch_mode=0, rebuild_every=2)
+        b, _ = _run_gpu(capi, dev, wc, pc, 5, prec=prec, offsets=wc.column_offsets, mui=mui_c,
+                        launch_mode=2, rebuild_every=2)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), (prec, k)
+
+
+def test_autotune_choices_and_table(dev, capi, tmp_path):
+    """The tuner returns valid block sizes and a launch mode, leaves the
+    caller's particles unchanged, and the chosen block sizes do not change a
+    single bit of the step (each particle's arithmetic is the same)."""
+    wc = W.columns(ncol=8, n_lo=500, n_hi=4000, only=list(range(8)))
+    pc = W.param_dict(wc)
+    mui_c = [dict(_dicts(pc)[0], mu_s=float(m)) for m in wc.mu_s_col]
+    m, eos = _dicts(pc)
+    ctx = capi.Context(wc.n, max_columns=8, cap=64)
+    st = {k: T(wc.state[k], dev) for k in capi.FIELDS}
+    table = str(tmp_path / "tuning.txt")
+    t1 = capi.lp_autotune(ctx, st, mui_c, eos, _prm(pc, precision=1), pc["dt"], 3,
+                          table_path=table, column_offsets=wc.column_offsets)
+    for k in ("block_neighbors", "block_pass1", "block_pass2"):
+        assert t1[k] in (64, 128, 256)
+    assert t1["launch_mode"] in (1, 2) and t1["ms_per_step"] > 0 and t1["from_table"] == 0
+    for k in capi.FIELDS:
+        assert np.array_equal(st[k].cpu().numpy(), wc.state[k]), k
+    t2 = capi.lp_autotune(ctx, st, mui_c, eos, _prm(pc, precision=1), pc["dt"], 3,
+                          table_path=table, column_offsets=wc.column_offsets)
+    assert t2["from_table"] == 1
+    for k in ("block_neighbors", "block_pass1", "block_pass2", "launch_mode"):
+        assert t2[k] == t1[k]
+    ref, _ = _run_gpu(capi, dev, wc, pc, 4, prec=1, offsets=wc.column_offsets, mui=mui_c)
+    for bs in (64, 256):
+        ctx2 = capi.Context(wc.n, max_columns=8, cap=64)
+        capi.lp_ctx_set_tuning(ctx2, bs, bs, bs)
+        s2 = {k: T(wc.state[k], dev) for k in capi.FIELDS}
+        capi.lp_step(ctx2, s2, mui_c, eos, _prm(pc, precision=1), pc["dt"], 4,
+                     column_offsets=wc.column_offsets)
+        ctx2.sync()
+        for k in capi.FIELDS:
+            assert np.array_equal(s2[k].cpu().numpy(), ref[k]), (bs, k)
 
 
 def test_step_rebuild_period_matches_oracle(dev, capi, orc):
@@ -337,7 +395,7 @@ def test_step_full_size_cylinder(dev, capi, orc):
     wl = W.cylinder()
     pd = W.param_dict(wl)
     ref, _ = orc.step(wl.state, orc.params(**pd), 3, brute=False)
-    got, d = _run_gpu(capi, dev, wl, pd, 3, use_graph=0)
+    got, d = _run_gpu(capi, dev, wl, pd, 3, launch_mode=0)
     e = _state_err(got, ref, wl.state)
     print("cylinder 3-step FP64 errors:", {k: f"{v:.2e}" for k, v in e.items()})
     assert max(e.values()) <= 1e-9, e
