@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--precision", choices=("mixed_ff", "mixed", "fp64"), default="mixed_ff")
     ap.add_argument("--restart-every", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -133,6 +133,11 @@ def _traffic(kernel_key: str):
     return t.get("bytes_per_launch_full")
 
 
+PREC = {"fp64": 0, "mixed": 1, "mixed_ff": 2}
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate
+FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+
+
 def pass1_flops(prec: str, rows: float, n: int) -> float:
     """Algorithmic FP64 flops of one pass-1 launch (FMA = 2 flops).
 
@@ -143,6 +148,11 @@ def pass1_flops(prec: str, rows: float, n: int) -> float:
     9 + 3 + 54 (residual) + 54 (A^T r) = 126; per particle about 550."""
     if prec == "fp64":
         return 131.0 * rows + 1000.0 * n
+    if prec == "mixed_ff":
+        # FP32 flops: per row 33 (float-float offsets) + 60 (quadratic terms) +
+        # 423 (31 moments) + 438 (3 right-hand sides) = 954; per particle about
+        # 11,500 (three solves with two float-float refinements per field)
+        return 954.0 * rows + 11500.0 * n
     return 126.0 * rows + 550.0 * n
 
 
@@ -173,7 +183,7 @@ def our_arm(args):
     def params(prec, graph=1):
         return dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
                     floor_z=0.0, mirror_mode=1,
-                    precision=capi.LP_MIXED if prec == "mixed" else capi.LP_FP64,
+                    precision=PREC[prec],
                     rebuild_every=1, launch_mode=graph)
 
     def run(nsteps, prec, graph=1):
@@ -232,18 +242,22 @@ def our_arm(args):
     peaks = _peaks()
     per_phase = {k: v / max(prof["steps"], 1) for k, v in prof["ms"].items()}
     dom = max(per_phase, key=per_phase.get)
-    fp64_peak_tflops = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)
+    ff = args.precision == "mixed_ff"
+    peak = FP32_PEAK_TFLOPS if ff else FP64_PEAK_TFLOPS
+    punit = "TFLOP/s (FP32)" if ff else "TFLOP/s (FP64)"
+    psrc = ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if ff
+            else "nominal FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)")
     roof = {"kernel": {"pass1": "k_pass1", "pass2": "k_pass2", "neighbors": "k_neighbors",
                        "sort": "sort kernels"}[dom]}
     if dom == "pass1":
         flops = pass1_flops(args.precision, mean_m * n, n)
         ach = flops / (per_phase["pass1"] / 1e3) / 1e12
-        roof.update(bound="alu", achieved=ach, peak=fp64_peak_tflops, unit="TFLOP/s (FP64)",
-                    frac=ach / fp64_peak_tflops, peak_source="nominal FP64 rate (fallback)",
+        roof.update(bound="alu", achieved=ach, peak=peak, unit=punit,
+                    frac=ach / peak, peak_source=psrc,
                     flops_per_launch=flops, ms_per_launch=per_phase["pass1"],
                     traffic=_traffic(f"k_pass1_{args.precision}"))
     else:
-        roof.update(bound="alu", achieved=None, peak=fp64_peak_tflops, unit="TFLOP/s (FP64)",
+        roof.update(bound="alu", achieved=None, peak=peak, unit=punit,
                     frac=None, ms_per_launch=per_phase[dom], traffic=None)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_ach = value / world * B_ALG / 1e9
@@ -252,7 +266,8 @@ def our_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "dtype": {"mixed_ff": "f32 (float-float) + f64", "mixed": "f32+f64"}.get(args.precision,
+                                                                                 "f64"),
         "data": "synthetic (seeded jittered lattice column)",
         "config": {
             "workload": "cylindrical column collapse R=0.02 m H=2R h=R/50 jitter 0.05h "
@@ -272,13 +287,16 @@ def our_arm(args):
                                       "min_stencil", "max_stencil")},
     }
 
-    if not args.no_fp64 and args.precision == "mixed":
-        ms64, _, _, d64, prof64, _ = bench("fp64")
-        ph64 = {k: v / max(prof64["steps"], 1) for k, v in prof64["ms"].items()}
-        v64 = n * args.steps * world / (ms64 / 1e3)
-        fl64 = pass1_flops("fp64", mean_m * n, n)
-        line["fp64"] = {"value": v64, "ms_per_step": ms64 / args.steps, "phase_ms_per_step": ph64,
-                        "pass1_tflops": fl64 / (ph64["pass1"] / 1e3) / 1e12}
+    if not args.no_fp64:
+        for other in ("fp64", "mixed"):
+            if other == args.precision:
+                continue
+            mso, _, _, _, profo, _ = bench(other)
+            pho = {k: v / max(profo["steps"], 1) for k, v in profo["ms"].items()}
+            flo = pass1_flops(other, mean_m * n, n)
+            line[other] = {"value": n * args.steps * world / (mso / 1e3),
+                           "ms_per_step": mso / args.steps, "phase_ms_per_step": pho,
+                           "pass1_fp64_tflops": flo / (pho["pass1"] / 1e3) / 1e12}
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world)
@@ -315,7 +333,7 @@ def batched(args, dev, stream):
     init = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
     st = {k: v.clone() for k, v in init.items()}
     prm = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
-               floor_z=0.0, mirror_mode=1, precision=capi.LP_MIXED, rebuild_every=1,
+               floor_z=0.0, mirror_mode=1, precision=PREC[args.precision], rebuild_every=1,
                launch_mode=capi.LP_LAUNCH_GRAPH)
     ctx = capi.Context(wl.n, max_columns=ncol, cap=64)
     tune = capi.lp_autotune(ctx, init, mui_c, eos, prm, pd["dt"], 3, column_offsets=offs,
@@ -358,7 +376,7 @@ def batched(args, dev, stream):
     ctx.sync(stream, raise_on_error=False)
     ctx.close()
     upd = wl.n * steps
-    return {"workload": f"{ncol} columns, {wl.n} particles, mixed precision, {steps} steps",
+    return {"workload": f"{ncol} columns, {wl.n} particles, {args.precision}, {steps} steps",
             "value": upd / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / steps,
             "launch": chosen, "tuning": tune,
             "graph_ms_per_step": modes["graph"] / steps,

@@ -53,6 +53,12 @@ typedef int32_t lp_status;
 /* arithmetic of the least-squares fits */
 #define LP_FP64 0  /* FP64 moments, Cholesky and solve (QR fallback in FP64)   */
 #define LP_MIXED 1 /* FP32 moments and Cholesky + one FP64 refinement step     */
+#define LP_MIXED_FF 2 /* FP32 only on the stencil rows: offsets, moments and   */
+                      /* right-hand sides accumulated as float-float (FP32     */
+                      /* pairs, error-free transformations), FP32 Cholesky and */
+                      /* two refinement steps on those normal equations; FP64  */
+                      /* per particle (derived values, closure, update) and in */
+                      /* the pivoted-QR fallback. lp_step only.                */
 
 /* floor mirror particles (Sec. 3.1 item 9) */
 #define LP_MIRROR_NONE 0

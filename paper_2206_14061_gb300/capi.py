@@ -26,6 +26,7 @@ LP_ERR_OOM = 6
 LP_ERR_UNIMPLEMENTED = 7
 LP_FP64 = 0
 LP_MIXED = 1
+LP_MIXED_FF = 2
 LP_MIRROR_NONE = 0
 LP_MIRROR_NOSLIP = 1
 LP_MIRROR_FREESLIP = 2

@@ -98,6 +98,8 @@ struct lp_ctx {
   double** d_ptr = nullptr;  // caller pointers for the final scatter
   double** h_ptr = nullptr;  // pinned staging of d_ptr
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
+  float4 *Xh = nullptr, *Xl = nullptr, *Uh = nullptr, *Ul = nullptr, *GVff = nullptr;
+  float* Gff = nullptr;      // float-float Gram matrices (LP_MIXED_FF)
   int cx = 0, ci = 0;
   int64_t ncell = 0;
   std::vector<GridCol> h_grids;
@@ -313,6 +315,8 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.fbslot = c->fbslot; A.fb_list = c->fb_list; A.fb_count = c->fb_count; A.fb_cap = c->fb_cap;
   A.p1 = c->p1; A.fbgrad = c->fbgrad; A.dg = c->dg;
   A.K = K;
+  A.grids = c->d_grids;
+  A.Xh = c->Xh; A.Xl = c->Xl; A.Uh = c->Uh; A.Ul = c->Ul; A.GVff = c->GVff; A.Gff = c->Gff;
   return A;
 }
 
@@ -338,7 +342,7 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
   phase_mark(c, LP_PHASE_PASS2, true, st);
   launch_pass2(prec, A, st, c->bs_p2);
   phase_mark(c, LP_PHASE_PASS2, false, st);
-  c->launches += 4;
+  c->launches += prec == LP_MIXED_FF ? 6 : 4;
   c->steps += 1;
   c->cx ^= 1;
 }
@@ -438,7 +442,8 @@ bool valid_params(const lp_params* q, const lp_eos* e, double dt) {
   if (!q || !e) return false;
   if (!finite_pos(q->h) || !finite_pos(q->radius) || !std::isfinite(dt) || dt < 0) return false;
   if (q->mirror_mode < 0 || q->mirror_mode > 2) return false;
-  if (q->precision != LP_FP64 && q->precision != LP_MIXED) return false;
+  if (q->precision != LP_FP64 && q->precision != LP_MIXED && q->precision != LP_MIXED_FF)
+    return false;
   if (q->rebuild_every < 1) return false;
   if (q->launch_mode < LP_LAUNCH_KERNELS || q->launch_mode > LP_LAUNCH_PERSISTENT) return false;
   if (!(e->phi_min < e->phi_max && e->phi_max < e->phi_c)) return false;
@@ -510,6 +515,12 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->d_tab, 2 * 2 * 2 * kTabFields);
   if (s == LP_OK) s = dalloc(c, &c->d_ptr, kTabFields);
   if (s == LP_OK) s = dalloc(c, &c->bar, 2);
+  if (s == LP_OK) s = dalloc(c, &c->Xh, n);
+  if (s == LP_OK) s = dalloc(c, &c->Xl, n);
+  if (s == LP_OK) s = dalloc(c, &c->Uh, n);
+  if (s == LP_OK) s = dalloc(c, &c->Ul, n);
+  if (s == LP_OK) s = dalloc(c, &c->GVff, n);
+  if (s == LP_OK) s = dalloc(c, &c->Gff, n * 2 * kTri);
   if (s == LP_OK && cudaMemset(c->bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) s = LP_ERR_CUDA;
   if (s == LP_OK) s = ensure_cells(c, 1 << 16);
   if (s == LP_OK) {

@@ -49,6 +49,16 @@ __global__ void __launch_bounds__(64) k_pass2_fallback(const StepArgs A) {
     pass2_fallback_item(A, t);
 }
 
+__global__ void k_split_state(const StepArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) split_state_body(A, s);
+}
+
+__global__ void k_split_p1(const StepArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) split_p1_body(A, s);
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kMaxBlock) k_pass2(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,15 +255,23 @@ __global__ void k_mui_stress(int64_t n, ColMui mui, double phi_c, double phi_min
 
 void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs) {
   const int nb = (A.n + bs - 1) / bs;
-  if (prec == LP_FP64) k_pass1<LP_FP64><<<nb, bs, 0, st>>>(A);
-  else k_pass1<LP_MIXED><<<nb, bs, 0, st>>>(A);
+  if (prec == LP_FP64) {
+    k_pass1<LP_FP64><<<nb, bs, 0, st>>>(A);
+  } else if (prec == LP_MIXED) {
+    k_pass1<LP_MIXED><<<nb, bs, 0, st>>>(A);
+  } else {
+    k_split_state<<<(A.n + 255) / 256, 256, 0, st>>>(A);
+    k_pass1<LP_MIXED_FF><<<nb, bs, 0, st>>>(A);
+  }
   k_pass1_fallback<<<152, 64, 0, st>>>(A);
 }
 void launch_pass2(int prec, const StepArgs& A, cudaStream_t st, int bs) {
+  if (prec == LP_MIXED_FF) k_split_p1<<<(A.n + 255) / 256, 256, 0, st>>>(A);
   k_pass2_fallback<<<152, 64, 0, st>>>(A);
   const int nb = (A.n + bs - 1) / bs;
   if (prec == LP_FP64) k_pass2<LP_FP64><<<nb, bs, 0, st>>>(A);
-  else k_pass2<LP_MIXED><<<nb, bs, 0, st>>>(A);
+  else if (prec == LP_MIXED) k_pass2<LP_MIXED><<<nb, bs, 0, st>>>(A);
+  else k_pass2<LP_MIXED_FF><<<nb, bs, 0, st>>>(A);
 }
 void launch_fit(int prec, const FitArgs& F, cudaStream_t st) {
   const int nb = (F.n + kBlock - 1) / kBlock;

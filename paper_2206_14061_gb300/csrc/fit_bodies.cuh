@@ -61,8 +61,14 @@ __device__ __forceinline__ void push_fallback(const StepArgs& A, int s) {
 
 // ------------------------------------------------------------ pass 1
 
+__device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s);
+
 template <int PREC>
 __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
+  if (PREC == LP_MIXED_FF) {
+    pass1_ff_body(A, s);
+    return;
+  }
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);
   const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
@@ -257,6 +263,249 @@ static __device__ __noinline__ void pass2_fallback_item(const StepArgs& A, int t
   }
 }
 
+// ------------------------------------------------------ float-float mode
+// LP_MIXED_FF: nothing on a stencil row touches the FP64 pipe. Positions are
+// scaled and split once per particle and step (X = (x - origin)/h as hi + lo
+// floats, with the floor-mirror height in w), velocities likewise; each row's
+// offsets, Taylor terms, the 31 moments and the right-hand sides are carried as
+// float-float. The normal equations G c = A^T b are then solved with an FP32
+// Cholesky factor of hi(G) and refined twice on the float-float G and A^T b.
+
+// scaled, split positions and velocities of the current state
+__device__ __forceinline__ void split_state_body(const StepArgs& A, int s) {
+  const GridCol g = A.grids[A.colid[s]];
+  const double ih = A.K.inv_h;
+  const ff fx = ff_of((A.x[s] - g.ox) * ih), fy = ff_of((A.y[s] - g.oy) * ih);
+  const ff fz = ff_of((A.z[s] - g.oz) * ih);
+  const ff fm = ff_of((2.0 * A.K.floor_z - A.z[s] - g.oz) * ih);
+  A.Xh[s] = make_float4(fx.h, fy.h, fz.h, fm.h);
+  A.Xl[s] = make_float4(fx.l, fy.l, fz.l, fm.l);
+  const ff fu = ff_of(A.u[s]), fv = ff_of(A.v[s]), fw = ff_of(A.w[s]);
+  A.Uh[s] = make_float4(fu.h, fv.h, fw.h, 0.f);
+  A.Ul[s] = make_float4(fu.l, fv.l, fw.l, 0.f);
+}
+
+// split |gdot|^n and V^{n+1} (pass-1 outputs, FP64) for pass 2
+__device__ __forceinline__ void split_p1_body(const StepArgs& A, int s) {
+  const ff g = ff_of(A.p1[P1_GN * A.n + s]), v = ff_of(A.p1[P1_VN * A.n + s]);
+  A.GVff[s] = make_float4(g.h, g.l, v.h, v.l);
+}
+
+// float-float offset between two split coordinates
+__device__ __forceinline__ ff ff_diff(float jh, float jl, float ih_, float il) {
+  const ff d = two_sum(jh, -ih_);
+  return fast_two_sum(d.h, __fadd_rn(d.l, __fsub_rn(jl, il)));
+}
+
+// Taylor row of a float-float offset and its quadratic terms
+struct FFRow {
+  ff dx, dy, dz, qxx, qyy, qzz, qxy, qxz, qyz;
+};
+__device__ __forceinline__ FFRow ff_row(const StepArgs& A, int s, const float4& hi,
+                                        const float4& lo, uint32_t code) {
+  const int j = code & ~kMirrorBit;
+  const bool mir = code >> 31;
+  const float4 jh = A.Xh[j], jl = A.Xl[j];
+  FFRow r;
+  r.dx = ff_diff(jh.x, jl.x, hi.x, lo.x);
+  r.dy = ff_diff(jh.y, jl.y, hi.y, lo.y);
+  r.dz = mir ? ff_diff(jh.w, jl.w, hi.z, lo.z) : ff_diff(jh.z, jl.z, hi.z, lo.z);
+  r.qxx = ff_mul(r.dx, r.dx); r.qyy = ff_mul(r.dy, r.dy); r.qzz = ff_mul(r.dz, r.dz);
+  r.qxy = ff_mul(r.dx, r.dy); r.qxz = ff_mul(r.dx, r.dz); r.qyz = ff_mul(r.dy, r.dz);
+  return r;
+}
+__device__ __forceinline__ void ff_taylor(const FFRow& r, ff* a) {
+  a[0] = r.dx; a[1] = r.dy; a[2] = r.dz;
+  a[3] = ff_scale(r.qxx, 0.5f); a[4] = ff_scale(r.qyy, 0.5f); a[5] = ff_scale(r.qzz, 0.5f);
+  a[6] = r.qxy; a[7] = r.qxz; a[8] = r.qyz;
+}
+
+// the 31 distinct Gram moments: deg 2 (0..5), deg 3 (6..15), deg 4 (16..30)
+__device__ __forceinline__ void ff_moments_add(ff* mo, const FFRow& r) {
+  ff_acc1(mo[0], r.qxx); ff_acc1(mo[1], r.qyy); ff_acc1(mo[2], r.qzz);
+  ff_acc1(mo[3], r.qxy); ff_acc1(mo[4], r.qxz); ff_acc1(mo[5], r.qyz);
+  ff_acc(mo[6], r.dx, r.qxx);  ff_acc(mo[7], r.dy, r.qyy);  ff_acc(mo[8], r.dz, r.qzz);
+  ff_acc(mo[9], r.dy, r.qxx);  ff_acc(mo[10], r.dz, r.qxx); ff_acc(mo[11], r.dx, r.qyy);
+  ff_acc(mo[12], r.dz, r.qyy); ff_acc(mo[13], r.dx, r.qzz); ff_acc(mo[14], r.dy, r.qzz);
+  ff_acc(mo[15], r.dz, r.qxy);
+  ff_acc(mo[16], r.qxx, r.qxx); ff_acc(mo[17], r.qyy, r.qyy); ff_acc(mo[18], r.qzz, r.qzz);
+  ff_acc(mo[19], r.qxx, r.qxy); ff_acc(mo[20], r.qxx, r.qxz); ff_acc(mo[21], r.qyy, r.qxy);
+  ff_acc(mo[22], r.qyy, r.qyz); ff_acc(mo[23], r.qzz, r.qxz); ff_acc(mo[24], r.qzz, r.qyz);
+  ff_acc(mo[25], r.qxx, r.qyy); ff_acc(mo[26], r.qxx, r.qzz); ff_acc(mo[27], r.qyy, r.qzz);
+  ff_acc(mo[28], r.qxx, r.qyz); ff_acc(mo[29], r.qyy, r.qxz); ff_acc(mo[30], r.qzz, r.qxy);
+}
+
+// packed Gram matrix from the moments (same entries as Moments::gram)
+__device__ __forceinline__ void ff_gram(const ff* mo, ff* g) {
+  const float h = 0.5f, q = 0.25f;
+  g[tri(0, 0)] = mo[0];
+  g[tri(1, 0)] = mo[3];               g[tri(1, 1)] = mo[1];
+  g[tri(2, 0)] = mo[4];               g[tri(2, 1)] = mo[5];               g[tri(2, 2)] = mo[2];
+  g[tri(3, 0)] = ff_scale(mo[6], h);  g[tri(3, 1)] = ff_scale(mo[9], h);  g[tri(3, 2)] = ff_scale(mo[10], h);
+  g[tri(3, 3)] = ff_scale(mo[16], q);
+  g[tri(4, 0)] = ff_scale(mo[11], h); g[tri(4, 1)] = ff_scale(mo[7], h);  g[tri(4, 2)] = ff_scale(mo[12], h);
+  g[tri(4, 3)] = ff_scale(mo[25], q); g[tri(4, 4)] = ff_scale(mo[17], q);
+  g[tri(5, 0)] = ff_scale(mo[13], h); g[tri(5, 1)] = ff_scale(mo[14], h); g[tri(5, 2)] = ff_scale(mo[8], h);
+  g[tri(5, 3)] = ff_scale(mo[26], q); g[tri(5, 4)] = ff_scale(mo[27], q); g[tri(5, 5)] = ff_scale(mo[18], q);
+  g[tri(6, 0)] = mo[9];               g[tri(6, 1)] = mo[11];              g[tri(6, 2)] = mo[15];
+  g[tri(6, 3)] = ff_scale(mo[19], h); g[tri(6, 4)] = ff_scale(mo[21], h); g[tri(6, 5)] = ff_scale(mo[30], h);
+  g[tri(6, 6)] = mo[25];
+  g[tri(7, 0)] = mo[10];              g[tri(7, 1)] = mo[15];              g[tri(7, 2)] = mo[13];
+  g[tri(7, 3)] = ff_scale(mo[20], h); g[tri(7, 4)] = ff_scale(mo[29], h); g[tri(7, 5)] = ff_scale(mo[23], h);
+  g[tri(7, 6)] = mo[28];              g[tri(7, 7)] = mo[26];
+  g[tri(8, 0)] = mo[15];              g[tri(8, 1)] = mo[12];              g[tri(8, 2)] = mo[14];
+  g[tri(8, 3)] = ff_scale(mo[28], h); g[tri(8, 4)] = ff_scale(mo[22], h); g[tri(8, 5)] = ff_scale(mo[24], h);
+  g[tri(8, 6)] = mo[29];              g[tri(8, 7)] = mo[30];              g[tri(8, 8)] = mo[27];
+}
+
+// Solve G c = r: FP32 Cholesky solve, then two refinement steps with the
+// float-float residual r - G c. Returns c as doubles.
+__device__ __forceinline__ void ff_refined_solve(const ff* G, const float* L, const ff* r,
+                                                 double* c_out) {
+  ff c[kNB];
+#pragma unroll
+  for (int q = 0; q < kNB; ++q) c[q] = {0.f, 0.f};
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    float d[kNB];
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+      ff g = r[q];
+      if (it > 0) {
+#pragma unroll
+        for (int p = 0; p < kNB; ++p) {
+          const ff Gqp = q >= p ? G[tri(q, p)] : G[tri(p, q)];
+          ff_acc(g, Gqp, ff{-c[p].h, -c[p].l});
+        }
+      }
+      d[q] = __fadd_rn(g.h, g.l);
+    }
+    chol9_solve(L, d);
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) c[q] = ff_add(c[q], ff{d[q], 0.f});
+  }
+#pragma unroll
+  for (int q = 0; q < kNB; ++q) c_out[q] = ff_to_double(c[q]);
+}
+
+__device__ __forceinline__ void pass1_finish(const StepArgs& A, int s, const double (*c)[kNB]);
+__device__ __forceinline__ void push_fallback(const StepArgs& A, int s);
+
+// pass 1 in float-float: fits of u, v, w
+__device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
+  const int n = A.n;
+  const int m = min(A.cnt[s], A.cap);
+  const float4 hi = A.Xh[s], lo = A.Xl[s];
+  const float4 uh = A.Uh[s], ul = A.Ul[s];
+  const int mm = A.K.mirror_mode;
+  const float sg[3] = {mm == LP_MIRROR_NOSLIP ? -1.f : 1.f, mm == LP_MIRROR_NOSLIP ? -1.f : 1.f,
+                       mm != LP_MIRROR_NONE ? -1.f : 1.f};
+  ff mo[31], R[3][kNB];
+#pragma unroll
+  for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+  for (int k = 0; k < m; ++k) {
+    const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
+    const FFRow r = ff_row(A, s, hi, lo, code);
+    ff_moments_add(mo, r);
+    ff a[kNB];
+    ff_taylor(r, a);
+    const int j = code & ~kMirrorBit;
+    const bool mir = code >> 31;
+    const float4 jh = A.Uh[j], jl = A.Ul[j];
+    const float ujh[3] = {jh.x, jh.y, jh.z}, ujl[3] = {jl.x, jl.y, jl.z};
+    const float uih[3] = {uh.x, uh.y, uh.z}, uil[3] = {ul.x, ul.y, ul.z};
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const float sj = mir ? sg[f] : 1.f;
+      const ff b = ff_diff(sj * ujh[f], sj * ujl[f], uih[f], uil[f]);
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) ff_acc(R[f][q], b, a[q]);
+    }
+  }
+  ff G[kTri];
+  ff_gram(mo, G);
+  float L[kTri];
+#pragma unroll
+  for (int k = 0; k < kTri; ++k) {
+    G[k] = ff_norm(G[k]);
+    L[k] = G[k].h;
+  }
+  const bool ok = chol9(L, 1e-4f) && m >= kNB;
+  if (!ok) {
+    push_fallback(A, s);
+    return;
+  }
+  A.fbslot[s] = -1;
+#pragma unroll
+  for (int k = 0; k < kTri; ++k) {
+    A.Gff[(int64_t)k * n + s] = G[k].h;
+    A.Gff[(int64_t)(kTri + k) * n + s] = G[k].l;
+  }
+  double c[3][kNB];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    ff r[kNB];
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) r[q] = ff_norm(R[f][q]);
+    ff_refined_solve(G, L, r, c[f]);
+  }
+  pass1_finish(A, s, c);
+}
+
+// pass-2 fits in float-float: gradients of |gdot|^n and V^{n+1}
+__device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, double* gg,
+                                               double* gV) {
+  const int n = A.n;
+  const float4 hi = A.Xh[s], lo = A.Xl[s];
+  const float4 gvi = A.GVff[s];
+  ff R[2][kNB];
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+  for (int k = 0; k < m; ++k) {
+    const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
+    const FFRow r = ff_row(A, s, hi, lo, code);
+    ff a[kNB];
+    ff_taylor(r, a);
+    const int j = code & ~kMirrorBit;
+    const bool mir = code >> 31;
+    const float4 gvj = A.GVff[j];
+    const ff bg = mir ? ff{-gvi.x, -gvi.y} : ff_diff(gvj.x, gvj.y, gvi.x, gvi.y);
+    const ff bv = ff_diff(gvj.z, gvj.w, gvi.z, gvi.w);
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+      ff_acc(R[0][q], bg, a[q]);
+      ff_acc(R[1][q], bv, a[q]);
+    }
+  }
+  ff G[kTri];
+  float L[kTri];
+#pragma unroll
+  for (int k = 0; k < kTri; ++k) {
+    G[k] = {A.Gff[(int64_t)k * n + s], A.Gff[(int64_t)(kTri + k) * n + s]};
+    L[k] = G[k].h;
+  }
+  chol9(L, 0.f);  // succeeded in pass 1 on the same matrix
+  const double ih = A.K.inv_h;
+  double c[kNB];
+  ff r[kNB];
+#pragma unroll
+  for (int q = 0; q < kNB; ++q) r[q] = ff_norm(R[0][q]);
+  ff_refined_solve(G, L, r, c);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) gg[q] = c[q] * ih;
+#pragma unroll
+  for (int q = 0; q < kNB; ++q) r[q] = ff_norm(R[1][q]);
+  ff_refined_solve(G, L, r, c);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) gV[q] = c[q] * ih;
+}
+
 // ------------------------------------------------------------ pass 2
 
 // every lane of the warp must call it (live or not)
@@ -281,7 +530,9 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
       }
     } else if (slot == -1) {
       const int m = min(A.cnt[s], A.cap);
-      if (PREC == LP_FP64) {
+      if (PREC == LP_MIXED_FF) {
+        pass2_ff_grads(A, s, m, gg, gV);
+      } else if (PREC == LP_FP64) {
         double R[2][kNB];
 #pragma unroll
         for (int f = 0; f < 2; ++f)

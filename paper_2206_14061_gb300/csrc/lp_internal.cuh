@@ -56,6 +56,60 @@ struct DevDiag {
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
+// ------------------------------------------------------------ float-float
+// Unevaluated sums hi + lo of two floats (about 48 significant bits), built
+// from the error-free transformations TwoSum (Knuth) and TwoProduct (an FMA
+// gives the exact rounding error of a product). The _rn intrinsics keep the
+// compiler from contracting or reordering these steps.
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, {-b.h, -b.l}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_scale(ff a, float s) { return {a.h * s, a.l * s}; }  // s = 2^k
+// acc += a b, keeping acc unnormalised (lo collects all low-order terms)
+__device__ __forceinline__ void ff_acc(ff& acc, ff a, ff b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const ff s = two_sum(acc.h, p);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
+}
+// acc += a
+__device__ __forceinline__ void ff_acc1(ff& acc, ff a) {
+  const ff s = two_sum(acc.h, a.h);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, a.l));
+}
+__device__ __forceinline__ ff ff_norm(ff a) { return fast_two_sum(a.h, a.l); }
+__device__ __forceinline__ ff ff_of(double d) {
+  const float h = __double2float_rn(d);
+  return {h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.h + (double)a.l; }
+
 // clamped cell coordinate; NaN maps to 0 (fmax returns the non-NaN operand)
 __device__ __forceinline__ int cell_coord(double p, double o, double inv_c, int n) {
   double t = (p - o) * inv_c;
@@ -94,6 +148,12 @@ struct StepArgs {
   StepConsts K;
   double* coef1;    // optional (FP64 only): pass-1 coefficients, 27 * n (k-major)
   double* coef2;    // optional (FP64 only): pass-2 coefficients of |gdot|, V^{n+1}, 18 * n
+  // float-float mode (LP_MIXED_FF): scaled positions X = (x - origin)/h split
+  // into hi and lo floats (w = mirror height), velocities split likewise,
+  // |gdot| and V^{n+1} split (hi, lo, hi, lo), Gram matrices in float-float
+  const GridCol* grids;
+  float4 *Xh, *Xl, *Uh, *Ul, *GVff;
+  float* Gff;       // 90 * n: hi (45) then lo (45), k-major
 };
 
 struct FitArgs {

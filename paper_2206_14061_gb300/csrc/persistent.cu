@@ -127,6 +127,8 @@ __global__ void __launch_bounds__(kBlock) k_step_persistent(const PersistArgs P)
     }
   }
   if (tid == 0) *S.fb_count = 0;
+  if (PREC == LP_MIXED_FF)
+    for (int s = tid; s < n; s += nth) split_state_body(S, s);
   LP_SYNC_OR_LEAVE();
   for (int s = tid; s < n; s += nth) pass1_body<PREC>(S, s);
   LP_SYNC_OR_LEAVE();
@@ -134,6 +136,10 @@ __global__ void __launch_bounds__(kBlock) k_step_persistent(const PersistArgs P)
   for (int t = tid; t < nfb; t += nth) pass1_fallback_item(S, t);
   if (tid == 0 && nfb > 0) atomicAdd(&S.dg->n_fallback, (unsigned long long)nfb);
   LP_SYNC_OR_LEAVE();
+  if (PREC == LP_MIXED_FF) {
+    for (int s = tid; s < n; s += nth) split_p1_body(S, s);
+    LP_SYNC_OR_LEAVE();
+  }
   for (int t = tid; t < nfb; t += nth) pass2_fallback_item(S, t);
   LP_SYNC_OR_LEAVE();
   for (int base = 0; base < n; base += nth) {
@@ -143,19 +149,21 @@ __global__ void __launch_bounds__(kBlock) k_step_persistent(const PersistArgs P)
 }
 
 // Largest co-resident grid for the persistent kernel (cached per precision).
+template <int PREC>
+int blocks_of() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_persistent<PREC>, kBlock, 0);
+  return per > 0 ? per * sms : 0;
+}
+
 int persistent_blocks(int prec) {
-  static int cached[2] = {0, 0};
-  const int k = prec == LP_FP64 ? 0 : 1;
-  if (!cached[k]) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (prec == LP_FP64)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_persistent<LP_FP64>, kBlock, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_persistent<LP_MIXED>, kBlock, 0);
-    cached[k] = per > 0 ? per * sms : 0;
-  }
+  static int cached[3] = {0, 0, 0};
+  const int k = prec < 0 || prec > 2 ? 0 : prec;
+  if (!cached[k])
+    cached[k] = prec == LP_FP64 ? blocks_of<LP_FP64>()
+                                : (prec == LP_MIXED ? blocks_of<LP_MIXED>() : blocks_of<LP_MIXED_FF>());
   return cached[k];
 }
 
@@ -163,11 +171,10 @@ cudaError_t launch_persistent(int prec, const PersistArgs& P, cudaStream_t st) {
   const int nb = persistent_blocks(prec);
   if (nb <= 0) return cudaErrorLaunchFailure;
   void* args[] = {(void*)&P};
-  if (prec == LP_FP64)
-    return cudaLaunchCooperativeKernel((void*)k_step_persistent<LP_FP64>, dim3(nb), dim3(kBlock),
-                                       args, 0, st);
-  return cudaLaunchCooperativeKernel((void*)k_step_persistent<LP_MIXED>, dim3(nb), dim3(kBlock),
-                                     args, 0, st);
+  void* fn = prec == LP_FP64 ? (void*)k_step_persistent<LP_FP64>
+             : prec == LP_MIXED ? (void*)k_step_persistent<LP_MIXED>
+                                : (void*)k_step_persistent<LP_MIXED_FF>;
+  return cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kBlock), args, 0, st);
 }
 
 }  // namespace lp

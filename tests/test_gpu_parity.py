@@ -270,6 +270,18 @@ def test_step_mixed_error_bound(dev, capi, orc):
     assert max(e.values()) <= 1e-6, e
 
 
+def test_step_mixed_ff_error_bound(dev, capi, orc):
+    """Float-float mode (no FP64 on stencil rows) against the FP64 oracle."""
+    wl = W.cube(20)
+    pd = W.param_dict(wl)
+    ref, _ = orc.step(wl.state, orc.params(**pd), 50, brute=False)
+    got, d = _run_gpu(capi, dev, wl, pd, 50, prec=2)
+    e = _state_err(got, ref, wl.state)
+    print("MIXED_FF 50-step errors:", {k: f"{v:.2e}" for k, v in e.items()})
+    assert max(e.values()) <= 1e-8, e
+    assert d["n_nonfinite"] == 0
+
+
 def test_step_graph_replay_is_bitwise_identical(dev, capi):
     wl = W.cube(12)
     pd = W.param_dict(wl)
@@ -294,7 +306,7 @@ def test_step_persistent_launch_is_bitwise_identical(dev, capi):
     wc = W.columns(ncol=6, n_lo=300, n_hi=3000, only=list(range(6)))
     pc = W.param_dict(wc)
     mui_c = [dict(_dicts(pc)[0], mu_s=float(m)) for m in wc.mu_s_col]
-    for prec in (0, 1):
+    for prec in (0, 1, 2):
         a, _ = _run_gpu(capi, dev, wc, pc, 5, prec=prec, offsets=wc.column_offsets, mui=mui_c,
                         launch_mode=0, rebuild_every=2)
         b, _ = _run_gpu(capi, dev, wc, pc, 5, prec=prec, offsets=wc.column_offsets, mui=mui_c,
@@ -403,3 +415,7 @@ def test_step_full_size_cylinder(dev, capi, orc):
     em = _state_err(gotm, ref, wl.state)
     print("cylinder 3-step MIXED errors:", {k: f"{v:.2e}" for k, v in em.items()})
     assert max(em.values()) <= 1e-6, em
+    gotf, _ = _run_gpu(capi, dev, wl, pd, 3, prec=2)
+    ef = _state_err(gotf, ref, wl.state)
+    print("cylinder 3-step MIXED_FF errors:", {k: f"{v:.2e}" for k, v in ef.items()})
+    assert max(ef.values()) <= 1e-8, ef
