@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("mixed_ff", "mixed", "fp64"), default="mixed_ff")
     ap.add_argument("--restart-every", type=int, default=10)
+    ap.add_argument("--skin", type=float, default=0.1,
+                    help="Verlet skin in lattice spacings (0: full search every step)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
@@ -184,7 +186,7 @@ def our_arm(args):
         return dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
                     floor_z=0.0, mirror_mode=1,
                     precision=PREC[prec],
-                    rebuild_every=1, launch_mode=graph)
+                    rebuild_every=1, launch_mode=graph, skin=args.skin * pd["h"])
 
     def run(nsteps, prec, graph=1):
         done = 0
@@ -274,6 +276,7 @@ def our_arm(args):
                         f"({n} particles), mu_s 0.38 mu_2 0.64 I0 0.28 d 5e-4 rho 2500, "
                         "dt 1e-5, stencil radius 2.2h, no-slip floor mirrors",
             "precision": args.precision, "graph": True, "restart_every": R,
+            "verlet_skin_h": args.skin,
             "mean_stencil": mean_m, "parallelism": f"replicas x{world}",
             "l2": "per-step working set (state, stencils, factors) is larger than L2",
         },
@@ -334,7 +337,7 @@ def batched(args, dev, stream):
     st = {k: v.clone() for k, v in init.items()}
     prm = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
                floor_z=0.0, mirror_mode=1, precision=PREC[args.precision], rebuild_every=1,
-               launch_mode=capi.LP_LAUNCH_GRAPH)
+               launch_mode=capi.LP_LAUNCH_GRAPH, skin=args.skin * pd["h"])
     ctx = capi.Context(wl.n, max_columns=ncol, cap=64)
     tune = capi.lp_autotune(ctx, init, mui_c, eos, prm, pd["dt"], 3, column_offsets=offs,
                             stream=stream)

@@ -130,6 +130,13 @@ typedef struct {
   int32_t precision;     /* LP_FP64 or LP_MIXED                                 */
   int32_t rebuild_every; /* rebuild stencils every k steps (1 = every step)     */
   int32_t launch_mode;   /* LP_LAUNCH_*                                         */
+  double skin;           /* > 0 (with rebuild_every == 1): Verlet candidate lists.
+                          * A full search collects all neighbours within
+                          * radius + skin; every step filters them with the exact
+                          * radius test (same stencils as a full search); a new
+                          * search runs once some particle has moved more than
+                          * skin/2 since the last one. 0: full search every step.
+                          * Not used by LP_LAUNCH_PERSISTENT.                      */
 } lp_params;
 
 /* Stencils produced by lp_build_neighbors: library-owned device memory, valid
@@ -172,6 +179,15 @@ lp_status lp_ctx_destroy(lp_ctx* ctx);
  * LP_ERR_STENCIL_OVERFLOW, non-finite -> LP_ERR_NONFINITE, timeout ->
  * LP_ERR_TIMEOUT) or LP_OK. Synchronises. */
 lp_status lp_ctx_sync(lp_ctx* ctx, void* stream, lp_diag* diag);
+
+/* Bounded waits of the persistent launch (failure detection, not in the
+ * paper). Every grid barrier of LP_LAUNCH_PERSISTENT spins at most max_spins
+ * rounds of __nanosleep(64) (default 2^25, about 2 s), then sets
+ * LP_FLAG_TIMEOUT and leaves the kernel; lp_ctx_sync then returns
+ * LP_ERR_TIMEOUT and the context stays usable. extra_arrivals > 0 makes each
+ * barrier wait for that many blocks that do not exist, so the wait runs out:
+ * a test aid only (0 restores normal operation). */
+lp_status lp_ctx_set_wait_limit(lp_ctx* ctx, int64_t max_spins, int32_t extra_arrivals);
 
 /* Per-phase timing (profiling aid, not in the paper). While enabled, lp_step
  * records a CUDA event pair around each phase of every step and does not use

@@ -60,7 +60,8 @@ class LpEos(ctypes.Structure):
 
 class LpParams(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("h", "radius", "gx", "gy", "gz", "floor_z")] + [
-        (k, ctypes.c_int32) for k in ("mirror_mode", "precision", "rebuild_every", "launch_mode")]
+        (k, ctypes.c_int32) for k in ("mirror_mode", "precision", "rebuild_every", "launch_mode")] + [
+        ("skin", ctypes.c_double)]
 
 
 class LpNeighbors(ctypes.Structure):
@@ -100,6 +101,7 @@ _SIGS = {
     "lp_ctx_destroy": ([_vp], ctypes.c_int32),
     "lp_ctx_sync": ([_vp, _vp, _P(LpDiag)], ctypes.c_int32),
     "lp_ctx_profile": ([_vp, ctypes.c_int32], ctypes.c_int32),
+    "lp_ctx_set_wait_limit": ([_vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int32),
     "lp_ctx_phase_times": ([_vp, _vp, _P(ctypes.c_double), _P(ctypes.c_int64),
                             _P(ctypes.c_int64)], ctypes.c_int32),
     "lp_ctx_set_tuning": ([_vp, _P(LpTuning)], ctypes.c_int32),
@@ -208,7 +210,7 @@ def params_struct(q) -> LpParams:
     return LpParams(float(q["h"]), float(q["radius"]), float(q["gx"]), float(q["gy"]),
                     float(q["gz"]), float(q.get("floor_z", 0.0)), int(q.get("mirror_mode", 1)),
                     int(q.get("precision", LP_FP64)), int(q.get("rebuild_every", 1)),
-                    int(q.get("launch_mode", LP_LAUNCH_KERNELS)))
+                    int(q.get("launch_mode", LP_LAUNCH_KERNELS)), float(q.get("skin", 0.0)))
 
 
 class Context:
@@ -234,6 +236,10 @@ class Context:
         if raise_on_error:
             _check(st, "lp_ctx_sync")
         return out
+
+    def set_wait_limit(self, max_spins: int = 1 << 25, extra_arrivals: int = 0):
+        _check(lib().lp_ctx_set_wait_limit(self.handle, int(max_spins), int(extra_arrivals)),
+               "lp_ctx_set_wait_limit")
 
     def profile(self, enable: bool = True):
         _check(lib().lp_ctx_profile(self.handle, int(bool(enable))), "lp_ctx_profile")

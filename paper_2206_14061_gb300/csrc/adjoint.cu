@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_prepare(const AdjArgs A) {
       for (int k = 0; k < m; ++k) {
         const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
         const int j = code & ~kMirrorBit;
+        if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
         const double zj = (code >> 31) ? f2 - A.z[j] : A.z[j];
         M.add((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih);
       }
@@ -254,6 +255,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
     const int j = code & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
     const double zj = mir ? f2 - A.z[j] : A.z[j];
     const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass1(const AdjArgs A) {
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
     const int j = code & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
     const double zj = mir ? f2 - A.z[j] : A.z[j];
     const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
@@ -385,6 +388,7 @@ __global__ void k_gather_fields(int n, const int32_t* __restrict__ idx,
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int o = idx[s];
+  if ((unsigned)o >= (unsigned)n) return;
   for (int f = 0; f < nf; ++f) dst[f][s] = src[f][o];
 }
 

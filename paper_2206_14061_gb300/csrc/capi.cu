@@ -17,22 +17,28 @@ void launch_bbox(int n, int ncol, const double* x, const double* y, const double
                  cudaStream_t st);
 void launch_keys(int n, const double* x, const double* y, const double* z, const int32_t* colid,
                  const GridCol* grids, int64_t ncell, uint32_t* key, uint32_t* count,
-                 cudaStream_t st);
+                 cudaStream_t st, const int* search = nullptr);
 void exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* tile_sum, int64_t n,
                     cudaStream_t st);
 int64_t scan_tiles(int64_t n);
 void launch_scatter(int n, const uint32_t* key, const uint32_t* start, uint32_t* fill,
-                    int32_t* tmp, cudaStream_t st);
+                    int32_t* tmp, cudaStream_t st, const int* search = nullptr);
 void launch_cell_sort(int64_t ncell, const uint32_t* start, int32_t* tmp, const int32_t* ids,
-                      cudaStream_t st);
+                      cudaStream_t st, const int* search = nullptr);
 void launch_gather(int n, const int32_t* tmp, const double* const* src, double* const* dst,
                    int nsrc, const int32_t* ids_in, int32_t* ids_out, const int32_t* col_in,
-                   int32_t* col_out, const GridCol* grids, float4* pf, cudaStream_t st);
+                   int32_t* col_out, const GridCol* grids, float4* pf, cudaStream_t st,
+                   const int32_t* iota = nullptr, const int* search = nullptr);
 void launch_neighbors(bool keep, int n, const double* x, const double* y, const double* z,
                       const float4* pf, const int32_t* colid, const int32_t* ids,
                       const GridCol* grids, const uint32_t* start, const double* radius,
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
-                      int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs = kBlock);
+                      int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs = kBlock,
+                      const int* search = nullptr, double* xref = nullptr);
+void launch_filter(int n, const double* x, const double* y, const double* z, const float4* pf,
+                   const int32_t* cand, const int32_t* ccnt, int capc, const GridCol* grids,
+                   const int32_t* colid, double r, double floor_z, int cap, int32_t* nbr,
+                   int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs);
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st);
 // fit.cu
@@ -100,6 +106,14 @@ struct lp_ctx {
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
   float4 *Xh = nullptr, *Xl = nullptr, *Uh = nullptr, *Ul = nullptr, *GVff = nullptr;
   float* Gff = nullptr;      // float-float Gram matrices (LP_MIXED_FF)
+  // Verlet candidate lists (lp_params.skin)
+  int32_t* cand = nullptr;   // capc x n, k-major
+  int32_t* ccnt = nullptr;
+  int capc = 0;
+  double* xref = nullptr;    // positions at the last search, 3 x n
+  int* d_search = nullptr;   // device flag: search at the next step
+  int32_t* iota = nullptr;   // 0..n-1 (identity gather)
+  double skin = 0.0;         // skin of the current lp_step call (0: off)
   int cx = 0, ci = 0;
   int64_t ncell = 0;
   std::vector<GridCol> h_grids;
@@ -111,6 +125,9 @@ struct lp_ctx {
   std::vector<int> ev_phase;  // phase of each recorded pair
   int64_t launches = 0;
   int64_t steps = 0;
+  // bounded waits of the persistent kernel (lp_ctx_set_wait_limit)
+  unsigned long long max_spins = 1ull << 25;
+  unsigned extra_arrivals = 0;
   // launch configuration (lp_ctx_set_tuning / lp_autotune)
   int bs_nbr = kBlock, bs_p1 = kBlock, bs_p2 = kBlock;
 };
@@ -279,22 +296,23 @@ void phase_mark(lp_ctx* c, int phase, bool start, cudaStream_t st) {
 
 // Counting sort by cell (stable by original index) from buffer c->cx into
 // the other buffer; nsrc fields of table `kind`.
-void sort_particles(lp_ctx* c, int n, int kind, int nsrc, cudaStream_t st) {
+void sort_particles(lp_ctx* c, int n, int kind, int nsrc, cudaStream_t st,
+                    const int* search = nullptr) {
   const int d = c->cx;
   uint32_t* count = c->cells;
   uint32_t* fill = c->cells + c->cell_capacity;
   uint32_t* start = c->cells + 2 * c->cell_capacity;
   cudaMemsetAsync(c->cells, 0, sizeof(uint32_t) * 2 * c->cell_capacity, st);
   launch_keys(n, c->X[d][0], c->X[d][1], c->X[d][2], c->colid[c->ci], c->d_grids, c->ncell,
-              c->key, count, st);
+              c->key, count, st, search);
   // cells 0..ncell-1, the bucket of non-finite particles (ncell), the total
   exclusive_scan(count, start, c->tile, c->ncell + 2, st);
-  launch_scatter(n, c->key, start, fill, c->tmp, st);
-  launch_cell_sort(c->ncell, start, c->tmp, c->ids[c->ci], st);
+  launch_scatter(n, c->key, start, fill, c->tmp, st, search);
+  launch_cell_sort(c->ncell, start, c->tmp, c->ids[c->ci], st, search);
   const double* const* src = (const double* const*)(c->d_tab + ((d * 2 + kind) * 2 + 0) * kTabFields);
   double* const* dst = c->d_tab + ((d * 2 + kind) * 2 + 1) * kTabFields;
   launch_gather(n, c->tmp, src, dst, nsrc, c->ids[c->ci], c->ids[1 - c->ci], c->colid[c->ci],
-                c->colid[1 - c->ci], c->d_grids, c->pf, st);
+                c->colid[1 - c->ci], c->d_grids, c->pf, st, c->iota, search);
   c->cx ^= 1;
   c->ci ^= 1;
   c->launches += 7;
@@ -317,12 +335,35 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.K = K;
   A.grids = c->d_grids;
   A.Xh = c->Xh; A.Xl = c->Xl; A.Uh = c->Uh; A.Ul = c->Ul; A.GVff = c->GVff; A.Gff = c->Gff;
+  if (c->skin > 0.0) {
+    A.xref = c->xref;
+    const double hs = 0.5 * c->skin;
+    A.half_skin2 = hs * hs * (1.0 - 0x1p-20);
+    A.need_search = c->d_search;
+  }
   return A;
 }
 
 // One LP step on the context's internal (sorted) state.
 void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cudaStream_t st) {
-  if (rebuild) {
+  if (rebuild && c->skin > 0.0) {
+    // Verlet candidate lists: search (radius + skin) only when flagged, then
+    // the exact filter every step
+    phase_mark(c, LP_PHASE_SORT, true, st);
+    sort_particles(c, n, 0, 7, st, c->d_search);
+    phase_mark(c, LP_PHASE_SORT, false, st);
+    phase_mark(c, LP_PHASE_NEIGHBORS, true, st);
+    const int e = c->cx;
+    launch_neighbors(false, n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf, c->colid[c->ci],
+                     c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity, nullptr,
+                     K.radius + c->skin, K.mirror_mode, K.floor_z, c->capc, c->cand, c->ccnt,
+                     c->dg, st, c->bs_nbr, c->d_search, c->xref);
+    launch_filter(n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf, c->cand, c->ccnt, c->capc,
+                  c->d_grids, c->colid[c->ci], K.radius, K.floor_z, c->cap, c->nbr, c->cnt,
+                  c->dg, c->d_search, st, c->bs_nbr);
+    phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
+    c->launches += 2;
+  } else if (rebuild) {
     phase_mark(c, LP_PHASE_SORT, true, st);
     sort_particles(c, n, 0, 7, st);
     phase_mark(c, LP_PHASE_SORT, false, st);
@@ -379,7 +420,8 @@ lp_status run_step_persistent(lp_ctx* c, int n, const StepConsts& K, int prec, b
   }
   P.S = step_args(c, n, K);
   P.bar = c->bar;
-  P.max_spins = 1ull << 25;  // about 2 s of __nanosleep(64)
+  P.max_spins = c->max_spins;  // default about 2 s of __nanosleep(64)
+  P.extra_arrivals = c->extra_arrivals;
   cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st);
   if (launch_persistent(prec, P, st) != cudaSuccess) {
     cudaGetLastError();
@@ -446,6 +488,7 @@ bool valid_params(const lp_params* q, const lp_eos* e, double dt) {
     return false;
   if (q->rebuild_every < 1) return false;
   if (q->launch_mode < LP_LAUNCH_KERNELS || q->launch_mode > LP_LAUNCH_PERSISTENT) return false;
+  if (!(q->skin >= 0.0) || !std::isfinite(q->skin) || q->skin > q->radius) return false;
   if (!(e->phi_min < e->phi_max && e->phi_max < e->phi_c)) return false;
   return true;
 }
@@ -521,6 +564,28 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->Ul, n);
   if (s == LP_OK) s = dalloc(c, &c->GVff, n);
   if (s == LP_OK) s = dalloc(c, &c->Gff, n * 2 * kTri);
+  c->capc = std::min(c->cap + 32, 96);
+  if (s == LP_OK) s = dalloc(c, &c->cand, n * c->capc);
+  if (s == LP_OK) s = dalloc(c, &c->ccnt, n);
+  if (s == LP_OK) s = dalloc(c, &c->xref, 3 * n);
+  if (s == LP_OK) s = dalloc(c, &c->d_search, 1);
+  if (s == LP_OK) s = dalloc(c, &c->iota, n);
+  if (s == LP_OK) {
+    // every index buffer starts valid: identity permutations, empty stencils
+    launch_iota((int)n, c->iota, 0);
+    launch_iota((int)n, c->ids[0], 0);
+    launch_iota((int)n, c->ids[1], 0);
+    launch_iota((int)n, c->tmp, 0);
+    cudaMemset(c->colid[0], 0, n * sizeof(int32_t));
+    cudaMemset(c->colid[1], 0, n * sizeof(int32_t));
+    cudaMemset(c->cnt, 0, n * sizeof(int32_t));
+    cudaMemset(c->nbr, 0, n * c->cap * sizeof(int32_t));
+    cudaMemset(c->ccnt, 0, n * sizeof(int32_t));
+    cudaMemset(c->cand, 0, n * c->capc * sizeof(int32_t));
+    cudaMemset(c->key, 0, n * sizeof(uint32_t));
+    cudaMemset(c->fbslot, 0xff, n * sizeof(int32_t));
+    if (cudaDeviceSynchronize() != cudaSuccess) s = LP_ERR_CUDA;
+  }
   if (s == LP_OK && cudaMemset(c->bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) s = LP_ERR_CUDA;
   if (s == LP_OK) s = ensure_cells(c, 1 << 16);
   if (s == LP_OK) {
@@ -594,6 +659,14 @@ lp_status lp_ctx_sync(lp_ctx* c, void* stream, lp_diag* diag) {
   if (d.flags & LP_FLAG_TIMEOUT) return LP_ERR_TIMEOUT;
   if (d.flags & LP_FLAG_OVERFLOW) return LP_ERR_STENCIL_OVERFLOW;
   if (d.flags & LP_FLAG_NONFINITE) return LP_ERR_NONFINITE;
+  return LP_OK;
+}
+
+lp_status lp_ctx_set_wait_limit(lp_ctx* c, int64_t max_spins, int32_t extra_arrivals) {
+  if (!c || max_spins < 1 || extra_arrivals < 0 || extra_arrivals > 1024)
+    return LP_ERR_INVALID_ARG;
+  c->max_spins = (unsigned long long)max_spins;
+  c->extra_arrivals = (unsigned)extra_arrivals;
   return LP_OK;
 }
 
@@ -801,9 +874,30 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   const StepConsts K = step_consts(eos, q, dt, c->cap);
   LP_TRY(load_state(c, p, mui, st));
   const int d = c->cx;
+  c->skin = (q->skin > 0.0 && q->rebuild_every == 1 && q->launch_mode != LP_LAUNCH_PERSISTENT)
+                ? q->skin
+                : 0.0;
+  if (c->skin > 0.0) {
+    const int one = 1;
+    cudaMemcpyAsync(c->d_search, &one, sizeof(int), cudaMemcpyHostToDevice, st);
+  }
   LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
   LP_TRY(setup_grids(c, p->ncolumns, q->radius, st));
-  LP_TRY(run_steps(c, n, K, q->precision, q->rebuild_every, q->launch_mode, nsteps, st));
+  const lp_status rs = run_steps(c, n, K, q->precision, q->rebuild_every, q->launch_mode, nsteps,
+                                 st);
+  c->skin = 0.0;
+  LP_TRY(rs);
+  // after a bounded wait gave up, the internal state is incomplete: leave the
+  // caller's arrays as they were (lp_ctx_sync reports LP_ERR_TIMEOUT)
+  if (q->launch_mode == LP_LAUNCH_PERSISTENT) {
+    unsigned flags = 0;
+    if (cudaMemcpyAsync(&c->h_dg->flags, &c->dg->flags, sizeof(unsigned),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return LP_ERR_CUDA;
+    flags = c->h_dg->flags;
+    if (flags & LP_FLAG_TIMEOUT) return LP_OK;
+  }
   // internal state -> caller arrays (original order)
   {
     const int e = c->cx;

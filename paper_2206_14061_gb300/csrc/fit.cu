@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_fit(const FitArgs F) {
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
     const int j = code & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const double zj = (code >> 31) ? F.f2 - F.z[j] : F.z[j];
     M.add(T((F.x[j] - xi) * ih), T((F.y[j] - yi) * ih), T((zj - zi) * ih));
   }
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_fit(const FitArgs F) {
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
       const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? F.f2 - F.z[j] : F.z[j];
       T a[kNB];
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(kBlock) k_fit(const FitArgs F) {
       for (int k = 0; k < m; ++k) {
         const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
         const int j = code & ~kMirrorBit;
+        if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
         const bool mir = code >> 31;
         const double zj = mir ? F.f2 - F.z[j] : F.z[j];
         double a[kNB];
@@ -185,6 +188,7 @@ __global__ void __launch_bounds__(64) k_fit_fallback(const FitArgs F) {
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
       const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const double zj = (code >> 31) ? F.f2 - F.z[j] : F.z[j];
       taylor_row((F.x[j] - xi) * F.inv_h, (F.y[j] - yi) * F.inv_h, (zj - zi) * F.inv_h,
                  &Acopy[k * kNB]);
@@ -194,6 +198,7 @@ __global__ void __launch_bounds__(64) k_fit_fallback(const FitArgs F) {
       for (int k = 0; k < m; ++k) {
         const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
         const int j = code & ~kMirrorBit;
+        if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
         const bool mir = code >> 31;
         for (int q = 0; q < kNB; ++q) Am[k * kNB + q] = Acopy[k * kNB + q];
         for (int f = 0; f < nf; ++f) {

@@ -88,6 +88,7 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
       const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
       const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
@@ -133,6 +134,7 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
       const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
       const float dx = (float)((A.x[j] - xi) * ih), dy = (float)((A.y[j] - yi) * ih);
@@ -174,6 +176,7 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
       const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
       const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
@@ -215,6 +218,7 @@ static __device__ __noinline__ void pass1_fallback_item(const StepArgs& A, int t
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
       const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
       taylor_row((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih, &Am[k * kNB]);
@@ -247,6 +251,7 @@ static __device__ __noinline__ void pass2_fallback_item(const StepArgs& A, int t
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
       const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
       taylor_row((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih, &Am[k * kNB]);
@@ -303,7 +308,8 @@ struct FFRow {
 };
 __device__ __forceinline__ FFRow ff_row(const StepArgs& A, int s, const float4& hi,
                                         const float4& lo, uint32_t code) {
-  const int j = code & ~kMirrorBit;
+  int j = code & ~kMirrorBit;
+  if ((unsigned)j >= (unsigned)A.n) j = s;  // never read outside the arrays (zero row)
   const bool mir = code >> 31;
   const float4 jh = A.Xh[j], jl = A.Xl[j];
   FFRow r;
@@ -414,6 +420,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
     ff a[kNB];
     ff_taylor(r, a);
     const int j = code & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
     const float4 jh = A.Uh[j], jl = A.Ul[j];
     const float ujh[3] = {jh.x, jh.y, jh.z}, ujl[3] = {jl.x, jl.y, jl.z};
@@ -473,6 +480,7 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
     ff a[kNB];
     ff_taylor(r, a);
     const int j = code & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
     const float4 gvj = A.GVff[j];
     const ff bg = mir ? ff{-gvi.x, -gvi.y} : ff_diff(gvj.x, gvj.y, gvi.x, gvi.y);
@@ -541,6 +549,7 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
         for (int k = 0; k < m; ++k) {
           const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
           const int j = code & ~kMirrorBit;
+          if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
           double a[kNB];
@@ -582,6 +591,7 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
         for (int k = 0; k < m; ++k) {
           const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
           const int j = code & ~kMirrorBit;
+          if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
           float a[kNB];
@@ -606,6 +616,7 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
         for (int k = 0; k < m; ++k) {
           const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
           const int j = code & ~kMirrorBit;
+          if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
           double a[kNB];
@@ -683,6 +694,10 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     A.Vo[s] = Vi;
     nonfin = !(isfinite(u1) && isfinite(v1) && isfinite(w1) && isfinite(x1) && isfinite(y1) &&
                isfinite(z1) && isfinite(Vi));
+    if (A.xref) {
+      const double ex = x1 - A.xref[s], ey = y1 - A.xref[A.n + s], ez = z1 - A.xref[2 * A.n + s];
+      if (!(((ex * ex) + (ey * ey)) + (ez * ez) <= A.half_skin2)) *A.need_search = 1;
+    }
     below = A.K.mirror_mode != LP_MIRROR_NONE && z1 < A.K.floor_z;
   }
   warp_count(&A.dg->n_gas, live && regime == 0);

@@ -154,6 +154,11 @@ struct StepArgs {
   const GridCol* grids;
   float4 *Xh, *Xl, *Uh, *Ul, *GVff;
   float* Gff;       // 90 * n: hi (45) then lo (45), k-major
+  // Verlet candidate lists: positions at the last search and the flag that
+  // requests a new search when a particle has moved more than skin/2
+  const double* xref;  // 3 * n, or NULL when candidate lists are off
+  double half_skin2;
+  int* need_search;
 };
 
 struct FitArgs {
@@ -195,6 +200,7 @@ struct PersistArgs {
   // barrier: [0] arrivals, [1] generation
   unsigned* bar;
   unsigned long long max_spins;
+  unsigned extra_arrivals;  // 0 in production; > 0 only to test the bounded wait
 };
 
 // arguments of the adjoint kernels (adjoint.cu)

@@ -15,6 +15,7 @@ __global__ void k_scatter_state(int n, const int32_t* __restrict__ ids,
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int o = ids[s];
+  if ((unsigned)o >= (unsigned)n) return;  // never write outside the caller's arrays
   for (int f = 0; f < nf; ++f) dst[f][o] = src[f][s];
 }
 

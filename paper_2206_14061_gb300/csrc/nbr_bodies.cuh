@@ -95,7 +95,7 @@ __device__ __forceinline__ void cell_sort_body(int64_t c, const uint32_t* __rest
 
 // Gather the state into the new order; FP32 origin-relative positions for the
 // prefilter.
-__device__ __forceinline__ void gather_body(int t, const int32_t* __restrict__ tmp,
+__device__ __forceinline__ void gather_body(int t, int n, const int32_t* __restrict__ tmp,
                                             const double* const* __restrict__ src,
                                             double* const* __restrict__ dst, int nsrc,
                                             const int32_t* __restrict__ ids_in,
@@ -104,7 +104,8 @@ __device__ __forceinline__ void gather_body(int t, const int32_t* __restrict__ t
                                             int32_t* __restrict__ col_out,
                                             const GridCol* __restrict__ grids,
                                             float4* __restrict__ pf) {
-  const int s = tmp[t];
+  int s = tmp[t];
+  if ((unsigned)s >= (unsigned)n) s = t;  // stay inside the buffers whatever tmp holds
   for (int f = 0; f < nsrc; ++f) dst[f][t] = src[f][s];
   ids_out[t] = ids_in[s];
   const int c = col_in[s];

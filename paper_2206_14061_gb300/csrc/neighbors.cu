@@ -95,12 +95,16 @@ __global__ void k_bbox(int n, const double* __restrict__ x, const double* __rest
   }
 }
 
+// `search` (may be NULL: always) gates the sort kernels on a device flag
+__device__ __forceinline__ bool searching(const int* search) { return !search || *search; }
+
 __global__ void k_keys(int n, const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, const int32_t* __restrict__ colid,
                        const GridCol* __restrict__ grids, uint32_t ncell,
-                       uint32_t* __restrict__ key, uint32_t* __restrict__ count) {
+                       uint32_t* __restrict__ key, uint32_t* __restrict__ count,
+                       const int* search) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) keys_body(s, x, y, z, colid, grids, ncell, key, count);
+  if (s < n && searching(search)) keys_body(s, x, y, z, colid, grids, ncell, key, count);
 }
 
 // --------------------------------------------------- exclusive scan (u32)
@@ -161,24 +165,29 @@ int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
 __global__ void k_scatter(int n, const uint32_t* __restrict__ key,
                           const uint32_t* __restrict__ start, uint32_t* __restrict__ fill,
-                          int32_t* __restrict__ tmp) {
+                          int32_t* __restrict__ tmp, const int* search) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) scatter_body(s, key, start, fill, tmp);
+  if (s < n && searching(search)) scatter_body(s, key, start, fill, tmp);
 }
 
 __global__ void k_cell_sort(int64_t ncell, const uint32_t* __restrict__ start,
-                            int32_t* __restrict__ tmp, const int32_t* __restrict__ ids) {
+                            int32_t* __restrict__ tmp, const int32_t* __restrict__ ids,
+                            const int* search) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < ncell) cell_sort_body(c, start, tmp, ids);
+  if (c < ncell && searching(search)) cell_sort_body(c, start, tmp, ids);
 }
 
+// without a search (flag clear) the gather keeps the order: an identity copy
 __global__ void k_gather(int n, const int32_t* __restrict__ tmp, const double* const* __restrict__ src,
                          double* const* __restrict__ dst, int nsrc,
                          const int32_t* __restrict__ ids_in, int32_t* __restrict__ ids_out,
                          const int32_t* __restrict__ col_in, int32_t* __restrict__ col_out,
-                         const GridCol* __restrict__ grids, float4* __restrict__ pf) {
+                         const GridCol* __restrict__ grids, float4* __restrict__ pf,
+                         const int32_t* __restrict__ iota, const int* search) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) gather_body(t, tmp, src, dst, nsrc, ids_in, ids_out, col_in, col_out, grids, pf);
+  if (t < n)
+    gather_body(t, n, searching(search) ? tmp : iota, src, dst, nsrc, ids_in, ids_out, col_in,
+                col_out, grids, pf);
 }
 
 // ------------------------------------------------------- neighbour search
@@ -191,10 +200,87 @@ k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
             const GridCol* __restrict__ grids, const uint32_t* __restrict__ start,
             const double* __restrict__ radius, double r_const, int mirror_mode, double floor_z,
             int cap, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt,
-            DevDiag* __restrict__ dg) {
+            DevDiag* __restrict__ dg, const int* search, double* __restrict__ xref) {
+  if (!searching(search)) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xref && s < n) {  // positions of this search, for the displacement test
+    xref[s] = x[s];
+    xref[n + s] = y[s];
+    xref[2 * n + s] = z[s];
+  }
   neighbors_body<KEEP>(s, s < n, n, x, y, z, pf, colid, ids, grids, start, radius, r_const,
                        mirror_mode, floor_z, cap, nbr, cnt, dg);
+}
+
+// Verlet filter: the stencil of this step is every candidate (found within
+// radius + skin at the last search) that passes the exact radius test, in
+// candidate order. Same FP32 prefilter and uncontracted FP64 test as the
+// search. Thread 0 clears the search flag for the displacement test of this
+// step's update.
+__global__ void __launch_bounds__(kMaxBlock)
+k_filter(int n, const double* __restrict__ x, const double* __restrict__ y,
+         const double* __restrict__ z, const float4* __restrict__ pf,
+         const int32_t* __restrict__ cand, const int32_t* __restrict__ ccnt, int capc,
+         const GridCol* __restrict__ grids, const int32_t* __restrict__ colid, double r,
+         double floor_z, int cap, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt,
+         DevDiag* __restrict__ dg, int* search) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = s < n;
+  if (s == 0) *search = 0;
+  int c = 0;
+  bool over = false;
+  if (live) {
+    const GridCol g = grids[colid[s]];
+    const double xi = x[s], yi = y[s], zi = z[s];
+    const double r2 = r * r;
+    const float r2f = __double2float_rn(r2);
+    const float lo = r2f * (1.0f - 0.015625f), hi = r2f * (1.0f + 0.015625f);
+    const float4 pi = pf[s];
+    const float lim = 4096.0f * __double2float_rn(r);
+    const bool exact_only = !(fabsf(pi.x) <= lim && fabsf(pi.y) <= lim && fabsf(pi.z) <= lim);
+    const float fz2 = __double2float_rn(2.0 * (floor_z - g.oz));
+    const int m = min(ccnt[s], capc);
+    for (int k = 0; k < m; ++k) {
+      const uint32_t code = (uint32_t)cand[(int64_t)k * n + s];
+      const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
+      const bool mir = code >> 31;
+      const float4 pj = pf[j];
+      const float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
+      const float dzf = (mir ? fz2 - pj.z : pj.z) - pi.z;
+      const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+      if (!exact_only && d2f > hi) continue;
+      bool in;
+      if (!exact_only && d2f < lo) {
+        in = true;
+      } else {
+        double d2;
+        const double zj = mir ? __dsub_rn(2.0 * floor_z, z[j]) : z[j];
+        in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2);
+      }
+      if (!in) continue;
+      if (c < cap) nbr[(int64_t)c * n + s] = (int32_t)code;
+      ++c;
+    }
+    over = c > cap || ccnt[s] > capc;
+    cnt[s] = c;
+  }
+  warp_count(&dg->n_overflow, live && over);
+  if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
+  unsigned long long rows = live ? (unsigned long long)min(c, cap) : 0ull;
+  for (int o = 16; o > 0; o >>= 1) rows += __shfl_xor_sync(0xffffffffu, rows, o);
+  const unsigned live_n = __popc(__ballot_sync(0xffffffffu, live));
+  int mn = live ? c : INT32_MAX, mx = live ? c : 0;
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0 && live_n) {
+    atomicAdd(&dg->n_stencil_rows, rows);
+    atomicAdd(&dg->n_stencils, (unsigned long long)live_n);
+    atomicMin(&dg->min_stencil, mn);
+    atomicMax(&dg->max_stencil, mx);
+  }
 }
 
 // Stencils from sorted indices to caller indices.
@@ -226,35 +312,47 @@ void launch_bbox(int n, int ncol, const double* x, const double* y, const double
 }
 void launch_keys(int n, const double* x, const double* y, const double* z, const int32_t* colid,
                  const GridCol* grids, int64_t ncell, uint32_t* key, uint32_t* count,
-                 cudaStream_t st) {
-  k_keys<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, z, colid, grids, (uint32_t)ncell, key, count);
+                 cudaStream_t st, const int* search) {
+  k_keys<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, z, colid, grids, (uint32_t)ncell, key, count,
+                                          search);
 }
 void launch_scatter(int n, const uint32_t* key, const uint32_t* start, uint32_t* fill,
-                    int32_t* tmp, cudaStream_t st) {
-  k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, key, start, fill, tmp);
+                    int32_t* tmp, cudaStream_t st, const int* search) {
+  k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, key, start, fill, tmp, search);
 }
 void launch_cell_sort(int64_t ncell, const uint32_t* start, int32_t* tmp, const int32_t* ids,
-                      cudaStream_t st) {
-  k_cell_sort<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(ncell, start, tmp, ids);
+                      cudaStream_t st, const int* search) {
+  k_cell_sort<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(ncell, start, tmp, ids, search);
 }
 void launch_gather(int n, const int32_t* tmp, const double* const* src, double* const* dst,
                    int nsrc, const int32_t* ids_in, int32_t* ids_out, const int32_t* col_in,
-                   int32_t* col_out, const GridCol* grids, float4* pf, cudaStream_t st) {
+                   int32_t* col_out, const GridCol* grids, float4* pf, cudaStream_t st,
+                   const int32_t* iota, const int* search) {
   k_gather<<<(n + 255) / 256, 256, 0, st>>>(n, tmp, src, dst, nsrc, ids_in, ids_out, col_in,
-                                            col_out, grids, pf);
+                                            col_out, grids, pf, iota, search);
 }
 void launch_neighbors(bool keep, int n, const double* x, const double* y, const double* z,
                       const float4* pf, const int32_t* colid, const int32_t* ids,
                       const GridCol* grids, const uint32_t* start, const double* radius,
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
-                      int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs) {
+                      int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs, const int* search,
+                      double* xref) {
   const int nb = (n + bs - 1) / bs;
   if (keep)
     k_neighbors<true><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
-                                          r_const, mirror_mode, floor_z, cap, nbr, cnt, dg);
+                                          r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
+                                          search, xref);
   else
     k_neighbors<false><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
-                                           r_const, mirror_mode, floor_z, cap, nbr, cnt, dg);
+                                           r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
+                                           search, xref);
+}
+void launch_filter(int n, const double* x, const double* y, const double* z, const float4* pf,
+                   const int32_t* cand, const int32_t* ccnt, int capc, const GridCol* grids,
+                   const int32_t* colid, double r, double floor_z, int cap, int32_t* nbr,
+                   int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs) {
+  k_filter<<<(n + bs - 1) / bs, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
+                                             floor_z, cap, nbr, cnt, dg, search);
 }
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st) {

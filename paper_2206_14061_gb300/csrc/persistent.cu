@@ -19,7 +19,7 @@ int64_t persistent_scan_tiles(int64_t len) { return (len + kPTile - 1) / kPTile;
 
 // Grid barrier with a bounded wait. Returns false if this block gave up.
 __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long max_spins,
-                                          DevDiag* dg) {
+                                          unsigned extra, DevDiag* dg) {
   __shared__ int gave_up;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -28,7 +28,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long max_
     const unsigned gen = *vgen;
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-    if (arrived == gridDim.x) {
+    if (arrived == gridDim.x + extra) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -51,7 +51,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long max_
 
 #define LP_SYNC_OR_LEAVE()                                  \
   do {                                                      \
-    if (!grid_sync(P.bar, P.max_spins, P.S.dg)) return;    \
+    if (!grid_sync(P.bar, P.max_spins, P.extra_arrivals, P.S.dg)) return; \
   } while (0)
 
 template <int PREC>
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(kBlock) k_step_persistent(const PersistArgs P)
     for (int64_t c = tid; c < P.ncell; c += nth) cell_sort_body(c, P.start, P.tmp, P.ids_in);
     LP_SYNC_OR_LEAVE();
     for (int t = tid; t < n; t += nth)
-      gather_body(t, P.tmp, P.src, P.dst, P.nsrc, P.ids_in, P.ids_out, P.colid_in, P.colid_out,
-                  P.grids, P.pf);
+      gather_body(t, n, P.tmp, P.src, P.dst, P.nsrc, P.ids_in, P.ids_out, P.colid_in,
+                  P.colid_out, P.grids, P.pf);
     LP_SYNC_OR_LEAVE();
     // every lane of a warp runs the same number of rounds (warp-wide reductions)
     for (int base = 0; base < n; base += nth) {

@@ -46,7 +46,7 @@ def _dicts(pd):
 def _prm(pd, **kw):
     q = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
              floor_z=pd["floor_z"], mirror_mode=pd["mirror_mode"], precision=0, rebuild_every=1,
-             launch_mode=0)
+             launch_mode=0, skin=0.0)
     q.update(kw)
     return q
 
@@ -348,6 +348,47 @@ def test_autotune_choices_and_table(dev, capi, tmp_path):
         ctx2.sync()
         for k in capi.FIELDS:
             assert np.array_equal(s2[k].cpu().numpy(), ref[k]), (bs, k)
+
+
+def test_step_verlet_skin_matches_full_search(dev, capi, orc):
+    """Candidate lists within radius + skin, filtered every step with the
+    exact test, give the stencils of a full search: the same state (up to the
+    row order inside a stencil), including when the displacement test
+    triggers new searches during the run."""
+    wl = W.cube(16)
+    pd = W.param_dict(wl)
+    ref, _ = _run_gpu(capi, dev, wl, pd, 20, launch_mode=0)
+    s = torch.cuda.Stream()
+    for skin, mode in ((0.1 * pd["h"], 0), (0.1 * pd["h"], 1), (2e-4 * pd["h"], 1)):
+        got, d = _run_gpu(capi, dev, wl, pd, 20, launch_mode=mode, skin=skin, stream=s)
+        assert d["n_overflow"] == 0
+        e = _state_err(got, ref, wl.state)
+        assert max(e.values()) <= 1e-12, (skin, mode, e)
+    orc_ref, _ = orc.step(wl.state, orc.params(**pd), 20, brute=False)
+    e = _state_err(got, orc_ref, wl.state)
+    assert max(e.values()) <= 1e-9, e
+
+
+def test_persistent_bounded_wait_reports_timeout(dev, capi):
+    """A grid barrier that waits for blocks that do not exist gives up after
+    its spin limit: the kernel ends, lp_ctx_sync reports LP_ERR_TIMEOUT, and
+    the same context then runs a normal step (no GPU fault, no hang)."""
+    wl = W.cube(10)
+    pd = W.param_dict(wl)
+    m, eos = _dicts(pd)
+    ctx = capi.Context(wl.n, cap=64)
+    st = {k: T(wl.state[k], dev) for k in capi.FIELDS}
+    ctx.set_wait_limit(max_spins=2000, extra_arrivals=1)
+    capi.lp_step(ctx, st, m, eos, _prm(pd, launch_mode=2), pd["dt"], 1)
+    d = ctx.sync(raise_on_error=False)
+    assert d["status"] == capi.LP_ERR_TIMEOUT and d["flags"] & 0x4
+    ctx.set_wait_limit()
+    st = {k: T(wl.state[k], dev) for k in capi.FIELDS}
+    capi.lp_step(ctx, st, m, eos, _prm(pd, launch_mode=2), pd["dt"], 2)
+    assert ctx.sync()["status"] == 0
+    ref, _ = _run_gpu(capi, dev, wl, pd, 2, launch_mode=0)
+    for k in capi.FIELDS:
+        assert np.array_equal(st[k].cpu().numpy(), ref[k]), k
 
 
 def test_step_rebuild_period_matches_oracle(dev, capi, orc):
