@@ -874,15 +874,19 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   const StepConsts K = step_consts(eos, q, dt, c->cap);
   LP_TRY(load_state(c, p, mui, st));
   const int d = c->cx;
-  c->skin = (q->skin > 0.0 && q->rebuild_every == 1 && q->launch_mode != LP_LAUNCH_PERSISTENT)
-                ? q->skin
-                : 0.0;
-  if (c->skin > 0.0) {
-    const int one = 1;
-    cudaMemcpyAsync(c->d_search, &one, sizeof(int), cudaMemcpyHostToDevice, st);
-  }
+  // Verlet candidate lists: the grid must hold radius + skin in one cell
+  const double skin = (q->skin > 0.0 && q->rebuild_every == 1 &&
+                       q->launch_mode != LP_LAUNCH_PERSISTENT)
+                          ? q->skin
+                          : 0.0;
   LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
-  LP_TRY(setup_grids(c, p->ncolumns, q->radius, st));
+  LP_TRY(setup_grids(c, p->ncolumns, q->radius + skin, st));
+  if (skin > 0.0) {
+    const int one = 1;
+    if (cudaMemcpyAsync(c->d_search, &one, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return LP_ERR_CUDA;
+  }
+  c->skin = skin;
   const lp_status rs = run_steps(c, n, K, q->precision, q->rebuild_every, q->launch_mode, nsteps,
                                  st);
   c->skin = 0.0;

@@ -147,11 +147,18 @@ __device__ __forceinline__ void neighbors_body(
     const double r = radius ? radius[s] : r_const;
     const double r2 = r * r;
     const float r2f = __double2float_rn(r2);
-    const float lo = r2f * (1.0f - 0.015625f), hi = r2f * (1.0f + 0.015625f);
     const float4 pi = pf[s];
-    const float lim = 4096.0f * __double2float_rn(r);
-    const bool exact_only = !(fabsf(pi.x) <= lim && fabsf(pi.y) <= lim && fabsf(pi.z) <= lim);
     const float fz2 = __double2float_rn(2.0 * (floor_z - g.oz));
+    // FP32 prefilter band. Coordinates are origin-relative floats with error
+    // <= 2^-24 |coordinate|; for a pair near the sphere the squared-distance
+    // error is below about (4 L + 2) 2^-23 r^2 with L the largest coordinate
+    // (mirror height included) over r. Pairs inside the band take the FP64 test.
+    const float rf = __double2float_rn(r);
+    const float L = (4.0f * fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))) +
+                     4.0f * rf) / rf;
+    const float band = (1.0f + L) * 0x1p-19f;
+    const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
+    const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
     double cd2[KEEP ? kMaxCand : 1];
     uint32_t cj[KEEP ? kMaxCand : 1];
     const int ncx = g.nx, ncy = g.ny, ncz = g.nz;

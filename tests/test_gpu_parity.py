@@ -369,6 +369,27 @@ def test_step_verlet_skin_matches_full_search(dev, capi, orc):
     assert max(e.values()) <= 1e-9, e
 
 
+def test_step_verlet_skin_under_shear_drift(dev, capi):
+    """Gas-regime shear flow u = G z (no stresses, so no instability): pairs
+    drift across the stencil radius and particles move beyond skin/2, so the
+    candidate lists are searched again during the run; the state equals the
+    full-search run's."""
+    wl = W.cube(14)
+    s = dict(wl.state)
+    s["u"] = 50.0 * s["z"]
+    s["V"] = np.full(wl.n, 1.0 / 0.3)  # phi below phi_min: gas, a = g
+    wl.state = s
+    pd = dict(W.param_dict(wl), mirror_mode=0, gz=0.0)
+    ref, _ = _run_gpu(capi, dev, wl, pd, 40, launch_mode=0)
+    moved = np.abs(ref["x"] - s["x"]).max() / pd["h"]
+    assert moved > 0.1  # several searches were needed with skin 0.1h
+    for mode in (0, 1):
+        got, d = _run_gpu(capi, dev, wl, pd, 40, launch_mode=mode, skin=0.1 * pd["h"],
+                          stream=torch.cuda.Stream())
+        e = _state_err(got, ref, s)
+        assert max(e.values()) <= 1e-12, (mode, e)
+
+
 def test_persistent_bounded_wait_reports_timeout(dev, capi):
     """A grid barrier that waits for blocks that do not exist gives up after
     its spin limit: the kernel ends, lp_ctx_sync reports LP_ERR_TIMEOUT, and
