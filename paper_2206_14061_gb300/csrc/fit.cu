@@ -49,6 +49,14 @@ __global__ void __launch_bounds__(64) k_pass2_fallback(const StepArgs A) {
     pass2_fallback_item(A, t);
 }
 
+// float-float passes: at most 128 threads per block and 3 blocks per SM
+// (170 registers), more warps per SM than the 255-register default
+constexpr int kFFBlock = 128;
+__global__ void __launch_bounds__(kFFBlock, 3) k_pass1_ff(const StepArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) pass1_body<LP_MIXED_FF>(A, s);
+}
+
 __global__ void k_split_state(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < A.n) split_state_body(A, s);
@@ -63,6 +71,11 @@ template <int PREC>
 __global__ void __launch_bounds__(kMaxBlock) k_pass2(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   pass2_body<PREC>(A, s, s < A.n);
+}
+
+__global__ void __launch_bounds__(kFFBlock, 3) k_pass2_ff(const StepArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  pass2_body<LP_MIXED_FF>(A, s, s < A.n);
 }
 
 // ------------------------------------------------ lp_fit_derivatives
@@ -266,7 +279,8 @@ void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs) {
     k_pass1<LP_MIXED><<<nb, bs, 0, st>>>(A);
   } else {
     k_split_state<<<(A.n + 255) / 256, 256, 0, st>>>(A);
-    k_pass1<LP_MIXED_FF><<<nb, bs, 0, st>>>(A);
+    const int b = bs < kFFBlock ? bs : kFFBlock;
+    k_pass1_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
   }
   k_pass1_fallback<<<152, 64, 0, st>>>(A);
 }
@@ -276,7 +290,10 @@ void launch_pass2(int prec, const StepArgs& A, cudaStream_t st, int bs) {
   const int nb = (A.n + bs - 1) / bs;
   if (prec == LP_FP64) k_pass2<LP_FP64><<<nb, bs, 0, st>>>(A);
   else if (prec == LP_MIXED) k_pass2<LP_MIXED><<<nb, bs, 0, st>>>(A);
-  else k_pass2<LP_MIXED_FF><<<nb, bs, 0, st>>>(A);
+  else {
+    const int b = bs < kFFBlock ? bs : kFFBlock;
+    k_pass2_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
+  }
 }
 void launch_fit(int prec, const FitArgs& F, cudaStream_t st) {
   const int nb = (F.n + kBlock - 1) / kBlock;

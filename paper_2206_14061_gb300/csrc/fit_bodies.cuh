@@ -365,13 +365,15 @@ __device__ __forceinline__ void ff_gram(const ff* mo, ff* g) {
 }
 
 // Solve G c = r: FP32 Cholesky solve, then two refinement steps with the
-// float-float residual r - G c. Returns c as doubles.
-__device__ __forceinline__ void ff_refined_solve(const ff* G, const float* L, const ff* r,
+// float-float residual r - G c. Returns c as doubles. Kept out of line with a
+// rolled iteration loop: one copy of its code serves every field of both
+// passes (the unrolled form stalled on instruction fetch).
+static __device__ __noinline__ void ff_refined_solve(const ff* G, const float* L, const ff* r,
                                                  double* c_out) {
   ff c[kNB];
 #pragma unroll
   for (int q = 0; q < kNB; ++q) c[q] = {0.f, 0.f};
-#pragma unroll
+#pragma unroll 1
   for (int it = 0; it < 3; ++it) {
     float d[kNB];
 #pragma unroll

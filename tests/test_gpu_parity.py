@@ -462,6 +462,82 @@ def test_step_edge_cases(dev, capi, orc):
 
 
 @pytest.mark.slow
+def test_derivative_sweep_full_size(dev, capi, orc):
+    """Derivative-operator sweep at full size: 126^3 = 2,000,376 particles,
+    jitter +-0.2h, radius U(1.8h, 2.6h), the 48 nearest, four fields.
+    Stencils bit-exact on every particle; FP64 derivatives within 1e-11 of
+    the oracle; the mixed mode's error and both modes' error against the
+    analytic derivatives are reported."""
+    x, y, z, rad, fields, spec = W.sweep_lattice(n_side=126)
+    n = x.size
+    ref_nbr, ref_cnt, _ = orc.neighbors(x, y, z, radius=rad, mirror_mode=0, cap=48,
+                                        keep_nearest=True, brute=False)
+    ctx = capi.Context(n, cap=64)
+    X = [T(a, dev) for a in (x, y, z)]
+    nb = capi.lp_build_neighbors(ctx, *X, radius=T(rad, dev), mirror_mode=0, cap=48,
+                                 keep_nearest=True)
+    ctx.sync()
+    got_nbr, got_cnt = nb.export()
+    assert np.array_equal(got_cnt, ref_cnt)
+    assert np.array_equal(got_nbr, ref_nbr[:, :48])
+    interior = ((x > 3e-3) & (x < 123e-3) & (y > 3e-3) & (y < 123e-3) & (z > 3e-3) &
+                (z < 123e-3))
+    assert got_cnt[interior].min() >= 16 and got_cnt.max() == 48
+    ref, _ = orc.fit(x, y, z, ref_nbr, ref_cnt, fields, [1.0] * 4, 1e-3)
+    F = [T(f, dev) for f in fields]
+    g64 = capi.lp_fit_derivatives(ctx, *X, nb, F, [1.0] * 4, 1e-3,
+                                  precision=capi.LP_FP64).cpu().numpy()
+    gmx = capi.lp_fit_derivatives(ctx, *X, nb, F, [1.0] * 4, 1e-3,
+                                  precision=capi.LP_MIXED).cpu().numpy()
+    ctx.sync()
+    e64, emx = _class_err(g64, ref), _class_err(gmx, ref)
+    # analytic derivatives of the seeded fields (interior particles)
+    inner = ((x > 10e-3) & (x < 116e-3) & (y > 10e-3) & (y < 116e-3) & (z > 10e-3) & (z < 116e-3))
+    ana = np.zeros((inner.sum(), 4, 9))
+    for f, (a, kv, ph) in enumerate(spec):
+        for k in range(len(a)):
+            arg = kv[k, 0] * x[inner] + kv[k, 1] * y[inner] + kv[k, 2] * z[inner] + ph[k]
+            c, s_ = np.cos(arg), np.sin(arg)
+            for q in range(3):
+                ana[:, f, q] += a[k] * kv[k, q] * c
+            pairs = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+            for q, (i1, i2) in enumerate(pairs):
+                ana[:, f, 3 + q] -= a[k] * kv[k, i1] * kv[k, i2] * s_
+    ea = _class_err(ref[inner], ana)
+    print(f"sweep 2,000,376: FP64 vs oracle {e64:.2e}, mixed vs oracle {emx:.2e}, "
+          f"oracle vs analytic {ea:.2e}")
+    assert e64 <= 1e-11, e64
+    assert emx <= 1e-5, emx
+
+
+def test_columns_smallest_four_match_oracle(dev, capi, orc):
+    """The batched workload's four smallest columns, advanced together on
+    the GPU (FP64 and float-float modes), against the oracle run column by
+    column (30 steps: inside the stable horizon at h = 1e-3)."""
+    full = W.columns()
+    sizes = np.diff(full.column_offsets)
+    four = sorted(np.argsort(sizes)[:4].tolist())
+    wl = W.columns(only=four)
+    pd = W.param_dict(wl)
+    mui_c = [dict(_dicts(pd)[0], mu_s=float(m)) for m in wl.mu_s_col]
+    offs = wl.column_offsets
+    refs = []
+    for c in range(4):
+        b, e = offs[c], offs[c + 1]
+        sc = {k: v[b:e] for k, v in wl.state.items()}
+        refs.append((sc, orc.step(sc, orc.params(**dict(pd, mu_s=float(wl.mu_s_col[c]))), 30,
+                                  brute=False)[0]))
+    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+        got, d = _run_gpu(capi, dev, wl, pd, 30, prec=prec, offsets=offs, mui=mui_c,
+                          launch_mode=1, stream=torch.cuda.Stream())
+        assert d["n_nonfinite"] == 0
+        for c in range(4):
+            b, e = offs[c], offs[c + 1]
+            err = _state_err({k: got[k][b:e] for k in got}, refs[c][1], refs[c][0])
+            assert max(err.values()) <= tol, (prec, c, err)
+
+
+@pytest.mark.slow
 def test_step_full_size_cylinder(dev, capi, orc):
     """The column of radius 0.02 m at spacing R/50 (785k particles), three FP64
     steps in the launch configuration the benchmark uses, against the oracle on
