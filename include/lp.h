@@ -55,8 +55,8 @@ typedef int32_t lp_status;
 #define LP_MIXED 1 /* FP32 moments and Cholesky + one FP64 refinement step     */
 #define LP_MIXED_FF 2 /* FP32 only on the stencil rows: offsets, moments and   */
                       /* right-hand sides accumulated as float-float (FP32     */
-                      /* pairs, error-free transformations), FP32 Cholesky and */
-                      /* two refinement steps on those normal equations; FP64  */
+                      /* pairs, error-free transformations), the Gram matrix   */
+                      /* factored and solved in float-float (Cholesky); FP64   */
                       /* per particle (derived values, closure, update) and in */
                       /* the pivoted-QR fallback. lp_step only.                */
 

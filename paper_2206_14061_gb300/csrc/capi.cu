@@ -105,7 +105,7 @@ struct lp_ctx {
   double** h_ptr = nullptr;  // pinned staging of d_ptr
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
   float4 *Xh = nullptr, *Xl = nullptr, *Uh = nullptr, *Ul = nullptr, *GVff = nullptr;
-  float* Gff = nullptr;      // float-float Gram matrices (LP_MIXED_FF)
+  float* Lff = nullptr;      // float-float Cholesky factors (LP_MIXED_FF)
   // Verlet candidate lists (lp_params.skin)
   int32_t* cand = nullptr;   // capc x n, k-major
   int32_t* ccnt = nullptr;
@@ -334,7 +334,7 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.p1 = c->p1; A.fbgrad = c->fbgrad; A.dg = c->dg;
   A.K = K;
   A.grids = c->d_grids;
-  A.Xh = c->Xh; A.Xl = c->Xl; A.Uh = c->Uh; A.Ul = c->Ul; A.GVff = c->GVff; A.Gff = c->Gff;
+  A.Xh = c->Xh; A.Xl = c->Xl; A.Uh = c->Uh; A.Ul = c->Ul; A.GVff = c->GVff; A.Lff = c->Lff;
   if (c->skin > 0.0) {
     A.xref = c->xref;
     const double hs = 0.5 * c->skin;
@@ -383,7 +383,7 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
   phase_mark(c, LP_PHASE_PASS2, true, st);
   launch_pass2(prec, A, st, c->bs_p2);
   phase_mark(c, LP_PHASE_PASS2, false, st);
-  c->launches += prec == LP_MIXED_FF ? 6 : 4;
+  c->launches += prec == LP_MIXED_FF ? 7 : 4;
   c->steps += 1;
   c->cx ^= 1;
 }
@@ -563,7 +563,7 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->Uh, n);
   if (s == LP_OK) s = dalloc(c, &c->Ul, n);
   if (s == LP_OK) s = dalloc(c, &c->GVff, n);
-  if (s == LP_OK) s = dalloc(c, &c->Gff, n * 2 * kTri);
+  if (s == LP_OK) s = dalloc(c, &c->Lff, n * 2 * kTri);
   c->capc = std::min(c->cap + 32, 96);
   if (s == LP_OK) s = dalloc(c, &c->cand, n * c->capc);
   if (s == LP_OK) s = dalloc(c, &c->ccnt, n);

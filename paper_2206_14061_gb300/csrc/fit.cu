@@ -49,10 +49,15 @@ __global__ void __launch_bounds__(64) k_pass2_fallback(const StepArgs A) {
     pass2_fallback_item(A, t);
 }
 
-// float-float passes: at most 128 threads per block and 3 blocks per SM
-// (170 registers), more warps per SM than the 255-register default
+// float-float kernels: 128 threads per block, at most 128 registers so that
+// 4 blocks (16 warps) share an SM
 constexpr int kFFBlock = 128;
-__global__ void __launch_bounds__(kFFBlock, 3) k_pass1_ff(const StepArgs A) {
+__global__ void __launch_bounds__(kFFBlock, 4) k_gram_ff(const StepArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) gram_ff_body(A, s);
+}
+
+__global__ void __launch_bounds__(kFFBlock, 4) k_pass1_ff(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < A.n) pass1_body<LP_MIXED_FF>(A, s);
 }
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_pass2(const StepArgs A) {
   pass2_body<PREC>(A, s, s < A.n);
 }
 
-__global__ void __launch_bounds__(kFFBlock, 3) k_pass2_ff(const StepArgs A) {
+__global__ void __launch_bounds__(kFFBlock, 5) k_pass2_ff(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   pass2_body<LP_MIXED_FF>(A, s, s < A.n);
 }
@@ -280,6 +285,7 @@ void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs) {
   } else {
     k_split_state<<<(A.n + 255) / 256, 256, 0, st>>>(A);
     const int b = bs < kFFBlock ? bs : kFFBlock;
+    k_gram_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
     k_pass1_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
   }
   k_pass1_fallback<<<152, 64, 0, st>>>(A);

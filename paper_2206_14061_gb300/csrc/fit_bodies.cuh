@@ -273,8 +273,10 @@ static __device__ __noinline__ void pass2_fallback_item(const StepArgs& A, int t
 // scaled and split once per particle and step (X = (x - origin)/h as hi + lo
 // floats, with the floor-mirror height in w), velocities likewise; each row's
 // offsets, Taylor terms, the 31 moments and the right-hand sides are carried as
-// float-float. The normal equations G c = A^T b are then solved with an FP32
-// Cholesky factor of hi(G) and refined twice on the float-float G and A^T b.
+// float-float. The Gram matrix is factored once per particle and step in
+// float-float (Cholesky, own kernel: positions and stencil only) and both
+// passes solve with that factor in float-float, so the coefficients carry
+// about 2^-44 cond(G) relative error, the accuracy of the float-float G.
 
 // scaled, split positions and velocities of the current state
 __device__ __forceinline__ void split_state_body(const StepArgs& A, int s) {
@@ -364,43 +366,105 @@ __device__ __forceinline__ void ff_gram(const ff* mo, ff* g) {
   g[tri(8, 6)] = mo[29];              g[tri(8, 7)] = mo[30];              g[tri(8, 8)] = mo[27];
 }
 
-// Solve G c = r: FP32 Cholesky solve, then two refinement steps with the
-// float-float residual r - G c. Returns c as doubles. Kept out of line with a
-// rolled iteration loop: one copy of its code serves every field of both
-// passes (the unrolled form stalled on instruction fetch).
-static __device__ __noinline__ void ff_refined_solve(const ff* G, const float* L, const ff* r,
-                                                 double* c_out) {
-  ff c[kNB];
+// In-place float-float Cholesky factor of a packed 9x9 Gram matrix (entries
+// normalised): the strictly lower entries become L and the diagonal 1/L_jj.
+// Same pivot test as chol9: the Schur complement of column j must stay above
+// rel_tol times the original diagonal entry, else the stencil is too
+// ill-conditioned for the normal equations.
+__device__ __forceinline__ bool ff_chol9(ff* a, float rel_tol) {
+  bool ok = true;
 #pragma unroll
-  for (int q = 0; q < kNB; ++q) c[q] = {0.f, 0.f};
-#pragma unroll 1
-  for (int it = 0; it < 3; ++it) {
-    float d[kNB];
+  for (int j = 0; j < kNB; ++j) {
+    ff d = a[tri(j, j)];
+    const float d0 = d.h;
 #pragma unroll
-    for (int q = 0; q < kNB; ++q) {
-      ff g = r[q];
-      if (it > 0) {
+    for (int k = 0; k < j; ++k) ff_acc(d, a[tri(j, k)], ff_neg(a[tri(j, k)]));
+    d = ff_norm(d);
+    const bool good = d.h > rel_tol * d0;
+    ok = ok && good;
+    const ff inv = good ? ff_rsqrt(d) : ff{0.f, 0.f};
+    a[tri(j, j)] = inv;
 #pragma unroll
-        for (int p = 0; p < kNB; ++p) {
-          const ff Gqp = q >= p ? G[tri(q, p)] : G[tri(p, q)];
-          ff_acc(g, Gqp, ff{-c[p].h, -c[p].l});
-        }
-      }
-      d[q] = __fadd_rn(g.h, g.l);
+    for (int i = j + 1; i < kNB; ++i) {
+      ff s = a[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) ff_acc(s, a[tri(i, k)], ff_neg(a[tri(j, k)]));
+      a[tri(i, j)] = ff_mul(ff_norm(s), inv);
     }
-    chol9_solve(L, d);
-#pragma unroll
-    for (int q = 0; q < kNB; ++q) c[q] = ff_add(c[q], ff{d[q], 0.f});
   }
-#pragma unroll
-  for (int q = 0; q < kNB; ++q) c_out[q] = ff_to_double(c[q]);
+  return ok;
 }
 
-__device__ __forceinline__ void pass1_finish(const StepArgs& A, int s, const double (*c)[kNB]);
-__device__ __forceinline__ void push_fallback(const StepArgs& A, int s);
+// Solve L L^T c = r for NF right-hand sides at once with the factor that
+// gram_ff_body stored for particle s; each factor entry is loaded once per
+// sweep and used for every right-hand side. r (unnormalised accumulators on
+// entry) is overwritten by c.
+template <int NF>
+__device__ __forceinline__ void ff_chol_solve(const StepArgs& A, int s, ff (*r)[kNB]) {
+  const int64_t n = A.n;
+  const float* Lh = A.Lff + s;
+  const float* Ll = A.Lff + (int64_t)kTri * n + s;
+#pragma unroll
+  for (int i = 0; i < kNB; ++i) {
+#pragma unroll
+    for (int k = 0; k < i; ++k) {
+      const ff l = {Lh[tri(i, k) * n], Ll[tri(i, k) * n]};
+#pragma unroll
+      for (int f = 0; f < NF; ++f) ff_acc(r[f][i], l, ff_neg(r[f][k]));
+    }
+    const ff inv = {Lh[tri(i, i) * n], Ll[tri(i, i) * n]};
+#pragma unroll
+    for (int f = 0; f < NF; ++f) r[f][i] = ff_mul(ff_norm(r[f][i]), inv);
+  }
+#pragma unroll
+  for (int i = kNB - 1; i >= 0; --i) {
+#pragma unroll
+    for (int k = i + 1; k < kNB; ++k) {
+      const ff l = {Lh[tri(k, i) * n], Ll[tri(k, i) * n]};
+#pragma unroll
+      for (int f = 0; f < NF; ++f) ff_acc(r[f][i], l, ff_neg(r[f][k]));
+    }
+    const ff inv = {Lh[tri(i, i) * n], Ll[tri(i, i) * n]};
+#pragma unroll
+    for (int f = 0; f < NF; ++f) r[f][i] = ff_mul(ff_norm(r[f][i]), inv);
+  }
+}
 
-// pass 1 in float-float: fits of u, v, w
+// Gram matrix of a stencil in float-float (positions only): the 31 moments,
+// the Cholesky factor with the pivot test, stored for both passes. Stencils
+// that fail the test (or have fewer than 9 rows) are queued for the
+// pivoted-QR fit.
+__device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
+  const int n = A.n;
+  const int m = min(A.cnt[s], A.cap);
+  const float4 hi = A.Xh[s], lo = A.Xl[s];
+  ff mo[31];
+#pragma unroll
+  for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+  for (int k = 0; k < m; ++k) {
+    const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
+    ff_moments_add(mo, ff_row(A, s, hi, lo, code));
+  }
+  ff G[kTri];
+  ff_gram(mo, G);
+#pragma unroll
+  for (int k = 0; k < kTri; ++k) G[k] = ff_norm(G[k]);
+  const bool ok = ff_chol9(G, 1e-4f) && m >= kNB;
+  if (!ok) {
+    push_fallback(A, s);
+    return;
+  }
+  A.fbslot[s] = -1;
+#pragma unroll
+  for (int k = 0; k < kTri; ++k) {
+    A.Lff[(int64_t)k * n + s] = G[k].h;
+    A.Lff[(int64_t)(kTri + k) * n + s] = G[k].l;
+  }
+}
+
+// pass 1 in float-float: right-hand sides of u, v, w and the solves
 __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
+  if (A.fbslot[s] != -1) return;  // queued for the pivoted-QR fit
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);
   const float4 hi = A.Xh[s], lo = A.Xl[s];
@@ -408,9 +472,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   const int mm = A.K.mirror_mode;
   const float sg[3] = {mm == LP_MIRROR_NOSLIP ? -1.f : 1.f, mm == LP_MIRROR_NOSLIP ? -1.f : 1.f,
                        mm != LP_MIRROR_NONE ? -1.f : 1.f};
-  ff mo[31], R[3][kNB];
-#pragma unroll
-  for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+  ff R[3][kNB];
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -418,7 +480,6 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
     const FFRow r = ff_row(A, s, hi, lo, code);
-    ff_moments_add(mo, r);
     ff a[kNB];
     ff_taylor(r, a);
     const int j = code & ~kMirrorBit;
@@ -435,33 +496,12 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
       for (int q = 0; q < kNB; ++q) ff_acc(R[f][q], b, a[q]);
     }
   }
-  ff G[kTri];
-  ff_gram(mo, G);
-  float L[kTri];
-#pragma unroll
-  for (int k = 0; k < kTri; ++k) {
-    G[k] = ff_norm(G[k]);
-    L[k] = G[k].h;
-  }
-  const bool ok = chol9(L, 1e-4f) && m >= kNB;
-  if (!ok) {
-    push_fallback(A, s);
-    return;
-  }
-  A.fbslot[s] = -1;
-#pragma unroll
-  for (int k = 0; k < kTri; ++k) {
-    A.Gff[(int64_t)k * n + s] = G[k].h;
-    A.Gff[(int64_t)(kTri + k) * n + s] = G[k].l;
-  }
+  ff_chol_solve<3>(A, s, R);
   double c[3][kNB];
 #pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    ff r[kNB];
+  for (int f = 0; f < 3; ++f)
 #pragma unroll
-    for (int q = 0; q < kNB; ++q) r[q] = ff_norm(R[f][q]);
-    ff_refined_solve(G, L, r, c[f]);
-  }
+    for (int q = 0; q < kNB; ++q) c[f][q] = ff_to_double(R[f][q]);
   pass1_finish(A, s, c);
 }
 
@@ -493,27 +533,13 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
       ff_acc(R[1][q], bv, a[q]);
     }
   }
-  ff G[kTri];
-  float L[kTri];
-#pragma unroll
-  for (int k = 0; k < kTri; ++k) {
-    G[k] = {A.Gff[(int64_t)k * n + s], A.Gff[(int64_t)(kTri + k) * n + s]};
-    L[k] = G[k].h;
-  }
-  chol9(L, 0.f);  // succeeded in pass 1 on the same matrix
+  ff_chol_solve<2>(A, s, R);
   const double ih = A.K.inv_h;
-  double c[kNB];
-  ff r[kNB];
 #pragma unroll
-  for (int q = 0; q < kNB; ++q) r[q] = ff_norm(R[0][q]);
-  ff_refined_solve(G, L, r, c);
-#pragma unroll
-  for (int q = 0; q < 3; ++q) gg[q] = c[q] * ih;
-#pragma unroll
-  for (int q = 0; q < kNB; ++q) r[q] = ff_norm(R[1][q]);
-  ff_refined_solve(G, L, r, c);
-#pragma unroll
-  for (int q = 0; q < 3; ++q) gV[q] = c[q] * ih;
+  for (int q = 0; q < 3; ++q) {
+    gg[q] = ff_to_double(R[0][q]) * ih;
+    gV[q] = ff_to_double(R[1][q]) * ih;
+  }
 }
 
 // ------------------------------------------------------------ pass 2

@@ -104,6 +104,17 @@ __device__ __forceinline__ void ff_acc1(ff& acc, ff a) {
   acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, a.l));
 }
 __device__ __forceinline__ ff ff_norm(ff a) { return fast_two_sum(a.h, a.l); }
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+// 1/sqrt(d) in float-float: the correctly rounded FP32 value refined by one
+// Newton-Raphson step y + (y/2)(1 - d y^2), whose residual is formed exactly
+// enough in float-float (y^2 is split exactly with an FMA).
+__device__ __forceinline__ ff ff_rsqrt(ff d) {
+  const float y = __frsqrt_rn(d.h);
+  const float p = __fmul_rn(y, y);
+  const ff t = ff_mul(d, ff{p, __fmaf_rn(y, y, -p)});
+  const float delta = __fsub_rn(__fsub_rn(1.f, t.h), t.l);
+  return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), delta));
+}
 __device__ __forceinline__ ff ff_of(double d) {
   const float h = __double2float_rn(d);
   return {h, __double2float_rn(d - (double)h)};
@@ -153,7 +164,8 @@ struct StepArgs {
   // |gdot| and V^{n+1} split (hi, lo, hi, lo), Gram matrices in float-float
   const GridCol* grids;
   float4 *Xh, *Xl, *Uh, *Ul, *GVff;
-  float* Gff;       // 90 * n: hi (45) then lo (45), k-major
+  float* Lff;       // 90 * n: float-float Cholesky factor of the Gram matrix,
+                    // hi (45) then lo (45), k-major; the diagonal holds 1/L_jj
   // Verlet candidate lists: positions at the last search and the flag that
   // requests a new search when a particle has moved more than skin/2
   const double* xref;  // 3 * n, or NULL when candidate lists are off

@@ -130,6 +130,10 @@ __global__ void __launch_bounds__(kBlock) k_step_persistent(const PersistArgs P)
   if (PREC == LP_MIXED_FF)
     for (int s = tid; s < n; s += nth) split_state_body(S, s);
   LP_SYNC_OR_LEAVE();
+  if (PREC == LP_MIXED_FF) {
+    for (int s = tid; s < n; s += nth) gram_ff_body(S, s);
+    LP_SYNC_OR_LEAVE();
+  }
   for (int s = tid; s < n; s += nth) pass1_body<PREC>(S, s);
   LP_SYNC_OR_LEAVE();
   const int nfb = min(*S.fb_count, S.fb_cap);
