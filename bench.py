@@ -120,42 +120,56 @@ def _peaks():
         return {}
 
 
-def _traffic(kernel_key: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel (else None)."""
+KERNEL_SOURCES = ("fit.cu", "fit_bodies.cuh", "lp_internal.cuh")
+
+
+def kernel_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the fit kernels' sources."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2206_14061_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(key: str):
+    """DRAM bytes (read + write) per launch of the roofline kernels from a
+    committed ncu summary, if it was taken on the current kernel sources
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        t = json.load(open(path))[kernel_key]
+        t = json.load(open(path))[key]
     except (OSError, ValueError, KeyError):
         return None
-    src = os.path.join(ROOT, "paper_2206_14061_gb300", "csrc", "fit.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if t.get("fit_cu_sha256_16") != h:
+    if t.get("src_sha256_16") != kernel_source_hash():
         return None
     return t.get("bytes_per_launch_full")
 
 
 PREC = {"fp64": 0, "mixed": 1, "mixed_ff": 2}
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate
-FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TOPS = 40.27    # 152 SMs x 128 FP32 lanes x 2.07 GHz, one op per lane and cycle
 
 
-def pass1_flops(prec: str, rows: float, n: int) -> float:
-    """Algorithmic FP64 flops of one pass-1 launch (FMA = 2 flops).
+def pass1_work(prec: str, rows: float, n: int):
+    """Algorithmic arithmetic of one pass-1 phase and the peak it runs against.
 
-    FP64: per stencil row 6 (offsets) + 6 (quadratic terms) + 62 (31 moments)
-    + 3 (differences) + 54 (3 right-hand sides x 9) = 131; per particle about
-    1000 (9x9 Cholesky, three solves, derived quantities).
-    MIXED (FP64 part only; the FP32 moments run on the FP32 pipe): per row 6 +
-    9 + 3 + 54 (residual) + 54 (A^T r) = 126; per particle about 550."""
-    if prec == "fp64":
-        return 131.0 * rows + 1000.0 * n
+    FP64 (flops, FMA = 2): per stencil row 6 (offsets) + 6 (quadratic terms) +
+    62 (31 moments) + 3 (differences) + 54 (3 right-hand sides x 9) = 131; per
+    particle about 1000 (9x9 Cholesky, three solves, derived quantities).
+    MIXED (FP64 flops only; the FP32 moments run on the FP32 pipe): per row 6 +
+    9 + 3 + 54 (residual) + 54 (A^T r) = 126; per particle about 550.
+    MIXED_FF (FP32 lane operations: every FP32 add, multiply or FMA is one op,
+    since float-float arithmetic is mostly additions): per row 75 (float-float
+    offsets and quadratic terms) + 6 (Taylor scaling) + 348 (31 moments) +
+    363 (3 right-hand sides) = 792, counted once although both fit kernels
+    form the row; per particle 183 (Gram matrix) + 2016 (float-float Cholesky)
+    + 3132 (three float-float solves) = 5331."""
     if prec == "mixed_ff":
-        # FP32 flops: per row 33 (float-float offsets) + 60 (quadratic terms) +
-        # 423 (31 moments) + 438 (3 right-hand sides) = 954; per particle about
-        # 11,500 (three solves with two float-float refinements per field)
-        return 954.0 * rows + 11500.0 * n
-    return 126.0 * rows + 550.0 * n
+        return (792.0 * rows + 5331.0 * n, "T FP32 lane-ops/s", FP32_PEAK_TOPS,
+                "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz")
+    flops = 131.0 * rows + 1000.0 * n if prec == "fp64" else 126.0 * rows + 550.0 * n
+    return (flops, "TFLOP/s (FP64)", FP64_PEAK_TFLOPS,
+            "nominal FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)")
 
 
 def our_arm(args):
@@ -244,20 +258,16 @@ def our_arm(args):
     peaks = _peaks()
     per_phase = {k: v / max(prof["steps"], 1) for k, v in prof["ms"].items()}
     dom = max(per_phase, key=per_phase.get)
-    ff = args.precision == "mixed_ff"
-    peak = FP32_PEAK_TFLOPS if ff else FP64_PEAK_TFLOPS
-    punit = "TFLOP/s (FP32)" if ff else "TFLOP/s (FP64)"
-    psrc = ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if ff
-            else "nominal FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)")
-    roof = {"kernel": {"pass1": "k_pass1", "pass2": "k_pass2", "neighbors": "k_neighbors",
+    work, punit, peak, psrc = pass1_work(args.precision, mean_m * n, n)
+    kname = "k_gram_ff + k_pass1_ff" if args.precision == "mixed_ff" else "k_pass1"
+    roof = {"kernel": {"pass1": kname, "pass2": "k_pass2", "neighbors": "k_neighbors",
                        "sort": "sort kernels"}[dom]}
     if dom == "pass1":
-        flops = pass1_flops(args.precision, mean_m * n, n)
-        ach = flops / (per_phase["pass1"] / 1e3) / 1e12
+        ach = work / (per_phase["pass1"] / 1e3) / 1e12
         roof.update(bound="alu", achieved=ach, peak=peak, unit=punit,
                     frac=ach / peak, peak_source=psrc,
-                    flops_per_launch=flops, ms_per_launch=per_phase["pass1"],
-                    traffic=_traffic(f"k_pass1_{args.precision}"))
+                    work_per_launch=work, ms_per_launch=per_phase["pass1"],
+                    traffic=_traffic(f"pass1_{args.precision}"))
     else:
         roof.update(bound="alu", achieved=None, peak=peak, unit=punit,
                     frac=None, ms_per_launch=per_phase[dom], traffic=None)
@@ -291,15 +301,16 @@ def our_arm(args):
     }
 
     if not args.no_fp64:
-        for other in ("fp64", "mixed"):
+        for other in ("fp64", "mixed", "mixed_ff"):
             if other == args.precision:
                 continue
             mso, _, _, _, profo, _ = bench(other)
             pho = {k: v / max(profo["steps"], 1) for k, v in profo["ms"].items()}
-            flo = pass1_flops(other, mean_m * n, n)
+            wo, uo, po, _ = pass1_work(other, mean_m * n, n)
             line[other] = {"value": n * args.steps * world / (mso / 1e3),
                            "ms_per_step": mso / args.steps, "phase_ms_per_step": pho,
-                           "pass1_fp64_tflops": flo / (pho["pass1"] / 1e3) / 1e12}
+                           "pass1_achieved": wo / (pho["pass1"] / 1e3) / 1e12,
+                           "pass1_unit": uo, "pass1_frac": wo / (pho["pass1"] / 1e3) / 1e12 / po}
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world)

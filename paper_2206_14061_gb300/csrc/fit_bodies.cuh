@@ -308,12 +308,17 @@ __device__ __forceinline__ ff ff_diff(float jh, float jl, float ih_, float il) {
 struct FFRow {
   ff dx, dy, dz, qxx, qyy, qzz, qxy, qxz, qyz;
 };
-__device__ __forceinline__ FFRow ff_row(const StepArgs& A, int s, const float4& hi,
-                                        const float4& lo, uint32_t code) {
+// split position of the neighbour named by a stencil code
+__device__ __forceinline__ void ff_gather(const StepArgs& A, int s, uint32_t code, float4& jh,
+                                          float4& jl) {
   int j = code & ~kMirrorBit;
   if ((unsigned)j >= (unsigned)A.n) j = s;  // never read outside the arrays (zero row)
+  jh = A.Xh[j];
+  jl = A.Xl[j];
+}
+__device__ __forceinline__ FFRow ff_row_of(const float4& hi, const float4& lo, const float4& jh,
+                                           const float4& jl, uint32_t code) {
   const bool mir = code >> 31;
-  const float4 jh = A.Xh[j], jl = A.Xl[j];
   FFRow r;
   r.dx = ff_diff(jh.x, jl.x, hi.x, lo.x);
   r.dy = ff_diff(jh.y, jl.y, hi.y, lo.y);
@@ -441,9 +446,22 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
   ff mo[31];
 #pragma unroll
   for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+  // software pipeline: stencil codes are loaded two rows ahead and the
+  // neighbour's values one row ahead, so the dependent loads of a row
+  // overlap the arithmetic of the previous one (same in both passes)
+  uint32_t code = m > 0 ? (uint32_t)A.nbr[s] : 0u;
+  uint32_t nxt = m > 1 ? (uint32_t)A.nbr[(int64_t)n + s] : 0u;
+  float4 jh = make_float4(0.f, 0.f, 0.f, 0.f), jl = jh;
+  if (m > 0) ff_gather(A, s, code, jh, jl);
   for (int k = 0; k < m; ++k) {
-    const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-    ff_moments_add(mo, ff_row(A, s, hi, lo, code));
+    const uint32_t c0 = code;
+    const float4 h0 = jh, l0 = jl;
+    if (k + 1 < m) {
+      code = nxt;
+      ff_gather(A, s, code, jh, jl);
+      if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
+    }
+    ff_moments_add(mo, ff_row_of(hi, lo, h0, l0, c0));
   }
   ff G[kTri];
   ff_gram(mo, G);
@@ -477,15 +495,30 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   for (int f = 0; f < 3; ++f)
 #pragma unroll
     for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+  uint32_t code = m > 0 ? (uint32_t)A.nbr[s] : 0u;
+  uint32_t nxt = m > 1 ? (uint32_t)A.nbr[(int64_t)n + s] : 0u;
+  float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh, vh = xh, vl = xh;
+  if (m > 0) {
+    ff_gather(A, s, code, xh, xl);
+    const unsigned jj = min((unsigned)(code & ~kMirrorBit), (unsigned)(n - 1));
+    vh = A.Uh[jj]; vl = A.Ul[jj];
+  }
   for (int k = 0; k < m; ++k) {
-    const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-    const FFRow r = ff_row(A, s, hi, lo, code);
+    const uint32_t c0 = code;
+    const float4 h0 = xh, l0 = xl, jh = vh, jl = vl;
+    if (k + 1 < m) {
+      code = nxt;
+      ff_gather(A, s, code, xh, xl);
+      const unsigned jj = min((unsigned)(code & ~kMirrorBit), (unsigned)(n - 1));
+      vh = A.Uh[jj]; vl = A.Ul[jj];
+      if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
+    }
+    const FFRow r = ff_row_of(hi, lo, h0, l0, c0);
     ff a[kNB];
     ff_taylor(r, a);
-    const int j = code & ~kMirrorBit;
+    const int j = c0 & ~kMirrorBit;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
-    const bool mir = code >> 31;
-    const float4 jh = A.Uh[j], jl = A.Ul[j];
+    const bool mir = c0 >> 31;
     const float ujh[3] = {jh.x, jh.y, jh.z}, ujl[3] = {jl.x, jl.y, jl.z};
     const float uih[3] = {uh.x, uh.y, uh.z}, uil[3] = {ul.x, ul.y, ul.z};
 #pragma unroll
@@ -516,15 +549,28 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
   for (int f = 0; f < 2; ++f)
 #pragma unroll
     for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+  uint32_t code = m > 0 ? (uint32_t)A.nbr[s] : 0u;
+  uint32_t nxt = m > 1 ? (uint32_t)A.nbr[(int64_t)n + s] : 0u;
+  float4 jh = make_float4(0.f, 0.f, 0.f, 0.f), jl = jh, jg = jh;
+  if (m > 0) {
+    ff_gather(A, s, code, jh, jl);
+    jg = A.GVff[min((unsigned)(code & ~kMirrorBit), (unsigned)(n - 1))];
+  }
   for (int k = 0; k < m; ++k) {
-    const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-    const FFRow r = ff_row(A, s, hi, lo, code);
+    const uint32_t c0 = code;
+    const float4 h0 = jh, l0 = jl, gvj = jg;
+    if (k + 1 < m) {
+      code = nxt;
+      ff_gather(A, s, code, jh, jl);
+      jg = A.GVff[min((unsigned)(code & ~kMirrorBit), (unsigned)(n - 1))];
+      if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
+    }
+    const FFRow r = ff_row_of(hi, lo, h0, l0, c0);
     ff a[kNB];
     ff_taylor(r, a);
-    const int j = code & ~kMirrorBit;
+    const int j = c0 & ~kMirrorBit;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
-    const bool mir = code >> 31;
-    const float4 gvj = A.GVff[j];
+    const bool mir = c0 >> 31;
     const ff bg = mir ? ff{-gvi.x, -gvi.y} : ff_diff(gvj.x, gvj.y, gvi.x, gvi.y);
     const ff bv = ff_diff(gvj.z, gvj.w, gvi.z, gvi.w);
 #pragma unroll
