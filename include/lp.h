@@ -127,7 +127,7 @@ typedef struct {
   double gx, gy, gz;  /* body force (m/s^2)                                     */
   double floor_z;     /* height of the floor plane for mirrors                  */
   int32_t mirror_mode;   /* LP_MIRROR_*                                         */
-  int32_t precision;     /* LP_FP64 or LP_MIXED                                 */
+  int32_t precision;     /* LP_FP64, LP_MIXED or LP_MIXED_FF                    */
   int32_t rebuild_every; /* rebuild stencils every k steps (1 = every step)     */
   int32_t launch_mode;   /* LP_LAUNCH_*                                         */
   double skin;           /* > 0 (with rebuild_every == 1): Verlet candidate lists.
@@ -136,7 +136,8 @@ typedef struct {
                           * radius test (same stencils as a full search); a new
                           * search runs once some particle has moved more than
                           * skin/2 since the last one. 0: full search every step.
-                          * Not used by LP_LAUNCH_PERSISTENT.                      */
+                          * All launch modes; the persistent launch takes the
+                          * search branch inside the kernel.                      */
 } lp_params;
 
 /* Stencils produced by lp_build_neighbors: library-owned device memory, valid

@@ -415,6 +415,13 @@ lp_status run_step_persistent(lp_ctx* c, int n, const StepConsts& K, int prec, b
     P.pf = c->pf;
     P.radius = K.radius; P.floor_z = K.floor_z; P.mirror_mode = K.mirror_mode; P.cap = c->cap;
     P.nbr = c->nbr; P.cnt = c->cnt;
+    if (c->skin > 0.0) {
+      P.search = c->d_search;
+      P.iota = c->iota;
+      P.cand = c->cand; P.ccnt = c->ccnt; P.capc = c->capc;
+      P.rsearch = K.radius + c->skin;
+      P.xref = c->xref;
+    }
     c->cx ^= 1;  // the gather fills the other buffer
     c->ci ^= 1;
   }
@@ -875,10 +882,7 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   LP_TRY(load_state(c, p, mui, st));
   const int d = c->cx;
   // Verlet candidate lists: the grid must hold radius + skin in one cell
-  const double skin = (q->skin > 0.0 && q->rebuild_every == 1 &&
-                       q->launch_mode != LP_LAUNCH_PERSISTENT)
-                          ? q->skin
-                          : 0.0;
+  const double skin = (q->skin > 0.0 && q->rebuild_every == 1) ? q->skin : 0.0;
   LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
   LP_TRY(setup_grids(c, p->ncolumns, q->radius + skin, st));
   if (skin > 0.0) {

@@ -209,6 +209,15 @@ struct PersistArgs {
   double radius, floor_z;
   int mirror_mode, cap;
   int32_t *nbr, *cnt;
+  // Verlet candidate lists (search != nullptr): the sort and a search within
+  // radius + skin run only when *search is set, the exact filter every
+  // rebuild step; otherwise the gather is the identity (iota)
+  int* search;
+  const int32_t* iota;
+  int32_t *cand, *ccnt;
+  int capc;
+  double rsearch;
+  double* xref;
   // barrier: [0] arrivals, [1] generation
   unsigned* bar;
   unsigned long long max_spins;

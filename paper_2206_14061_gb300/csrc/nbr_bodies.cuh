@@ -130,7 +130,10 @@ __device__ __forceinline__ bool cand_less(double da, uint32_t ka, double db, uin
   return ka < kb;  // ka = (orig id << 1) | mirror
 }
 
+__device__ __forceinline__ void stencil_stats(bool live, int c, int cap, DevDiag* dg);
+
 // Stencil of particle s; every lane of the warp must call it (live or not).
+// stats = false leaves the stencil-size statistics alone (candidate lists).
 template <bool KEEP>
 __device__ __forceinline__ void neighbors_body(
     int s, bool live, int n, const double* __restrict__ x, const double* __restrict__ y,
@@ -138,7 +141,8 @@ __device__ __forceinline__ void neighbors_body(
     const int32_t* __restrict__ colid, const int32_t* __restrict__ ids,
     const GridCol* __restrict__ grids, const uint32_t* __restrict__ start,
     const double* __restrict__ radius, double r_const, int mirror_mode, double floor_z, int cap,
-    int32_t* __restrict__ nbr, int32_t* __restrict__ cnt, DevDiag* __restrict__ dg) {
+    int32_t* __restrict__ nbr, int32_t* __restrict__ cnt, DevDiag* __restrict__ dg,
+    bool stats = true) {
   int c = 0;
   bool over = false;
   if (live) {
@@ -230,6 +234,13 @@ __device__ __forceinline__ void neighbors_body(
     cnt[s] = c;
   }
   warp_count(&dg->n_overflow, live && over);
+  if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
+  if (stats) stencil_stats(live, c, cap, dg);
+}
+
+// Stencil size statistics of one warp (every lane calls it): total rows,
+// stencils, smallest and largest stencil.
+__device__ __forceinline__ void stencil_stats(bool live, int c, int cap, DevDiag* dg) {
   {
     // total stencil rows and stencils (warp-reduced)
     unsigned long long rows = live ? (unsigned long long)min(c, cap) : 0ull;
@@ -240,7 +251,6 @@ __device__ __forceinline__ void neighbors_body(
       atomicAdd(&dg->n_stencils, (unsigned long long)live_n);
     }
   }
-  if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
   // stencil size range (warp-reduced)
   int mn = live ? c : INT32_MAX, mx = live ? c : 0;
   for (int o = 16; o > 0; o >>= 1) {
@@ -251,6 +261,73 @@ __device__ __forceinline__ void neighbors_body(
     if (mn != INT32_MAX) atomicMin(&dg->min_stencil, mn);
     atomicMax(&dg->max_stencil, mx);
   }
+}
+
+// Verlet filter of particle s: the stencil of this step is every candidate
+// (found within radius + skin at the last search) that passes the exact
+// radius test, in candidate order. Same FP32 prefilter and uncontracted FP64
+// test as the search. Every lane of the warp must call it (live or not).
+__device__ __forceinline__ void filter_body(
+    int s, bool live, int n, const double* __restrict__ x, const double* __restrict__ y,
+    const double* __restrict__ z, const float4* __restrict__ pf,
+    const int32_t* __restrict__ cand, const int32_t* __restrict__ ccnt, int capc,
+    const GridCol* __restrict__ grids, const int32_t* __restrict__ colid, double r,
+    double floor_z, int cap, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt,
+    DevDiag* __restrict__ dg) {
+  int c = 0;
+  bool over = false;
+  if (live) {
+    const GridCol g = grids[colid[s]];
+    const double xi = x[s], yi = y[s], zi = z[s];
+    const double r2 = r * r;
+    const float r2f = __double2float_rn(r2);
+    const float4 pi = pf[s];
+    const float fz2 = __double2float_rn(2.0 * (floor_z - g.oz));
+    // FP32 prefilter band, as in neighbors_body
+    const float rf = __double2float_rn(r);
+    const float L = (4.0f * fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))) +
+                     4.0f * rf) / rf;
+    const float band = (1.0f + L) * 0x1p-19f;
+    const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
+    const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
+    const int m = min(ccnt[s], capc);
+    // software pipeline: candidate codes two ahead, their positions one ahead
+    uint32_t nc = m > 0 ? (uint32_t)cand[s] : 0u;
+    uint32_t nn = m > 1 ? (uint32_t)cand[(int64_t)n + s] : 0u;
+    float4 np = m > 0 ? pf[min(nc & ~kMirrorBit, (uint32_t)(n - 1))] : pi;
+    for (int k = 0; k < m; ++k) {
+      const uint32_t code = nc;
+      const float4 pj = np;
+      if (k + 1 < m) {
+        nc = nn;
+        np = pf[min(nc & ~kMirrorBit, (uint32_t)(n - 1))];
+        if (k + 2 < m) nn = (uint32_t)cand[(int64_t)(k + 2) * n + s];
+      }
+      const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
+      const bool mir = code >> 31;
+      const float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
+      const float dzf = (mir ? fz2 - pj.z : pj.z) - pi.z;
+      const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+      if (!exact_only && d2f > hi) continue;
+      bool in;
+      if (!exact_only && d2f < lo) {
+        in = true;
+      } else {
+        double d2;
+        const double zj = mir ? __dsub_rn(2.0 * floor_z, z[j]) : z[j];
+        in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2);
+      }
+      if (!in) continue;
+      if (c < cap) nbr[(int64_t)c * n + s] = (int32_t)code;
+      ++c;
+    }
+    over = c > cap || ccnt[s] > capc;
+    cnt[s] = c;
+  }
+  warp_count(&dg->n_overflow, live && over);
+  if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
+  stencil_stats(live, c, cap, dg);
 }
 
 }  // namespace lp

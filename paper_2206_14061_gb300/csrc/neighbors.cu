@@ -209,14 +209,11 @@ k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
     xref[2 * n + s] = z[s];
   }
   neighbors_body<KEEP>(s, s < n, n, x, y, z, pf, colid, ids, grids, start, radius, r_const,
-                       mirror_mode, floor_z, cap, nbr, cnt, dg);
+                       mirror_mode, floor_z, cap, nbr, cnt, dg, xref == nullptr);
 }
 
-// Verlet filter: the stencil of this step is every candidate (found within
-// radius + skin at the last search) that passes the exact radius test, in
-// candidate order. Same FP32 prefilter and uncontracted FP64 test as the
-// search. Thread 0 clears the search flag for the displacement test of this
-// step's update.
+// Verlet filter (filter_body). Thread 0 clears the search flag for the
+// displacement test of this step's update.
 __global__ void __launch_bounds__(kMaxBlock)
 k_filter(int n, const double* __restrict__ x, const double* __restrict__ y,
          const double* __restrict__ z, const float4* __restrict__ pf,
@@ -225,69 +222,9 @@ k_filter(int n, const double* __restrict__ x, const double* __restrict__ y,
          double floor_z, int cap, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt,
          DevDiag* __restrict__ dg, int* search) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = s < n;
   if (s == 0) *search = 0;
-  int c = 0;
-  bool over = false;
-  if (live) {
-    const GridCol g = grids[colid[s]];
-    const double xi = x[s], yi = y[s], zi = z[s];
-    const double r2 = r * r;
-    const float r2f = __double2float_rn(r2);
-    const float4 pi = pf[s];
-    const float fz2 = __double2float_rn(2.0 * (floor_z - g.oz));
-    // FP32 prefilter band. Coordinates are origin-relative floats with error
-    // <= 2^-24 |coordinate|; for a pair near the sphere the squared-distance
-    // error is below about (4 L + 2) 2^-23 r^2 with L the largest coordinate
-    // (mirror height included) over r. Pairs inside the band take the FP64 test.
-    const float rf = __double2float_rn(r);
-    const float L = (4.0f * fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))) +
-                     4.0f * rf) / rf;
-    const float band = (1.0f + L) * 0x1p-19f;
-    const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
-    const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
-    const int m = min(ccnt[s], capc);
-    for (int k = 0; k < m; ++k) {
-      const uint32_t code = (uint32_t)cand[(int64_t)k * n + s];
-      const int j = code & ~kMirrorBit;
-      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
-      const bool mir = code >> 31;
-      const float4 pj = pf[j];
-      const float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
-      const float dzf = (mir ? fz2 - pj.z : pj.z) - pi.z;
-      const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
-      if (!exact_only && d2f > hi) continue;
-      bool in;
-      if (!exact_only && d2f < lo) {
-        in = true;
-      } else {
-        double d2;
-        const double zj = mir ? __dsub_rn(2.0 * floor_z, z[j]) : z[j];
-        in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2);
-      }
-      if (!in) continue;
-      if (c < cap) nbr[(int64_t)c * n + s] = (int32_t)code;
-      ++c;
-    }
-    over = c > cap || ccnt[s] > capc;
-    cnt[s] = c;
-  }
-  warp_count(&dg->n_overflow, live && over);
-  if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
-  unsigned long long rows = live ? (unsigned long long)min(c, cap) : 0ull;
-  for (int o = 16; o > 0; o >>= 1) rows += __shfl_xor_sync(0xffffffffu, rows, o);
-  const unsigned live_n = __popc(__ballot_sync(0xffffffffu, live));
-  int mn = live ? c : INT32_MAX, mx = live ? c : 0;
-  for (int o = 16; o > 0; o >>= 1) {
-    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  }
-  if ((threadIdx.x & 31) == 0 && live_n) {
-    atomicAdd(&dg->n_stencil_rows, rows);
-    atomicAdd(&dg->n_stencils, (unsigned long long)live_n);
-    atomicMin(&dg->min_stencil, mn);
-    atomicMax(&dg->max_stencil, mx);
-  }
+  filter_body(s, s < n, n, x, y, z, pf, cand, ccnt, capc, grids, colid, r, floor_z, cap, nbr,
+              cnt, dg);
 }
 
 // Stencils from sorted indices to caller indices.

@@ -54,13 +54,22 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long max_
     if (!grid_sync(P.bar, P.max_spins, P.extra_arrivals, P.S.dg)) return; \
   } while (0)
 
+// float-float: at most 128 registers (4 blocks per SM), as the per-phase
+// float-float kernels; FP64 and MIXED at 3 blocks per SM (168 registers),
+// where their bodies do not spill much
 template <int PREC>
-__global__ void __launch_bounds__(kBlock) k_step_persistent(const PersistArgs P) {
+__global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
+    k_step_persistent(const PersistArgs P) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const int n = P.n;
   const StepArgs& S = P.S;
-  if (P.rebuild) {
+  // The search flag is read before the first barrier and cleared only by the
+  // filter phase, after several barriers, so every block takes the same
+  // branch. Without candidate lists every rebuild searches.
+  const bool skin = P.search != nullptr;
+  const bool srch = P.rebuild && (!skin || *(volatile int*)P.search != 0);
+  if (srch) {
     // cell counts and fill counters start at zero
     for (int64_t i = tid; i < 2 * (P.ncell + 2); i += nth) {
       if (i < P.ncell + 2) P.count[i] = 0u;
@@ -114,16 +123,41 @@ __global__ void __launch_bounds__(kBlock) k_step_persistent(const PersistArgs P)
     LP_SYNC_OR_LEAVE();
     for (int64_t c = tid; c < P.ncell; c += nth) cell_sort_body(c, P.start, P.tmp, P.ids_in);
     LP_SYNC_OR_LEAVE();
+  }
+  if (P.rebuild) {
     for (int t = tid; t < n; t += nth)
-      gather_body(t, n, P.tmp, P.src, P.dst, P.nsrc, P.ids_in, P.ids_out, P.colid_in,
-                  P.colid_out, P.grids, P.pf);
+      gather_body(t, n, srch ? P.tmp : P.iota, P.src, P.dst, P.nsrc, P.ids_in, P.ids_out,
+                  P.colid_in, P.colid_out, P.grids, P.pf);
     LP_SYNC_OR_LEAVE();
+  }
+  if (srch) {
     // every lane of a warp runs the same number of rounds (warp-wide reductions)
     for (int base = 0; base < n; base += nth) {
       const int s = base + tid;
-      neighbors_body<false>(s, s < n, n, S.x, S.y, S.z, P.pf, S.colid, P.ids_out, P.grids,
-                            P.start, nullptr, P.radius, P.mirror_mode, P.floor_z, P.cap, P.nbr,
-                            P.cnt, S.dg);
+      if (skin) {
+        if (s < n) {  // positions of this search, for the displacement test
+          P.xref[s] = S.x[s];
+          P.xref[n + s] = S.y[s];
+          P.xref[2 * n + s] = S.z[s];
+        }
+        neighbors_body<false>(s, s < n, n, S.x, S.y, S.z, P.pf, S.colid, P.ids_out, P.grids,
+                              P.start, nullptr, P.rsearch, P.mirror_mode, P.floor_z, P.capc,
+                              P.cand, P.ccnt, S.dg, false);
+      } else {
+        neighbors_body<false>(s, s < n, n, S.x, S.y, S.z, P.pf, S.colid, P.ids_out, P.grids,
+                              P.start, nullptr, P.radius, P.mirror_mode, P.floor_z, P.cap,
+                              P.nbr, P.cnt, S.dg);
+      }
+    }
+  }
+  // the filter of particle s reads only the candidate list that this thread
+  // wrote for it above (same particle-to-thread map): no barrier needed
+  if (P.rebuild && skin) {
+    if (tid == 0) *P.search = 0;
+    for (int base = 0; base < n; base += nth) {
+      const int s = base + tid;
+      filter_body(s, s < n, n, S.x, S.y, S.z, P.pf, P.cand, P.ccnt, P.capc, P.grids, S.colid,
+                  P.radius, P.floor_z, P.cap, P.nbr, P.cnt, S.dg);
     }
   }
   if (tid == 0) *S.fb_count = 0;

@@ -313,6 +313,16 @@ def test_step_persistent_launch_is_bitwise_identical(dev, capi):
                         launch_mode=2, rebuild_every=2)
         for k in a:
             assert np.array_equal(a[k], b[k]), (prec, k)
+    # with Verlet candidate lists the persistent kernel takes the search
+    # branch from the device flag and filters every step
+    for prec in (0, 1, 2):
+        a, _ = _run_gpu(capi, dev, wc, pc, 6, prec=prec, offsets=wc.column_offsets, mui=mui_c,
+                        launch_mode=0, skin=0.1 * pc["h"])
+        b, d = _run_gpu(capi, dev, wc, pc, 6, prec=prec, offsets=wc.column_offsets, mui=mui_c,
+                        launch_mode=2, skin=0.1 * pc["h"])
+        assert d["status"] == 0 and d["flags"] == 0
+        for k in a:
+            assert np.array_equal(a[k], b[k]), ("skin", prec, k)
 
 
 def test_autotune_choices_and_table(dev, capi, tmp_path):
@@ -359,7 +369,8 @@ def test_step_verlet_skin_matches_full_search(dev, capi, orc):
     pd = W.param_dict(wl)
     ref, _ = _run_gpu(capi, dev, wl, pd, 20, launch_mode=0)
     s = torch.cuda.Stream()
-    for skin, mode in ((0.1 * pd["h"], 0), (0.1 * pd["h"], 1), (2e-4 * pd["h"], 1)):
+    for skin, mode in ((0.1 * pd["h"], 0), (0.1 * pd["h"], 1), (2e-4 * pd["h"], 1),
+                       (0.1 * pd["h"], 2), (2e-4 * pd["h"], 2)):
         got, d = _run_gpu(capi, dev, wl, pd, 20, launch_mode=mode, skin=skin, stream=s)
         assert d["n_overflow"] == 0
         e = _state_err(got, ref, wl.state)
@@ -383,7 +394,7 @@ def test_step_verlet_skin_under_shear_drift(dev, capi):
     ref, _ = _run_gpu(capi, dev, wl, pd, 40, launch_mode=0)
     moved = np.abs(ref["x"] - s["x"]).max() / pd["h"]
     assert moved > 0.1  # several searches were needed with skin 0.1h
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         got, d = _run_gpu(capi, dev, wl, pd, 40, launch_mode=mode, skin=0.1 * pd["h"],
                           stream=torch.cuda.Stream())
         e = _state_err(got, ref, s)
