@@ -15,6 +15,12 @@
 //     an independent uniform-grid scan; plus floor mirror particles (Sec. 3.1
 //     item 9, solid boundary) j* = (x_j, y_j, 2 f - z_j), tested with the same
 //     predicate (the particle's own mirror included);
+//   * optionally (free_surface = 1) ghost particles at free boundaries (Sec. 3.1
+//     items 6 and 9): a particle whose stencil is one-sided gets the point
+//     reflections of its inner entries; a ghost carries the particle's velocity,
+//     a solid fraction just below phi_min and the |gdot| that keeps the
+//     inertial pressure continuous (see add_ghosts for the test and placement
+//     the paper leaves open);
 //   * GFD least-squares fit (Sec. 3.1 item 7): 3D form of the 2D Taylor matrix
 //     with rows  [dx, dy, dz, dx^2/2, dy^2/2, dz^2/2, dx dy, dx dz, dy dz]
 //     (offsets divided by h), right-hand side s_k - s_i, solved by Householder
@@ -96,7 +102,7 @@ typedef struct {
   double gx, gy, gz;                          // body force
   double floor_z, dt;
   int32_t mirror_mode;  // 0 none, 1 no-slip (u* = -u), 2 free-slip (w* = -w)
-  int32_t pad;
+  int32_t free_surface;  // 1: ghost particles complete free-surface stencils
 } orc_params;
 
 typedef struct {
@@ -107,6 +113,10 @@ typedef struct {
 }  // extern "C"
 
 static const uint32_t MIRROR_BIT = 0x80000000u;
+// Ghost particle (free boundary, Sec. 3.1 item 9): the point reflection,
+// through particle i, of the stencil entry (j, mirror flag) of i.
+static const uint32_t GHOST_BIT = 0x40000000u;
+static const uint32_t INDEX_MASK = 0x3fffffffu;
 
 // ------------------------------------------------------- neighbour search ---
 
@@ -344,9 +354,11 @@ static int lsq_qrcp(int m, T* A, int nf, T* B, T* C /* nf x 9 */) {
   return rank;
 }
 
-// Fit nf fields on the stencil of particle i. `field(q, j, mirror)` returns the
-// value of field q at neighbour j (or its floor mirror). Outputs the unscaled
-// coefficients (gradient * h, second derivatives * h^2) in C[nf][9].
+// Fit nf fields on the stencil of particle i. `field(q, j, mirror, ghost)`
+// returns the value of field q at neighbour j, at its floor mirror, or at the
+// ghost particle that reflects entry j through i (whose row takes the entry's
+// offset negated). Outputs the unscaled coefficients (gradient * h, second
+// derivatives * h^2) in C[nf][9].
 template <class T, class FieldFn>
 static int fit_particle(int64_t i, const T* x, const T* y, const T* z, const int32_t* row,
                         int32_t m, double h, double floor_z, int nf, FieldFn field, T* C) {
@@ -354,11 +366,18 @@ static int fit_particle(int64_t i, const T* x, const T* y, const T* z, const int
   for (int32_t k = 0; k < m; ++k) {
     uint32_t code = (uint32_t)row[k];
     bool mir = code & MIRROR_BIT;
-    int64_t j = code & ~MIRROR_BIT;
+    bool ghost = code & GHOST_BIT;
+    int64_t j = code & INDEX_MASK;
     T zj = mir ? T(2.0 * floor_z) - z[j] : z[j];
     T dx = (x[j] - x[i]) / h, dy = (y[j] - y[i]) / h, dz = (zj - z[i]) / h;
+    if (ghost) {
+      dx = -dx;
+      dy = -dy;
+      dz = -dz;
+    }
     taylor_row(dx, dy, dz, &A[(size_t)k * NB]);
-    for (int q = 0; q < nf; ++q) B[(size_t)k * nf + q] = field(q, j, mir) - field(q, i, false);
+    for (int q = 0; q < nf; ++q)
+      B[(size_t)k * nf + q] = field(q, j, mir, ghost) - field(q, i, false, false);
   }
   return lsq_qrcp<T>(m, A.data(), nf, B.data(), C);
 }
@@ -417,6 +436,9 @@ struct Stencils {
   std::vector<int32_t> nbr, cnt;
 };
 
+static void add_ghosts(int64_t n, const double* x, const double* y, const double* z,
+                       const orc_params* p, Stencils& st);
+
 static void build_stencils(int64_t n, const double* x, const double* y, const double* z,
                            const orc_params* p, int brute, Stencils& st) {
   // the step never truncates; lists are sized for any lattice stencil
@@ -429,7 +451,90 @@ static void build_stencils(int64_t n, const double* x, const double* y, const do
   else
     neighbors_grid(n, x, y, z, nullptr, p->radius, p->mirror_mode, p->floor_z, st.cap, 0,
                    st.nbr.data(), st.cnt.data());
+  if (p->free_surface) add_ghosts(n, x, y, z, p, st);
 }
+
+// ------------------------------------------------------- free boundary ---
+// Sec. 3.1 items 6 and 9: a particle that cannot find neighbours in some
+// directions gets ghost particles that complete its neighbourhood. The paper
+// leaves the test and the placement open; here:
+//  - offsets are taken in fixed point, o_k = round(2^12 (x_k - x_i) / h), so
+//    that the sums below are exact integers, independent of the entry order;
+//  - each entry is weighted by w_k = max(0, R2 - |o_k|^2), R2 = round((2^12
+//    r / h)^2), which fades entries out at the stencil radius (an unweighted
+//    mean is dominated by which lattice points of the outermost shell happen
+//    to fall inside r);
+//  - the stencil is one-sided when the weighted summed offset S = sum w_k o_k
+//    satisfies |S| > kSurfaceTilt 2^12 sum w_k (lattice with 0.05-0.2 h jitter
+//    and r = 2.2 h: interior and second-layer particles stay below 0.16,
+//    free-surface particles above 0.29);
+//  - every entry k with o_k . S >= kGhostDepth 2^12 |S| (at least h/2 on the
+//    inner side) whose reflection -o_k has no stencil entry within h/2 gets a
+//    ghost at that reflection, except below the floor when floor mirrors are
+//    on (the solid boundary is the mirrors' side: (z_i + z_i) - z_k < floor_z).
+// Products that could overflow 64-bit integers are formed in FP64 in a fixed
+// order, so the decisions are reproducible bit for bit.
+static const double kSurfaceTilt = 0.22, kGhostDepth = 0.5, kFix = 4096.0;
+static const int64_t kGhostClear2 = (int64_t)1 << 22;  // (h/2)^2 in fixed point
+
+static void add_ghosts(int64_t n, const double* x, const double* y, const double* z,
+                       const orc_params* p, Stencils& st) {
+  const double h = p->h;
+  const double rf = (p->radius / h) * kFix;
+  const int64_t R2 = std::llrint(rf * rf);
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t* row = st.nbr.data() + i * (int64_t)st.cap;
+    const int32_t m = st.cnt[i];
+    if (m == 0) continue;
+    std::vector<int64_t> o(3 * (size_t)m);
+    std::vector<double> zk((size_t)m);
+    int64_t S[3] = {0, 0, 0}, Wsum = 0;
+    for (int32_t k = 0; k < m; ++k) {
+      const uint32_t code = (uint32_t)row[k];
+      const int64_t j = code & INDEX_MASK;
+      const double zj = (code & MIRROR_BIT) ? 2.0 * p->floor_z - z[j] : z[j];
+      zk[k] = zj;
+      const double d[3] = {x[j] - x[i], y[j] - y[i], zj - z[i]};
+      for (int a = 0; a < 3; ++a) o[3 * k + a] = std::llrint((d[a] / h) * kFix);
+      const int64_t q = (o[3 * k] * o[3 * k] + o[3 * k + 1] * o[3 * k + 1]) +
+                        o[3 * k + 2] * o[3 * k + 2];
+      const int64_t w = q < R2 ? R2 - q : 0;
+      for (int a = 0; a < 3; ++a) S[a] += w * o[3 * k + a];
+      Wsum += w;
+    }
+    const double sx = (double)S[0], sy = (double)S[1], sz = (double)S[2];
+    const double s2 = ((sx * sx) + (sy * sy)) + (sz * sz);
+    const double lim = (kSurfaceTilt * kFix) * (double)Wsum;
+    if (!(s2 > lim * lim)) continue;
+    int32_t c = m;
+    for (int32_t k = 0; k < m; ++k) {
+      const double ds = (((double)o[3 * k] * sx) + ((double)o[3 * k + 1] * sy)) +
+                        ((double)o[3 * k + 2] * sz);
+      const double dep = kGhostDepth * kFix;
+      if (!(ds > 0.0 && ds * ds >= (dep * dep) * s2)) continue;
+      if (p->mirror_mode != 0 && (z[i] + z[i]) - zk[k] < p->floor_z) continue;
+      bool clear = true;
+      for (int32_t l = 0; l < m && clear; ++l) {
+        const int64_t ex = o[3 * l] + o[3 * k], ey = o[3 * l + 1] + o[3 * k + 1];
+        const int64_t ez = o[3 * l + 2] + o[3 * k + 2];
+        clear = (ex * ex + ey * ey) + ez * ez >= kGhostClear2;
+      }
+      if (clear && c < st.cap) row[c++] = (int32_t)((uint32_t)row[k] | GHOST_BIT);
+    }
+    st.cnt[i] = c;
+  }
+}
+
+// Solid fraction of a ghost particle: just below phi_min (gas side of the
+// pressure law), 1e-3 relative.
+static inline double ghost_phi(const orc_params* p) { return p->phi_min * (1.0 - 1e-3); }
+
+// |gdot| of a ghost of particle F (Sec. 3.1 item 9): the value that keeps the
+// inertial pressure phi_s (2 a d |gdot| / (phi_c - phi))^2 continuous,
+// |gdot|_G = |gdot|_F (phi_c - phi_G) / (phi_c - phi_F); outside the inertial
+// regime F's own value (its acceleration does not use grad |gdot|).
+template <class T>
+static inline T ghost_gn(const orc_params* p, const T& phi_f, const T& gn_f);
 
 // Per-particle intermediates of one step, exported for kernel-level parity.
 template <class T>
@@ -440,6 +545,12 @@ struct Detail {
       : gd(6 * n), gn(n), gV(3 * n), lapdiv(3 * n), div(n), gg(3 * n), acc(3 * n), Vnew(n),
         reg(n) {}
 };
+
+template <class T>
+static inline T ghost_gn(const orc_params* p, const T& phi_f, const T& gn_f) {
+  if (regime_of(val(phi_f), p->phi_min, p->phi_max) != REG_INERTIAL) return gn_f;
+  return gn_f * ((p->phi_c - ghost_phi(p)) / (T(p->phi_c) - phi_f));
+}
 
 // One explicit step (Sec. 3.1 items 7, 8 and 10).
 // Time levels: the difference equations of item 8 print V, V_X, ... on their
@@ -466,11 +577,12 @@ static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const St
   for (int64_t i = 0; i < n; ++i) {
     const int32_t* row = st.nbr.data() + i * (int64_t)st.cap;
     int32_t m = st.cnt[i];
-    auto field = [&](int q, int64_t j, bool mir) -> T {
+    auto field = [&](int q, int64_t j, bool mir, bool ghost) -> T {
+      if (ghost) j = i;  // free surface: the ghost carries the velocity of i
       switch (q) {
-        case 0: return mir ? usgn(0) * s.u[j] : s.u[j];
-        case 1: return mir ? usgn(1) * s.v[j] : s.v[j];
-        default: return mir ? usgn(2) * s.w[j] : s.w[j];
+        case 0: return mir && !ghost ? usgn(0) * s.u[j] : s.u[j];
+        case 1: return mir && !ghost ? usgn(1) * s.v[j] : s.v[j];
+        default: return mir && !ghost ? usgn(2) * s.w[j] : s.w[j];
       }
     };
     T C[3 * NB];
@@ -515,7 +627,13 @@ static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const St
   for (int64_t i = 0; i < n; ++i) {
     const int32_t* row = st.nbr.data() + i * (int64_t)st.cap;
     int32_t m = st.cnt[i];
-    auto field = [&](int q, int64_t j, bool mir) -> T {
+    // free surface (Sec. 3.1 item 9): a ghost has solid fraction phi_G just
+    // below phi_min and the |gdot| that keeps the inertial pressure of i
+    // continuous, |gdot|_G = |gdot|_i (phi_c - phi_G) / (phi_c - phi_i)
+    const double phi_g = ghost_phi(p);
+    const T gn_ghost = ghost_gn<T>(p, T(1.0) / o.Vnew[i], o.gn[i]);
+    auto field = [&](int q, int64_t j, bool mir, bool ghost) -> T {
+      if (ghost) return q == 0 ? gn_ghost : T(1.0 / phi_g);
       if (q == 0) return mir ? T(0.0) : o.gn[j];
       return o.Vnew[j];
     };
@@ -665,9 +783,9 @@ int orc_fit(int64_t n, const double* x, const double* y, const double* z, const 
   int64_t nrd = 0;
 #pragma omp parallel for schedule(dynamic, 32) reduction(+ : nrd)
   for (int64_t i = 0; i < n; ++i) {
-    auto field = [&](int q, int64_t j, bool mir) -> double {
-      double s = fields[(int64_t)q * n + j];
-      return mir ? mirror_sign[q] * s : s;
+    auto field = [&](int q, int64_t j, bool mir, bool ghost) -> double {
+      double s = fields[(int64_t)q * n + (ghost ? i : j)];  // not produced by the search
+      return mir && !ghost ? mirror_sign[q] * s : s;
     };
     std::vector<double> C((size_t)nf * NB);
     int m = std::min(cnt[i], cap);
@@ -742,6 +860,34 @@ static void load_state(int64_t n, PState<double>& s, const double* x, const doub
 }
 
 // nsteps LP steps in place. Returns 0.
+// Stencils of one step (the neighbour lists plus, with p->free_surface, the
+// ghost entries), in the step's own order; rows of `cap` entries.
+int orc_step_stencils(int64_t n, const double* x, const double* y, const double* z,
+                      const orc_params* p, int brute, int32_t cap, int32_t* nbr, int32_t* cnt,
+                      int nthreads) {
+  set_threads(nthreads);
+  Stencils st;
+  build_stencils(n, x, y, z, p, brute, st);
+  int over = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t m = st.cnt[i];
+    if (m > cap) over = 1;
+    for (int32_t k = 0; k < m && k < cap; ++k) nbr[i * (int64_t)cap + k] = st.nbr[i * (int64_t)st.cap + k];
+    cnt[i] = m;
+  }
+  return over;
+}
+
+// Ghost-particle state of fluid particles with solid fraction phi[i] and
+// |gdot| gn[i]: phi_G and |gdot|_G.
+void orc_ghost_state(int64_t n, const double* phi, const double* gn, const orc_params* p,
+                     double* phi_g, double* gn_g) {
+  for (int64_t i = 0; i < n; ++i) {
+    phi_g[i] = ghost_phi(p);
+    gn_g[i] = ghost_gn<double>(p, phi[i], gn[i]);
+  }
+}
+
 int orc_step(int64_t n, double* x, double* y, double* z, double* u, double* v, double* w,
              double* V, const orc_params* p, int nsteps, int rebuild_every, int brute,
              int nthreads, orc_diag* diag) {

@@ -25,13 +25,14 @@ _lock = threading.Lock()
 _lib = None
 
 MIRROR_BIT = 0x80000000
+GHOST_BIT = 0x40000000  # ghost particle: entry reflected through the particle
 
 
 class OrcParams(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in (
         "mu_s", "mu_2", "I0", "d", "rho_s", "phi_c", "phi_min", "phi_max", "alpha", "beta",
         "h", "radius", "gx", "gy", "gz", "floor_z", "dt")] + [
-        ("mirror_mode", ctypes.c_int32), ("pad", ctypes.c_int32)]
+        ("mirror_mode", ctypes.c_int32), ("free_surface", ctypes.c_int32)]
 
 
 class OrcDiag(ctypes.Structure):
@@ -80,6 +81,11 @@ def lib():
                                                           ctypes.c_int, ctypes.c_int,
                                                           ctypes.c_int, vp]
         L.orc_step_tangent.restype = ctypes.c_int
+        L.orc_step_stencils.argtypes = [i64, vp, vp, vp, P(OrcParams), ctypes.c_int, i32, vp,
+                                        vp, ctypes.c_int]
+        L.orc_step_stencils.restype = ctypes.c_int
+        L.orc_ghost_state.argtypes = [i64, vp, vp, P(OrcParams), vp, vp]
+        L.orc_ghost_state.restype = None
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = ctypes.c_int
         _lib = L
@@ -164,6 +170,28 @@ def mui_stress(V, grad_u, p: OrcParams):
 
 
 FIELDS = ("x", "y", "z", "u", "v", "w", "V")
+
+
+def step_stencils(x, y, z, p: OrcParams, brute: bool = True, cap: int = 256, nthreads: int = 0):
+    """Stencils one step uses (Sec. 3.1 items 5-6 and 9): the neighbour lists
+    and, with p.free_surface, the ghost entries (code | GHOST_BIT: the point
+    reflection of entry `code` through the particle). Returns (nbr, cnt, over)."""
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    n = x.size
+    nbr = np.zeros((n, cap), dtype=np.int32)
+    cnt = np.zeros(n, dtype=np.int32)
+    over = lib().orc_step_stencils(n, _p(x), _p(y), _p(z), ctypes.byref(p), int(bool(brute)),
+                                   cap, _p(nbr), _p(cnt), int(nthreads))
+    return nbr, cnt, over
+
+
+def ghost_state(phi, gnorm, p: OrcParams):
+    """Solid fraction and |gdot| of the ghost particles of fluid particles with
+    solid fraction phi and |gdot| gnorm (Sec. 3.1 item 9)."""
+    phi, gnorm = _f64(phi), _f64(gnorm)
+    phi_g, gn_g = np.zeros(phi.size), np.zeros(phi.size)
+    lib().orc_ghost_state(phi.size, _p(phi), _p(gnorm), ctypes.byref(p), _p(phi_g), _p(gn_g))
+    return phi_g, gn_g
 
 
 def step(state: dict, p: OrcParams, nsteps: int, rebuild_every: int = 1, brute: bool = True,

@@ -1,0 +1,176 @@
+"""Pins of the oracle's free-boundary ghost particles (Sec. 3.1 items 6 and 9).
+
+The paper fixes what ghosts are for (complete the neighbourhood of a particle
+that lacks neighbours in some directions) and the state they carry (velocity
+and pressure continuous with the fluid particle, solid fraction just below
+phi_min). The tests check those properties against geometry and the pressure
+law, not against the oracle's own formulas:
+- on a flat face of an unjittered lattice the completed stencil is exactly the
+  full lattice ball, enumerated independently;
+- interior and second-layer particles get no ghost, and no ghost lands on a
+  real or mirror particle;
+- the ghost |gdot| keeps the inertial pressure of the pressure law continuous;
+- rest, rigid translation and the tangent-linear run hold with ghosts on.
+"""
+import numpy as np
+
+from paper_2206_14061_gb300 import workloads as W
+
+MB, GB, IDX = 0x80000000, 0x40000000, 0x3FFFFFFF
+
+
+def _p(orc, **kw):
+    d = dict(W.MUI)
+    d.update(W.EOS)
+    d.update(h=1e-3, radius=2.2e-3, gx=0.0, gy=0.0, gz=-9.81, floor_z=0.0, dt=1e-5,
+             mirror_mode=1, free_surface=1)
+    d.update(kw)
+    return orc.params(**d)
+
+
+def _ball(r2=4.84):
+    """Integer offsets of the full lattice ball 0 < |d|^2 <= r2."""
+    out = []
+    rng = range(-3, 4)
+    for a in rng:
+        for b in rng:
+            for c in rng:
+                if 0 < a * a + b * b + c * c <= r2:
+                    out.append((a, b, c))
+    return sorted(out)
+
+
+def _offsets(i, row, x, y, z, h):
+    """Integer lattice offsets of a step stencil's entries (mirror through the
+    floor z = 0, ghost = point reflection through particle i)."""
+    out = []
+    for code in row.astype(np.int64) & 0xFFFFFFFF:
+        j = int(code) & IDX
+        zj = -z[j] if code & MB else z[j]
+        d = np.array([x[j] - x[i], y[j] - y[i], zj - z[i]]) / h
+        if code & GB:
+            d = -d
+        r = np.rint(d)
+        assert np.abs(d - r).max() < 1e-9
+        out.append(tuple(int(v) for v in r))
+    return out
+
+
+def test_ghosts_complete_flat_faces_exactly(orc):
+    h, n = 1e-3, 10
+    x, y, z = W.lattice_box(n, n, n, h, 0.0, np.random.default_rng(0))
+    nbr, cnt, over = orc.step_stencils(x, y, z, _p(orc), brute=True)
+    assert over == 0
+    ix, iy, iz = [np.rint(c / h - 0.5).astype(int) for c in (x, y, z)]
+    ball = _ball()
+    assert len(ball) == 32
+    inner = lambda a: (a >= 2) & (a <= n - 3)
+    faces = {
+        "top": (iz == n - 1) & inner(ix) & inner(iy),
+        "side x": (ix == n - 1) & inner(iy) & inner(iz),
+        "side -y": (iy == 0) & inner(ix) & inner(iz),
+    }
+    for name, sel in faces.items():
+        idx = np.flatnonzero(sel)
+        assert idx.size == 36
+        for i in idx:
+            row = nbr[i, :cnt[i]]
+            got = sorted(_offsets(i, row, x, y, z, h))
+            assert got == ball, (name, i)
+            assert (row.astype(np.int64) & GB).any(), (name, i)
+    # interior, second layer below the top and the floor layer: no ghost
+    quiet = (inner(ix) & inner(iy) & ((iz <= n - 2)))
+    for i in np.flatnonzero(quiet):
+        assert not (nbr[i, :cnt[i]].astype(np.int64) & GB).any(), i
+
+
+def test_ghosts_never_land_on_particles(orc):
+    """Every ghost of every particle (faces, edges, corners; jittered lattice)
+    lies at least 0.3 h from every real particle and floor mirror."""
+    spatial = __import__("pytest").importorskip("scipy.spatial")
+    h, n = 1e-3, 9
+    x, y, z = W.lattice_box(n, n, n, h, 0.05, np.random.default_rng(3))
+    nbr, cnt, over = orc.step_stencils(x, y, z, _p(orc), brute=True)
+    assert over == 0
+    pts = np.stack([x, y, z], 1)
+    tree = spatial.cKDTree(np.concatenate([pts, pts * np.array([1, 1, -1])]))
+    n_ghosts = 0
+    for i in range(x.size):
+        for code in nbr[i, :cnt[i]].astype(np.int64) & 0xFFFFFFFF:
+            if not code & GB:
+                continue
+            j = int(code) & IDX
+            pj = pts[j] * (np.array([1, 1, -1]) if code & MB else 1)
+            g = 2 * pts[i] - pj
+            d, _ = tree.query(g)
+            assert d >= 0.3 * h, (i, j, d / h)
+            n_ghosts += 1
+    assert n_ghosts > 0
+
+
+def test_ghost_state_keeps_pressure_continuous(orc):
+    """phi_G just below phi_min; the inertial pressure law
+    P = phi_s (2 a d |gdot| / (phi_c - phi))^2 gives the same pressure at the
+    ghost as at the fluid particle; outside the inertial regime |gdot|_G is the
+    fluid particle's own."""
+    p = _p(orc)
+    rng = np.random.default_rng(5)
+    phi = rng.uniform(p.phi_min + 1e-3, p.phi_max, 200)
+    gn = rng.uniform(0.0, 50.0, 200)
+    phi_g, gn_g = orc.ghost_state(phi, gn, p)
+    assert (phi_g < p.phi_min).all() and (phi_g > 0.99 * p.phi_min).all()
+    a = p.phi_c - p.phi_min
+    P = lambda f, g: p.rho_s * (2 * a * p.d * g / (p.phi_c - f)) ** 2
+    assert np.allclose(P(phi_g, gn_g), P(phi, gn), rtol=1e-13, atol=0)
+    other = np.concatenate([rng.uniform(0.2, p.phi_min, 20), rng.uniform(p.phi_max + 1e-6, 0.62, 20)])
+    gno = rng.uniform(0.0, 50.0, other.size)
+    _, gno_g = orc.ghost_state(other, gno, p)
+    assert np.array_equal(gno_g, gno)
+
+
+def _state(x, y, z, u=None, v=None, w=None, V=None):
+    n = x.size
+    z0 = np.zeros(n)
+    return dict(x=x, y=y, z=z, u=z0.copy() if u is None else u, v=z0.copy() if v is None else v,
+                w=z0.copy() if w is None else w, V=np.full(n, 1 / 0.585) if V is None else V)
+
+
+def test_rest_and_rigid_translation_with_ghosts(orc):
+    rng = np.random.default_rng(2)
+    h = 1e-3
+    x, y, z = W.lattice_box(6, 6, 6, h, 0.05, rng)
+    s0 = _state(x, y, z)
+    s1, _ = orc.step(s0, _p(orc, gz=0.0), 5)
+    for k in s0:
+        assert np.array_equal(s0[k], s1[k]), k
+    # uniform velocity, no gravity, no floor: gdot = 0, x advances by u t
+    n, nst = x.size, 7
+    U = np.array([0.3, -0.2, 0.1])
+    st = _state(x, y, z + 0.01, np.full(n, U[0]), np.full(n, U[1]), np.full(n, U[2]))
+    s2, _ = orc.step(st, _p(orc, mirror_mode=0, gz=0.0), nst)
+    t = nst * 1e-5
+    for c, k in enumerate("xyz"):
+        assert np.allclose(s2[k] - st[k], U[c] * t, rtol=1e-9, atol=1e-17)
+    assert np.allclose(s2["u"], U[0], rtol=1e-13)
+
+
+def test_tangent_linear_with_ghosts_matches_central_differences(orc):
+    rng = np.random.default_rng(14)
+    h = 1e-3
+    x, y, z = W.lattice_box(6, 6, 6, h, 0.05, rng)
+    st = _state(x, y, z, u=20.0 * z)
+    nst = reb = 8
+    p = _p(orc)
+    nbr, cnt, _ = orc.step_stencils(x, y, z, p, brute=True)
+    assert (nbr.astype(np.int64) & GB).any()
+    _, tan = orc.step_tangent(st, p, nst, rebuild_every=reb)
+    for kix, name in enumerate(("mu_s", "mu_2", "I0")):
+        eps = 1e-5
+        sp_, _ = orc.step(st, _p(orc, **{name: getattr(p, name) + eps}), nst, rebuild_every=reb)
+        sm_, _ = orc.step(st, _p(orc, **{name: getattr(p, name) - eps}), nst, rebuild_every=reb)
+        for f, key in enumerate(("u", "v", "w", "V")):
+            fd = (sp_[key] - sm_[key]) / (2 * eps)
+            t = tan[kix, 3 + f]
+            scale = np.abs(t).max()
+            assert scale > 0
+            assert np.abs(fd - t).max() <= 1e-5 * scale, (name, key)
