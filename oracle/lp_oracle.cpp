@@ -458,34 +458,46 @@ static void build_stencils(int64_t n, const double* x, const double* y, const do
 // Sec. 3.1 items 6 and 9: a particle that cannot find neighbours in some
 // directions gets ghost particles that complete its neighbourhood. The paper
 // leaves the test and the placement open; here:
-//  - offsets are taken in fixed point, o_k = round(2^12 (x_k - x_i) / h), so
-//    that the sums below are exact integers, independent of the entry order;
-//  - each entry is weighted by w_k = max(0, R2 - |o_k|^2), R2 = round((2^12
-//    r / h)^2), which fades entries out at the stencil radius (an unweighted
-//    mean is dominated by which lattice points of the outermost shell happen
-//    to fall inside r);
+//  - positions are taken in fixed point on a power-of-two grid, X = round(K x)
+//    with K the largest power of two such that K h <= 2^12 (so the scaling is
+//    exact), and offsets are the exact integer differences o_k = X_k - X_i:
+//    every sum below is an exact integer, independent of the entry order;
+//  - each entry is weighted by w_k = max(0, R2 - |o_k|^2), R2 = round((K r)^2),
+//    which fades entries out at the stencil radius (an unweighted mean is
+//    dominated by which lattice points of the outermost shell happen to fall
+//    inside r);
 //  - the stencil is one-sided when the weighted summed offset S = sum w_k o_k
-//    satisfies |S| > kSurfaceTilt 2^12 sum w_k (lattice with 0.05-0.2 h jitter
-//    and r = 2.2 h: interior and second-layer particles stay below 0.16,
-//    free-surface particles above 0.29);
-//  - every entry k with o_k . S >= kGhostDepth 2^12 |S| (at least h/2 on the
+//    satisfies |S| > kSurfaceTilt K h sum w_k (lattice with 0.05-0.2 h jitter
+//    and r = 2.2 h: interior and second-layer particles stay below 0.16 h,
+//    free-surface particles above 0.29 h);
+//  - every entry k with o_k . S >= kGhostDepth K h |S| (at least h/2 on the
 //    inner side) whose reflection -o_k has no stencil entry within h/2 gets a
 //    ghost at that reflection, except below the floor when floor mirrors are
 //    on (the solid boundary is the mirrors' side: (z_i + z_i) - z_k < floor_z).
 // Products that could overflow 64-bit integers are formed in FP64 in a fixed
 // order, so the decisions are reproducible bit for bit.
-static const double kSurfaceTilt = 0.22, kGhostDepth = 0.5, kFix = 4096.0;
-static const int64_t kGhostClear2 = (int64_t)1 << 22;  // (h/2)^2 in fixed point
+static const double kSurfaceTilt = 0.22, kGhostDepth = 0.5;
+
+static double ghost_grid(double h) {  // K: largest power of two with K h <= 4096
+  double K = 1.0;
+  while (K * h > 4096.0) K *= 0.5;
+  while (2.0 * K * h <= 4096.0) K *= 2.0;
+  return K;
+}
 
 static void add_ghosts(int64_t n, const double* x, const double* y, const double* z,
                        const orc_params* p, Stencils& st) {
-  const double h = p->h;
-  const double rf = (p->radius / h) * kFix;
-  const int64_t R2 = std::llrint(rf * rf);
+  const double h = p->h, K = ghost_grid(h);
+  const double rk = p->radius * K;
+  const int64_t R2 = std::llrint(rk * rk);
+  const double hk = h * K;
+  const int64_t clear2 = std::llrint((0.5 * hk) * (0.5 * hk));
+  auto fix = [&](double v) { return (int64_t)std::llrint(v * K); };
   for (int64_t i = 0; i < n; ++i) {
     int32_t* row = st.nbr.data() + i * (int64_t)st.cap;
     const int32_t m = st.cnt[i];
     if (m == 0) continue;
+    const int64_t Xi[3] = {fix(x[i]), fix(y[i]), fix(z[i])};
     std::vector<int64_t> o(3 * (size_t)m);
     std::vector<double> zk((size_t)m);
     int64_t S[3] = {0, 0, 0}, Wsum = 0;
@@ -494,8 +506,9 @@ static void add_ghosts(int64_t n, const double* x, const double* y, const double
       const int64_t j = code & INDEX_MASK;
       const double zj = (code & MIRROR_BIT) ? 2.0 * p->floor_z - z[j] : z[j];
       zk[k] = zj;
-      const double d[3] = {x[j] - x[i], y[j] - y[i], zj - z[i]};
-      for (int a = 0; a < 3; ++a) o[3 * k + a] = std::llrint((d[a] / h) * kFix);
+      o[3 * k] = fix(x[j]) - Xi[0];
+      o[3 * k + 1] = fix(y[j]) - Xi[1];
+      o[3 * k + 2] = fix(zj) - Xi[2];
       const int64_t q = (o[3 * k] * o[3 * k] + o[3 * k + 1] * o[3 * k + 1]) +
                         o[3 * k + 2] * o[3 * k + 2];
       const int64_t w = q < R2 ? R2 - q : 0;
@@ -504,20 +517,20 @@ static void add_ghosts(int64_t n, const double* x, const double* y, const double
     }
     const double sx = (double)S[0], sy = (double)S[1], sz = (double)S[2];
     const double s2 = ((sx * sx) + (sy * sy)) + (sz * sz);
-    const double lim = (kSurfaceTilt * kFix) * (double)Wsum;
+    const double lim = (kSurfaceTilt * hk) * (double)Wsum;
     if (!(s2 > lim * lim)) continue;
+    const double dep = kGhostDepth * hk;
     int32_t c = m;
     for (int32_t k = 0; k < m; ++k) {
       const double ds = (((double)o[3 * k] * sx) + ((double)o[3 * k + 1] * sy)) +
                         ((double)o[3 * k + 2] * sz);
-      const double dep = kGhostDepth * kFix;
       if (!(ds > 0.0 && ds * ds >= (dep * dep) * s2)) continue;
       if (p->mirror_mode != 0 && (z[i] + z[i]) - zk[k] < p->floor_z) continue;
       bool clear = true;
       for (int32_t l = 0; l < m && clear; ++l) {
         const int64_t ex = o[3 * l] + o[3 * k], ey = o[3 * l + 1] + o[3 * k + 1];
         const int64_t ez = o[3 * l + 2] + o[3 * k + 2];
-        clear = (ex * ex + ey * ey) + ez * ez >= kGhostClear2;
+        clear = (ex * ex + ey * ey) + ez * ez >= clear2;
       }
       if (clear && c < st.cap) row[c++] = (int32_t)((uint32_t)row[k] | GHOST_BIT);
     }
