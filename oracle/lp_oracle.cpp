@@ -107,7 +107,7 @@ typedef struct {
 
 typedef struct {
   int64_t n_gas, n_inertial, n_quasistatic, n_over_c, n_below_floor,
-      n_rank_deficient, min_stencil, max_stencil;
+      n_rank_deficient, min_stencil, max_stencil, n_ghosts;
 } orc_diag;
 
 }  // extern "C"
@@ -459,9 +459,10 @@ static void build_stencils(int64_t n, const double* x, const double* y, const do
 // directions gets ghost particles that complete its neighbourhood. The paper
 // leaves the test and the placement open; here:
 //  - positions are taken in fixed point on a power-of-two grid, X = round(K x)
-//    with K the largest power of two such that K h <= 2^12 (so the scaling is
-//    exact), and offsets are the exact integer differences o_k = X_k - X_i:
-//    every sum below is an exact integer, independent of the entry order;
+//    with K the largest power of two such that K r <= 2^13 (so the scaling is
+//    exact and every offset, square and pair sum below fits 32-bit integers),
+//    and offsets are the exact integer differences o_k = X_k - X_i: every sum
+//    below is an exact integer, independent of the entry order;
 //  - each entry is weighted by w_k = max(0, R2 - |o_k|^2), R2 = round((K r)^2),
 //    which fades entries out at the stencil radius (an unweighted mean is
 //    dominated by which lattice points of the outermost shell happen to fall
@@ -474,20 +475,21 @@ static void build_stencils(int64_t n, const double* x, const double* y, const do
 //    inner side) whose reflection -o_k has no stencil entry within h/2 gets a
 //    ghost at that reflection, except below the floor when floor mirrors are
 //    on (the solid boundary is the mirrors' side: (z_i + z_i) - z_k < floor_z).
-// Products that could overflow 64-bit integers are formed in FP64 in a fixed
-// order, so the decisions are reproducible bit for bit.
+// The dot products o_k . S are exact 64-bit integers; only the squared
+// comparisons are formed in FP64, in a fixed order, so the decisions are
+// reproducible bit for bit.
 static const double kSurfaceTilt = 0.22, kGhostDepth = 0.5;
 
-static double ghost_grid(double h) {  // K: largest power of two with K h <= 4096
+static double ghost_grid(double r) {  // K: largest power of two with K r <= 8192
   double K = 1.0;
-  while (K * h > 4096.0) K *= 0.5;
-  while (2.0 * K * h <= 4096.0) K *= 2.0;
+  while (K * r > 8192.0) K *= 0.5;
+  while (2.0 * K * r <= 8192.0) K *= 2.0;
   return K;
 }
 
 static void add_ghosts(int64_t n, const double* x, const double* y, const double* z,
                        const orc_params* p, Stencils& st) {
-  const double h = p->h, K = ghost_grid(h);
+  const double h = p->h, K = ghost_grid(p->radius);
   const double rk = p->radius * K;
   const int64_t R2 = std::llrint(rk * rk);
   const double hk = h * K;
@@ -522,8 +524,8 @@ static void add_ghosts(int64_t n, const double* x, const double* y, const double
     const double dep = kGhostDepth * hk;
     int32_t c = m;
     for (int32_t k = 0; k < m; ++k) {
-      const double ds = (((double)o[3 * k] * sx) + ((double)o[3 * k + 1] * sy)) +
-                        ((double)o[3 * k + 2] * sz);
+      // o_k . S exactly (|o| <= 2^13 + 1, |S| < 2^46), then one rounding
+      const double ds = (double)((o[3 * k] * S[0] + o[3 * k + 1] * S[1]) + o[3 * k + 2] * S[2]);
       if (!(ds > 0.0 && ds * ds >= (dep * dep) * s2)) continue;
       if (p->mirror_mode != 0 && (z[i] + z[i]) - zk[k] < p->floor_z) continue;
       bool clear = true;
@@ -740,6 +742,9 @@ static void lp_run(int64_t n, PState<T>& s, const TParams<T>& tp, int nsteps, in
         if (1.0 / val(o.Vnew[i]) > p->phi_c) dg->n_over_c++;
         dg->min_stencil = std::min<int64_t>(dg->min_stencil, st.cnt[i]);
         dg->max_stencil = std::max<int64_t>(dg->max_stencil, st.cnt[i]);
+        if (step % rebuild_every == 0)
+          for (int32_t k = 0; k < st.cnt[i]; ++k)
+            if ((uint32_t)st.nbr[i * (int64_t)st.cap + k] & GHOST_BIT) dg->n_ghosts++;
       }
     }
     lp_update<T>(n, s, o, p->dt);

@@ -38,7 +38,7 @@ class OrcParams(ctypes.Structure):
 class OrcDiag(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n_gas", "n_inertial", "n_quasistatic", "n_over_c", "n_below_floor",
-        "n_rank_deficient", "min_stencil", "max_stencil")]
+        "n_rank_deficient", "min_stencil", "max_stencil", "n_ghosts")]
 
 
 def build(force: bool = False) -> str:
