@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--restart-every", type=int, default=10)
     ap.add_argument("--skin", type=float, default=0.1,
                     help="Verlet skin in lattice spacings (0: full search every step)")
+    ap.add_argument("--free-surface", action="store_true",
+                    help="ghost particles at free boundaries (Sec. 3.1 item 9)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
@@ -200,7 +202,8 @@ def our_arm(args):
         return dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
                     floor_z=0.0, mirror_mode=1,
                     precision=PREC[prec],
-                    rebuild_every=1, launch_mode=graph, skin=args.skin * pd["h"])
+                    rebuild_every=1, launch_mode=graph, skin=args.skin * pd["h"],
+                    free_surface=int(args.free_surface))
 
     def run(nsteps, prec, graph=1):
         done = 0
@@ -286,7 +289,7 @@ def our_arm(args):
                         f"({n} particles), mu_s 0.38 mu_2 0.64 I0 0.28 d 5e-4 rho 2500, "
                         "dt 1e-5, stencil radius 2.2h, no-slip floor mirrors",
             "precision": args.precision, "graph": True, "restart_every": R,
-            "verlet_skin_h": args.skin,
+            "verlet_skin_h": args.skin, "free_surface_ghosts": bool(args.free_surface),
             "mean_stencil": mean_m, "parallelism": f"replicas x{world}",
             "l2": "per-step working set (state, stencils, factors) is larger than L2",
         },

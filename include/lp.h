@@ -138,6 +138,18 @@ typedef struct {
                           * skin/2 since the last one. 0: full search every step.
                           * All launch modes; the persistent launch takes the
                           * search branch inside the kernel.                      */
+  int32_t free_surface;  /* 1: ghost particles at free boundaries (Sec. 3.1 items
+                          * 6 and 9). A particle whose stencil is one-sided (its
+                          * weighted mean offset, weights r^2 - d^2, exceeds
+                          * 0.22 h) gets ghosts at the point reflections of its
+                          * entries at least h/2 on the inner side, none within
+                          * h/2 of an entry or below a mirrored floor. A ghost
+                          * carries the particle's velocity, solid fraction
+                          * phi_min (1 - 1e-3) and the |gdot| that keeps the
+                          * inertial pressure continuous. Stencil entries plus
+                          * ghosts must fit in cap (else LP_ERR_STENCIL_OVERFLOW).
+                          * lp_step_adjoint: LP_ERR_UNIMPLEMENTED.              */
+  int32_t pad;
 } lp_params;
 
 /* Stencils produced by lp_build_neighbors: library-owned device memory, valid
@@ -162,6 +174,7 @@ typedef struct {
   int64_t n_nonfinite, n_below_floor;
   int64_t n_stencil_rows;  /* sum of stencil sizes over all stencils built     */
   int64_t n_stencils;      /* number of stencils built                          */
+  int64_t n_ghosts;        /* ghost entries added to stencils (free_surface)    */
 } lp_diag;
 
 /* Version string of the library build. Never fails. */

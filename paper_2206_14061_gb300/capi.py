@@ -61,7 +61,7 @@ class LpEos(ctypes.Structure):
 class LpParams(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("h", "radius", "gx", "gy", "gz", "floor_z")] + [
         (k, ctypes.c_int32) for k in ("mirror_mode", "precision", "rebuild_every", "launch_mode")] + [
-        ("skin", ctypes.c_double)]
+        ("skin", ctypes.c_double), ("free_surface", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class LpNeighbors(ctypes.Structure):
@@ -74,7 +74,7 @@ class LpDiag(ctypes.Structure):
                 ("max_stencil", ctypes.c_int32), ("pad", ctypes.c_int32)] + [
         (k, ctypes.c_int64) for k in ("n_overflow", "n_fallback", "n_gas", "n_quasistatic",
                                       "n_over_c", "n_nonfinite", "n_below_floor",
-                                      "n_stencil_rows", "n_stencils")]
+                                      "n_stencil_rows", "n_stencils", "n_ghosts")]
 
 
 class LpTuning(ctypes.Structure):
@@ -210,7 +210,8 @@ def params_struct(q) -> LpParams:
     return LpParams(float(q["h"]), float(q["radius"]), float(q["gx"]), float(q["gy"]),
                     float(q["gz"]), float(q.get("floor_z", 0.0)), int(q.get("mirror_mode", 1)),
                     int(q.get("precision", LP_FP64)), int(q.get("rebuild_every", 1)),
-                    int(q.get("launch_mode", LP_LAUNCH_KERNELS)), float(q.get("skin", 0.0)))
+                    int(q.get("launch_mode", LP_LAUNCH_KERNELS)), float(q.get("skin", 0.0)),
+                    int(q.get("free_surface", 0)), 0)
 
 
 class Context:

@@ -39,6 +39,10 @@ void launch_filter(int n, const double* x, const double* y, const double* z, con
                    const int32_t* cand, const int32_t* ccnt, int capc, const GridCol* grids,
                    const int32_t* colid, double r, double floor_z, int cap, int32_t* nbr,
                    int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs);
+void launch_ghosts(int n, const double* x, const double* y, const double* z,
+                   const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
+                   const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
+                   cudaStream_t st, int bs);
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st);
 // fit.cu
@@ -105,6 +109,9 @@ struct lp_ctx {
   double** h_ptr = nullptr;  // pinned staging of d_ptr
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
   float4 *Xh = nullptr, *Xl = nullptr, *Uh = nullptr, *Ul = nullptr, *GVff = nullptr;
+  int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
+  int32_t* gcnt = nullptr;    // ghost entries per stencil
+  float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
   float* Lff = nullptr;      // float-float Cholesky factors (LP_MIXED_FF)
   // Verlet candidate lists (lp_params.skin)
   int32_t* cand = nullptr;   // capc x n, k-major
@@ -335,6 +342,9 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.K = K;
   A.grids = c->d_grids;
   A.Xh = c->Xh; A.Xl = c->Xl; A.Uh = c->Uh; A.Ul = c->Ul; A.GVff = c->GVff; A.Lff = c->Lff;
+  A.Xfix = c->Xfix;
+  A.gcnt = c->gcnt;
+  A.Tg = c->Tg; A.T2 = c->T2;
   if (c->skin > 0.0) {
     A.xref = c->xref;
     const double hs = 0.5 * c->skin;
@@ -342,6 +352,14 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
     A.need_search = c->d_search;
   }
   return A;
+}
+
+// Twin sums of the float-float free-surface path, allocated on first use
+// (62 + 36 floats per particle).
+lp_status ensure_twin_buffers(lp_ctx* c, const lp_params* q) {
+  if (!q->free_surface || c->Tg) return LP_OK;
+  LP_TRY(dalloc(c, &c->Tg, (size_t)c->cap_n * 62));
+  return dalloc(c, &c->T2, (size_t)c->cap_n * 36);
 }
 
 // One LP step on the context's internal (sorted) state.
@@ -361,6 +379,11 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
     launch_filter(n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf, c->cand, c->ccnt, c->capc,
                   c->d_grids, c->colid[c->ci], K.radius, K.floor_z, c->cap, c->nbr, c->cnt,
                   c->dg, c->d_search, st, c->bs_nbr);
+    if (K.free_surface) {
+      launch_ghosts(n, c->X[e][0], c->X[e][1], c->X[e][2], c->colid[c->ci], c->d_grids, c->Xfix,
+                    c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr);
+      c->launches += 2;
+    }
     phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
     c->launches += 2;
   } else if (rebuild) {
@@ -372,6 +395,11 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
                      c->colid[c->ci], c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity,
                      nullptr, K.radius, K.mirror_mode, K.floor_z, c->cap, c->nbr, c->cnt, c->dg,
                      st, c->bs_nbr);
+    if (K.free_surface) {
+      launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
+                    c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr);
+      c->launches += 2;
+    }
     phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
     c->launches += 1;
   }
@@ -383,7 +411,7 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
   phase_mark(c, LP_PHASE_PASS2, true, st);
   launch_pass2(prec, A, st, c->bs_p2);
   phase_mark(c, LP_PHASE_PASS2, false, st);
-  c->launches += prec == LP_MIXED_FF ? 7 : 4;
+  c->launches += prec == LP_MIXED_FF ? (K.free_surface ? 9 : 7) : 4;
   c->steps += 1;
   c->cx ^= 1;
 }
@@ -496,6 +524,7 @@ bool valid_params(const lp_params* q, const lp_eos* e, double dt) {
   if (q->rebuild_every < 1) return false;
   if (q->launch_mode < LP_LAUNCH_KERNELS || q->launch_mode > LP_LAUNCH_PERSISTENT) return false;
   if (!(q->skin >= 0.0) || !std::isfinite(q->skin) || q->skin > q->radius) return false;
+  if (q->free_surface != 0 && q->free_surface != 1) return false;
   if (!(e->phi_min < e->phi_max && e->phi_max < e->phi_c)) return false;
   return true;
 }
@@ -571,6 +600,8 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->Ul, n);
   if (s == LP_OK) s = dalloc(c, &c->GVff, n);
   if (s == LP_OK) s = dalloc(c, &c->Lff, n * 2 * kTri);
+  if (s == LP_OK) s = dalloc(c, &c->Xfix, n);
+  if (s == LP_OK) s = dalloc(c, &c->gcnt, n);
   c->capc = std::min(c->cap + 32, 96);
   if (s == LP_OK) s = dalloc(c, &c->cand, n * c->capc);
   if (s == LP_OK) s = dalloc(c, &c->ccnt, n);
@@ -661,6 +692,7 @@ lp_status lp_ctx_sync(lp_ctx* c, void* stream, lp_diag* diag) {
     diag->n_below_floor = (int64_t)d.n_below_floor;
     diag->n_stencil_rows = (int64_t)d.n_stencil_rows;
     diag->n_stencils = (int64_t)d.n_stencils;
+    diag->n_ghosts = (int64_t)d.n_ghosts;
   }
   LP_TRY(reset_diag(c, st));
   if (d.flags & LP_FLAG_TIMEOUT) return LP_ERR_TIMEOUT;
@@ -839,6 +871,21 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
   K.h = q->h; K.inv_h = 1.0 / q->h; K.radius = q->radius; K.r2 = q->radius * q->radius;
   K.gx = q->gx; K.gy = q->gy; K.gz = q->gz; K.floor_z = q->floor_z; K.dt = dt;
   K.mirror_mode = q->mirror_mode; K.cap = cap;
+  K.free_surface = q->free_surface != 0;
+  if (K.free_surface) {
+    // ghost particles (Sec. 3.1 items 6 and 9): fixed-point grid K r <= 8192
+    double g = 1.0;
+    while (g * q->radius > 8192.0) g *= 0.5;
+    while (2.0 * g * q->radius <= 8192.0) g *= 2.0;
+    K.ghost_grid = g;
+    const double rk = q->radius * g;
+    K.ghost_R2 = std::llrint(rk * rk);
+    K.ghost_hk = q->h * g;
+    K.ghost_clear2 = std::llrint((0.5 * K.ghost_hk) * (0.5 * K.ghost_hk));
+    const double phi_g = eos->phi_min * (1.0 - 1e-3);
+    K.ghost_V = 1.0 / phi_g;
+    K.ghost_num = eos->phi_c - phi_g;
+  }
   return K;
 }
 
@@ -885,6 +932,7 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   const double skin = (q->skin > 0.0 && q->rebuild_every == 1) ? q->skin : 0.0;
   LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
   LP_TRY(setup_grids(c, p->ncolumns, q->radius + skin, st));
+  LP_TRY(ensure_twin_buffers(c, q));
   if (skin > 0.0) {
     const int one = 1;
     if (cudaMemcpyAsync(c->d_search, &one, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -980,6 +1028,7 @@ lp_status lp_autotune(lp_ctx* c, const lp_particles* p, const lp_mui* mui, const
   LP_TRY(load_state(c, p, mui, st));
   LP_TRY(begin_columns(c, p, nullptr, c->cx, offs, st));
   LP_TRY(setup_grids(c, p->ncolumns, q->radius, st));
+  LP_TRY(ensure_twin_buffers(c, q));
   // block sizes: per-phase device time of each candidate
   const int cand[3] = {64, 128, 256};
   double best_ms[LP_NPHASES];
@@ -1060,6 +1109,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, initial, offs, true));
   if (!valid_params(q, eos, dt) || q->precision != LP_FP64) return LP_ERR_INVALID_ARG;
+  if (q->free_surface) return LP_ERR_UNIMPLEMENTED;  // adjoint of the ghost rows not built
   if (seed->n != initial->n || (initial->n > 0 && (!seed->x || !seed->y || !seed->z || !seed->u ||
                                                    !seed->v || !seed->w || !seed->V)))
     return LP_ERR_INVALID_ARG;

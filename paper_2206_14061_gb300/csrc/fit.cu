@@ -67,6 +67,16 @@ __global__ void k_split_state(const StepArgs A) {
   if (s < A.n) split_state_body(A, s);
 }
 
+// rows of the entries with a ghost (free surface), ahead of the main kernels
+__global__ void k_gram_twins(const StepArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) gram_twins_body(A, s);
+}
+__global__ void k_pass2_twins(const StepArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) pass2_twins_body(A, s);
+}
+
 __global__ void k_split_p1(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < A.n) split_p1_body(A, s);
@@ -285,13 +295,17 @@ void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs) {
   } else {
     k_split_state<<<(A.n + 255) / 256, 256, 0, st>>>(A);
     const int b = bs < kFFBlock ? bs : kFFBlock;
+    if (A.K.free_surface) k_gram_twins<<<(A.n + 127) / 128, 128, 0, st>>>(A);
     k_gram_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
     k_pass1_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
   }
   k_pass1_fallback<<<152, 64, 0, st>>>(A);
 }
 void launch_pass2(int prec, const StepArgs& A, cudaStream_t st, int bs) {
-  if (prec == LP_MIXED_FF) k_split_p1<<<(A.n + 255) / 256, 256, 0, st>>>(A);
+  if (prec == LP_MIXED_FF) {
+    k_split_p1<<<(A.n + 255) / 256, 256, 0, st>>>(A);
+    if (A.K.free_surface) k_pass2_twins<<<(A.n + 127) / 128, 128, 0, st>>>(A);
+  }
   k_pass2_fallback<<<152, 64, 0, st>>>(A);
   const int nb = (A.n + bs - 1) / bs;
   if (prec == LP_FP64) k_pass2<LP_FP64><<<nb, bs, 0, st>>>(A);

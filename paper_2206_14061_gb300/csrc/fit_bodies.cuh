@@ -59,6 +59,19 @@ __device__ __forceinline__ void push_fallback(const StepArgs& A, int s) {
   }
 }
 
+// Right-hand sides of a ghost row in pass 2 (free boundary, Sec. 3.1 item 9):
+// |gdot|_G - |gdot|_s and V_G - V_s^{n+1}, with |gdot|_G = |gdot|_s (phi_c -
+// phi_G) / (phi_c - phi_s) in the inertial regime (inertial pressure
+// continuous), |gdot|_s otherwise; phi_s = 1 / V_s^{n+1}.
+__device__ __forceinline__ void ghost_rhs2(const StepArgs& A, double gni, double Vi, double* bg,
+                                           double* bv) {
+  const double phi = 1.0 / Vi;
+  const bool inertial = phi > A.K.phi_min && phi <= A.K.phi_max;
+  const double gng = inertial ? gni * (A.K.ghost_num / (A.K.phi_c - phi)) : gni;
+  *bg = gng - gni;
+  *bv = A.K.ghost_V - Vi;
+}
+
 // ------------------------------------------------------------ pass 1
 
 __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s);
@@ -87,11 +100,12 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
       for (int c = 0; c < kNB; ++c) R[f][c] = 0.0;
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-      const int j = code & ~kMirrorBit;
+      const int j = code & kIndexMask;
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
       const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+      if (code & kGhostBit) M.add(-dx, -dy, -dz);  // its ghost: reflected row, b = 0
       double uj = A.u[j], vj = A.v[j], wj = A.w[j];
       if (mir) { uj *= su; vj *= sv; wj *= sw; }
       M.add(dx, dy, dz);
@@ -133,12 +147,13 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
       for (int c = 0; c < kNB; ++c) Rf[f][c] = 0.f;
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-      const int j = code & ~kMirrorBit;
+      const int j = code & kIndexMask;
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
       const float dx = (float)((A.x[j] - xi) * ih), dy = (float)((A.y[j] - yi) * ih);
       const float dz = (float)((zj - zi) * ih);
+      if (code & kGhostBit) M.add(-dx, -dy, -dz);  // its ghost: reflected row, b = 0
       double uj = A.u[j], vj = A.v[j], wj = A.w[j];
       if (mir) { uj *= su; vj *= sv; wj *= sw; }
       M.add(dx, dy, dz);
@@ -175,23 +190,27 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
       for (int q = 0; q < kNB; ++q) g[f][q] = 0.0;
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-      const int j = code & ~kMirrorBit;
+      const int j = code & kIndexMask;
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
       const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
       double uj = A.u[j], vj = A.v[j], wj = A.w[j];
       if (mir) { uj *= su; vj *= sv; wj *= sw; }
-      double a[kNB];
-      taylor_row(dx, dy, dz, a);
-      const double b[3] = {uj - ui, vj - vi, wj - wi};
+      // the entry's row, then (flagged entries) its ghost: reflected row, b = 0
+      for (int t = 0; t < ((code & kGhostBit) ? 2 : 1); ++t) {
+        const double rs = t ? -1.0 : 1.0;
+        double a[kNB];
+        taylor_row(rs * dx, rs * dy, rs * dz, a);
+        const double b[3] = {t ? 0.0 : uj - ui, t ? 0.0 : vj - vi, t ? 0.0 : wj - wi};
 #pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        double r = b[f];
+        for (int f = 0; f < 3; ++f) {
+          double r = b[f];
 #pragma unroll
-        for (int q = 0; q < kNB; ++q) r -= a[q] * c[f][q];
+          for (int q = 0; q < kNB; ++q) r -= a[q] * c[f][q];
 #pragma unroll
-        for (int q = 0; q < kNB; ++q) g[f][q] += a[q] * r;
+          for (int q = 0; q < kNB; ++q) g[f][q] += a[q] * r;
+        }
       }
     }
 #pragma unroll
@@ -215,18 +234,25 @@ static __device__ __noinline__ void pass1_fallback_item(const StepArgs& A, int t
     const double ui = A.u[s], vi = A.v[s], wi = A.w[s];
     const double ih = A.K.inv_h, f2 = 2.0 * A.K.floor_z;
     const int mm = A.K.mirror_mode;
+    int rows = 0;  // a flagged entry adds its ghost: reflected row, b = 0
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-      const int j = code & ~kMirrorBit;
+      const int j = code & kIndexMask;
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
-      taylor_row((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih, &Am[k * kNB]);
+      const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
       double uj = A.u[j], vj = A.v[j], wj = A.w[j];
       if (mir) { uj *= usign(mm, 0); vj *= usign(mm, 1); wj *= usign(mm, 2); }
-      Bm[k * 3 + 0] = uj - ui; Bm[k * 3 + 1] = vj - vi; Bm[k * 3 + 2] = wj - wi;
+      for (int t = 0; t < ((code & kGhostBit) ? 2 : 1) && rows < LP_MAX_CAP; ++t, ++rows) {
+        const double rs = t ? -1.0 : 1.0;
+        taylor_row(rs * dx, rs * dy, rs * dz, &Am[rows * kNB]);
+        Bm[rows * 3 + 0] = t ? 0.0 : uj - ui;
+        Bm[rows * 3 + 1] = t ? 0.0 : vj - vi;
+        Bm[rows * 3 + 2] = t ? 0.0 : wj - wi;
+      }
     }
-    qr_pivoted_solve(m, Am, 3, Bm, C);
+    qr_pivoted_solve(rows, Am, 3, Bm, C);
     double c[3][kNB];
     for (int f = 0; f < 3; ++f)
       for (int q = 0; q < kNB; ++q) c[f][q] = C[f * kNB + q];
@@ -248,17 +274,24 @@ static __device__ __noinline__ void pass2_fallback_item(const StepArgs& A, int t
     const double ih = A.K.inv_h, f2 = 2.0 * A.K.floor_z;
     const double* gn = A.p1 + P1_GN * n;
     const double* Vn = A.p1 + P1_VN * n;
+    double bg_gh = 0.0, bv_gh = 0.0;
+    if (A.K.free_surface) ghost_rhs2(A, gn[s], Vn[s], &bg_gh, &bv_gh);
+    int rows = 0;  // a flagged entry adds its ghost: reflected row
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-      const int j = code & ~kMirrorBit;
+      const int j = code & kIndexMask;
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
-      taylor_row((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih, &Am[k * kNB]);
-      Bm[k * 2 + 0] = (mir ? 0.0 : gn[j]) - gn[s];
-      Bm[k * 2 + 1] = Vn[j] - Vn[s];
+      const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+      for (int t = 0; t < ((code & kGhostBit) ? 2 : 1) && rows < LP_MAX_CAP; ++t, ++rows) {
+        const double rs = t ? -1.0 : 1.0;
+        taylor_row(rs * dx, rs * dy, rs * dz, &Am[rows * kNB]);
+        Bm[rows * 2 + 0] = t ? bg_gh : (mir ? 0.0 : gn[j]) - gn[s];
+        Bm[rows * 2 + 1] = t ? bv_gh : Vn[j] - Vn[s];
+      }
     }
-    qr_pivoted_solve(m, Am, 2, Bm, C);
+    qr_pivoted_solve(rows, Am, 2, Bm, C);
     if (A.coef2)
       for (int q = 0; q < 2 * kNB; ++q) A.coef2[(int64_t)q * n + s] = C[q];
     for (int q = 0; q < 3; ++q) {
@@ -311,7 +344,7 @@ struct FFRow {
 // split position of the neighbour named by a stencil code
 __device__ __forceinline__ void ff_gather(const StepArgs& A, int s, uint32_t code, float4& jh,
                                           float4& jl) {
-  int j = code & ~kMirrorBit;
+  int j = code & kIndexMask;
   if ((unsigned)j >= (unsigned)A.n) j = s;  // never read outside the arrays (zero row)
   jh = A.Xh[j];
   jl = A.Xl[j];
@@ -326,6 +359,17 @@ __device__ __forceinline__ FFRow ff_row_of(const float4& hi, const float4& lo, c
   r.qxx = ff_mul(r.dx, r.dx); r.qyy = ff_mul(r.dy, r.dy); r.qzz = ff_mul(r.dz, r.dz);
   r.qxy = ff_mul(r.dx, r.dy); r.qxz = ff_mul(r.dx, r.dz); r.qyz = ff_mul(r.dy, r.dz);
   return r;
+}
+// Row of stencil entry `code` of particle s, gathered without pipelining.
+__device__ __forceinline__ FFRow ff_entry_row(const StepArgs& A, int s, const float4& hi,
+                                              const float4& lo, uint32_t code) {
+  float4 jh, jl;
+  ff_gather(A, s, code, jh, jl);
+  return ff_row_of(hi, lo, jh, jl, code);
+}
+// Number of entries with a ghost (kGhostBit), at the end of the stencil of s.
+__device__ __forceinline__ int ghost_count(const StepArgs& A, int s, int m) {
+  return A.K.free_surface ? min(max(A.gcnt[s], 0), m) : 0;
 }
 __device__ __forceinline__ void ff_taylor(const FFRow& r, ff* a) {
   a[0] = r.dx; a[1] = r.dy; a[2] = r.dz;
@@ -346,6 +390,21 @@ __device__ __forceinline__ void ff_moments_add(ff* mo, const FFRow& r) {
   ff_acc(mo[22], r.qyy, r.qyz); ff_acc(mo[23], r.qzz, r.qxz); ff_acc(mo[24], r.qzz, r.qyz);
   ff_acc(mo[25], r.qxx, r.qyy); ff_acc(mo[26], r.qxx, r.qzz); ff_acc(mo[27], r.qyy, r.qzz);
   ff_acc(mo[28], r.qxx, r.qyz); ff_acc(mo[29], r.qyy, r.qxz); ff_acc(mo[30], r.qzz, r.qxy);
+}
+
+// Moments of an entry and its ghost (the entry reflected through the
+// particle): the reflection flips the odd (degree-3) terms, so together they
+// add the even moments twice and the odd ones not at all.
+__device__ __forceinline__ void ff_moments_add_twin(ff* mo, const FFRow& r) {
+  const ff xx2 = ff_scale(r.qxx, 2.f), yy2 = ff_scale(r.qyy, 2.f), zz2 = ff_scale(r.qzz, 2.f);
+  ff_acc1(mo[0], xx2); ff_acc1(mo[1], yy2); ff_acc1(mo[2], zz2);
+  ff_acc1(mo[3], ff_scale(r.qxy, 2.f)); ff_acc1(mo[4], ff_scale(r.qxz, 2.f));
+  ff_acc1(mo[5], ff_scale(r.qyz, 2.f));
+  ff_acc(mo[16], xx2, r.qxx); ff_acc(mo[17], yy2, r.qyy); ff_acc(mo[18], zz2, r.qzz);
+  ff_acc(mo[19], xx2, r.qxy); ff_acc(mo[20], xx2, r.qxz); ff_acc(mo[21], yy2, r.qxy);
+  ff_acc(mo[22], yy2, r.qyz); ff_acc(mo[23], zz2, r.qxz); ff_acc(mo[24], zz2, r.qyz);
+  ff_acc(mo[25], xx2, r.qyy); ff_acc(mo[26], xx2, r.qzz); ff_acc(mo[27], yy2, r.qzz);
+  ff_acc(mo[28], xx2, r.qyz); ff_acc(mo[29], yy2, r.qxz); ff_acc(mo[30], zz2, r.qxy);
 }
 
 // packed Gram matrix from the moments (same entries as Moments::gram)
@@ -435,6 +494,80 @@ __device__ __forceinline__ void ff_chol_solve(const StepArgs& A, int s, ff (*r)[
   }
 }
 
+// Entries with a ghost sit at the end of the stencil (kGhostBit). Their rows
+// are handled by the two bodies below, in kernels of their own, so that the
+// main row loops keep their register allocation; the main bodies add the
+// stored sums.
+
+// Moments of the entries with a ghost together with their ghosts (even
+// moments twice, odd ones cancel): Tg, 31 float-float, hi then lo, k-major.
+__device__ __forceinline__ void gram_twins_body(const StepArgs& A, int s) {
+  const int n = A.n;
+  const int m = min(A.cnt[s], A.cap);
+  const int mr = m - ghost_count(A, s, m);
+  if (mr == m) return;
+  const float4 hi = A.Xh[s], lo = A.Xl[s];
+  ff t[31];
+#pragma unroll
+  for (int q = 0; q < 31; ++q) t[q] = {0.f, 0.f};
+#pragma unroll 1
+  for (int k = mr; k < m; ++k)
+    ff_moments_add_twin(t, ff_entry_row(A, s, hi, lo, (uint32_t)A.nbr[(int64_t)k * n + s]));
+#pragma unroll
+  for (int q = 0; q < 31; ++q) {
+    const ff v = ff_norm(t[q]);
+    A.Tg[(int64_t)q * n + s] = v.h;
+    A.Tg[(int64_t)(31 + q) * n + s] = v.l;
+  }
+}
+
+// Pass-2 right-hand-side terms of the entries with a ghost and their ghosts
+// (reflected row, right-hand sides fixed by the particle): b_j a + b_G a~,
+// a~ the row with its linear terms negated. T2: 2 x 9 float-float, hi then
+// lo, k-major. Needs the pass-1 outputs and their split copy (GVff).
+__device__ __forceinline__ void pass2_twins_body(const StepArgs& A, int s) {
+  const int n = A.n;
+  const int m = min(A.cnt[s], A.cap);
+  const int mr = m - ghost_count(A, s, m);
+  if (mr == m || A.fbslot[s] != -1) return;
+  const float4 hi = A.Xh[s], lo = A.Xl[s];
+  const float4 gvi = A.GVff[s];
+  double bgd, bvd;
+  ghost_rhs2(A, A.p1[P1_GN * n + s], A.p1[P1_VN * n + s], &bgd, &bvd);
+  const ff bgg = ff_of(bgd), bvg = ff_of(bvd);
+  ff R[2][kNB];
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+#pragma unroll 1
+  for (int k = mr; k < m; ++k) {
+    const uint32_t c0 = (uint32_t)A.nbr[(int64_t)k * n + s];
+    const int j = c0 & kIndexMask;
+    if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
+    ff a[kNB];
+    ff_taylor(ff_entry_row(A, s, hi, lo, c0), a);
+    const float4 gvj = A.GVff[j];
+    const ff bg = (c0 >> 31) ? ff{-gvi.x, -gvi.y} : ff_diff(gvj.x, gvj.y, gvi.x, gvi.y);
+    const ff bv = ff_diff(gvj.z, gvj.w, gvi.z, gvi.w);
+    const ff lin[2] = {ff_sub(bg, bgg), ff_sub(bv, bvg)};
+    const ff quad[2] = {ff_add(bg, bgg), ff_add(bv, bvg)};
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+      ff_acc(R[0][q], q < 3 ? lin[0] : quad[0], a[q]);
+      ff_acc(R[1][q], q < 3 ? lin[1] : quad[1], a[q]);
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+      const ff v = ff_norm(R[f][q]);
+      A.T2[(int64_t)(f * kNB + q) * n + s] = v.h;
+      A.T2[(int64_t)(18 + f * kNB + q) * n + s] = v.l;
+    }
+}
+
 // Gram matrix of a stencil in float-float (positions only): the 31 moments,
 // the Cholesky factor with the pivot test, stored for both passes. Stencils
 // that fail the test (or have fewer than 9 rows) are queued for the
@@ -443,23 +576,32 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);
   const float4 hi = A.Xh[s], lo = A.Xl[s];
+  // entries with a ghost (at the end of the stencil): their moments, with
+  // their ghosts', come from gram_twins_body and seed the sums
+  const int mr = m - ghost_count(A, s, m);
   ff mo[31];
+  if (mr < m) {
 #pragma unroll
-  for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+    for (int q = 0; q < 31; ++q)
+      mo[q] = ff{A.Tg[(int64_t)q * n + s], A.Tg[(int64_t)(31 + q) * n + s]};
+  } else {
+#pragma unroll
+    for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+  }
   // software pipeline: stencil codes are loaded two rows ahead and the
   // neighbour's values one row ahead, so the dependent loads of a row
-  // overlap the arithmetic of the previous one (same in both passes)
-  uint32_t code = m > 0 ? (uint32_t)A.nbr[s] : 0u;
-  uint32_t nxt = m > 1 ? (uint32_t)A.nbr[(int64_t)n + s] : 0u;
+  // overlap the arithmetic of the previous one (same in both passes).
+  uint32_t code = mr > 0 ? (uint32_t)A.nbr[s] : 0u;
+  uint32_t nxt = mr > 1 ? (uint32_t)A.nbr[(int64_t)n + s] : 0u;
   float4 jh = make_float4(0.f, 0.f, 0.f, 0.f), jl = jh;
-  if (m > 0) ff_gather(A, s, code, jh, jl);
-  for (int k = 0; k < m; ++k) {
+  if (mr > 0) ff_gather(A, s, code, jh, jl);
+  for (int k = 0; k < mr; ++k) {
     const uint32_t c0 = code;
     const float4 h0 = jh, l0 = jl;
-    if (k + 1 < m) {
+    if (k + 1 < mr) {
       code = nxt;
       ff_gather(A, s, code, jh, jl);
-      if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
+      if (k + 2 < mr) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
     ff_moments_add(mo, ff_row_of(hi, lo, h0, l0, c0));
   }
@@ -484,7 +626,7 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
 __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   if (A.fbslot[s] != -1) return;  // queued for the pivoted-QR fit
   const int n = A.n;
-  const int m = min(A.cnt[s], A.cap);
+  const int m = min(A.cnt[s], A.cap);  // ghost rows carry b = 0: no right-hand side
   const float4 hi = A.Xh[s], lo = A.Xl[s];
   const float4 uh = A.Uh[s], ul = A.Ul[s];
   const int mm = A.K.mirror_mode;
@@ -500,7 +642,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh, vh = xh, vl = xh;
   if (m > 0) {
     ff_gather(A, s, code, xh, xl);
-    const unsigned jj = min((unsigned)(code & ~kMirrorBit), (unsigned)(n - 1));
+    const unsigned jj = min(code & kIndexMask, (unsigned)(n - 1));
     vh = A.Uh[jj]; vl = A.Ul[jj];
   }
   for (int k = 0; k < m; ++k) {
@@ -509,14 +651,14 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
     if (k + 1 < m) {
       code = nxt;
       ff_gather(A, s, code, xh, xl);
-      const unsigned jj = min((unsigned)(code & ~kMirrorBit), (unsigned)(n - 1));
+      const unsigned jj = min(code & kIndexMask, (unsigned)(n - 1));
       vh = A.Uh[jj]; vl = A.Ul[jj];
       if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
     const FFRow r = ff_row_of(hi, lo, h0, l0, c0);
     ff a[kNB];
     ff_taylor(r, a);
-    const int j = c0 & ~kMirrorBit;
+    const int j = c0 & kIndexMask;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = c0 >> 31;
     const float ujh[3] = {jh.x, jh.y, jh.z}, ujl[3] = {jl.x, jl.y, jl.z};
@@ -539,22 +681,34 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
 }
 
 // pass-2 fits in float-float: gradients of |gdot|^n and V^{n+1}
-__device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, double* gg,
-                                               double* gV) {
+__device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, double gni,
+                                               double Vi, double* gg, double* gV) {
   const int n = A.n;
   const float4 hi = A.Xh[s], lo = A.Xl[s];
   const float4 gvi = A.GVff[s];
+  // entries with a ghost (at the end of the stencil): their terms, with their
+  // ghosts', come from pass2_twins_body and seed the sums
+  const int mg = ghost_count(A, s, m);
+  m -= mg;
   ff R[2][kNB];
+  if (mg) {
 #pragma unroll
-  for (int f = 0; f < 2; ++f)
+    for (int f = 0; f < 2; ++f)
 #pragma unroll
-    for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+      for (int q = 0; q < kNB; ++q)
+        R[f][q] = ff{A.T2[(int64_t)(f * kNB + q) * n + s], A.T2[(int64_t)(18 + f * kNB + q) * n + s]};
+  } else {
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+  }
   uint32_t code = m > 0 ? (uint32_t)A.nbr[s] : 0u;
   uint32_t nxt = m > 1 ? (uint32_t)A.nbr[(int64_t)n + s] : 0u;
   float4 jh = make_float4(0.f, 0.f, 0.f, 0.f), jl = jh, jg = jh;
   if (m > 0) {
     ff_gather(A, s, code, jh, jl);
-    jg = A.GVff[min((unsigned)(code & ~kMirrorBit), (unsigned)(n - 1))];
+    jg = A.GVff[min(code & kIndexMask, (unsigned)(n - 1))];
   }
   for (int k = 0; k < m; ++k) {
     const uint32_t c0 = code;
@@ -562,13 +716,13 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
     if (k + 1 < m) {
       code = nxt;
       ff_gather(A, s, code, jh, jl);
-      jg = A.GVff[min((unsigned)(code & ~kMirrorBit), (unsigned)(n - 1))];
+      jg = A.GVff[min(code & kIndexMask, (unsigned)(n - 1))];
       if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
     const FFRow r = ff_row_of(hi, lo, h0, l0, c0);
     ff a[kNB];
     ff_taylor(r, a);
-    const int j = c0 & ~kMirrorBit;
+    const int j = c0 & kIndexMask;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = c0 >> 31;
     const ff bg = mir ? ff{-gvi.x, -gvi.y} : ff_diff(gvj.x, gvj.y, gvi.x, gvi.y);
@@ -613,27 +767,34 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     } else if (slot == -1) {
       const int m = min(A.cnt[s], A.cap);
       if (PREC == LP_MIXED_FF) {
-        pass2_ff_grads(A, s, m, gg, gV);
+        pass2_ff_grads(A, s, m, gni, Vi, gg, gV);
       } else if (PREC == LP_FP64) {
         double R[2][kNB];
 #pragma unroll
         for (int f = 0; f < 2; ++f)
 #pragma unroll
           for (int c = 0; c < kNB; ++c) R[f][c] = 0.0;
+        double bg_gh = 0.0, bv_gh = 0.0;
+        if (A.K.free_surface) ghost_rhs2(A, gni, Vi, &bg_gh, &bv_gh);
         for (int k = 0; k < m; ++k) {
           const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-          const int j = code & ~kMirrorBit;
+          const int j = code & kIndexMask;
           if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
-          double a[kNB];
-          taylor_row((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih, a);
-          const double bg = (mir ? 0.0 : gn[j]) - gni;
-          const double bv = Vn[j] - Vi;
+          const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+          // the entry's row, then (flagged entries) its ghost's reflected row
+          for (int t = 0; t < ((code & kGhostBit) ? 2 : 1); ++t) {
+            const double rs = t ? -1.0 : 1.0;
+            double a[kNB];
+            taylor_row(rs * dx, rs * dy, rs * dz, a);
+            const double bg = t ? bg_gh : (mir ? 0.0 : gn[j]) - gni;
+            const double bv = t ? bv_gh : Vn[j] - Vi;
 #pragma unroll
-          for (int c = 0; c < kNB; ++c) {
-            R[0][c] += bg * a[c];
-            R[1][c] += bv * a[c];
+            for (int c = 0; c < kNB; ++c) {
+              R[0][c] += bg * a[c];
+              R[1][c] += bv * a[c];
+            }
           }
         }
         double L[kTri];
@@ -662,21 +823,27 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
         for (int f = 0; f < 2; ++f)
 #pragma unroll
           for (int c = 0; c < kNB; ++c) Rf[f][c] = 0.f;
+        double bg_gh = 0.0, bv_gh = 0.0;
+        if (A.K.free_surface) ghost_rhs2(A, gni, Vi, &bg_gh, &bv_gh);
         for (int k = 0; k < m; ++k) {
           const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-          const int j = code & ~kMirrorBit;
+          const int j = code & kIndexMask;
           if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
-          float a[kNB];
-          taylor_row((float)((A.x[j] - xi) * ih), (float)((A.y[j] - yi) * ih),
-                     (float)((zj - zi) * ih), a);
-          const float bg = (float)((mir ? 0.0 : gn[j]) - gni);
-          const float bv = (float)(Vn[j] - Vi);
+          const float dx = (float)((A.x[j] - xi) * ih), dy = (float)((A.y[j] - yi) * ih);
+          const float dz = (float)((zj - zi) * ih);
+          for (int t = 0; t < ((code & kGhostBit) ? 2 : 1); ++t) {
+            const float rs = t ? -1.f : 1.f;
+            float a[kNB];
+            taylor_row(rs * dx, rs * dy, rs * dz, a);
+            const float bg = (float)(t ? bg_gh : (mir ? 0.0 : gn[j]) - gni);
+            const float bv = (float)(t ? bv_gh : Vn[j] - Vi);
 #pragma unroll
-          for (int c = 0; c < kNB; ++c) {
-            Rf[0][c] += bg * a[c];
-            Rf[1][c] += bv * a[c];
+            for (int c = 0; c < kNB; ++c) {
+              Rf[0][c] += bg * a[c];
+              Rf[1][c] += bv * a[c];
+            }
           }
         }
         chol9_solve(L, Rf[0]);
@@ -689,22 +856,26 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
         }
         for (int k = 0; k < m; ++k) {
           const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-          const int j = code & ~kMirrorBit;
+          const int j = code & kIndexMask;
           if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
-          double a[kNB];
-          taylor_row((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih, a);
-          double r0 = (mir ? 0.0 : gn[j]) - gni, r1 = Vn[j] - Vi;
+          const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+          for (int t = 0; t < ((code & kGhostBit) ? 2 : 1); ++t) {
+            const double rs = t ? -1.0 : 1.0;
+            double a[kNB];
+            taylor_row(rs * dx, rs * dy, rs * dz, a);
+            double r0 = t ? bg_gh : (mir ? 0.0 : gn[j]) - gni, r1 = t ? bv_gh : Vn[j] - Vi;
 #pragma unroll
-          for (int q = 0; q < kNB; ++q) {
-            r0 -= a[q] * c2[0][q];
-            r1 -= a[q] * c2[1][q];
-          }
+            for (int q = 0; q < kNB; ++q) {
+              r0 -= a[q] * c2[0][q];
+              r1 -= a[q] * c2[1][q];
+            }
 #pragma unroll
-          for (int q = 0; q < kNB; ++q) {
-            g[0][q] += a[q] * r0;
-            g[1][q] += a[q] * r1;
+            for (int q = 0; q < kNB; ++q) {
+              g[0][q] += a[q] * r0;
+              g[1][q] += a[q] * r1;
+            }
           }
         }
         chol9_solve(L, g[0]);

@@ -12,6 +12,10 @@
 namespace lp {
 
 constexpr uint32_t kMirrorBit = 0x80000000u;
+// ghost particle: point reflection, through the particle, of the entry in the
+// low bits (free boundary, Sec. 3.1 item 9); indices are below 2^30
+constexpr uint32_t kGhostBit = 0x40000000u;
+constexpr uint32_t kIndexMask = 0x3fffffffu;
 constexpr int kNB = 9;            // quadratic Taylor basis in 3D, no constant term
 constexpr int kTri = 45;          // packed lower triangle of a 9x9 matrix
 constexpr int kMaxColumns = 4096;
@@ -43,6 +47,11 @@ struct StepConsts {
   double gx, gy, gz, floor_z, dt;
   int mirror_mode;
   int cap;
+  // free-surface ghosts: fixed-point grid K (power of two, K r <= 8192),
+  // round((K r)^2), K h, round((K h / 2)^2), 1/phi_G, phi_c - phi_G
+  int free_surface;
+  double ghost_grid, ghost_hk, ghost_V, ghost_num;
+  long long ghost_R2, ghost_clear2;
 };
 
 // device diagnostics, accumulated until lp_ctx_sync
@@ -51,7 +60,7 @@ struct DevDiag {
   int min_stencil, max_stencil;
   int pad;
   unsigned long long n_overflow, n_fallback, n_gas, n_quasistatic, n_over_c, n_nonfinite,
-      n_below_floor, n_stencil_rows, n_stencils;
+      n_below_floor, n_stencil_rows, n_stencils, n_ghosts;
 };
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
@@ -164,6 +173,11 @@ struct StepArgs {
   // |gdot| and V^{n+1} split (hi, lo, hi, lo), Gram matrices in float-float
   const GridCol* grids;
   float4 *Xh, *Xl, *Uh, *Ul, *GVff;
+  int4* Xfix;       // free surface: round(K (x, y, z, 2 floor_z - z)) per particle,
+                    // relative to the column's fixed-point origin
+  int32_t* gcnt;    // free surface: entries with a ghost, at the end of each stencil
+  float *Tg, *T2;   // free surface: sums over those entries and their ghosts
+                    // (Gram moments 62 x n, pass-2 right-hand sides 36 x n)
   float* Lff;       // 90 * n: float-float Cholesky factor of the Gram matrix,
                     // hi (45) then lo (45), k-major; the diagonal holds 1/L_jj
   // Verlet candidate lists: positions at the last search and the flag that

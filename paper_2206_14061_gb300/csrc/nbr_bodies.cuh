@@ -330,4 +330,133 @@ __device__ __forceinline__ void filter_body(
   stencil_stats(live, c, cap, dg);
 }
 
+// ------------------------------------------------------- free boundary
+// Ghost particles (Sec. 3.1 items 6 and 9). The paper leaves the test and the
+// placement open; the reading, also the oracle's:
+//  - positions in fixed point, X = round(K x) on a power-of-two grid K with
+//    K r <= 8192, offsets o_k = X_k - X_i (exact integers; for stencil
+//    entries |o| <= 8193, so squares and pair sums fit 32 bits);
+//  - weights w_k = max(0, R2 - |o_k|^2), R2 = round((K r)^2);
+//  - one-sided stencil: |S| > 0.22 K h sum w_k with S = sum w_k o_k;
+//  - a ghost at -o_k for every entry with o_k . S >= (K h / 2) |S| (o_k . S
+//    exact in 64 bits) whose reflection has no entry within h/2 and, with
+//    floor mirrors, does not lie below the floor ((z_i + z_i) - z_k <
+//    floor_z).
+// The FP64 operations are _rn intrinsics in the oracle's order, so the
+// decisions are the oracle's bit for bit.
+//
+// A ghost is the reflection of an existing entry, so it is stored as a flag
+// (kGhostBit) on that entry: the entry stands for two rows, itself and its
+// reflection. Flagged entries are moved to the end of the stencil and
+// gcnt[s] counts them; the stencil size is unchanged, but entries plus
+// ghosts must fit in cap (else LP_FLAG_OVERFLOW). Positions are stored
+// relative to the column's fixed-point origin (an exact integer shift), as
+// 32-bit integers.
+
+// fixed-point position (x, y, z, floor-mirror height) of particle s
+__device__ __forceinline__ void ghost_fix_body(int s, const double* __restrict__ x,
+                                               const double* __restrict__ y,
+                                               const double* __restrict__ z,
+                                               const int32_t* __restrict__ colid,
+                                               const GridCol* __restrict__ grids, double grid,
+                                               double floor_z, int4* __restrict__ X) {
+  const GridCol g = grids[colid[s]];
+  const long long ox = __double2ll_rn(__dmul_rn(g.ox, grid));
+  const long long oy = __double2ll_rn(__dmul_rn(g.oy, grid));
+  const long long oz = __double2ll_rn(__dmul_rn(g.oz, grid));
+  const double zm = __dsub_rn(__dmul_rn(2.0, floor_z), z[s]);
+  X[s] = make_int4((int)(__double2ll_rn(__dmul_rn(x[s], grid)) - ox),
+                   (int)(__double2ll_rn(__dmul_rn(y[s], grid)) - oy),
+                   (int)(__double2ll_rn(__dmul_rn(z[s], grid)) - oz),
+                   (int)(__double2ll_rn(__dmul_rn(zm, grid)) - oz));
+}
+
+// Flags the entries of particle s whose reflections are ghosts; every lane of
+// the warp must call it (live or not).
+__device__ __forceinline__ void ghost_body(int s, bool live, int n, const double* __restrict__ z,
+                                           const int4* __restrict__ X,
+                                           int32_t* __restrict__ nbr, const int32_t* __restrict__ cnt,
+                                           int32_t* __restrict__ gcnt, const StepConsts& K,
+                                           DevDiag* __restrict__ dg) {
+  int twins = 0;
+  bool over = false;
+  if (live) {
+    const int m = min(cnt[s], K.cap);
+    const int4 xi = X[s];
+    short o[3][LP_MAX_CAP];  // offsets of the entries (|o| <= 8193)
+    long long S0 = 0, S1 = 0, S2 = 0, W = 0;
+    const int R2 = (int)K.ghost_R2;
+    bool ok = m > 0;
+    // software pipeline: codes two entries ahead, positions one ahead
+    uint32_t nc = m > 0 ? (uint32_t)nbr[s] : 0u;
+    uint32_t nn = m > 1 ? (uint32_t)nbr[(int64_t)n + s] : 0u;
+    int4 nx = m > 0 ? X[min(nc & kIndexMask, (uint32_t)(n - 1))] : xi;
+    for (int k = 0; k < m; ++k) {
+      const uint32_t code = nc;
+      const int4 xj = nx;
+      if (k + 1 < m) {
+        nc = nn;
+        nx = X[min(nc & kIndexMask, (uint32_t)(n - 1))];
+        if (k + 2 < m) nn = (uint32_t)nbr[(int64_t)(k + 2) * n + s];
+      }
+      if ((code & kIndexMask) >= (uint32_t)n || (code & kGhostBit)) { ok = false; break; }
+      const int o0 = xj.x - xi.x, o1 = xj.y - xi.y;
+      const int o2 = ((code & kMirrorBit) ? xj.w : xj.z) - xi.z;
+      o[0][k] = (short)o0; o[1][k] = (short)o1; o[2][k] = (short)o2;
+      const int q = (o0 * o0 + o1 * o1) + o2 * o2;
+      const int w = q < R2 ? R2 - q : 0;
+      S0 += (long long)w * o0;
+      S1 += (long long)w * o1;
+      S2 += (long long)w * o2;
+      W += w;
+    }
+    const double sx = (double)S0, sy = (double)S1, sz = (double)S2;
+    const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
+    const double lim = __dmul_rn(__dmul_rn(0.22, K.ghost_hk), (double)W);
+    if (ok && s2 > __dmul_rn(lim, lim)) {
+      const double dep = __dmul_rn(0.5, K.ghost_hk);
+      const double dep2s2 = __dmul_rn(__dmul_rn(dep, dep), s2);
+      const double zi = z[s];
+      const double f2 = __dmul_rn(2.0, K.floor_z);
+      const int clear2 = (int)K.ghost_clear2;
+      unsigned long long tw = 0ull;
+      for (int k = 0; k < m; ++k) {
+        const int o0 = o[0][k], o1 = o[1][k], o2 = o[2][k];
+        const double ds = (double)(((long long)o0 * S0 + (long long)o1 * S1) + (long long)o2 * S2);
+        if (!(ds > 0.0 && __dmul_rn(ds, ds) >= dep2s2)) continue;
+        if (K.mirror_mode != LP_MIRROR_NONE) {
+          const uint32_t code = (uint32_t)nbr[(int64_t)k * n + s];
+          const int j = code & kIndexMask;
+          const double zk = (code & kMirrorBit) ? __dsub_rn(f2, z[j]) : z[j];
+          if (__dsub_rn(__dadd_rn(zi, zi), zk) < K.floor_z) continue;
+        }
+        int hits = 0;  // entries within h/2 of the reflection
+        for (int l = 0; l < m; ++l) {
+          const int e0 = o[0][l] + o0, e1 = o[1][l] + o1, e2 = o[2][l] + o2;
+          hits += (e0 * e0 + e1 * e1) + e2 * e2 < clear2;
+        }
+        if (!hits) tw |= 1ull << k;
+      }
+      twins = __popcll(tw);
+      if (twins) {
+        over = m + twins > K.cap;
+        // entries without a ghost first (in their order), then the flagged ones
+        int32_t cd[LP_MAX_CAP];
+        for (int k = 0; k < m; ++k) cd[k] = nbr[(int64_t)k * n + s];
+        int w = 0;
+        for (int k = 0; k < m; ++k)
+          if (!((tw >> k) & 1ull)) nbr[(int64_t)(w++) * n + s] = cd[k];
+        for (int k = 0; k < m; ++k)
+          if ((tw >> k) & 1ull) nbr[(int64_t)(w++) * n + s] = (int32_t)((uint32_t)cd[k] | kGhostBit);
+      }
+    }
+    gcnt[s] = twins;
+  }
+  unsigned long long a = (unsigned long long)twins;
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0 && a) atomicAdd(&dg->n_ghosts, a);
+  warp_count(&dg->n_overflow, live && over);
+  if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
+}
+
 }  // namespace lp

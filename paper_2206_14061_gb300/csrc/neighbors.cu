@@ -227,6 +227,24 @@ k_filter(int n, const double* __restrict__ x, const double* __restrict__ y,
               cnt, dg);
 }
 
+// Free-surface ghosts (ghost_body): fixed-point positions, then completion of
+// the stencils of one-sided particles.
+__global__ void k_ghost_fix(int n, const double* __restrict__ x, const double* __restrict__ y,
+                            const double* __restrict__ z, const int32_t* __restrict__ colid,
+                            const GridCol* __restrict__ grids, double grid, double floor_z,
+                            int4* __restrict__ X) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) ghost_fix_body(s, x, y, z, colid, grids, grid, floor_z, X);
+}
+
+__global__ void __launch_bounds__(kMaxBlock)
+k_ghosts(int n, const double* __restrict__ z, const int4* __restrict__ X,
+         int32_t* __restrict__ nbr, const int32_t* __restrict__ cnt, int32_t* __restrict__ gcnt,
+         const StepConsts K, DevDiag* __restrict__ dg) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  ghost_body(s, s < n, n, z, X, nbr, cnt, gcnt, K, dg);
+}
+
 // Stencils from sorted indices to caller indices.
 __global__ void k_nbr_to_caller(int n, int cap, const int32_t* __restrict__ ids,
                                 const int32_t* __restrict__ nbr_s, const int32_t* __restrict__ cnt_s,
@@ -297,6 +315,14 @@ void launch_filter(int n, const double* x, const double* y, const double* z, con
                    int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs) {
   k_filter<<<(n + bs - 1) / bs, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
                                              floor_z, cap, nbr, cnt, dg, search);
+}
+void launch_ghosts(int n, const double* x, const double* y, const double* z,
+                   const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
+                   const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
+                   cudaStream_t st, int bs) {
+  k_ghost_fix<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, z, colid, grids, K.ghost_grid, K.floor_z,
+                                               X);
+  k_ghosts<<<(n + bs - 1) / bs, bs, 0, st>>>(n, z, X, nbr, cnt, gcnt, K, dg);
 }
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st) {

@@ -125,9 +125,13 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
     LP_SYNC_OR_LEAVE();
   }
   if (P.rebuild) {
-    for (int t = tid; t < n; t += nth)
+    for (int t = tid; t < n; t += nth) {
       gather_body(t, n, srch ? P.tmp : P.iota, P.src, P.dst, P.nsrc, P.ids_in, P.ids_out,
                   P.colid_in, P.colid_out, P.grids, P.pf);
+      // free surface: fixed-point position of the slot this thread just wrote
+      if (S.K.free_surface)
+        ghost_fix_body(t, S.x, S.y, S.z, S.colid, S.grids, S.K.ghost_grid, S.K.floor_z, S.Xfix);
+    }
     LP_SYNC_OR_LEAVE();
   }
   if (srch) {
@@ -160,12 +164,23 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
                   P.radius, P.floor_z, P.cap, P.nbr, P.cnt, S.dg);
     }
   }
+  // ghosts complete the stencils this thread just built (positions of all
+  // particles were fixed before the last barrier)
+  if (P.rebuild && S.K.free_surface) {
+    for (int base = 0; base < n; base += nth) {
+      const int s = base + tid;
+      ghost_body(s, s < n, n, S.z, S.Xfix, P.nbr, P.cnt, S.gcnt, S.K, S.dg);
+    }
+  }
   if (tid == 0) *S.fb_count = 0;
   if (PREC == LP_MIXED_FF)
     for (int s = tid; s < n; s += nth) split_state_body(S, s);
   LP_SYNC_OR_LEAVE();
   if (PREC == LP_MIXED_FF) {
-    for (int s = tid; s < n; s += nth) gram_ff_body(S, s);
+    for (int s = tid; s < n; s += nth) {
+      if (S.K.free_surface) gram_twins_body(S, s);  // read back by the same thread
+      gram_ff_body(S, s);
+    }
     LP_SYNC_OR_LEAVE();
   }
   for (int s = tid; s < n; s += nth) pass1_body<PREC>(S, s);
@@ -182,6 +197,7 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
   LP_SYNC_OR_LEAVE();
   for (int base = 0; base < n; base += nth) {
     const int s = base + tid;
+    if (PREC == LP_MIXED_FF && S.K.free_surface && s < n) pass2_twins_body(S, s);
     pass2_body<PREC>(S, s, s < n);
   }
 }
