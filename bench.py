@@ -49,6 +49,8 @@ def parse():
                     help="Verlet skin in lattice spacings (0: full search every step)")
     ap.add_argument("--free-surface", action="store_true",
                     help="ghost particles at free boundaries (Sec. 3.1 item 9)")
+    ap.add_argument("--no-free-surface", action="store_true",
+                    help="skip the line with free-surface ghosts")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
@@ -198,12 +200,14 @@ def our_arm(args):
     stream = torch.cuda.Stream(device=dev)
     R = max(1, args.restart_every)
 
+    ghosts = {"on": int(args.free_surface)}
+
     def params(prec, graph=1):
         return dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
                     floor_z=0.0, mirror_mode=1,
                     precision=PREC[prec],
                     rebuild_every=1, launch_mode=graph, skin=args.skin * pd["h"],
-                    free_surface=int(args.free_surface))
+                    free_surface=ghosts["on"])
 
     def run(nsteps, prec, graph=1):
         done = 0
@@ -314,6 +318,17 @@ def our_arm(args):
                            "ms_per_step": mso / args.steps, "phase_ms_per_step": pho,
                            "pass1_achieved": wo / (pho["pass1"] / 1e3) / 1e12,
                            "pass1_unit": uo, "pass1_frac": wo / (pho["pass1"] / 1e3) / 1e12 / po}
+
+    if not args.no_free_surface and not args.free_surface:
+        # the same workload with free-surface ghost particles (Sec. 3.1 item 9)
+        ghosts["on"] = 1
+        msg, _, _, dgg, profg, _ = bench(args.precision)
+        ghosts["on"] = 0
+        line["free_surface"] = {
+            "value": n * args.steps * world / (msg / 1e3), "unit": UNIT,
+            "ms_per_step": msg / args.steps,
+            "phase_ms_per_step": {k: v / max(profg["steps"], 1) for k, v in profg["ms"].items()},
+            "ghost_entries_per_step": dgg["n_ghosts"] / max(args.steps, 1)}
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world)
