@@ -103,6 +103,8 @@ typedef struct {
   double floor_z, dt;
   int32_t mirror_mode;  // 0 none, 1 no-slip (u* = -u), 2 free-slip (w* = -w)
   int32_t free_surface;  // 1: ghost particles complete free-surface stencils
+  int32_t time_scheme;   // 0: the paper's step (V first), 1: Heun's method (RK2)
+  int32_t pad;
 } orc_params;
 
 typedef struct {
@@ -575,9 +577,11 @@ static inline T ghost_gn(const orc_params* p, const T& phi_f, const T& gn_f) {
 // gradient, the closure and the regime at phi^{n+1} = 1/V^{n+1}) together with
 // the time-n velocity quantities gdot^n, |gdot|^n, grad |gdot|^n, LAP u^n and
 // grad DIV u^n. Pass 1 fits u, v, w; pass 2 fits |gdot|^n and V^{n+1}.
+// With euler = true, pass 2 takes V^n (not V^{n+1}): the right-hand side
+// of the semi-discrete system at one time level, for Heun's method.
 template <class T>
 static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const Stencils& st,
-                   Detail<T>& o, int64_t* n_rank_deficient) {
+                   Detail<T>& o, int64_t* n_rank_deficient, bool euler = false) {
   const orc_params* p = tp.p;
   const double h = p->h;
   const double dt = p->dt;
@@ -645,12 +649,13 @@ static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const St
     // free surface (Sec. 3.1 item 9): a ghost has solid fraction phi_G just
     // below phi_min and the |gdot| that keeps the inertial pressure of i
     // continuous, |gdot|_G = |gdot|_i (phi_c - phi_G) / (phi_c - phi_i)
+    const std::vector<T>& Vf = euler ? s.V : o.Vnew;  // V of the closure and the fit
     const double phi_g = ghost_phi(p);
-    const T gn_ghost = ghost_gn<T>(p, T(1.0) / o.Vnew[i], o.gn[i]);
+    const T gn_ghost = ghost_gn<T>(p, T(1.0) / Vf[i], o.gn[i]);
     auto field = [&](int q, int64_t j, bool mir, bool ghost) -> T {
       if (ghost) return q == 0 ? gn_ghost : T(1.0 / phi_g);
       if (q == 0) return mir ? T(0.0) : o.gn[j];
-      return o.Vnew[j];
+      return Vf[j];
     };
     T C[2 * NB];
     fit_particle<T>(i, s.x.data(), s.y.data(), s.z.data(), row, m, h, p->floor_z, 2, field, C);
@@ -660,7 +665,7 @@ static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const St
       o.gg[3 * i + c] = gg[c];
       o.gV[3 * i + c] = gV[c];
     }
-    const T Vi = o.Vnew[i];
+    const T Vi = Vf[i];
     const T phi = T(1.0) / Vi;
     int r = regime_of(val(phi), p->phi_min, p->phi_max);
     o.reg[i] = (int8_t)r;
@@ -709,6 +714,22 @@ static void lp_update(int64_t n, PState<T>& s, const Detail<T>& o, double dt) {
   }
 }
 
+// Forward-Euler update of the semi-discrete system (stage of Heun's method):
+// x advances with u^n.
+template <class T>
+static void lp_update_euler(int64_t n, PState<T>& s, const Detail<T>& o, double dt) {
+  for (int64_t i = 0; i < n; ++i) {
+    T un = s.u[i], vn = s.v[i], wn = s.w[i];
+    s.V[i] = o.Vnew[i];
+    s.u[i] = un + dt * o.acc[3 * i + 0];
+    s.v[i] = vn + dt * o.acc[3 * i + 1];
+    s.w[i] = wn + dt * o.acc[3 * i + 2];
+    s.x[i] = s.x[i] + dt * un;
+    s.y[i] = s.y[i] + dt * vn;
+    s.z[i] = s.z[i] + dt * wn;
+  }
+}
+
 template <class T>
 static void values_of(const std::vector<T>& a, std::vector<double>& out) {
   out.resize(a.size());
@@ -731,7 +752,9 @@ static void lp_run(int64_t n, PState<T>& s, const TParams<T>& tp, int nsteps, in
       build_stencils(n, vx.data(), vy.data(), vz.data(), p, brute, st);
     }
     int64_t nrd = 0;
-    lp_rhs<T>(n, s, tp, st, o, &nrd);
+    const bool heun = p->time_scheme == 1;
+    PState<T> s0 = heun ? s : PState<T>(0);
+    lp_rhs<T>(n, s, tp, st, o, &nrd, heun);
     if (dg) {
       dg->n_rank_deficient += nrd;
       for (int64_t i = 0; i < n; ++i) {
@@ -747,7 +770,22 @@ static void lp_run(int64_t n, PState<T>& s, const TParams<T>& tp, int nsteps, in
             if ((uint32_t)st.nbr[i * (int64_t)st.cap + k] & GHOST_BIT) dg->n_ghosts++;
       }
     }
-    lp_update<T>(n, s, o, p->dt);
+    if (heun) {
+      // Heun's method (second order; the paper plans a second-order scheme,
+      // Sec. 3.1 item 8): y* = y + dt F(y), y** = y* + dt F(y*) on the same
+      // stencils, y^{n+1} = (y + y**) / 2
+      lp_update_euler<T>(n, s, o, p->dt);
+      lp_rhs<T>(n, s, tp, st, o, &nrd, true);
+      lp_update_euler<T>(n, s, o, p->dt);
+      for (int64_t i = 0; i < n; ++i) {
+        s.x[i] = 0.5 * (s0.x[i] + s.x[i]); s.y[i] = 0.5 * (s0.y[i] + s.y[i]);
+        s.z[i] = 0.5 * (s0.z[i] + s.z[i]); s.u[i] = 0.5 * (s0.u[i] + s.u[i]);
+        s.v[i] = 0.5 * (s0.v[i] + s.v[i]); s.w[i] = 0.5 * (s0.w[i] + s.w[i]);
+        s.V[i] = 0.5 * (s0.V[i] + s.V[i]);
+      }
+    } else {
+      lp_update<T>(n, s, o, p->dt);
+    }
     if (dg)
       for (int64_t i = 0; i < n; ++i)
         if (val(s.z[i]) < p->floor_z) dg->n_below_floor++;
