@@ -60,6 +60,10 @@ typedef int32_t lp_status;
                       /* per particle (derived values, closure, update) and in */
                       /* the pivoted-QR fallback. lp_step only.                */
 
+/* time integration (lp_params.time_scheme) */
+#define LP_TIME_PAPER 0
+#define LP_TIME_HEUN 1
+
 /* floor mirror particles (Sec. 3.1 item 9) */
 #define LP_MIRROR_NONE 0
 #define LP_MIRROR_NOSLIP 1   /* mirror velocity -u (all components)            */
@@ -149,7 +153,14 @@ typedef struct {
                           * inertial pressure continuous. Stencil entries plus
                           * ghosts must fit in cap (else LP_ERR_STENCIL_OVERFLOW).
                           * lp_step_adjoint: LP_ERR_UNIMPLEMENTED.              */
-  int32_t pad;
+  int32_t time_scheme;   /* LP_TIME_PAPER: the paper's step (Sec. 3.1 items 8,
+                          * 10: V first, momentum with V^{n+1}, x with the mean
+                          * velocity; first order). LP_TIME_HEUN: Heun's method
+                          * on the semi-discrete system (second order; the paper
+                          * plans a second-order scheme): two stages on the
+                          * step's stencils, y* = y + dt F(y), y** = y* +
+                          * dt F(y*), y^{n+1} = (y + y**) / 2, F taking V at its
+                          * own time level. lp_step_adjoint: UNIMPLEMENTED.     */
 } lp_params;
 
 /* Stencils produced by lp_build_neighbors: library-owned device memory, valid

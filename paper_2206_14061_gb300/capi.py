@@ -24,6 +24,8 @@ LP_ERR_TIMEOUT = 4
 LP_ERR_CUDA = 5
 LP_ERR_OOM = 6
 LP_ERR_UNIMPLEMENTED = 7
+LP_TIME_PAPER = 0
+LP_TIME_HEUN = 1
 LP_FP64 = 0
 LP_MIXED = 1
 LP_MIXED_FF = 2
@@ -61,7 +63,8 @@ class LpEos(ctypes.Structure):
 class LpParams(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("h", "radius", "gx", "gy", "gz", "floor_z")] + [
         (k, ctypes.c_int32) for k in ("mirror_mode", "precision", "rebuild_every", "launch_mode")] + [
-        ("skin", ctypes.c_double), ("free_surface", ctypes.c_int32), ("pad", ctypes.c_int32)]
+        ("skin", ctypes.c_double), ("free_surface", ctypes.c_int32),
+        ("time_scheme", ctypes.c_int32)]
 
 
 class LpNeighbors(ctypes.Structure):
@@ -211,7 +214,7 @@ def params_struct(q) -> LpParams:
                     float(q["gz"]), float(q.get("floor_z", 0.0)), int(q.get("mirror_mode", 1)),
                     int(q.get("precision", LP_FP64)), int(q.get("rebuild_every", 1)),
                     int(q.get("launch_mode", LP_LAUNCH_KERNELS)), float(q.get("skin", 0.0)),
-                    int(q.get("free_surface", 0)), 0)
+                    int(q.get("free_surface", 0)), int(q.get("time_scheme", 0)))
 
 
 class Context:

@@ -43,6 +43,8 @@ void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
                    const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
                    cudaStream_t st, int bs);
+void launch_copy_state(int n, double* const* dst, double* const* src, cudaStream_t st);
+void launch_heun_combine(int n, double* const* y, double* const* y0, cudaStream_t st);
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st);
 // fit.cu
@@ -112,6 +114,7 @@ struct lp_ctx {
   int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
   int32_t* gcnt = nullptr;    // ghost entries per stencil
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
+  double* Y0[7] = {};                  // Heun: state at the start of the step (on first use)
   float* Lff = nullptr;      // float-float Cholesky factors (LP_MIXED_FF)
   // Verlet candidate lists (lp_params.skin)
   int32_t* cand = nullptr;   // capc x n, k-major
@@ -354,16 +357,22 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   return A;
 }
 
-// Twin sums of the float-float free-surface path, allocated on first use
-// (62 + 36 floats per particle).
+// Twin sums of the float-float free-surface path (62 + 36 floats per
+// particle) and the saved state of Heun's method (7 doubles per particle),
+// allocated on first use.
 lp_status ensure_twin_buffers(lp_ctx* c, const lp_params* q) {
+  if (q->time_scheme == LP_TIME_HEUN && !c->Y0[0])
+    for (int f = 0; f < 7; ++f) LP_TRY(dalloc(c, &c->Y0[f], (size_t)c->cap_n));
   if (!q->free_surface || c->Tg) return LP_OK;
   LP_TRY(dalloc(c, &c->Tg, (size_t)c->cap_n * 62));
   return dalloc(c, &c->T2, (size_t)c->cap_n * 36);
 }
 
 // One LP step on the context's internal (sorted) state.
-void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cudaStream_t st) {
+// save_y0: copy the (sorted) state to c->Y0 once the stencils are built
+// (first stage of Heun's method).
+void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cudaStream_t st,
+              bool save_y0 = false) {
   if (rebuild && c->skin > 0.0) {
     // Verlet candidate lists: search (radius + skin) only when flagged, then
     // the exact filter every step
@@ -403,6 +412,10 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
     phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
     c->launches += 1;
   }
+  if (save_y0) {
+    launch_copy_state(n, c->Y0, c->X[c->cx], st);
+    c->launches += 1;
+  }
   cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
   StepArgs A = step_args(c, n, K);
   phase_mark(c, LP_PHASE_PASS1, true, st);
@@ -416,12 +429,30 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
   c->cx ^= 1;
 }
 
+// One step of the chosen time scheme: the paper's step, or Heun's method as
+// two stages on the step's stencils and the average y <- (y0 + y**) / 2.
+void one_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cudaStream_t st) {
+  if (!K.euler) {
+    run_step(c, n, K, prec, rebuild, st);
+    return;
+  }
+  run_step(c, n, K, prec, rebuild, st, true);
+  run_step(c, n, K, prec, false, st);
+  launch_heun_combine(n, c->X[c->cx], c->Y0, st);
+  c->launches += 1;
+  c->steps -= 1;  // two stages, one step
+}
+
 // One LP step as a single persistent cooperative launch (same buffers and
 // toggles as run_step).
 lp_status run_step_persistent(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool save_y0 = false) {
   PersistArgs P{};
   P.n = n;
+  if (save_y0) {
+    for (int f = 0; f < 7; ++f) P.y0[f] = c->Y0[f];
+    P.save_y0 = 1;
+  }
   P.rebuild = rebuild ? 1 : 0;
   P.ncell = c->ncell;
   const int d = c->cx;
@@ -476,8 +507,15 @@ lp_status run_steps(lp_ctx* c, int n, const StepConsts& K, int prec, int R, int 
   const int period = 2 * R;  // buffer toggles repeat after 2R steps
   if (launch_mode == LP_LAUNCH_PERSISTENT) {
     for (int k = 0; k < nsteps; ++k) {
-      const lp_status r = run_step_persistent(c, n, K, prec, (k % R) == 0, st);
+      const lp_status r = run_step_persistent(c, n, K, prec, (k % R) == 0, st, K.euler);
       if (r != LP_OK) return r;
+      if (K.euler) {  // Heun's method: second stage on the same stencils, average
+        const lp_status r2 = run_step_persistent(c, n, K, prec, false, st);
+        if (r2 != LP_OK) return r2;
+        launch_heun_combine(n, c->X[c->cx], c->Y0, st);
+        c->launches += 1;
+        c->steps -= 1;
+      }
     }
     done = nsteps;
   } else if (launch_mode == LP_LAUNCH_GRAPH && !c->profile && st != nullptr &&
@@ -490,7 +528,7 @@ lp_status run_steps(lp_ctx* c, int n, const StepConsts& K, int prec, int R, int 
     const int64_t launches0 = c->launches, steps0 = c->steps;
     c->launches = 0;
     c->steps = 0;
-    for (int k = 0; k < period; ++k) run_step(c, n, K, prec, k % R == 0, st);
+    for (int k = 0; k < period; ++k) one_step(c, n, K, prec, k % R == 0, st);
     if (cudaStreamEndCapture(st, &g) != cudaSuccess || c->cx != cx0 || c->ci != ci0) {
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
@@ -511,7 +549,7 @@ lp_status run_steps(lp_ctx* c, int n, const StepConsts& K, int prec, int R, int 
     cudaGraphExecDestroy(ge);
     cudaGraphDestroy(g);
   }
-  for (int k = done; k < nsteps; ++k) run_step(c, n, K, prec, (k % R) == 0, st);
+  for (int k = done; k < nsteps; ++k) one_step(c, n, K, prec, (k % R) == 0, st);
   return LP_OK;
 }
 
@@ -525,6 +563,7 @@ bool valid_params(const lp_params* q, const lp_eos* e, double dt) {
   if (q->launch_mode < LP_LAUNCH_KERNELS || q->launch_mode > LP_LAUNCH_PERSISTENT) return false;
   if (!(q->skin >= 0.0) || !std::isfinite(q->skin) || q->skin > q->radius) return false;
   if (q->free_surface != 0 && q->free_surface != 1) return false;
+  if (q->time_scheme != LP_TIME_PAPER && q->time_scheme != LP_TIME_HEUN) return false;
   if (!(e->phi_min < e->phi_max && e->phi_max < e->phi_c)) return false;
   return true;
 }
@@ -872,6 +911,7 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
   K.gx = q->gx; K.gy = q->gy; K.gz = q->gz; K.floor_z = q->floor_z; K.dt = dt;
   K.mirror_mode = q->mirror_mode; K.cap = cap;
   K.free_surface = q->free_surface != 0;
+  K.euler = q->time_scheme == LP_TIME_HEUN;
   if (K.free_surface) {
     // ghost particles (Sec. 3.1 items 6 and 9): fixed-point grid K r <= 8192
     double g = 1.0;
@@ -1110,6 +1150,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   LP_TRY(check_particles(c, initial, offs, true));
   if (!valid_params(q, eos, dt) || q->precision != LP_FP64) return LP_ERR_INVALID_ARG;
   if (q->free_surface) return LP_ERR_UNIMPLEMENTED;  // adjoint of the ghost rows not built
+  if (q->time_scheme != LP_TIME_PAPER) return LP_ERR_UNIMPLEMENTED;
   if (seed->n != initial->n || (initial->n > 0 && (!seed->x || !seed->y || !seed->z || !seed->u ||
                                                    !seed->v || !seed->w || !seed->V)))
     return LP_ERR_INVALID_ARG;

@@ -273,7 +273,7 @@ static __device__ __noinline__ void pass2_fallback_item(const StepArgs& A, int t
     const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
     const double ih = A.K.inv_h, f2 = 2.0 * A.K.floor_z;
     const double* gn = A.p1 + P1_GN * n;
-    const double* Vn = A.p1 + P1_VN * n;
+    const double* Vn = A.K.euler ? A.V : A.p1 + P1_VN * n;  // V of the pass-2 fit
     double bg_gh = 0.0, bv_gh = 0.0;
     if (A.K.free_surface) ghost_rhs2(A, gn[s], Vn[s], &bg_gh, &bv_gh);
     int rows = 0;  // a flagged entry adds its ghost: reflected row
@@ -327,7 +327,8 @@ __device__ __forceinline__ void split_state_body(const StepArgs& A, int s) {
 
 // split |gdot|^n and V^{n+1} (pass-1 outputs, FP64) for pass 2
 __device__ __forceinline__ void split_p1_body(const StepArgs& A, int s) {
-  const ff g = ff_of(A.p1[P1_GN * A.n + s]), v = ff_of(A.p1[P1_VN * A.n + s]);
+  const ff g = ff_of(A.p1[P1_GN * A.n + s]);
+  const ff v = ff_of(A.K.euler ? A.V[s] : A.p1[P1_VN * A.n + s]);  // V of the pass-2 fit
   A.GVff[s] = make_float4(g.h, g.l, v.h, v.l);
 }
 
@@ -533,7 +534,7 @@ __device__ __forceinline__ void pass2_twins_body(const StepArgs& A, int s) {
   const float4 hi = A.Xh[s], lo = A.Xl[s];
   const float4 gvi = A.GVff[s];
   double bgd, bvd;
-  ghost_rhs2(A, A.p1[P1_GN * n + s], A.p1[P1_VN * n + s], &bgd, &bvd);
+  ghost_rhs2(A, A.p1[P1_GN * n + s], A.K.euler ? A.V[s] : A.p1[P1_VN * n + s], &bgd, &bvd);
   const ff bgg = ff_of(bgd), bvg = ff_of(bvd);
   ff R[2][kNB];
 #pragma unroll
@@ -754,8 +755,11 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
     const double ih = A.K.inv_h, f2 = 2.0 * A.K.floor_z;
     const double* gn = A.p1 + P1_GN * n;
-    const double* Vn = A.p1 + P1_VN * n;
+    // V of the fits and the closure: V^{n+1} (the paper's step) or V^n (a
+    // stage of Heun's method, whose right-hand side takes one time level)
+    const double* Vn = A.K.euler ? A.V : A.p1 + P1_VN * n;
     const double gni = gn[s], Vi = Vn[s];
+    const double Vnext = A.p1[P1_VN * n + s];
     double gg[3], gV[3];
     const int slot = A.fbslot[s];
     if (slot >= 0) {
@@ -931,14 +935,16 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     const double dt = A.K.dt;
     const double un = A.u[s], vn = A.v[s], wn = A.w[s];
     const double u1 = un + dt * acc[0], v1 = vn + dt * acc[1], w1 = wn + dt * acc[2];
-    const double x1 = xi + (0.5 * dt) * (un + u1);
-    const double y1 = yi + (0.5 * dt) * (vn + v1);
-    const double z1 = zi + (0.5 * dt) * (wn + w1);
+    // x with the mean velocity (the paper's step) or with u^n (Heun stage)
+    const double hx = A.K.euler ? dt : 0.5 * dt;
+    const double x1 = xi + hx * (A.K.euler ? un : un + u1);
+    const double y1 = yi + hx * (A.K.euler ? vn : vn + v1);
+    const double z1 = zi + hx * (A.K.euler ? wn : wn + w1);
     A.uo[s] = u1; A.vo[s] = v1; A.wo[s] = w1;
     A.xo[s] = x1; A.yo[s] = y1; A.zo[s] = z1;
-    A.Vo[s] = Vi;
+    A.Vo[s] = Vnext;
     nonfin = !(isfinite(u1) && isfinite(v1) && isfinite(w1) && isfinite(x1) && isfinite(y1) &&
-               isfinite(z1) && isfinite(Vi));
+               isfinite(z1) && isfinite(Vnext));
     if (A.xref) {
       const double ex = x1 - A.xref[s], ey = y1 - A.xref[A.n + s], ez = z1 - A.xref[2 * A.n + s];
       if (!(((ex * ex) + (ey * ey)) + (ez * ez) <= A.half_skin2)) *A.need_search = 1;

@@ -50,6 +50,7 @@ struct StepConsts {
   // free-surface ghosts: fixed-point grid K (power of two, K r <= 8192),
   // round((K r)^2), K h, round((K h / 2)^2), 1/phi_G, phi_c - phi_G
   int free_surface;
+  int euler;  // Heun stage: pass 2 takes V^n, x advances with u^n
   double ghost_grid, ghost_hk, ghost_V, ghost_num;
   long long ghost_R2, ghost_clear2;
 };
@@ -232,6 +233,9 @@ struct PersistArgs {
   int capc;
   double rsearch;
   double* xref;
+  // Heun's method, first stage: copy the (sorted) state here before pass 1
+  double* y0[7];
+  int save_y0;
   // barrier: [0] arrivals, [1] generation
   unsigned* bar;
   unsigned long long max_spins;

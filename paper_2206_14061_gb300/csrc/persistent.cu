@@ -173,6 +173,12 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
     }
   }
   if (tid == 0) *S.fb_count = 0;
+  if (P.save_y0) {  // Heun's method: the state at the start of the step
+    const double* src[7] = {S.x, S.y, S.z, S.u, S.v, S.w, S.V};
+    for (int s = tid; s < n; s += nth)
+#pragma unroll
+      for (int f = 0; f < 7; ++f) P.y0[f][s] = src[f][s];
+  }
   if (PREC == LP_MIXED_FF)
     for (int s = tid; s < n; s += nth) split_state_body(S, s);
   LP_SYNC_OR_LEAVE();

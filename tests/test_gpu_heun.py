@@ -1,0 +1,149 @@
+"""Heun's method (lp_params.time_scheme = LP_TIME_HEUN) on the GPU against the
+oracle, and its observed order in time measured on the GPU alone."""
+import numpy as np
+import pytest
+
+from paper_2206_14061_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_14061_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def capi(dev):
+    from paper_2206_14061_gb300 import capi as C
+    C.lib()
+    return C
+
+
+def T(a, dev):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+
+
+def _dicts(pd):
+    mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
+    eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max", "alpha", "beta")}
+    return mui, eos
+
+
+def _prm(pd, **kw):
+    q = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
+             floor_z=pd["floor_z"], mirror_mode=pd["mirror_mode"], precision=0, rebuild_every=1,
+             launch_mode=0, skin=0.0, free_surface=0, time_scheme=1)
+    q.update(kw)
+    return q
+
+
+def _rel(diff, scale):
+    m = np.abs(scale).max()
+    d = np.abs(diff).max()
+    if m == 0.0:
+        return 0.0 if d == 0.0 else np.inf
+    return d / m
+
+
+def _state_err(got, ref, s0):
+    e = {}
+    for k in "xyz":
+        e[k] = _rel((got[k] - s0[k]) - (ref[k] - s0[k]), ref[k] - s0[k])
+    for k in "uvw":
+        e[k] = _rel(got[k] - ref[k], ref[k])
+    e["V"] = _rel((got["V"] - s0["V"]) - (ref["V"] - s0["V"]), ref["V"] - s0["V"])
+    return e
+
+
+def _run_gpu(capi, dev, state, n, pd, nsteps, offsets=None, mui=None, stream=None, dt=None,
+             **kw):
+    ctx = capi.Context(n, max_columns=1 if offsets is None else len(offsets) - 1, cap=64)
+    st = {k: T(state[k], dev) for k in capi.FIELDS}
+    m, eos = _dicts(pd)
+    capi.lp_step(ctx, st, mui if mui is not None else m, eos, _prm(pd, **kw),
+                 pd["dt"] if dt is None else dt, nsteps, column_offsets=offsets, stream=stream)
+    d = ctx.sync(stream)
+    return {k: st[k].cpu().numpy() for k in capi.FIELDS}, d
+
+
+def test_heun_parity_50_steps(dev, capi, orc):
+    wl = W.cube(20)
+    pd = W.param_dict(wl)
+    ref, _ = orc.step(wl.state, orc.params(**dict(pd, time_scheme=1)), 50, brute=False)
+    for prec, tol in ((0, 1e-9), (1, 1e-6), (2, 1e-8)):
+        got, d = _run_gpu(capi, dev, wl.state, wl.n, pd, 50, precision=prec)
+        e = _state_err(got, ref, wl.state)
+        print(f"Heun precision {prec} 50-step errors:", {k: f"{v:.2e}" for k, v in e.items()})
+        assert max(e.values()) <= tol, (prec, e)
+        assert d["n_nonfinite"] == 0
+    # Heun and the paper's step differ on this run
+    paper, _ = orc.step(wl.state, orc.params(**pd), 50, brute=False)
+    assert max(_state_err(paper, ref, wl.state).values()) > 1e-6
+
+
+def test_heun_with_ghosts_matches_oracle(dev, capi, orc):
+    wl = W.cube(16)
+    pd = W.param_dict(wl)
+    ref, rd = orc.step(wl.state, orc.params(**dict(pd, time_scheme=1, free_surface=1)), 20,
+                       brute=False)
+    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+        got, d = _run_gpu(capi, dev, wl.state, wl.n, pd, 20, precision=prec, free_surface=1)
+        assert d["n_ghosts"] == rd["n_ghosts"], prec
+        e = _state_err(got, ref, wl.state)
+        assert max(e.values()) <= tol, (prec, e)
+
+
+def test_heun_bitwise_across_launch_modes(dev, capi):
+    wc = W.columns(ncol=6, n_lo=300, n_hi=3000, only=list(range(6)))
+    pc = W.param_dict(wc)
+    m0, _ = _dicts(pc)
+    mui_c = [dict(m0, mu_s=float(mu)) for mu in wc.mu_s_col]
+    for prec in (0, 2):
+        for skin, fs in ((0.0, 0), (0.1 * pc["h"], 1)):
+            runs = [_run_gpu(capi, dev, wc.state, wc.n, pc, 6, offsets=wc.column_offsets,
+                             mui=mui_c, precision=prec, launch_mode=mode, skin=skin,
+                             free_surface=fs, stream=torch.cuda.Stream())
+                    for mode in (0, 1, 2)]
+            for got, _ in runs[1:]:
+                for k in got:
+                    assert np.array_equal(got[k], runs[0][0][k]), (prec, skin, fs, k)
+
+
+def test_heun_second_order_on_the_gpu(dev, capi):
+    """Sheared inertial block, 8e-5 s in 8/16/32/64 steps with the stencils of
+    the first step: the step-halving differences fall by four."""
+    n_side, h = 7, 1e-3
+    x, y, z = W.lattice_box(n_side, n_side, n_side, h, 0.05, np.random.default_rng(9))
+    L = n_side * h
+    phi = 0.585 + 0.002 * np.sin(2 * np.pi * x / L) * np.cos(2 * np.pi * z / L)
+    s0 = dict(x=x, y=y, z=z, u=20.0 * z + 0.01 * np.sin(2 * np.pi * y / L),
+              v=0.01 * np.cos(2 * np.pi * x / L), w=np.zeros(x.size), V=1.0 / phi)
+    pd = dict(W.MUI, **W.EOS, h=h, radius=2.2 * h, gx=0.0, gy=0.0, gz=-9.81, floor_z=0.0,
+              mirror_mode=0, dt=1e-5)
+    Tt = 8e-5
+    for scheme, lo, hi in ((0, 0.8, 1.2), (1, 1.8, 2.2)):
+        out = [_run_gpu(capi, dev, s0, x.size, pd, k, dt=Tt / k, rebuild_every=k,
+                        time_scheme=scheme)[0] for k in (8, 16, 32, 64)]
+        for f in ("x", "u", "v", "w", "V"):
+            e = [np.abs(out[a][f] - out[a + 1][f]).max() for a in range(3)]
+            p = np.log2(e[1] / e[2])
+            assert lo < p < hi, (scheme, f, p)
+
+
+def test_adjoint_with_heun_is_unimplemented(dev, capi):
+    wl = W.cube(6)
+    pd = W.param_dict(wl)
+    m, eos = _dicts(pd)
+    ctx = capi.Context(wl.n, cap=64)
+    st = {k: T(wl.state[k], dev) for k in capi.FIELDS}
+    seed = {k: torch.ones_like(v) for k, v in st.items()}
+    with pytest.raises(capi.LpError) as ei:
+        capi.lp_step_adjoint(ctx, st, m, eos, _prm(pd), pd["dt"], 4, 2, seed)
+    assert ei.value.status == capi.LP_ERR_UNIMPLEMENTED
