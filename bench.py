@@ -51,6 +51,8 @@ def parse():
                     help="ghost particles at free boundaries (Sec. 3.1 item 9)")
     ap.add_argument("--no-free-surface", action="store_true",
                     help="skip the line with free-surface ghosts")
+    ap.add_argument("--no-heun", action="store_true",
+                    help="skip the line with Heun's method")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
@@ -200,14 +202,14 @@ def our_arm(args):
     stream = torch.cuda.Stream(device=dev)
     R = max(1, args.restart_every)
 
-    ghosts = {"on": int(args.free_surface)}
+    mode = {"fs": int(args.free_surface), "ts": 0}  # free-surface ghosts, time scheme
 
     def params(prec, graph=1):
         return dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
                     floor_z=0.0, mirror_mode=1,
                     precision=PREC[prec],
                     rebuild_every=1, launch_mode=graph, skin=args.skin * pd["h"],
-                    free_surface=ghosts["on"])
+                    free_surface=mode["fs"], time_scheme=mode["ts"])
 
     def run(nsteps, prec, graph=1):
         done = 0
@@ -321,14 +323,24 @@ def our_arm(args):
 
     if not args.no_free_surface and not args.free_surface:
         # the same workload with free-surface ghost particles (Sec. 3.1 item 9)
-        ghosts["on"] = 1
+        mode["fs"] = 1
         msg, _, _, dgg, profg, _ = bench(args.precision)
-        ghosts["on"] = 0
+        mode["fs"] = 0
         line["free_surface"] = {
             "value": n * args.steps * world / (msg / 1e3), "unit": UNIT,
             "ms_per_step": msg / args.steps,
             "phase_ms_per_step": {k: v / max(profg["steps"], 1) for k, v in profg["ms"].items()},
             "ghost_entries_per_step": dgg["n_ghosts"] / max(args.steps, 1)}
+
+    if not args.no_heun:
+        # the same workload with Heun's method (two stages per step)
+        mode["ts"] = 1
+        msh, _, _, _, profh, _ = bench(args.precision)
+        mode["ts"] = 0
+        line["heun"] = {
+            "value": n * args.steps * world / (msh / 1e3), "unit": UNIT,
+            "ms_per_step": msh / args.steps,
+            "phase_ms_per_step": {k: v / max(profh["steps"], 1) for k, v in profh["ms"].items()}}
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world)
