@@ -21,6 +21,9 @@
 //     a solid fraction just below phi_min and the |gdot| that keeps the
 //     inertial pressure continuous (see add_ghosts for the test and placement
 //     the paper leaves open);
+//   * optionally (period_x / period_y > 0) periodic boundaries along x and/or
+//     y (Sec. 3.1 item 9): offsets are nearest images, positions stay in
+//     [0, L);
 //   * GFD least-squares fit (Sec. 3.1 item 7): 3D form of the 2D Taylor matrix
 //     with rows  [dx, dy, dz, dx^2/2, dy^2/2, dz^2/2, dx dy, dx dz, dy dz]
 //     (offsets divided by h), right-hand side s_k - s_i, solved by Householder
@@ -105,6 +108,7 @@ typedef struct {
   int32_t free_surface;  // 1: ghost particles complete free-surface stencils
   int32_t time_scheme;   // 0: the paper's step (V first), 1: Heun's method (RK2)
   int32_t pad;
+  double period_x, period_y;  // > 0: periodic in x / y with positions in [0, L)
 } orc_params;
 
 typedef struct {
@@ -122,11 +126,43 @@ static const uint32_t INDEX_MASK = 0x3fffffffu;
 
 // ------------------------------------------------------- neighbour search ---
 
+// Periodic boundaries (Sec. 3.1 item 9): offset d along an axis of period L
+// (L = 0: not periodic), taken as its nearest periodic image; unique when
+// L > 2 r.
+static inline double min_image(double d, double L) {
+  if (L > 0.0) {
+    if (d > 0.5 * L) d = d - L;
+    else if (d < -0.5 * L) d = d + L;
+  }
+  return d;
+}
+struct Periods {
+  double Lx = 0.0, Ly = 0.0;
+};
+template <class T>
+static inline T min_image_t(const T& d, double L) {
+  if (L > 0.0) {
+    if (val(d) > 0.5 * L) return d - T(L);
+    if (val(d) < -0.5 * L) return d + T(L);
+  }
+  return d;
+}
+// position moved back into [0, L) (a step moves a particle far less than L)
+template <class T>
+static inline T wrap_t(const T& x, double L) {
+  if (L > 0.0) {
+    if (val(x) >= L) return x - T(L);
+    if (val(x) < 0.0) return x + T(L);
+  }
+  return x;
+}
+
 // Inclusion predicate: d^2 <= r^2, evaluated in FP64 left to right with no
-// contraction; r*r is formed once by the caller.
+// contraction; r*r is formed once by the caller. Offsets along periodic axes
+// are nearest images.
 static inline bool in_ball(double xi, double yi, double zi, double xj, double yj,
-                           double zj, double r2, double* d2out) {
-  double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+                           double zj, double r2, double* d2out, const Periods& P = Periods()) {
+  double dx = min_image(xj - xi, P.Lx), dy = min_image(yj - yi, P.Ly), dz = zj - zi;
   double d2 = ((dx * dx) + (dy * dy)) + (dz * dz);
   *d2out = d2;
   return d2 <= r2;
@@ -171,7 +207,7 @@ static int store_stencil(std::vector<Cand>& c, int32_t cap, int keep_nearest,
 static int neighbors_brute(int64_t n, const double* x, const double* y, const double* z,
                            const double* radius, double r_const, int mirror_mode,
                            double floor_z, int32_t cap, int keep_nearest, int32_t* nbr,
-                           int32_t* cnt) {
+                           int32_t* cnt, const Periods& P = Periods()) {
   int over = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : over)
   for (int64_t i = 0; i < n; ++i) {
@@ -181,12 +217,12 @@ static int neighbors_brute(int64_t n, const double* x, const double* y, const do
     double d2;
     for (int64_t j = 0; j < n; ++j) {
       if (j == i) continue;
-      if (in_ball(x[i], y[i], z[i], x[j], y[j], z[j], r2, &d2)) c.push_back({d2, (uint32_t)j});
+      if (in_ball(x[i], y[i], z[i], x[j], y[j], z[j], r2, &d2, P)) c.push_back({d2, (uint32_t)j});
     }
     if (mirror_mode != 0) {
       for (int64_t j = 0; j < n; ++j) {
         double zm = 2.0 * floor_z - z[j];
-        if (in_ball(x[i], y[i], z[i], x[j], y[j], zm, r2, &d2))
+        if (in_ball(x[i], y[i], z[i], x[j], y[j], zm, r2, &d2, P))
           c.push_back({d2, (uint32_t)j | MIRROR_BIT});
       }
     }
@@ -195,13 +231,15 @@ static int neighbors_brute(int64_t n, const double* x, const double* y, const do
   return over;
 }
 
-// Independent uniform-grid scan (cell edge = largest radius); used to make
+// Independent uniform-grid scan (cell edge >= largest radius); used to make
 // large-N oracle runs affordable. Cell indices are clamped to the grid, which
-// keeps every pair within one cell of each other in each axis.
+// keeps every pair within one cell of each other in each axis; a periodic
+// axis covers [0, L) with floor(L / r) cells and wraps (at least 3 cells, else
+// the brute-force scan is used).
 static int neighbors_grid(int64_t n, const double* x, const double* y, const double* z,
                           const double* radius, double r_const, int mirror_mode,
                           double floor_z, int32_t cap, int keep_nearest, int32_t* nbr,
-                          int32_t* cnt) {
+                          int32_t* cnt, const Periods& P = Periods()) {
   if (n == 0) return 0;
   double rmax = r_const;
   if (radius) {
@@ -217,12 +255,23 @@ static int neighbors_grid(int64_t n, const double* x, const double* y, const dou
   double cell = rmax * (1.0 + 1e-9);
   if (!(cell > 0.0)) cell = 1.0;
   int64_t dim[3];
+  double ce[3] = {cell, cell, cell};
+  const double per[3] = {P.Lx, P.Ly, 0.0};
   for (int a = 0; a < 3; ++a) {
+    if (per[a] > 0.0) {  // periodic: whole cells over [0, L)
+      dim[a] = (int64_t)std::floor(per[a] / cell);
+      if (dim[a] < 3)
+        return neighbors_brute(n, x, y, z, radius, r_const, mirror_mode, floor_z, cap,
+                               keep_nearest, nbr, cnt, P);
+      lo[a] = 0.0;
+      ce[a] = per[a] / (double)dim[a];
+      continue;
+    }
     dim[a] = (int64_t)std::floor((hi[a] - lo[a]) / cell) + 1;
     dim[a] = std::max<int64_t>(1, std::min<int64_t>(dim[a], 512));
   }
   auto cidx = [&](double p, int a) {
-    int64_t c = (int64_t)std::floor((p - lo[a]) / cell);
+    int64_t c = (int64_t)std::floor((p - lo[a]) / ce[a]);
     return std::max<int64_t>(0, std::min<int64_t>(c, dim[a] - 1));
   };
   int64_t ncell = dim[0] * dim[1] * dim[2];
@@ -249,22 +298,24 @@ static int neighbors_grid(int64_t n, const double* x, const double* y, const dou
       int64_t c0[3] = {cidx(x[i], 0), cidx(y[i], 1), cidx(qz, 2)};
       int64_t a0[3], a1[3];
       for (int a = 0; a < 3; ++a) {
-        a0[a] = std::max<int64_t>(0, c0[a] - 1);
-        a1[a] = std::min<int64_t>(dim[a] - 1, c0[a] + 1);
+        a0[a] = per[a] > 0.0 ? c0[a] - 1 : std::max<int64_t>(0, c0[a] - 1);
+        a1[a] = per[a] > 0.0 ? c0[a] + 1 : std::min<int64_t>(dim[a] - 1, c0[a] + 1);
       }
-      for (int64_t cz = a0[2]; cz <= a1[2]; ++cz)
-        for (int64_t cy = a0[1]; cy <= a1[1]; ++cy)
-          for (int64_t cx = a0[0]; cx <= a1[0]; ++cx) {
+      auto wrap = [&](int64_t v, int a) { return per[a] > 0.0 ? (v + dim[a]) % dim[a] : v; };
+      for (int64_t czz = a0[2]; czz <= a1[2]; ++czz)
+        for (int64_t cyy = a0[1]; cyy <= a1[1]; ++cyy)
+          for (int64_t cxx = a0[0]; cxx <= a1[0]; ++cxx) {
+            const int64_t cz = wrap(czz, 2), cy = wrap(cyy, 1), cx = wrap(cxx, 0);
             int64_t cc = (cz * dim[1] + cy) * dim[0] + cx;
             for (int64_t t = start[cc]; t < start[cc + 1]; ++t) {
               int64_t j = order[t];
               if (pass == 0) {
                 if (j == i) continue;
-                if (in_ball(x[i], y[i], z[i], x[j], y[j], z[j], r2, &d2))
+                if (in_ball(x[i], y[i], z[i], x[j], y[j], z[j], r2, &d2, P))
                   c.push_back({d2, (uint32_t)j});
               } else {
                 double zm = 2.0 * floor_z - z[j];
-                if (in_ball(x[i], y[i], z[i], x[j], y[j], zm, r2, &d2))
+                if (in_ball(x[i], y[i], z[i], x[j], y[j], zm, r2, &d2, P))
                   c.push_back({d2, (uint32_t)j | MIRROR_BIT});
               }
             }
@@ -363,7 +414,8 @@ static int lsq_qrcp(int m, T* A, int nf, T* B, T* C /* nf x 9 */) {
 // derivatives * h^2) in C[nf][9].
 template <class T, class FieldFn>
 static int fit_particle(int64_t i, const T* x, const T* y, const T* z, const int32_t* row,
-                        int32_t m, double h, double floor_z, int nf, FieldFn field, T* C) {
+                        int32_t m, double h, double floor_z, int nf, FieldFn field, T* C,
+                        const Periods& P = Periods()) {
   std::vector<T> A((size_t)std::max(m, 1) * NB), B((size_t)std::max(m, 1) * nf);
   for (int32_t k = 0; k < m; ++k) {
     uint32_t code = (uint32_t)row[k];
@@ -371,7 +423,8 @@ static int fit_particle(int64_t i, const T* x, const T* y, const T* z, const int
     bool ghost = code & GHOST_BIT;
     int64_t j = code & INDEX_MASK;
     T zj = mir ? T(2.0 * floor_z) - z[j] : z[j];
-    T dx = (x[j] - x[i]) / h, dy = (y[j] - y[i]) / h, dz = (zj - z[i]) / h;
+    T dx = min_image_t(x[j] - x[i], P.Lx) / h, dy = min_image_t(y[j] - y[i], P.Ly) / h;
+    T dz = (zj - z[i]) / h;
     if (ghost) {
       dx = -dx;
       dy = -dy;
@@ -447,12 +500,15 @@ static void build_stencils(int64_t n, const double* x, const double* y, const do
   st.cap = 256;
   st.nbr.assign((size_t)n * st.cap, 0);
   st.cnt.assign(n, 0);
+  Periods P;
+  P.Lx = p->period_x;
+  P.Ly = p->period_y;
   if (brute)
     neighbors_brute(n, x, y, z, nullptr, p->radius, p->mirror_mode, p->floor_z, st.cap, 0,
-                    st.nbr.data(), st.cnt.data());
+                    st.nbr.data(), st.cnt.data(), P);
   else
     neighbors_grid(n, x, y, z, nullptr, p->radius, p->mirror_mode, p->floor_z, st.cap, 0,
-                   st.nbr.data(), st.cnt.data());
+                   st.nbr.data(), st.cnt.data(), P);
   if (p->free_surface) add_ghosts(n, x, y, z, p, st);
 }
 
@@ -463,8 +519,9 @@ static void build_stencils(int64_t n, const double* x, const double* y, const do
 //  - positions are taken in fixed point on a power-of-two grid, X = round(K x)
 //    with K the largest power of two such that K r <= 2^13 (so the scaling is
 //    exact and every offset, square and pair sum below fits 32-bit integers),
-//    and offsets are the exact integer differences o_k = X_k - X_i: every sum
-//    below is an exact integer, independent of the entry order;
+//    and offsets are the exact integer differences o_k = X_k - X_i (along a
+//    periodic axis the nearest image modulo round(K L)): every sum below is an
+//    exact integer, independent of the entry order;
 //  - each entry is weighted by w_k = max(0, R2 - |o_k|^2), R2 = round((K r)^2),
 //    which fades entries out at the stencil radius (an unweighted mean is
 //    dominated by which lattice points of the outermost shell happen to fall
@@ -497,6 +554,16 @@ static void add_ghosts(int64_t n, const double* x, const double* y, const double
   const double hk = h * K;
   const int64_t clear2 = std::llrint((0.5 * hk) * (0.5 * hk));
   auto fix = [&](double v) { return (int64_t)std::llrint(v * K); };
+  // periodic axes: integer period round(K L); offsets take their nearest image
+  const int64_t PX = p->period_x > 0.0 ? std::llrint(K * p->period_x) : 0;
+  const int64_t PY = p->period_y > 0.0 ? std::llrint(K * p->period_y) : 0;
+  auto wrap_fix = [](int64_t o, int64_t P) {
+    if (P > 0) {
+      if (2 * o > P) return o - P;
+      if (2 * o < -P) return o + P;
+    }
+    return o;
+  };
   for (int64_t i = 0; i < n; ++i) {
     int32_t* row = st.nbr.data() + i * (int64_t)st.cap;
     const int32_t m = st.cnt[i];
@@ -510,8 +577,8 @@ static void add_ghosts(int64_t n, const double* x, const double* y, const double
       const int64_t j = code & INDEX_MASK;
       const double zj = (code & MIRROR_BIT) ? 2.0 * p->floor_z - z[j] : z[j];
       zk[k] = zj;
-      o[3 * k] = fix(x[j]) - Xi[0];
-      o[3 * k + 1] = fix(y[j]) - Xi[1];
+      o[3 * k] = wrap_fix(fix(x[j]) - Xi[0], PX);
+      o[3 * k + 1] = wrap_fix(fix(y[j]) - Xi[1], PY);
       o[3 * k + 2] = fix(zj) - Xi[2];
       const int64_t q = (o[3 * k] * o[3 * k] + o[3 * k + 1] * o[3 * k + 1]) +
                         o[3 * k + 2] * o[3 * k + 2];
@@ -585,6 +652,9 @@ static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const St
   const orc_params* p = tp.p;
   const double h = p->h;
   const double dt = p->dt;
+  Periods Pp;
+  Pp.Lx = p->period_x;
+  Pp.Ly = p->period_y;
   auto usgn = [&](int comp) -> double {  // mirror velocity sign per component
     if (p->mirror_mode == 1) return -1.0;
     if (p->mirror_mode == 2) return comp == 2 ? -1.0 : 1.0;
@@ -606,7 +676,7 @@ static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const St
     };
     T C[3 * NB];
     int rank = fit_particle<T>(i, s.x.data(), s.y.data(), s.z.data(), row, m, h, p->floor_z,
-                               3, field, C);
+                               3, field, C, Pp);
     if (rank < NB) n_rd++;
     // velocity gradient G[a][b] = d u_a / d x_b ; second derivatives H[a][.]
     // in the column order xx, yy, zz, xy, xz, yz
@@ -658,7 +728,8 @@ static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const St
       return Vf[j];
     };
     T C[2 * NB];
-    fit_particle<T>(i, s.x.data(), s.y.data(), s.z.data(), row, m, h, p->floor_z, 2, field, C);
+    fit_particle<T>(i, s.x.data(), s.y.data(), s.z.data(), row, m, h, p->floor_z, 2, field, C,
+                    Pp);
     T gg[3] = {C[0] / h, C[1] / h, C[2] / h};
     T gV[3] = {C[NB + 0] / h, C[NB + 1] / h, C[NB + 2] / h};
     for (int c = 0; c < 3; ++c) {
@@ -701,15 +772,16 @@ static void lp_rhs(int64_t n, const PState<T>& s, const TParams<T>& tp, const St
 
 // Explicit update (Sec. 3.1 item 8 for V and u, item 10 for x).
 template <class T>
-static void lp_update(int64_t n, PState<T>& s, const Detail<T>& o, double dt) {
+static void lp_update(int64_t n, PState<T>& s, const Detail<T>& o, double dt, double Lx,
+                      double Ly) {
   for (int64_t i = 0; i < n; ++i) {
     T un = s.u[i], vn = s.v[i], wn = s.w[i];
     s.V[i] = o.Vnew[i];
     s.u[i] = un + dt * o.acc[3 * i + 0];
     s.v[i] = vn + dt * o.acc[3 * i + 1];
     s.w[i] = wn + dt * o.acc[3 * i + 2];
-    s.x[i] = s.x[i] + (0.5 * dt) * (un + s.u[i]);
-    s.y[i] = s.y[i] + (0.5 * dt) * (vn + s.v[i]);
+    s.x[i] = wrap_t(s.x[i] + (0.5 * dt) * (un + s.u[i]), Lx);
+    s.y[i] = wrap_t(s.y[i] + (0.5 * dt) * (vn + s.v[i]), Ly);
     s.z[i] = s.z[i] + (0.5 * dt) * (wn + s.w[i]);
   }
 }
@@ -717,15 +789,16 @@ static void lp_update(int64_t n, PState<T>& s, const Detail<T>& o, double dt) {
 // Forward-Euler update of the semi-discrete system (stage of Heun's method):
 // x advances with u^n.
 template <class T>
-static void lp_update_euler(int64_t n, PState<T>& s, const Detail<T>& o, double dt) {
+static void lp_update_euler(int64_t n, PState<T>& s, const Detail<T>& o, double dt, double Lx,
+                            double Ly) {
   for (int64_t i = 0; i < n; ++i) {
     T un = s.u[i], vn = s.v[i], wn = s.w[i];
     s.V[i] = o.Vnew[i];
     s.u[i] = un + dt * o.acc[3 * i + 0];
     s.v[i] = vn + dt * o.acc[3 * i + 1];
     s.w[i] = wn + dt * o.acc[3 * i + 2];
-    s.x[i] = s.x[i] + dt * un;
-    s.y[i] = s.y[i] + dt * vn;
+    s.x[i] = wrap_t(s.x[i] + dt * un, Lx);
+    s.y[i] = wrap_t(s.y[i] + dt * vn, Ly);
     s.z[i] = s.z[i] + dt * wn;
   }
 }
@@ -774,17 +847,25 @@ static void lp_run(int64_t n, PState<T>& s, const TParams<T>& tp, int nsteps, in
       // Heun's method (second order; the paper plans a second-order scheme,
       // Sec. 3.1 item 8): y* = y + dt F(y), y** = y* + dt F(y*) on the same
       // stencils, y^{n+1} = (y + y**) / 2
-      lp_update_euler<T>(n, s, o, p->dt);
+      lp_update_euler<T>(n, s, o, p->dt, p->period_x, p->period_y);
       lp_rhs<T>(n, s, tp, st, o, &nrd, true);
-      lp_update_euler<T>(n, s, o, p->dt);
+      lp_update_euler<T>(n, s, o, p->dt, p->period_x, p->period_y);
       for (int64_t i = 0; i < n; ++i) {
-        s.x[i] = 0.5 * (s0.x[i] + s.x[i]); s.y[i] = 0.5 * (s0.y[i] + s.y[i]);
+        // periodic axes: the mean of the two positions taken on the same image
+        if (p->period_x > 0.0)
+          s.x[i] = wrap_t(s0.x[i] + 0.5 * min_image_t(s.x[i] - s0.x[i], p->period_x), p->period_x);
+        else
+          s.x[i] = 0.5 * (s0.x[i] + s.x[i]);
+        if (p->period_y > 0.0)
+          s.y[i] = wrap_t(s0.y[i] + 0.5 * min_image_t(s.y[i] - s0.y[i], p->period_y), p->period_y);
+        else
+          s.y[i] = 0.5 * (s0.y[i] + s.y[i]);
         s.z[i] = 0.5 * (s0.z[i] + s.z[i]); s.u[i] = 0.5 * (s0.u[i] + s.u[i]);
         s.v[i] = 0.5 * (s0.v[i] + s.v[i]); s.w[i] = 0.5 * (s0.w[i] + s.w[i]);
         s.V[i] = 0.5 * (s0.V[i] + s.V[i]);
       }
     } else {
-      lp_update<T>(n, s, o, p->dt);
+      lp_update<T>(n, s, o, p->dt, p->period_x, p->period_y);
     }
     if (dg)
       for (int64_t i = 0; i < n; ++i)

@@ -33,7 +33,8 @@ class OrcParams(ctypes.Structure):
         "mu_s", "mu_2", "I0", "d", "rho_s", "phi_c", "phi_min", "phi_max", "alpha", "beta",
         "h", "radius", "gx", "gy", "gz", "floor_z", "dt")] + [
         ("mirror_mode", ctypes.c_int32), ("free_surface", ctypes.c_int32),
-        ("time_scheme", ctypes.c_int32), ("pad", ctypes.c_int32)]
+        ("time_scheme", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("period_x", ctypes.c_double), ("period_y", ctypes.c_double)]
 
 
 class OrcDiag(ctypes.Structure):
