@@ -53,6 +53,8 @@ def parse():
                     help="skip the line with free-surface ghosts")
     ap.add_argument("--no-heun", action="store_true",
                     help="skip the line with Heun's method")
+    ap.add_argument("--no-periodic", action="store_true",
+                    help="skip the periodic-layer line (Sec. 3.1 item 9, Sec. 4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
@@ -342,6 +344,9 @@ def our_arm(args):
             "ms_per_step": msh / args.steps,
             "phase_ms_per_step": {k: v / max(profh["steps"], 1) for k, v in profh["ms"].items()}}
 
+    if not args.no_periodic:
+        line["periodic"] = periodic_layer(args, dev, stream, world)
+
     if not args.no_e2e:
         line["e2e"] = e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world)
 
@@ -427,6 +432,68 @@ def batched(args, dev, stream):
             "persistent_ms_per_step": modes["persistent"] / steps,
             "per_column_value": upd / (ms_c / 1e3), "per_column_ms_per_step": ms_c / steps,
             "speedup_vs_per_column": ms_c / ms_b}
+
+
+def periodic_layer(args, dev, stream, world):
+    """The paper's periodic layer (0.03 m high, periodic along x and y, at
+    rest under gravity with a small density gradient) at the size of the
+    default workload: 162 x 162 x 30 particles, free-surface ghosts at the
+    top, same precision, skin and restarts as the default line."""
+    import torch
+
+    from paper_2206_14061_gb300 import capi, workloads as W
+
+    wl = W.periodic_layer(n_xy=162)
+    pd = W.param_dict(wl)
+    L = wl.extra["L"]
+    n = wl.n
+    mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
+    eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max", "alpha", "beta")}
+    init = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
+    st = {k: v.clone() for k, v in init.items()}
+    prm = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
+               floor_z=0.0, mirror_mode=1, precision=PREC[args.precision], rebuild_every=1,
+               launch_mode=capi.LP_LAUNCH_GRAPH, skin=args.skin * pd["h"], free_surface=1,
+               period_x=L, period_y=L)
+    ctx = capi.Context(n, cap=64)
+    R = max(1, args.restart_every)
+
+    def run(nsteps, launch=capi.LP_LAUNCH_GRAPH):
+        done = 0
+        p = dict(prm, launch_mode=launch)
+        with torch.cuda.stream(stream):
+            while done < nsteps:
+                k = min(R, nsteps - done)
+                for f in capi.FIELDS:
+                    st[f].copy_(init[f])
+                capi.lp_step(ctx, st, mui, eos, p, pd["dt"], k, stream=stream)
+                done += k
+
+    run(args.warmup)
+    ctx.sync(stream)
+    ctx.phase_times(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    diag = ctx.sync(stream, raise_on_error=False)
+    ctx.phase_times(stream)
+    ctx.profile(True)
+    run(min(args.steps, R), launch=capi.LP_LAUNCH_KERNELS)
+    prof = ctx.phase_times(stream)
+    ctx.profile(False)
+    ctx.sync(stream, raise_on_error=False)
+    ctx.close()
+    return {"workload": f"periodic layer {wl.name}: {n} particles, L = {L} m along x and y, "
+                        "H = 0.03 m, free-surface ghosts, at rest under gravity",
+            "value": n * args.steps * world / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps,
+            "phase_ms_per_step": {k: v / max(prof["steps"], 1) for k, v in prof["ms"].items()},
+            "ghost_entries_per_step": diag["n_ghosts"] / max(args.steps, 1),
+            "n_nonfinite": diag["n_nonfinite"]}
 
 
 def e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world):

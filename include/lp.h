@@ -161,6 +161,18 @@ typedef struct {
                           * step's stencils, y* = y + dt F(y), y** = y* +
                           * dt F(y*), y^{n+1} = (y + y**) / 2, F taking V at its
                           * own time level. lp_step_adjoint: UNIMPLEMENTED.     */
+  double period_x, period_y; /* > 0: periodic boundaries along x / y (Sec. 3.1
+                          * item 9). lp_step first maps positions into [0, L)
+                          * (values already there are kept bit for bit); every
+                          * offset along the axis takes its nearest image, the
+                          * neighbour grid wraps, and each step moves positions
+                          * back into [0, L). Must be >= 3 (radius + skin).
+                          * Heun's average takes the two positions on the same
+                          * image. The floor and ghosts are unchanged (ghost
+                          * offsets wrap modulo round(K L) with K the fixed-
+                          * point scale). 0: not periodic. lp_build_neighbors
+                          * and lp_fit_derivatives are not periodic.
+                          * lp_step_adjoint: UNIMPLEMENTED.                    */
 } lp_params;
 
 /* Stencils produced by lp_build_neighbors: library-owned device memory, valid

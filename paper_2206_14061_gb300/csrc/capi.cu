@@ -34,17 +34,21 @@ void launch_neighbors(bool keep, int n, const double* x, const double* y, const 
                       const GridCol* grids, const uint32_t* start, const double* radius,
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
                       int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs = kBlock,
-                      const int* search = nullptr, double* xref = nullptr);
+                      const int* search = nullptr, double* xref = nullptr,
+                      bool periodic = false);
 void launch_filter(int n, const double* x, const double* y, const double* z, const float4* pf,
                    const int32_t* cand, const int32_t* ccnt, int capc, const GridCol* grids,
                    const int32_t* colid, double r, double floor_z, int cap, int32_t* nbr,
-                   int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs);
+                   int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs,
+                   bool periodic = false);
 void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
                    const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
                    cudaStream_t st, int bs);
 void launch_copy_state(int n, double* const* dst, double* const* src, cudaStream_t st);
-void launch_heun_combine(int n, double* const* y, double* const* y0, cudaStream_t st);
+void launch_heun_combine(int n, double* const* y, double* const* y0, double Lx, double Ly,
+                         cudaStream_t st);
+void launch_wrap_positions(int n, double* x, double* y, double Lx, double Ly, cudaStream_t st);
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st);
 // fit.cu
@@ -200,7 +204,10 @@ lp_status ensure_cells(lp_ctx* c, int64_t ncell) {
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 // Per-column grids from the bounding boxes (host), uploaded to the device.
-lp_status setup_grids(lp_ctx* c, int ncol, double rmax, cudaStream_t st) {
+// A periodic axis (period Lx or Ly > 0) has whole cells over [0, L), at least
+// three, each at least rmax wide.
+lp_status setup_grids(lp_ctx* c, int ncol, double rmax, cudaStream_t st, double Lx = 0.0,
+                      double Ly = 0.0) {
   const int margin = 4;
   const double base = rmax * (1.0 + 0x1p-20);
   const int64_t budget = std::max<int64_t>(4 * c->cap_n, (int64_t)1 << 20);
@@ -218,15 +225,24 @@ lp_status setup_grids(lp_ctx* c, int ncol, double rmax, cudaStream_t st) {
         ext[a] = (std::isfinite(b[a]) && std::isfinite(b[3 + a])) ? b[3 + a] - b[a] : 0.0;
       }
       int dims[3];
+      double org[3], edge[3];
+      const double per[3] = {Lx, Ly, 0.0};
       for (int a = 0; a < 3; ++a) {
+        if (per[a] > 0.0) {
+          dims[a] = (int)std::min(1024.0, std::max(3.0, std::floor(per[a] / cell)));
+          org[a] = 0.0;
+          edge[a] = per[a] / dims[a];
+          if (!(edge[a] >= base)) return LP_ERR_INVALID_ARG;  // period below 3 rmax
+          continue;
+        }
         double d = std::floor(ext[a] / cell) + 1 + 2 * margin;
         dims[a] = (int)std::min(1024.0, std::max(1.0, d));
+        org[a] = lo[a] - margin * cell;
+        edge[a] = cell;
       }
-      g.ox = lo[0] - margin * cell;
-      g.oy = lo[1] - margin * cell;
-      g.oz = lo[2] - margin * cell;
-      g.inv_c = 1.0 / cell;
-      g.cf = (float)cell;
+      g.ox = org[0]; g.oy = org[1]; g.oz = org[2];
+      g.icx = 1.0 / edge[0]; g.icy = 1.0 / edge[1]; g.icz = 1.0 / edge[2];
+      g.Lx = Lx; g.Ly = Ly;
       g.nx = dims[0]; g.ny = dims[1]; g.nz = dims[2];
       g.cell_off = total;
       total += (int64_t)dims[0] * dims[1] * dims[2];
@@ -384,10 +400,10 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
     launch_neighbors(false, n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf, c->colid[c->ci],
                      c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity, nullptr,
                      K.radius + c->skin, K.mirror_mode, K.floor_z, c->capc, c->cand, c->ccnt,
-                     c->dg, st, c->bs_nbr, c->d_search, c->xref);
+                     c->dg, st, c->bs_nbr, c->d_search, c->xref, K.periodic != 0);
     launch_filter(n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf, c->cand, c->ccnt, c->capc,
                   c->d_grids, c->colid[c->ci], K.radius, K.floor_z, c->cap, c->nbr, c->cnt,
-                  c->dg, c->d_search, st, c->bs_nbr);
+                  c->dg, c->d_search, st, c->bs_nbr, K.periodic != 0);
     if (K.free_surface) {
       launch_ghosts(n, c->X[e][0], c->X[e][1], c->X[e][2], c->colid[c->ci], c->d_grids, c->Xfix,
                     c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr);
@@ -403,7 +419,7 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
     launch_neighbors(false, n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->pf,
                      c->colid[c->ci], c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity,
                      nullptr, K.radius, K.mirror_mode, K.floor_z, c->cap, c->nbr, c->cnt, c->dg,
-                     st, c->bs_nbr);
+                     st, c->bs_nbr, nullptr, nullptr, K.periodic != 0);
     if (K.free_surface) {
       launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
                     c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr);
@@ -438,7 +454,7 @@ void one_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
   }
   run_step(c, n, K, prec, rebuild, st, true);
   run_step(c, n, K, prec, false, st);
-  launch_heun_combine(n, c->X[c->cx], c->Y0, st);
+  launch_heun_combine(n, c->X[c->cx], c->Y0, K.Lx, K.Ly, st);
   c->launches += 1;
   c->steps -= 1;  // two stages, one step
 }
@@ -512,7 +528,7 @@ lp_status run_steps(lp_ctx* c, int n, const StepConsts& K, int prec, int R, int 
       if (K.euler) {  // Heun's method: second stage on the same stencils, average
         const lp_status r2 = run_step_persistent(c, n, K, prec, false, st);
         if (r2 != LP_OK) return r2;
-        launch_heun_combine(n, c->X[c->cx], c->Y0, st);
+        launch_heun_combine(n, c->X[c->cx], c->Y0, K.Lx, K.Ly, st);
         c->launches += 1;
         c->steps -= 1;
       }
@@ -564,6 +580,13 @@ bool valid_params(const lp_params* q, const lp_eos* e, double dt) {
   if (!(q->skin >= 0.0) || !std::isfinite(q->skin) || q->skin > q->radius) return false;
   if (q->free_surface != 0 && q->free_surface != 1) return false;
   if (q->time_scheme != LP_TIME_PAPER && q->time_scheme != LP_TIME_HEUN) return false;
+  // periods: 0, or finite and at least three stencil radii (plus the skin);
+  // the fixed-point ghost test needs K L < 2^30
+  for (const double L : {q->period_x, q->period_y}) {
+    if (L == 0.0) continue;
+    if (!std::isfinite(L) || !(L >= 3.0 * (q->radius + q->skin) * (1.0 + 0x1p-16))) return false;
+    if (q->free_surface && !(L * (8192.0 / q->radius) < 0x1p29)) return false;
+  }
   if (!(e->phi_min < e->phi_max && e->phi_max < e->phi_c)) return false;
   return true;
 }
@@ -912,6 +935,12 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
   K.mirror_mode = q->mirror_mode; K.cap = cap;
   K.free_surface = q->free_surface != 0;
   K.euler = q->time_scheme == LP_TIME_HEUN;
+  // periodic boundaries (Sec. 3.1 item 9)
+  K.Lx = q->period_x; K.Ly = q->period_y;
+  K.periodic = (K.Lx > 0.0 || K.Ly > 0.0) ? 1 : 0;
+  const double lhx = K.Lx * K.inv_h, lhy = K.Ly * K.inv_h;
+  K.Lhx_h = (float)lhx; K.Lhx_l = (float)(lhx - (double)K.Lhx_h);
+  K.Lhy_h = (float)lhy; K.Lhy_l = (float)(lhy - (double)K.Lhy_h);
   if (K.free_surface) {
     // ghost particles (Sec. 3.1 items 6 and 9): fixed-point grid K r <= 8192
     double g = 1.0;
@@ -925,12 +954,16 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
     const double phi_g = eos->phi_min * (1.0 - 1e-3);
     K.ghost_V = 1.0 / phi_g;
     K.ghost_num = eos->phi_c - phi_g;
+    K.ghost_PX = K.Lx > 0.0 ? std::llrint(g * K.Lx) : 0;
+    K.ghost_PY = K.Ly > 0.0 ? std::llrint(g * K.Ly) : 0;
   }
   return K;
 }
 
 // caller state -> internal buffer in caller order; per-column mu(I) upload
-lp_status load_state(lp_ctx* c, const lp_particles* p, const lp_mui* mui, cudaStream_t st) {
+// (periods Lx, Ly > 0: positions along those axes mapped into [0, L))
+lp_status load_state(lp_ctx* c, const lp_particles* p, const lp_mui* mui, cudaStream_t st,
+                     double Lx = 0.0, double Ly = 0.0) {
   const int n = (int)p->n;
   std::vector<ColMui> hm(p->ncolumns);
   for (int k = 0; k < p->ncolumns; ++k)
@@ -942,6 +975,7 @@ lp_status load_state(lp_ctx* c, const lp_particles* p, const lp_mui* mui, cudaSt
   double* const src[7] = {p->x, p->y, p->z, p->u, p->v, p->w, p->V};
   for (int f = 0; f < 7; ++f)
     cudaMemcpyAsync(c->X[d][f], src[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (Lx > 0.0 || Ly > 0.0) launch_wrap_positions(n, c->X[d][0], c->X[d][1], Lx, Ly, st);
   launch_iota(n, c->ids[c->ci], st);
   // mu(I) parameters are read back from pageable memory only once the copy ran
   return cudaStreamSynchronize(st) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
@@ -966,12 +1000,12 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   const int n = (int)p->n;
   if (n == 0 || nsteps == 0) return LP_OK;
   const StepConsts K = step_consts(eos, q, dt, c->cap);
-  LP_TRY(load_state(c, p, mui, st));
+  LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y));
   const int d = c->cx;
   // Verlet candidate lists: the grid must hold radius + skin in one cell
   const double skin = (q->skin > 0.0 && q->rebuild_every == 1) ? q->skin : 0.0;
   LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
-  LP_TRY(setup_grids(c, p->ncolumns, q->radius + skin, st));
+  LP_TRY(setup_grids(c, p->ncolumns, q->radius + skin, st, q->period_x, q->period_y));
   LP_TRY(ensure_twin_buffers(c, q));
   if (skin > 0.0) {
     const int one = 1;
@@ -1061,13 +1095,13 @@ lp_status lp_autotune(lp_ctx* c, const lp_particles* p, const lp_mui* mui, const
   const int R = q->rebuild_every;
   // every trial starts from the caller's state (which is never modified)
   auto restart = [&]() -> lp_status {
-    LP_TRY(load_state(c, p, mui, st));
+    LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y));
     launch_fill_colid(n, c->d_offs, p->ncolumns, c->colid[c->ci], st);
     return LP_OK;
   };
-  LP_TRY(load_state(c, p, mui, st));
+  LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y));
   LP_TRY(begin_columns(c, p, nullptr, c->cx, offs, st));
-  LP_TRY(setup_grids(c, p->ncolumns, q->radius, st));
+  LP_TRY(setup_grids(c, p->ncolumns, q->radius, st, q->period_x, q->period_y));
   LP_TRY(ensure_twin_buffers(c, q));
   // block sizes: per-phase device time of each candidate
   const int cand[3] = {64, 128, 256};
@@ -1151,6 +1185,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   if (!valid_params(q, eos, dt) || q->precision != LP_FP64) return LP_ERR_INVALID_ARG;
   if (q->free_surface) return LP_ERR_UNIMPLEMENTED;  // adjoint of the ghost rows not built
   if (q->time_scheme != LP_TIME_PAPER) return LP_ERR_UNIMPLEMENTED;
+  if (q->period_x != 0.0 || q->period_y != 0.0) return LP_ERR_UNIMPLEMENTED;
   if (seed->n != initial->n || (initial->n > 0 && (!seed->x || !seed->y || !seed->z || !seed->u ||
                                                    !seed->v || !seed->w || !seed->V)))
     return LP_ERR_INVALID_ARG;

@@ -27,10 +27,10 @@ namespace lp {
 
 // ------------------------------------------------------------ kernels
 
-template <int PREC>
+template <int PREC, bool PER>
 __global__ void __launch_bounds__(kMaxBlock) k_pass1(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < A.n) pass1_body<PREC>(A, s);
+  if (s < A.n) pass1_body<PREC, PER>(A, s);
 }
 
 // pivoted-QR fallback of pass 1 (grid-stride over the queued particles)
@@ -52,14 +52,17 @@ __global__ void __launch_bounds__(64) k_pass2_fallback(const StepArgs A) {
 // float-float kernels: 128 threads per block, at most 128 registers so that
 // 4 blocks (16 warps) share an SM
 constexpr int kFFBlock = 128;
+// (PER: periodic axes, offsets take their nearest image)
+template <bool PER>
 __global__ void __launch_bounds__(kFFBlock, 4) k_gram_ff(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < A.n) gram_ff_body(A, s);
+  if (s < A.n) gram_ff_body<PER>(A, s);
 }
 
+template <bool PER>
 __global__ void __launch_bounds__(kFFBlock, 4) k_pass1_ff(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < A.n) pass1_body<LP_MIXED_FF>(A, s);
+  if (s < A.n) pass1_body<LP_MIXED_FF, PER>(A, s);
 }
 
 __global__ void k_split_state(const StepArgs A) {
@@ -68,13 +71,15 @@ __global__ void k_split_state(const StepArgs A) {
 }
 
 // rows of the entries with a ghost (free surface), ahead of the main kernels
+template <bool PER>
 __global__ void k_gram_twins(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < A.n) gram_twins_body(A, s);
+  if (s < A.n) gram_twins_body<PER>(A, s);
 }
+template <bool PER>
 __global__ void k_pass2_twins(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < A.n) pass2_twins_body(A, s);
+  if (s < A.n) pass2_twins_body<PER>(A, s);
 }
 
 __global__ void k_split_p1(const StepArgs A) {
@@ -82,15 +87,16 @@ __global__ void k_split_p1(const StepArgs A) {
   if (s < A.n) split_p1_body(A, s);
 }
 
-template <int PREC>
+template <int PREC, bool PER>
 __global__ void __launch_bounds__(kMaxBlock) k_pass2(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  pass2_body<PREC>(A, s, s < A.n);
+  pass2_body<PREC, PER>(A, s, s < A.n);
 }
 
+template <bool PER>
 __global__ void __launch_bounds__(kFFBlock, 5) k_pass2_ff(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  pass2_body<LP_MIXED_FF>(A, s, s < A.n);
+  pass2_body<LP_MIXED_FF, PER>(A, s, s < A.n);
 }
 
 // ------------------------------------------------ lp_fit_derivatives
@@ -288,31 +294,50 @@ __global__ void k_mui_stress(int64_t n, ColMui mui, double phi_c, double phi_min
 
 void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs) {
   const int nb = (A.n + bs - 1) / bs;
+  const bool per = A.K.periodic != 0;
   if (prec == LP_FP64) {
-    k_pass1<LP_FP64><<<nb, bs, 0, st>>>(A);
+    if (per) k_pass1<LP_FP64, true><<<nb, bs, 0, st>>>(A);
+    else k_pass1<LP_FP64, false><<<nb, bs, 0, st>>>(A);
   } else if (prec == LP_MIXED) {
-    k_pass1<LP_MIXED><<<nb, bs, 0, st>>>(A);
+    if (per) k_pass1<LP_MIXED, true><<<nb, bs, 0, st>>>(A);
+    else k_pass1<LP_MIXED, false><<<nb, bs, 0, st>>>(A);
   } else {
     k_split_state<<<(A.n + 255) / 256, 256, 0, st>>>(A);
     const int b = bs < kFFBlock ? bs : kFFBlock;
-    if (A.K.free_surface) k_gram_twins<<<(A.n + 127) / 128, 128, 0, st>>>(A);
-    k_gram_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
-    k_pass1_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
+    const int ng = (A.n + 127) / 128, nf = (A.n + b - 1) / b;
+    if (per) {
+      if (A.K.free_surface) k_gram_twins<true><<<ng, 128, 0, st>>>(A);
+      k_gram_ff<true><<<nf, b, 0, st>>>(A);
+      k_pass1_ff<true><<<nf, b, 0, st>>>(A);
+    } else {
+      if (A.K.free_surface) k_gram_twins<false><<<ng, 128, 0, st>>>(A);
+      k_gram_ff<false><<<nf, b, 0, st>>>(A);
+      k_pass1_ff<false><<<nf, b, 0, st>>>(A);
+    }
   }
   k_pass1_fallback<<<152, 64, 0, st>>>(A);
 }
 void launch_pass2(int prec, const StepArgs& A, cudaStream_t st, int bs) {
   if (prec == LP_MIXED_FF) {
     k_split_p1<<<(A.n + 255) / 256, 256, 0, st>>>(A);
-    if (A.K.free_surface) k_pass2_twins<<<(A.n + 127) / 128, 128, 0, st>>>(A);
+    if (A.K.free_surface) {
+      if (A.K.periodic) k_pass2_twins<true><<<(A.n + 127) / 128, 128, 0, st>>>(A);
+      else k_pass2_twins<false><<<(A.n + 127) / 128, 128, 0, st>>>(A);
+    }
   }
   k_pass2_fallback<<<152, 64, 0, st>>>(A);
   const int nb = (A.n + bs - 1) / bs;
-  if (prec == LP_FP64) k_pass2<LP_FP64><<<nb, bs, 0, st>>>(A);
-  else if (prec == LP_MIXED) k_pass2<LP_MIXED><<<nb, bs, 0, st>>>(A);
-  else {
+  const bool per = A.K.periodic != 0;
+  if (prec == LP_FP64) {
+    if (per) k_pass2<LP_FP64, true><<<nb, bs, 0, st>>>(A);
+    else k_pass2<LP_FP64, false><<<nb, bs, 0, st>>>(A);
+  } else if (prec == LP_MIXED) {
+    if (per) k_pass2<LP_MIXED, true><<<nb, bs, 0, st>>>(A);
+    else k_pass2<LP_MIXED, false><<<nb, bs, 0, st>>>(A);
+  } else {
     const int b = bs < kFFBlock ? bs : kFFBlock;
-    k_pass2_ff<<<(A.n + b - 1) / b, b, 0, st>>>(A);
+    if (per) k_pass2_ff<true><<<(A.n + b - 1) / b, b, 0, st>>>(A);
+    else k_pass2_ff<false><<<(A.n + b - 1) / b, b, 0, st>>>(A);
   }
 }
 void launch_fit(int prec, const FitArgs& F, cudaStream_t st) {

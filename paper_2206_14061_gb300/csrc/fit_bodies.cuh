@@ -74,12 +74,19 @@ __device__ __forceinline__ void ghost_rhs2(const StepArgs& A, double gni, double
 
 // ------------------------------------------------------------ pass 1
 
+template <bool PER>
 __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s);
 
-template <int PREC>
+// PER: periodic axes (offsets take their nearest image); without it the
+// periods are not read
+template <bool PER>
+__device__ __forceinline__ double per_off(double d, double L) {
+  return PER ? min_image(d, L) : d;
+}
+template <int PREC, bool PER = false>
 __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
   if (PREC == LP_MIXED_FF) {
-    pass1_ff_body(A, s);
+    pass1_ff_body<PER>(A, s);
     return;
   }
   const int n = A.n;
@@ -104,7 +111,8 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
-      const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+      const double dx = per_off<PER>(A.x[j] - xi, A.K.Lx) * ih;
+      const double dy = per_off<PER>(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
       if (code & kGhostBit) M.add(-dx, -dy, -dz);  // its ghost: reflected row, b = 0
       double uj = A.u[j], vj = A.v[j], wj = A.w[j];
       if (mir) { uj *= su; vj *= sv; wj *= sw; }
@@ -151,7 +159,8 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
-      const float dx = (float)((A.x[j] - xi) * ih), dy = (float)((A.y[j] - yi) * ih);
+      const float dx = (float)(per_off<PER>(A.x[j] - xi, A.K.Lx) * ih);
+      const float dy = (float)(per_off<PER>(A.y[j] - yi, A.K.Ly) * ih);
       const float dz = (float)((zj - zi) * ih);
       if (code & kGhostBit) M.add(-dx, -dy, -dz);  // its ghost: reflected row, b = 0
       double uj = A.u[j], vj = A.v[j], wj = A.w[j];
@@ -194,7 +203,8 @@ __device__ __forceinline__ void pass1_body(const StepArgs& A, int s) {
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
-      const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+      const double dx = per_off<PER>(A.x[j] - xi, A.K.Lx) * ih;
+      const double dy = per_off<PER>(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
       double uj = A.u[j], vj = A.v[j], wj = A.w[j];
       if (mir) { uj *= su; vj *= sv; wj *= sw; }
       // the entry's row, then (flagged entries) its ghost: reflected row, b = 0
@@ -241,7 +251,8 @@ static __device__ __noinline__ void pass1_fallback_item(const StepArgs& A, int t
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
-      const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+      const double dx = min_image(A.x[j] - xi, A.K.Lx) * ih;
+      const double dy = min_image(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
       double uj = A.u[j], vj = A.v[j], wj = A.w[j];
       if (mir) { uj *= usign(mm, 0); vj *= usign(mm, 1); wj *= usign(mm, 2); }
       for (int t = 0; t < ((code & kGhostBit) ? 2 : 1) && rows < LP_MAX_CAP; ++t, ++rows) {
@@ -283,7 +294,8 @@ static __device__ __noinline__ void pass2_fallback_item(const StepArgs& A, int t
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       const double zj = mir ? f2 - A.z[j] : A.z[j];
-      const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+      const double dx = min_image(A.x[j] - xi, A.K.Lx) * ih;
+      const double dy = min_image(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
       for (int t = 0; t < ((code & kGhostBit) ? 2 : 1) && rows < LP_MAX_CAP; ++t, ++rows) {
         const double rs = t ? -1.0 : 1.0;
         taylor_row(rs * dx, rs * dy, rs * dz, &Am[rows * kNB]);
@@ -350,23 +362,39 @@ __device__ __forceinline__ void ff_gather(const StepArgs& A, int s, uint32_t cod
   jh = A.Xh[j];
   jl = A.Xl[j];
 }
+// offset along an axis of period Lh (units of h, float-float; Lh = 0: not
+// periodic), taken as its nearest image
+__device__ __forceinline__ ff ff_min_image(ff d, float Lh_h, float Lh_l) {
+  if (Lh_h > 0.f) {
+    if (d.h > 0.5f * Lh_h) return ff_sub(d, ff{Lh_h, Lh_l});
+    if (d.h < -0.5f * Lh_h) return ff_add(d, ff{Lh_h, Lh_l});
+  }
+  return d;
+}
+template <bool PER>
 __device__ __forceinline__ FFRow ff_row_of(const float4& hi, const float4& lo, const float4& jh,
-                                           const float4& jl, uint32_t code) {
+                                           const float4& jl, uint32_t code,
+                                           const StepConsts& K) {
   const bool mir = code >> 31;
   FFRow r;
   r.dx = ff_diff(jh.x, jl.x, hi.x, lo.x);
   r.dy = ff_diff(jh.y, jl.y, hi.y, lo.y);
+  if (PER) {
+    r.dx = ff_min_image(r.dx, K.Lhx_h, K.Lhx_l);
+    r.dy = ff_min_image(r.dy, K.Lhy_h, K.Lhy_l);
+  }
   r.dz = mir ? ff_diff(jh.w, jl.w, hi.z, lo.z) : ff_diff(jh.z, jl.z, hi.z, lo.z);
   r.qxx = ff_mul(r.dx, r.dx); r.qyy = ff_mul(r.dy, r.dy); r.qzz = ff_mul(r.dz, r.dz);
   r.qxy = ff_mul(r.dx, r.dy); r.qxz = ff_mul(r.dx, r.dz); r.qyz = ff_mul(r.dy, r.dz);
   return r;
 }
 // Row of stencil entry `code` of particle s, gathered without pipelining.
+template <bool PER>
 __device__ __forceinline__ FFRow ff_entry_row(const StepArgs& A, int s, const float4& hi,
                                               const float4& lo, uint32_t code) {
   float4 jh, jl;
   ff_gather(A, s, code, jh, jl);
-  return ff_row_of(hi, lo, jh, jl, code);
+  return ff_row_of<PER>(hi, lo, jh, jl, code, A.K);
 }
 // Number of entries with a ghost (kGhostBit), at the end of the stencil of s.
 __device__ __forceinline__ int ghost_count(const StepArgs& A, int s, int m) {
@@ -502,6 +530,7 @@ __device__ __forceinline__ void ff_chol_solve(const StepArgs& A, int s, ff (*r)[
 
 // Moments of the entries with a ghost together with their ghosts (even
 // moments twice, odd ones cancel): Tg, 31 float-float, hi then lo, k-major.
+template <bool PER>
 __device__ __forceinline__ void gram_twins_body(const StepArgs& A, int s) {
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);
@@ -513,7 +542,7 @@ __device__ __forceinline__ void gram_twins_body(const StepArgs& A, int s) {
   for (int q = 0; q < 31; ++q) t[q] = {0.f, 0.f};
 #pragma unroll 1
   for (int k = mr; k < m; ++k)
-    ff_moments_add_twin(t, ff_entry_row(A, s, hi, lo, (uint32_t)A.nbr[(int64_t)k * n + s]));
+    ff_moments_add_twin(t, ff_entry_row<PER>(A, s, hi, lo, (uint32_t)A.nbr[(int64_t)k * n + s]));
 #pragma unroll
   for (int q = 0; q < 31; ++q) {
     const ff v = ff_norm(t[q]);
@@ -526,6 +555,7 @@ __device__ __forceinline__ void gram_twins_body(const StepArgs& A, int s) {
 // (reflected row, right-hand sides fixed by the particle): b_j a + b_G a~,
 // a~ the row with its linear terms negated. T2: 2 x 9 float-float, hi then
 // lo, k-major. Needs the pass-1 outputs and their split copy (GVff).
+template <bool PER>
 __device__ __forceinline__ void pass2_twins_body(const StepArgs& A, int s) {
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);
@@ -547,7 +577,7 @@ __device__ __forceinline__ void pass2_twins_body(const StepArgs& A, int s) {
     const int j = c0 & kIndexMask;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     ff a[kNB];
-    ff_taylor(ff_entry_row(A, s, hi, lo, c0), a);
+    ff_taylor(ff_entry_row<PER>(A, s, hi, lo, c0), a);
     const float4 gvj = A.GVff[j];
     const ff bg = (c0 >> 31) ? ff{-gvi.x, -gvi.y} : ff_diff(gvj.x, gvj.y, gvi.x, gvi.y);
     const ff bv = ff_diff(gvj.z, gvj.w, gvi.z, gvi.w);
@@ -573,6 +603,7 @@ __device__ __forceinline__ void pass2_twins_body(const StepArgs& A, int s) {
 // the Cholesky factor with the pivot test, stored for both passes. Stencils
 // that fail the test (or have fewer than 9 rows) are queued for the
 // pivoted-QR fit.
+template <bool PER>
 __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);
@@ -604,7 +635,7 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
       ff_gather(A, s, code, jh, jl);
       if (k + 2 < mr) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
-    ff_moments_add(mo, ff_row_of(hi, lo, h0, l0, c0));
+    ff_moments_add(mo, ff_row_of<PER>(hi, lo, h0, l0, c0, A.K));
   }
   ff G[kTri];
   ff_gram(mo, G);
@@ -624,6 +655,7 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
 }
 
 // pass 1 in float-float: right-hand sides of u, v, w and the solves
+template <bool PER>
 __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   if (A.fbslot[s] != -1) return;  // queued for the pivoted-QR fit
   const int n = A.n;
@@ -656,7 +688,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
       vh = A.Uh[jj]; vl = A.Ul[jj];
       if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
-    const FFRow r = ff_row_of(hi, lo, h0, l0, c0);
+    const FFRow r = ff_row_of<PER>(hi, lo, h0, l0, c0, A.K);
     ff a[kNB];
     ff_taylor(r, a);
     const int j = c0 & kIndexMask;
@@ -682,6 +714,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
 }
 
 // pass-2 fits in float-float: gradients of |gdot|^n and V^{n+1}
+template <bool PER>
 __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, double gni,
                                                double Vi, double* gg, double* gV) {
   const int n = A.n;
@@ -720,7 +753,7 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
       jg = A.GVff[min(code & kIndexMask, (unsigned)(n - 1))];
       if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
-    const FFRow r = ff_row_of(hi, lo, h0, l0, c0);
+    const FFRow r = ff_row_of<PER>(hi, lo, h0, l0, c0, A.K);
     ff a[kNB];
     ff_taylor(r, a);
     const int j = c0 & kIndexMask;
@@ -746,7 +779,7 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
 // ------------------------------------------------------------ pass 2
 
 // every lane of the warp must call it (live or not)
-template <int PREC>
+template <int PREC, bool PER = false>
 __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) {
   int regime = 1;
   bool overc = false, nonfin = false, below = false;
@@ -771,7 +804,7 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     } else if (slot == -1) {
       const int m = min(A.cnt[s], A.cap);
       if (PREC == LP_MIXED_FF) {
-        pass2_ff_grads(A, s, m, gni, Vi, gg, gV);
+        pass2_ff_grads<PER>(A, s, m, gni, Vi, gg, gV);
       } else if (PREC == LP_FP64) {
         double R[2][kNB];
 #pragma unroll
@@ -786,7 +819,8 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
           if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
-          const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+          const double dx = per_off<PER>(A.x[j] - xi, A.K.Lx) * ih;
+          const double dy = per_off<PER>(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
           // the entry's row, then (flagged entries) its ghost's reflected row
           for (int t = 0; t < ((code & kGhostBit) ? 2 : 1); ++t) {
             const double rs = t ? -1.0 : 1.0;
@@ -835,7 +869,8 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
           if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
-          const float dx = (float)((A.x[j] - xi) * ih), dy = (float)((A.y[j] - yi) * ih);
+          const float dx = (float)(per_off<PER>(A.x[j] - xi, A.K.Lx) * ih);
+          const float dy = (float)(per_off<PER>(A.y[j] - yi, A.K.Ly) * ih);
           const float dz = (float)((zj - zi) * ih);
           for (int t = 0; t < ((code & kGhostBit) ? 2 : 1); ++t) {
             const float rs = t ? -1.f : 1.f;
@@ -864,7 +899,8 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
           if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
           const bool mir = code >> 31;
           const double zj = mir ? f2 - A.z[j] : A.z[j];
-          const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+          const double dx = per_off<PER>(A.x[j] - xi, A.K.Lx) * ih;
+          const double dy = per_off<PER>(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
           for (int t = 0; t < ((code & kGhostBit) ? 2 : 1); ++t) {
             const double rs = t ? -1.0 : 1.0;
             double a[kNB];
@@ -937,8 +973,12 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     const double u1 = un + dt * acc[0], v1 = vn + dt * acc[1], w1 = wn + dt * acc[2];
     // x with the mean velocity (the paper's step) or with u^n (Heun stage)
     const double hx = A.K.euler ? dt : 0.5 * dt;
-    const double x1 = xi + hx * (A.K.euler ? un : un + u1);
-    const double y1 = yi + hx * (A.K.euler ? vn : vn + v1);
+    double x1 = xi + hx * (A.K.euler ? un : un + u1);
+    double y1 = yi + hx * (A.K.euler ? vn : vn + v1);
+    if (PER) {  // periodic axes: back into [0, L)
+      x1 = wrap_pos(x1, A.K.Lx);
+      y1 = wrap_pos(y1, A.K.Ly);
+    }
     const double z1 = zi + hx * (A.K.euler ? wn : wn + w1);
     A.uo[s] = u1; A.vo[s] = v1; A.wo[s] = w1;
     A.xo[s] = x1; A.yo[s] = y1; A.zo[s] = z1;
@@ -946,7 +986,9 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     nonfin = !(isfinite(u1) && isfinite(v1) && isfinite(w1) && isfinite(x1) && isfinite(y1) &&
                isfinite(z1) && isfinite(Vnext));
     if (A.xref) {
-      const double ex = x1 - A.xref[s], ey = y1 - A.xref[A.n + s], ez = z1 - A.xref[2 * A.n + s];
+      const double ex = per_off<PER>(x1 - A.xref[s], A.K.Lx);
+      const double ey = per_off<PER>(y1 - A.xref[A.n + s], A.K.Ly);
+      const double ez = z1 - A.xref[2 * A.n + s];
       if (!(((ex * ex) + (ey * ey)) + (ez * ez) <= A.half_skin2)) *A.need_search = 1;
     }
     below = A.K.mirror_mode != LP_MIRROR_NONE && z1 < A.K.floor_z;

@@ -28,11 +28,12 @@ constexpr int kMaxCand = 128;     // candidate buffer of the keep-nearest search
 // cell coordinates clamped into the grid (clamping keeps any two points within
 // one cell of each other per axis when they are within one cell edge).
 struct GridCol {
-  double ox, oy, oz;   // origin
-  double inv_c;        // 1 / cell edge
-  float cf;            // cell edge (FP32) for the prefilter bound
+  double ox, oy, oz;     // origin
+  double icx, icy, icz;  // 1 / cell edge per axis
+  double Lx, Ly;         // periods (0: not periodic); a periodic axis has origin 0 and
+                         // whole cells over [0, L), and its neighbour cells wrap
   int nx, ny, nz;
-  int64_t cell_off;    // first global cell id of this column
+  int64_t cell_off;      // first global cell id of this column
 };
 
 // per-column material parameters
@@ -51,6 +52,12 @@ struct StepConsts {
   // round((K r)^2), K h, round((K h / 2)^2), 1/phi_G, phi_c - phi_G
   int free_surface;
   int euler;  // Heun stage: pass 2 takes V^n, x advances with u^n
+  // periodic boundaries: periods (0: not periodic), their float-float copies
+  // in units of h, and the integer periods round(K L) of the ghost test
+  int periodic;
+  double Lx, Ly;
+  float Lhx_h, Lhx_l, Lhy_h, Lhy_l;
+  long long ghost_PX, ghost_PY;
   double ghost_grid, ghost_hk, ghost_V, ghost_num;
   long long ghost_R2, ghost_clear2;
 };
@@ -65,6 +72,25 @@ struct DevDiag {
 };
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
+
+// Periodic boundaries (Sec. 3.1 item 9): the offset d along an axis of period
+// L (0: not periodic) taken as its nearest image, and a position moved back
+// into [0, L) (a step moves a particle far less than L). Both in FP64 with
+// rounded operations in a fixed order.
+__device__ __forceinline__ double min_image(double d, double L) {
+  if (L > 0.0) {
+    if (d > __dmul_rn(0.5, L)) return __dsub_rn(d, L);
+    if (d < -__dmul_rn(0.5, L)) return __dadd_rn(d, L);
+  }
+  return d;
+}
+__device__ __forceinline__ double wrap_pos(double x, double L) {
+  if (L > 0.0) {
+    if (x >= L) return __dsub_rn(x, L);
+    if (x < 0.0) return __dadd_rn(x, L);
+  }
+  return x;
+}
 
 // ------------------------------------------------------------ float-float
 // Unevaluated sums hi + lo of two floats (about 48 significant bits), built

@@ -30,11 +30,35 @@ __global__ void k_copy_state(int n, State7 dst, State7 src) {
 #pragma unroll
   for (int k = 0; k < 7; ++k) dst.f[k][s] = src.f[k][s];
 }
-__global__ void k_heun_combine(int n, State7 y, State7 y0) {
+// (along a periodic axis, period L > 0: the mean of the two positions taken
+// on the same image, moved back into [0, L))
+__global__ void k_heun_combine(int n, State7 y, State7 y0, double Lx, double Ly) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) y.f[k][s] = __dmul_rn(0.5, __dadd_rn(y0.f[k][s], y.f[k][s]));
+  for (int k = 0; k < 7; ++k) {
+    const double a = y0.f[k][s], b = y.f[k][s];
+    const double L = k == 0 ? Lx : (k == 1 ? Ly : 0.0);
+    y.f[k][s] = L > 0.0
+                    ? wrap_pos(__dadd_rn(a, __dmul_rn(0.5, min_image(__dsub_rn(b, a), L))), L)
+                    : __dmul_rn(0.5, __dadd_rn(a, b));
+  }
+}
+
+// Caller positions along periodic axes mapped into [0, L) before the first
+// step (values already there are kept as they are; non-finite ones too)
+__device__ __forceinline__ double wrap_any(double v, double L) {
+  if ((v >= 0.0 && v < L) || !isfinite(v)) return v;
+  double r = fmod(v, L);  // exact, |r| < L, with the sign of v
+  if (r < 0.0) r = __dadd_rn(r, L);
+  return r < L ? r : 0.0;
+}
+__global__ void k_wrap_positions(int n, double* __restrict__ x, double* __restrict__ y,
+                                 double Lx, double Ly) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  if (Lx > 0.0) x[s] = wrap_any(x[s], Lx);
+  if (Ly > 0.0) y[s] = wrap_any(y[s], Ly);
 }
 
 void launch_copy_state(int n, double* const* dst, double* const* src, cudaStream_t st) {
@@ -42,10 +66,14 @@ void launch_copy_state(int n, double* const* dst, double* const* src, cudaStream
   for (int k = 0; k < 7; ++k) { d.f[k] = dst[k]; s.f[k] = src[k]; }
   k_copy_state<<<(n + 255) / 256, 256, 0, st>>>(n, d, s);
 }
-void launch_heun_combine(int n, double* const* y, double* const* y0, cudaStream_t st) {
+void launch_heun_combine(int n, double* const* y, double* const* y0, double Lx, double Ly,
+                         cudaStream_t st) {
   State7 a, b;
   for (int k = 0; k < 7; ++k) { a.f[k] = y[k]; b.f[k] = y0[k]; }
-  k_heun_combine<<<(n + 255) / 256, 256, 0, st>>>(n, a, b);
+  k_heun_combine<<<(n + 255) / 256, 256, 0, st>>>(n, a, b, Lx, Ly);
+}
+void launch_wrap_positions(int n, double* x, double* y, double Lx, double Ly, cudaStream_t st) {
+  k_wrap_positions<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, Lx, Ly);
 }
 
 void launch_iota(int n, int32_t* a, cudaStream_t st) {

@@ -22,9 +22,9 @@ __device__ __forceinline__ void keys_body(int s, const double* __restrict__ x,
     return;
   }
   const GridCol g = grids[colid[s]];
-  const int cx = cell_coord(x[s], g.ox, g.inv_c, g.nx);
-  const int cy = cell_coord(y[s], g.oy, g.inv_c, g.ny);
-  const int cz = cell_coord(z[s], g.oz, g.inv_c, g.nz);
+  const int cx = cell_coord(x[s], g.ox, g.icx, g.nx);
+  const int cy = cell_coord(y[s], g.oy, g.icy, g.ny);
+  const int cz = cell_coord(z[s], g.oz, g.icz, g.nz);
   const uint32_t k = (uint32_t)cell_id(g, cx, cy, cz);
   key[s] = k;
   atomicAdd(&count[k], 1u);
@@ -115,9 +115,12 @@ __device__ __forceinline__ void gather_body(int t, int n, const int32_t* __restr
                       __double2float_rn(src[2][s] - g.oz), 0.f);
 }
 
+// exact test d^2 <= r^2 (offsets along periodic axes: nearest images)
 __device__ __forceinline__ bool exact_in(double xi, double yi, double zi, double xj, double yj,
-                                         double zj, double r2, double* d2out) {
-  const double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
+                                         double zj, double r2, double* d2out, double Lx = 0.0,
+                                         double Ly = 0.0) {
+  const double dx = min_image(__dsub_rn(xj, xi), Lx), dy = min_image(__dsub_rn(yj, yi), Ly);
+  const double dz = __dsub_rn(zj, zi);
   const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   *d2out = d2;
   return d2 <= r2;
@@ -134,7 +137,8 @@ __device__ __forceinline__ void stencil_stats(bool live, int c, int cap, DevDiag
 
 // Stencil of particle s; every lane of the warp must call it (live or not).
 // stats = false leaves the stencil-size statistics alone (candidate lists).
-template <bool KEEP>
+// PER: the grid may have periodic axes (GridCol::Lx, Ly)
+template <bool KEEP, bool PER = false>
 __device__ __forceinline__ void neighbors_body(
     int s, bool live, int n, const double* __restrict__ x, const double* __restrict__ y,
     const double* __restrict__ z, const float4* __restrict__ pf,
@@ -158,57 +162,73 @@ __device__ __forceinline__ void neighbors_body(
     // error is below about (4 L + 2) 2^-23 r^2 with L the largest coordinate
     // (mirror height included) over r. Pairs inside the band take the FP64 test.
     const float rf = __double2float_rn(r);
-    const float L = (4.0f * fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))) +
-                     4.0f * rf) / rf;
+    // (A periodic axis adds a subtraction of the period: its length joins the
+    // largest coordinate.)
+    const float cmax = fmaxf(fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))),
+                             PER ? (float)fmax(g.Lx, g.Ly) : 0.f);
+    const float L = (4.0f * cmax + 4.0f * rf) / rf;
     const float band = (1.0f + L) * 0x1p-19f;
     const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
     const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
+    const float Lxf = (float)g.Lx, Lyf = (float)g.Ly;
     double cd2[KEEP ? kMaxCand : 1];
     uint32_t cj[KEEP ? kMaxCand : 1];
     const int ncx = g.nx, ncy = g.ny, ncz = g.nz;
-    const int cx = cell_coord(xi, g.ox, g.inv_c, ncx);
-    const int cy = cell_coord(yi, g.oy, g.inv_c, ncy);
-    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, ncx - 1);
-    const int y0 = max(cy - 1, 0), y1 = min(cy + 1, ncy - 1);
+    const bool perx = PER && g.Lx > 0.0, pery = PER && g.Ly > 0.0;  // wrap (>= 3 cells)
+    const int cx = cell_coord(xi, g.ox, g.icx, ncx);
+    const int cy = cell_coord(yi, g.oy, g.icy, ncy);
+    // cells cx-1..cx+1 along x as contiguous ranges of the cell table: one
+    // range, or on a periodic axis at the first or last cell two (the pair
+    // inside the grid, then the wrapped cell)
+    const bool split = perx && (cx == 0 || cx == ncx - 1);
+    const int xa0 = split ? (cx == 0 ? 0 : ncx - 2) : max(cx - 1, 0);
+    const int xb0 = split ? (cx == 0 ? 1 : ncx - 1) : min(cx + 1, ncx - 1);
+    const int xw = cx == 0 ? ncx - 1 : 0;  // the wrapped cell (split only)
+    const int y0 = pery ? cy - 1 : max(cy - 1, 0), y1 = pery ? cy + 1 : min(cy + 1, ncy - 1);
     for (int pass = 0; pass < (mirror_mode ? 2 : 1); ++pass) {
       const double qz = pass == 0 ? zi : 2.0 * floor_z - zi;
-      const int cz = cell_coord(qz, g.oz, g.inv_c, ncz);
+      const int cz = cell_coord(qz, g.oz, g.icz, ncz);
       const int z0 = max(cz - 1, 0), z1 = min(cz + 1, ncz - 1);
       for (int kz = z0; kz <= z1; ++kz)
-        for (int ky = y0; ky <= y1; ++ky) {
-          // cells kx = x0..x1 are contiguous in the cell table
-          const int64_t c0 = cell_id(g, x0, ky, kz), c1 = cell_id(g, x1, ky, kz);
-          const uint32_t b = start[c0], e = start[c1 + 1];
-          for (uint32_t j = b; j < e; ++j) {
-            if (pass == 0 && (int)j == s) continue;
-            const float4 pj = pf[j];
-            const float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
-            const float dzf = (pass == 0 ? pj.z : fz2 - pj.z) - pi.z;
-            const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
-            if (!exact_only && d2f > hi) continue;
-            double d2 = 0.0;
-            bool in;
-            if (!exact_only && d2f < lo && !KEEP) {
-              in = true;
-            } else {
-              const double zj = pass == 0 ? z[j] : __dsub_rn(2.0 * floor_z, z[j]);
-              in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2);
-            }
-            if (!in) continue;
-            const uint32_t code = j | (pass ? kMirrorBit : 0u);
-            if (KEEP) {
-              if (c < kMaxCand) {
-                cd2[c] = d2;
-                cj[c] = code;
+        for (int kyy = y0; kyy <= y1; ++kyy)
+          for (int sx = 0; sx < (split ? 2 : 1); ++sx) {
+            const int ky = pery ? (kyy + ncy) % ncy : kyy;
+            const int64_t c0 = cell_id(g, sx ? xw : xa0, ky, kz);
+            const int64_t c1 = cell_id(g, sx ? xw : xb0, ky, kz);
+            const uint32_t b = start[c0], e = start[c1 + 1];
+            for (uint32_t j = b; j < e; ++j) {
+              if (pass == 0 && (int)j == s) continue;
+              const float4 pj = pf[j];
+              float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
+              if (perx) dxf = dxf > 0.5f * Lxf ? dxf - Lxf : (dxf < -0.5f * Lxf ? dxf + Lxf : dxf);
+              if (pery) dyf = dyf > 0.5f * Lyf ? dyf - Lyf : (dyf < -0.5f * Lyf ? dyf + Lyf : dyf);
+              const float dzf = (pass == 0 ? pj.z : fz2 - pj.z) - pi.z;
+              const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+              if (!exact_only && d2f > hi) continue;
+              double d2 = 0.0;
+              bool in;
+              if (!exact_only && d2f < lo && !KEEP) {
+                in = true;
               } else {
-                over = true;
+                const double zj = pass == 0 ? z[j] : __dsub_rn(2.0 * floor_z, z[j]);
+                in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2, PER ? g.Lx : 0.0,
+                              PER ? g.Ly : 0.0);
               }
-            } else if (c < cap) {
-              nbr[(int64_t)c * n + s] = (int32_t)code;
+              if (!in) continue;
+              const uint32_t code = j | (pass ? kMirrorBit : 0u);
+              if (KEEP) {
+                if (c < kMaxCand) {
+                  cd2[c] = d2;
+                  cj[c] = code;
+                } else {
+                  over = true;
+                }
+              } else if (c < cap) {
+                nbr[(int64_t)c * n + s] = (int32_t)code;
+              }
+              ++c;
             }
-            ++c;
           }
-        }
     }
     if (KEEP) {
       int m = c < kMaxCand ? c : kMaxCand;
@@ -267,6 +287,7 @@ __device__ __forceinline__ void stencil_stats(bool live, int c, int cap, DevDiag
 // (found within radius + skin at the last search) that passes the exact
 // radius test, in candidate order. Same FP32 prefilter and uncontracted FP64
 // test as the search. Every lane of the warp must call it (live or not).
+template <bool PER = false>
 __device__ __forceinline__ void filter_body(
     int s, bool live, int n, const double* __restrict__ x, const double* __restrict__ y,
     const double* __restrict__ z, const float4* __restrict__ pf,
@@ -285,8 +306,11 @@ __device__ __forceinline__ void filter_body(
     const float fz2 = __double2float_rn(2.0 * (floor_z - g.oz));
     // FP32 prefilter band, as in neighbors_body
     const float rf = __double2float_rn(r);
-    const float L = (4.0f * fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))) +
-                     4.0f * rf) / rf;
+    const float cmax = fmaxf(fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))),
+                             PER ? (float)fmax(g.Lx, g.Ly) : 0.f);
+    const float L = (4.0f * cmax + 4.0f * rf) / rf;
+    const bool perx = PER && g.Lx > 0.0, pery = PER && g.Ly > 0.0;
+    const float Lxf = (float)g.Lx, Lyf = (float)g.Ly;
     const float band = (1.0f + L) * 0x1p-19f;
     const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
     const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
@@ -306,7 +330,9 @@ __device__ __forceinline__ void filter_body(
       const int j = code & ~kMirrorBit;
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
-      const float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
+      float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
+      if (perx) dxf = dxf > 0.5f * Lxf ? dxf - Lxf : (dxf < -0.5f * Lxf ? dxf + Lxf : dxf);
+      if (pery) dyf = dyf > 0.5f * Lyf ? dyf - Lyf : (dyf < -0.5f * Lyf ? dyf + Lyf : dyf);
       const float dzf = (mir ? fz2 - pj.z : pj.z) - pi.z;
       const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
       if (!exact_only && d2f > hi) continue;
@@ -316,7 +342,7 @@ __device__ __forceinline__ void filter_body(
       } else {
         double d2;
         const double zj = mir ? __dsub_rn(2.0 * floor_z, z[j]) : z[j];
-        in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2);
+        in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2, PER ? g.Lx : 0.0, PER ? g.Ly : 0.0);
       }
       if (!in) continue;
       if (c < cap) nbr[(int64_t)c * n + s] = (int32_t)code;
@@ -334,8 +360,9 @@ __device__ __forceinline__ void filter_body(
 // Ghost particles (Sec. 3.1 items 6 and 9). The paper leaves the test and the
 // placement open; the reading, also the oracle's:
 //  - positions in fixed point, X = round(K x) on a power-of-two grid K with
-//    K r <= 8192, offsets o_k = X_k - X_i (exact integers; for stencil
-//    entries |o| <= 8193, so squares and pair sums fit 32 bits);
+//    K r <= 8192, offsets o_k = X_k - X_i (exact integers, along a periodic
+//    axis the nearest image modulo round(K L); for stencil entries
+//    |o| <= 8193, so squares and pair sums fit 32 bits);
 //  - weights w_k = max(0, R2 - |o_k|^2), R2 = round((K r)^2);
 //  - one-sided stencil: |S| > 0.22 K h sum w_k with S = sum w_k o_k;
 //  - a ghost at -o_k for every entry with o_k . S >= (K h / 2) |S| (o_k . S
@@ -352,6 +379,11 @@ __device__ __forceinline__ void filter_body(
 // ghosts must fit in cap (else LP_FLAG_OVERFLOW). Positions are stored
 // relative to the column's fixed-point origin (an exact integer shift), as
 // 32-bit integers.
+
+// offset along an axis of integer period P (0: none), nearest image
+__device__ __forceinline__ int wrap_fix(int o, int P) {
+  return P > 0 ? (2 * o > P ? o - P : (2 * o < -P ? o + P : o)) : o;
+}
 
 // fixed-point position (x, y, z, floor-mirror height) of particle s
 __device__ __forceinline__ void ghost_fix_body(int s, const double* __restrict__ x,
@@ -386,6 +418,7 @@ __device__ __forceinline__ void ghost_body(int s, bool live, int n, const double
     short o[3][LP_MAX_CAP];  // offsets of the entries (|o| <= 8193)
     long long S0 = 0, S1 = 0, S2 = 0, W = 0;
     const int R2 = (int)K.ghost_R2;
+    const int PX = (int)K.ghost_PX, PY = (int)K.ghost_PY;  // integer periods (0: none)
     bool ok = m > 0;
     // software pipeline: codes two entries ahead, positions one ahead
     uint32_t nc = m > 0 ? (uint32_t)nbr[s] : 0u;
@@ -400,7 +433,7 @@ __device__ __forceinline__ void ghost_body(int s, bool live, int n, const double
         if (k + 2 < m) nn = (uint32_t)nbr[(int64_t)(k + 2) * n + s];
       }
       if ((code & kIndexMask) >= (uint32_t)n || (code & kGhostBit)) { ok = false; break; }
-      const int o0 = xj.x - xi.x, o1 = xj.y - xi.y;
+      const int o0 = wrap_fix(xj.x - xi.x, PX), o1 = wrap_fix(xj.y - xi.y, PY);
       const int o2 = ((code & kMirrorBit) ? xj.w : xj.z) - xi.z;
       o[0][k] = (short)o0; o[1][k] = (short)o1; o[2][k] = (short)o2;
       const int q = (o0 * o0 + o1 * o1) + o2 * o2;

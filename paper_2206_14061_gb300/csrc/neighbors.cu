@@ -192,7 +192,7 @@ __global__ void k_gather(int n, const int32_t* __restrict__ tmp, const double* c
 
 // ------------------------------------------------------- neighbour search
 
-template <bool KEEP>
+template <bool KEEP, bool PER>
 __global__ void __launch_bounds__(kMaxBlock)
 k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
             const double* __restrict__ z, const float4* __restrict__ pf,
@@ -208,12 +208,13 @@ k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
     xref[n + s] = y[s];
     xref[2 * n + s] = z[s];
   }
-  neighbors_body<KEEP>(s, s < n, n, x, y, z, pf, colid, ids, grids, start, radius, r_const,
-                       mirror_mode, floor_z, cap, nbr, cnt, dg, xref == nullptr);
+  neighbors_body<KEEP, PER>(s, s < n, n, x, y, z, pf, colid, ids, grids, start, radius, r_const,
+                            mirror_mode, floor_z, cap, nbr, cnt, dg, xref == nullptr);
 }
 
 // Verlet filter (filter_body). Thread 0 clears the search flag for the
 // displacement test of this step's update.
+template <bool PER>
 __global__ void __launch_bounds__(kMaxBlock)
 k_filter(int n, const double* __restrict__ x, const double* __restrict__ y,
          const double* __restrict__ z, const float4* __restrict__ pf,
@@ -223,8 +224,8 @@ k_filter(int n, const double* __restrict__ x, const double* __restrict__ y,
          DevDiag* __restrict__ dg, int* search) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s == 0) *search = 0;
-  filter_body(s, s < n, n, x, y, z, pf, cand, ccnt, capc, grids, colid, r, floor_z, cap, nbr,
-              cnt, dg);
+  filter_body<PER>(s, s < n, n, x, y, z, pf, cand, ccnt, capc, grids, colid, r, floor_z, cap,
+                   nbr, cnt, dg);
 }
 
 // Free-surface ghosts (ghost_body): fixed-point positions, then completion of
@@ -298,23 +299,33 @@ void launch_neighbors(bool keep, int n, const double* x, const double* y, const 
                       const GridCol* grids, const uint32_t* start, const double* radius,
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
                       int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs, const int* search,
-                      double* xref) {
+                      double* xref, bool periodic) {
   const int nb = (n + bs - 1) / bs;
-  if (keep)
-    k_neighbors<true><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
-                                          r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
-                                          search, xref);
+  if (keep)  // (stencils for callers: never periodic)
+    k_neighbors<true, false><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
+                                                 r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
+                                                 search, xref);
+  else if (periodic)
+    k_neighbors<false, true><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
+                                                 r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
+                                                 search, xref);
   else
-    k_neighbors<false><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
-                                           r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
-                                           search, xref);
+    k_neighbors<false, false><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start,
+                                                  radius, r_const, mirror_mode, floor_z, cap, nbr,
+                                                  cnt, dg, search, xref);
 }
 void launch_filter(int n, const double* x, const double* y, const double* z, const float4* pf,
                    const int32_t* cand, const int32_t* ccnt, int capc, const GridCol* grids,
                    const int32_t* colid, double r, double floor_z, int cap, int32_t* nbr,
-                   int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs) {
-  k_filter<<<(n + bs - 1) / bs, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
-                                             floor_z, cap, nbr, cnt, dg, search);
+                   int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs,
+                   bool periodic) {
+  const int nb = (n + bs - 1) / bs;
+  if (periodic)
+    k_filter<true><<<nb, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r, floor_z,
+                                      cap, nbr, cnt, dg, search);
+  else
+    k_filter<false><<<nb, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
+                                       floor_z, cap, nbr, cnt, dg, search);
 }
 void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,

@@ -1,7 +1,9 @@
 // One LP step as a single persistent, cooperative launch over all particles
 // of all columns: cell sort, neighbour search, pass 1 and pass 2 run as
 // phases of one kernel, separated by a grid barrier. The same device bodies
-// as the per-phase kernels are used, so results are identical.
+// as the per-phase kernels are used, so results are identical. The kernel
+// takes the bodies' periodic variants (PER) in every run: with both periods 0
+// they reduce to exactly the arithmetic of the non-periodic ones.
 //
 // The barrier is a generation counter in global memory. A block that waits
 // longer than the spin limit sets LP_FLAG_TIMEOUT and leaves the kernel, so
@@ -144,13 +146,13 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
           P.xref[n + s] = S.y[s];
           P.xref[2 * n + s] = S.z[s];
         }
-        neighbors_body<false>(s, s < n, n, S.x, S.y, S.z, P.pf, S.colid, P.ids_out, P.grids,
-                              P.start, nullptr, P.rsearch, P.mirror_mode, P.floor_z, P.capc,
-                              P.cand, P.ccnt, S.dg, false);
+        neighbors_body<false, true>(s, s < n, n, S.x, S.y, S.z, P.pf, S.colid, P.ids_out,
+                                    P.grids, P.start, nullptr, P.rsearch, P.mirror_mode,
+                                    P.floor_z, P.capc, P.cand, P.ccnt, S.dg, false);
       } else {
-        neighbors_body<false>(s, s < n, n, S.x, S.y, S.z, P.pf, S.colid, P.ids_out, P.grids,
-                              P.start, nullptr, P.radius, P.mirror_mode, P.floor_z, P.cap,
-                              P.nbr, P.cnt, S.dg);
+        neighbors_body<false, true>(s, s < n, n, S.x, S.y, S.z, P.pf, S.colid, P.ids_out,
+                                    P.grids, P.start, nullptr, P.radius, P.mirror_mode,
+                                    P.floor_z, P.cap, P.nbr, P.cnt, S.dg);
       }
     }
   }
@@ -160,8 +162,8 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
     if (tid == 0) *P.search = 0;
     for (int base = 0; base < n; base += nth) {
       const int s = base + tid;
-      filter_body(s, s < n, n, S.x, S.y, S.z, P.pf, P.cand, P.ccnt, P.capc, P.grids, S.colid,
-                  P.radius, P.floor_z, P.cap, P.nbr, P.cnt, S.dg);
+      filter_body<true>(s, s < n, n, S.x, S.y, S.z, P.pf, P.cand, P.ccnt, P.capc, P.grids,
+                        S.colid, P.radius, P.floor_z, P.cap, P.nbr, P.cnt, S.dg);
     }
   }
   // ghosts complete the stencils this thread just built (positions of all
@@ -184,12 +186,12 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
   LP_SYNC_OR_LEAVE();
   if (PREC == LP_MIXED_FF) {
     for (int s = tid; s < n; s += nth) {
-      if (S.K.free_surface) gram_twins_body(S, s);  // read back by the same thread
-      gram_ff_body(S, s);
+      if (S.K.free_surface) gram_twins_body<true>(S, s);  // read back by the same thread
+      gram_ff_body<true>(S, s);
     }
     LP_SYNC_OR_LEAVE();
   }
-  for (int s = tid; s < n; s += nth) pass1_body<PREC>(S, s);
+  for (int s = tid; s < n; s += nth) pass1_body<PREC, true>(S, s);
   LP_SYNC_OR_LEAVE();
   const int nfb = min(*S.fb_count, S.fb_cap);
   for (int t = tid; t < nfb; t += nth) pass1_fallback_item(S, t);
@@ -203,8 +205,8 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
   LP_SYNC_OR_LEAVE();
   for (int base = 0; base < n; base += nth) {
     const int s = base + tid;
-    if (PREC == LP_MIXED_FF && S.K.free_surface && s < n) pass2_twins_body(S, s);
-    pass2_body<PREC>(S, s, s < n);
+    if (PREC == LP_MIXED_FF && S.K.free_surface && s < n) pass2_twins_body<true>(S, s);
+    pass2_body<PREC, true>(S, s, s < n);
   }
 }
 

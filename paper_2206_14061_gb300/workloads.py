@@ -128,6 +128,24 @@ def columns(ncol=256, n_lo=2000, n_hi=64000, h=1e-3, index=3, only=None) -> Work
                     extra=dict(N_target=Nc[list(sel)], aspect=ac[list(sel)], R=np.asarray(R_all)))
 
 
+def periodic_layer(n_xy=16, H=0.03, h=1e-3, jitter=0.05, phi_bot=0.50, phi_top=0.48,
+                   index=5) -> Workload:
+    """Granular layer of height H on the floor, periodic along x and y with
+    period L = n_xy h (the 3D run of the paper's 1D/3D compaction check,
+    Sec. 4): at rest, solid fraction falling linearly from phi_bot at the
+    floor to phi_top at the top (the paper states only "a small gradient"),
+    positions in [0, L)."""
+    rng = _rng(index)
+    nz = int(round(H / h))
+    x, y, z = lattice_box(n_xy, n_xy, nz, h, jitter, rng)
+    L = n_xy * h
+    x, y = np.mod(x, L), np.mod(y, L)
+    st = _rest_state(x, y, z)
+    st["V"] = 1.0 / (phi_bot + (phi_top - phi_bot) * (z / H))
+    return Workload(f"periodic_layer{n_xy}x{n_xy}x{nz}", h, 2.2 * h, 1e-5, st,
+                    extra=dict(L=L, H=H))
+
+
 def sweep_lattice(n_side=126, h=1e-3, jitter=0.2, index=1, nfields=4, nterms=8):
     """Derivative-operator sweep: jittered lattice, per-particle radius
     U(1.8h, 2.6h), and nfields smooth fields s(x) = sum_k a_k sin(kvec_k . x + p_k)

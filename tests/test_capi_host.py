@@ -60,3 +60,39 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(capi, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         capi.lib()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding marshals has the size and field offsets that a
+    C compiler gives the declaration in include/lp.h."""
+    import os
+    import shutil
+    import subprocess
+    from paper_2206_14061_gb300 import capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"lp_ctx_desc": capi.LpCtxDesc, "lp_particles": capi.LpParticles,
+               "lp_mui": capi.LpMui, "lp_eos": capi.LpEos, "lp_params": capi.LpParams,
+               "lp_neighbors": capi.LpNeighbors, "lp_diag": capi.LpDiag,
+               "lp_tuning": capi.LpTuning}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lp.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", f"-I{inc}", str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
