@@ -243,6 +243,7 @@ lp_status setup_grids(lp_ctx* c, int ncol, double rmax, cudaStream_t st, double 
       g.ox = org[0]; g.oy = org[1]; g.oz = org[2];
       g.icx = 1.0 / edge[0]; g.icy = 1.0 / edge[1]; g.icz = 1.0 / edge[2];
       g.Lx = Lx; g.Ly = Ly;
+      g.Lxf = (float)Lx; g.Lyf = (float)Ly;
       g.nx = dims[0]; g.ny = dims[1]; g.nz = dims[2];
       g.cell_off = total;
       total += (int64_t)dims[0] * dims[1] * dims[2];

@@ -364,10 +364,11 @@ __device__ __forceinline__ void ff_gather(const StepArgs& A, int s, uint32_t cod
 }
 // offset along an axis of period Lh (units of h, float-float; Lh = 0: not
 // periodic), taken as its nearest image
+// (a branch taken only by pairs across the edge)
 __device__ __forceinline__ ff ff_min_image(ff d, float Lh_h, float Lh_l) {
-  if (Lh_h > 0.f) {
-    if (d.h > 0.5f * Lh_h) return ff_sub(d, ff{Lh_h, Lh_l});
-    if (d.h < -0.5f * Lh_h) return ff_add(d, ff{Lh_h, Lh_l});
+  if (Lh_h > 0.f && fabsf(d.h) > 0.5f * Lh_h) {
+    const bool pos = d.h > 0.f;
+    return ff_add(d, ff{pos ? -Lh_h : Lh_h, pos ? -Lh_l : Lh_l});
   }
   return d;
 }

@@ -32,6 +32,7 @@ struct GridCol {
   double icx, icy, icz;  // 1 / cell edge per axis
   double Lx, Ly;         // periods (0: not periodic); a periodic axis has origin 0 and
                          // whole cells over [0, L), and its neighbour cells wrap
+  float Lxf, Lyf;        // the periods rounded to float (FP32 prefilter)
   int nx, ny, nz;
   int64_t cell_off;      // first global cell id of this column
 };

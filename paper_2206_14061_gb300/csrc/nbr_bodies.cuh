@@ -115,6 +115,12 @@ __device__ __forceinline__ void gather_body(int t, int n, const int32_t* __restr
                       __double2float_rn(src[2][s] - g.oz), 0.f);
 }
 
+// FP32 offset along an axis of period L (float), nearest image; with L = 0
+// the value is returned unchanged (d - (+-0))
+__device__ __forceinline__ float min_image_f(float d, float L) {
+  return fabsf(d) > 0.5f * L ? d - copysignf(L, d) : d;
+}
+
 // exact test d^2 <= r^2 (offsets along periodic axes: nearest images)
 __device__ __forceinline__ bool exact_in(double xi, double yi, double zi, double xj, double yj,
                                          double zj, double r2, double* d2out, double Lx = 0.0,
@@ -165,16 +171,17 @@ __device__ __forceinline__ void neighbors_body(
     // (A periodic axis adds a subtraction of the period: its length joins the
     // largest coordinate.)
     const float cmax = fmaxf(fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))),
-                             PER ? (float)fmax(g.Lx, g.Ly) : 0.f);
+                             PER ? fmaxf(g.Lxf, g.Lyf) : 0.f);
     const float L = (4.0f * cmax + 4.0f * rf) / rf;
     const float band = (1.0f + L) * 0x1p-19f;
     const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
     const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
-    const float Lxf = (float)g.Lx, Lyf = (float)g.Ly;
+    const float Lxf = g.Lxf, Lyf = g.Lyf;
     double cd2[KEEP ? kMaxCand : 1];
     uint32_t cj[KEEP ? kMaxCand : 1];
     const int ncx = g.nx, ncy = g.ny, ncz = g.nz;
-    const bool perx = PER && g.Lx > 0.0, pery = PER && g.Ly > 0.0;  // wrap (>= 3 cells)
+    // periodic axes wrap (>= 3 cells); float tests keep the FP64 pipe free
+    const bool perx = PER && g.Lxf > 0.f, pery = PER && g.Lyf > 0.f;
     const int cx = cell_coord(xi, g.ox, g.icx, ncx);
     const int cy = cell_coord(yi, g.oy, g.icy, ncy);
     // cells cx-1..cx+1 along x as contiguous ranges of the cell table: one
@@ -192,7 +199,7 @@ __device__ __forceinline__ void neighbors_body(
       for (int kz = z0; kz <= z1; ++kz)
         for (int kyy = y0; kyy <= y1; ++kyy)
           for (int sx = 0; sx < (split ? 2 : 1); ++sx) {
-            const int ky = pery ? (kyy + ncy) % ncy : kyy;
+            const int ky = kyy < 0 ? kyy + ncy : (kyy >= ncy ? kyy - ncy : kyy);  // (pery)
             const int64_t c0 = cell_id(g, sx ? xw : xa0, ky, kz);
             const int64_t c1 = cell_id(g, sx ? xw : xb0, ky, kz);
             const uint32_t b = start[c0], e = start[c1 + 1];
@@ -200,8 +207,10 @@ __device__ __forceinline__ void neighbors_body(
               if (pass == 0 && (int)j == s) continue;
               const float4 pj = pf[j];
               float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
-              if (perx) dxf = dxf > 0.5f * Lxf ? dxf - Lxf : (dxf < -0.5f * Lxf ? dxf + Lxf : dxf);
-              if (pery) dyf = dyf > 0.5f * Lyf ? dyf - Lyf : (dyf < -0.5f * Lyf ? dyf + Lyf : dyf);
+              if (PER) {  // nearest image (exact no-op for a period of 0)
+                dxf = min_image_f(dxf, Lxf);
+                dyf = min_image_f(dyf, Lyf);
+              }
               const float dzf = (pass == 0 ? pj.z : fz2 - pj.z) - pi.z;
               const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
               if (!exact_only && d2f > hi) continue;
@@ -307,10 +316,9 @@ __device__ __forceinline__ void filter_body(
     // FP32 prefilter band, as in neighbors_body
     const float rf = __double2float_rn(r);
     const float cmax = fmaxf(fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(fz2))),
-                             PER ? (float)fmax(g.Lx, g.Ly) : 0.f);
+                             PER ? fmaxf(g.Lxf, g.Lyf) : 0.f);
     const float L = (4.0f * cmax + 4.0f * rf) / rf;
-    const bool perx = PER && g.Lx > 0.0, pery = PER && g.Ly > 0.0;
-    const float Lxf = (float)g.Lx, Lyf = (float)g.Ly;
+    const float Lxf = g.Lxf, Lyf = g.Lyf;
     const float band = (1.0f + L) * 0x1p-19f;
     const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
     const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
@@ -331,8 +339,10 @@ __device__ __forceinline__ void filter_body(
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const bool mir = code >> 31;
       float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
-      if (perx) dxf = dxf > 0.5f * Lxf ? dxf - Lxf : (dxf < -0.5f * Lxf ? dxf + Lxf : dxf);
-      if (pery) dyf = dyf > 0.5f * Lyf ? dyf - Lyf : (dyf < -0.5f * Lyf ? dyf + Lyf : dyf);
+      if (PER) {  // nearest image (exact no-op for a period of 0)
+        dxf = min_image_f(dxf, Lxf);
+        dyf = min_image_f(dyf, Lyf);
+      }
       const float dzf = (mir ? fz2 - pj.z : pj.z) - pi.z;
       const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
       if (!exact_only && d2f > hi) continue;
