@@ -133,7 +133,8 @@ def periodic_layer(n_xy=16, H=0.03, h=1e-3, jitter=0.05, phi_bot=0.50, phi_top=0
     """Granular layer of height H on the floor, periodic along x and y with
     period L = n_xy h (the 3D run of the paper's 1D/3D compaction check,
     Sec. 4): at rest, solid fraction falling linearly from phi_bot at the
-    floor to phi_top at the top (the paper states only "a small gradient"),
+    floor to phi_top at the top (the paper shows the initial profile only in a
+    figure; a slight linear decrease is this project's reading),
     positions in [0, L)."""
     rng = _rng(index)
     nz = int(round(H / h))

@@ -1,6 +1,6 @@
-"""Pins of the oracle's periodic boundaries (Sec. 3.1 item 9: states are
-reflected periodically between the left and right edges along one or two
-dimensions). Checked against what the geometry fixes:
+"""Pins of the oracle's periodic boundaries (Sec. 3.1 item 9: along one or two
+horizontal axes a particle near one edge sees the particles near the opposite
+edge as neighbours). Checked against what the geometry fixes:
 - neighbour sets equal a periodic KD-tree's (scipy, boxsize), by brute force
   and by the grid scan, floor mirrors included;
 - the step commutes with a translation along a periodic axis;
