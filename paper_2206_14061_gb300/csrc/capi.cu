@@ -942,6 +942,9 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
   const double lhx = K.Lx * K.inv_h, lhy = K.Ly * K.inv_h;
   K.Lhx_h = (float)lhx; K.Lhx_l = (float)(lhx - (double)K.Lhx_h);
   K.Lhy_h = (float)lhy; K.Lhy_l = (float)(lhy - (double)K.Lhy_h);
+  const double ih2 = K.inv_h * K.inv_h;
+  K.ih_h = (float)K.inv_h; K.ih_l = (float)(K.inv_h - (double)K.ih_h);
+  K.ih2_h = (float)ih2; K.ih2_l = (float)(ih2 - (double)K.ih2_h);
   if (K.free_surface) {
     // ghost particles (Sec. 3.1 items 6 and 9): fixed-point grid K r <= 8192
     double g = 1.0;

@@ -655,6 +655,53 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
   }
 }
 
+// Derived values of pass 1 from float-float coefficients (as pass1_finish):
+// gdot, |gdot|, (1/2) Lap u + (1/6) grad div u and div u are formed in
+// float-float and rounded to FP64 once each, so the per-particle FP64 work is
+// the 11 conversions and V^{n+1} = V^n + dt V^n div u (FP64).
+__device__ __forceinline__ void pass1_finish_ff(const StepArgs& A, int s, const ff (*c)[kNB]) {
+  const int n = A.n;
+  const ff ih{A.K.ih_h, A.K.ih_l}, ih2{A.K.ih2_h, A.K.ih2_l};
+  const ff third{0x1.555556p-2f, -0x1.555556p-27f}, sixth{0x1.555556p-3f, -0x1.555556p-28f};
+  ff G[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) G[a][b] = ff_mul(c[a][b], ih);
+  const ff div = ff_add(ff_add(G[0][0], G[1][1]), G[2][2]);
+  const ff d3 = ff_mul(div, third);
+  const ff gd[6] = {ff_sub(G[0][0], d3), ff_sub(G[1][1], d3), ff_sub(G[2][2], d3),
+                    ff_scale(ff_add(G[0][1], G[1][0]), 0.5f),
+                    ff_scale(ff_add(G[0][2], G[2][0]), 0.5f),
+                    ff_scale(ff_add(G[1][2], G[2][1]), 0.5f)};
+  const ff dia = ff_add(ff_add(ff_mul(gd[0], gd[0]), ff_mul(gd[1], gd[1])), ff_mul(gd[2], gd[2]));
+  const ff off = ff_add(ff_add(ff_mul(gd[3], gd[3]), ff_mul(gd[4], gd[4])), ff_mul(gd[5], gd[5]));
+  const ff half = ff_add(ff_scale(dia, 0.5f), off);  // (1/2) gdot:gdot
+  double gn;
+  if (half.h > 0x1p-120f) {
+    gn = ff_to_double(ff_mul(half, ff_rsqrt(half)));  // sqrt = x / sqrt(x)
+  } else {
+    gn = half.h > 0.f ? sqrt(ff_to_double(half)) : 0.0;  // (1/x^2 would overflow)
+  }
+  double* p = A.p1;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) p[(P1_GD + q) * n + s] = ff_to_double(gd[q]);
+  p[P1_GN * n + s] = gn;
+  // Hessian columns: 3 xx, 4 yy, 5 zz, 6 xy, 7 xz, 8 yz
+  const ff dd[3] = {ff_add(ff_add(c[0][3], c[1][6]), c[2][7]),
+                    ff_add(ff_add(c[0][6], c[1][4]), c[2][8]),
+                    ff_add(ff_add(c[0][7], c[1][8]), c[2][5])};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const ff lap = ff_add(ff_add(c[a][3], c[a][4]), c[a][5]);
+    const ff ld = ff_mul(ff_add(ff_scale(lap, 0.5f), ff_mul(dd[a], sixth)), ih2);
+    p[(P1_LD + a) * n + s] = ff_to_double(ld);
+  }
+  const double Vi = A.V[s], dv = ff_to_double(div);
+  p[P1_VN * n + s] = Vi + A.K.dt * (Vi * dv);
+  p[P1_DIV * n + s] = dv;
+}
+
 // pass 1 in float-float: right-hand sides of u, v, w and the solves
 template <bool PER>
 __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
@@ -706,12 +753,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
     }
   }
   ff_chol_solve<3>(A, s, R);
-  double c[3][kNB];
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < kNB; ++q) c[f][q] = ff_to_double(R[f][q]);
-  pass1_finish(A, s, c);
+  pass1_finish_ff(A, s, R);
 }
 
 // pass-2 fits in float-float: gradients of |gdot|^n and V^{n+1}

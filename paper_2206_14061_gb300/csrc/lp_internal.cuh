@@ -58,6 +58,7 @@ struct StepConsts {
   int periodic;
   double Lx, Ly;
   float Lhx_h, Lhx_l, Lhy_h, Lhy_l;
+  float ih_h, ih_l, ih2_h, ih2_l;  // 1/h and 1/h^2 as float-float
   long long ghost_PX, ghost_PY;
   double ghost_grid, ghost_hk, ghost_V, ghost_num;
   long long ghost_R2, ghost_clear2;
