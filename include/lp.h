@@ -140,6 +140,8 @@ typedef struct {
                           * radius test (same stencils as a full search); a new
                           * search runs once some particle has moved more than
                           * skin/2 since the last one. 0: full search every step.
+                          * The lists live for one lp_step call; calls of fewer
+                          * than 3 steps search every step (same stencils).
                           * All launch modes; the persistent launch takes the
                           * search branch inside the kernel.                      */
   int32_t free_surface;  /* 1: ghost particles at free boundaries (Sec. 3.1 items

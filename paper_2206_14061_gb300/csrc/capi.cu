@@ -1006,8 +1006,11 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   const StepConsts K = step_consts(eos, q, dt, c->cap);
   LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y));
   const int d = c->cx;
-  // Verlet candidate lists: the grid must hold radius + skin in one cell
-  const double skin = (q->skin > 0.0 && q->rebuild_every == 1) ? q->skin : 0.0;
+  // Verlet candidate lists: the grid must hold radius + skin in one cell. The
+  // lists live for one call, and the wider first search only pays off from
+  // about three steps on; fewer steps search with the radius alone (the
+  // stencils are the same either way).
+  const double skin = (q->skin > 0.0 && q->rebuild_every == 1 && nsteps >= 3) ? q->skin : 0.0;
   LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
   LP_TRY(setup_grids(c, p->ncolumns, q->radius + skin, st, q->period_x, q->period_y));
   LP_TRY(ensure_twin_buffers(c, q));
