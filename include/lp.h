@@ -173,8 +173,9 @@ typedef struct {
                           * image. The floor and ghosts are unchanged (ghost
                           * offsets wrap modulo round(K L) with K the fixed-
                           * point scale). 0: not periodic. lp_build_neighbors
-                          * and lp_fit_derivatives are not periodic.
-                          * lp_step_adjoint: UNIMPLEMENTED.                    */
+                          * and lp_fit_derivatives are not periodic;
+                          * lp_step_adjoint is (offsets shift by whole
+                          * periods, so the derivatives are unchanged).        */
 } lp_params;
 
 /* Stencils produced by lp_build_neighbors: library-owned device memory, valid

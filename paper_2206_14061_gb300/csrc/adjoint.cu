@@ -12,6 +12,9 @@
 // Least-squares adjoint, for c = G^{-1} A^T b with residual r = b - A c:
 //   z = G^{-1} cbar,  bbar = A z,  Abar = r z^T - (A z) c^T,
 // and Abar reaches the positions through the offsets d_k = (p_k - p_i)/h.
+// Along a periodic axis an offset is the nearest image of p_k - p_i, a
+// constant shift of it, and the position update wraps by whole periods: both
+// leave the derivatives as they are.
 // Regimes are frozen at their forward values; d|gdot|/dgdot is 0 where
 // |gdot| = 0. Parameter gradients w.r.t. (mu_s, mu_2, I0) enter through N and
 // R only. Stencils that took the pivoted-QR path in the forward step are
@@ -91,7 +94,8 @@ __global__ void __launch_bounds__(kBlock) k_adj_prepare(const AdjArgs A) {
         const int j = code & ~kMirrorBit;
         if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
         const double zj = (code >> 31) ? f2 - A.z[j] : A.z[j];
-        M.add((A.x[j] - xi) * ih, (A.y[j] - yi) * ih, (zj - zi) * ih);
+        M.add(min_image(A.x[j] - xi, A.K.Lx) * ih, min_image(A.y[j] - yi, A.K.Ly) * ih,
+              (zj - zi) * ih);
       }
       double L[kTri];
       M.gram(L);
@@ -258,7 +262,8 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
     const double zj = mir ? f2 - A.z[j] : A.z[j];
-    const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+    const double dx = min_image(A.x[j] - xi, A.K.Lx) * ih;
+    const double dy = min_image(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
     double a[kNB];
     taylor_row(dx, dy, dz, a);
     double rg = (mir ? 0.0 : Gn[j]) - gni, rV = Vn[j] - Vi, bg = 0.0, bV = 0.0;
@@ -354,7 +359,8 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass1(const AdjArgs A) {
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
     const double zj = mir ? f2 - A.z[j] : A.z[j];
-    const double dx = (A.x[j] - xi) * ih, dy = (A.y[j] - yi) * ih, dz = (zj - zi) * ih;
+    const double dx = min_image(A.x[j] - xi, A.K.Lx) * ih;
+    const double dy = min_image(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
     double a[kNB];
     taylor_row(dx, dy, dz, a);
     double ab[kNB];

@@ -1192,7 +1192,6 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   if (!valid_params(q, eos, dt) || q->precision != LP_FP64) return LP_ERR_INVALID_ARG;
   if (q->free_surface) return LP_ERR_UNIMPLEMENTED;  // adjoint of the ghost rows not built
   if (q->time_scheme != LP_TIME_PAPER) return LP_ERR_UNIMPLEMENTED;
-  if (q->period_x != 0.0 || q->period_y != 0.0) return LP_ERR_UNIMPLEMENTED;
   if (seed->n != initial->n || (initial->n > 0 && (!seed->x || !seed->y || !seed->z || !seed->u ||
                                                    !seed->v || !seed->w || !seed->V)))
     return LP_ERR_INVALID_ARG;
@@ -1223,12 +1222,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   if (cudaMemcpyAsync(c->d_mui, hm.data(), sizeof(ColMui) * initial->ncolumns,
                       cudaMemcpyHostToDevice, st) != cudaSuccess)
     return LP_ERR_CUDA;
-  StepConsts K{};
-  K.phi_c = eos->phi_c; K.phi_min = eos->phi_min; K.phi_max = eos->phi_max;
-  K.alpha = eos->alpha; K.beta = eos->beta;
-  K.h = q->h; K.inv_h = 1.0 / q->h; K.radius = q->radius; K.r2 = q->radius * q->radius;
-  K.gx = q->gx; K.gy = q->gy; K.gz = q->gz; K.floor_z = q->floor_z; K.dt = dt;
-  K.mirror_mode = q->mirror_mode; K.cap = c->cap;
+  const StepConsts K = step_consts(eos, q, dt, c->cap);  // periods included
 
   // workspace of this call: checkpoints, segment states, coefficients, adjoints
   const size_t N = (size_t)n;
@@ -1298,10 +1292,14 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
       cudaMemcpyAsync(c->X[c->cx][f], in[f], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
       cudaMemcpyAsync(tab[f], in[f], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     }
+    if (K.periodic) {  // positions along periodic axes into [0, L), as lp_step
+      launch_wrap_positions(n, c->X[c->cx][0], c->X[c->cx][1], K.Lx, K.Ly, st);
+      launch_wrap_positions(n, tab[0], tab[1], K.Lx, K.Ly, st);
+    }
     launch_iota(n, c->ids[c->ci], st);
     rs = begin_columns(c, initial, nullptr, c->cx, offs, st);
     if (rs != LP_OK) break;
-    rs = setup_grids(c, initial->ncolumns, q->radius, st);
+    rs = setup_grids(c, initial->ncolumns, q->radius, st, q->period_x, q->period_y);
     if (rs != LP_OK) break;
     for (int k = 0; k < nsteps; ++k) {
       if (k > 0 && k % C == 0)
@@ -1325,7 +1323,8 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
       launch_neighbors(false, n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->pf,
                        c->colid[c->ci], c->ids[c->ci], c->d_grids,
                        c->cells + 2 * c->cell_capacity, nullptr, K.radius, K.mirror_mode,
-                       K.floor_z, c->cap, c->nbr, c->cnt, c->dg, st);
+                       K.floor_z, c->cap, c->nbr, c->cnt, c->dg, st, kBlock, nullptr, nullptr,
+                       K.periodic != 0);
       for (int f = 0; f < 7; ++f)
         cudaMemcpyAsync(tab[tseg + f], c->X[c->cx][f], sizeof(double) * N,
                         cudaMemcpyDeviceToDevice, st);

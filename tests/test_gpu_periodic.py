@@ -130,6 +130,23 @@ def test_periodic_stencils_and_parity_50_steps(dev, capi, orc):
     assert max(_state_err(plain, ref, s0, L).values()) > 1e-6
 
 
+@pytest.mark.parametrize("axes", ["x", "y"])
+def test_one_periodic_axis_parity(dev, capi, orc, axes):
+    """Periodic along one axis only; the other axis has free sides (ghosts on)."""
+    s0, pd, L = _layer(n_xy=12)
+    pd = dict(pd, period_x=L if axes == "x" else 0.0, period_y=L if axes == "y" else 0.0)
+    op = _opar(orc, pd, free_surface=1)
+    ref, rd = orc.step(s0, op, 30, brute=False)
+    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+        got, d = _run_gpu(capi, dev, s0, pd, 30, precision=prec, free_surface=1)
+        assert d["n_ghosts"] == rd["n_ghosts"], (axes, prec)
+        e = _state_err(got, ref, s0, L)
+        print(f"periodic {axes} precision {prec}:", {k: f"{v:.2e}" for k, v in e.items()})
+        assert max(e.values()) <= tol, (axes, prec, e)
+        k = "x" if axes == "x" else "y"
+        assert (got[k] >= 0.0).all() and (got[k] < L).all()
+
+
 def test_periodic_ghost_counts_and_parity(dev, capi, orc):
     """With periodic sides only the top of the layer is a free surface."""
     s0, pd, L = _layer()
@@ -230,7 +247,47 @@ def test_periodic_parameter_checks(dev, capi):
     with pytest.raises(capi.LpError) as ei:  # period below 3 (radius + skin)
         capi.lp_step(ctx, st, m, eos, _prm(pd, period_y=3.05 * r, skin=0.2 * r), pd["dt"], 1)
     assert ei.value.status == capi.LP_ERR_INVALID_ARG
-    seed = {k: torch.ones_like(v) for k, v in st.items()}
-    with pytest.raises(capi.LpError) as ei:
-        capi.lp_step_adjoint(ctx, st, m, eos, _prm(pd), pd["dt"], 4, 2, seed)
-    assert ei.value.status == capi.LP_ERR_UNIMPLEMENTED
+
+
+def test_periodic_adjoint_matches_oracle_tangent(dev, capi, orc):
+    """lp_step_adjoint with periodic x and y (sheared layer sliding across the
+    edges, 12 FP64 steps, stencils rebuilt every 4) against the oracle's
+    tangent-linear run, and dL/d(initial state) of particles on the edges
+    against central differences of lp_step."""
+    s0, pd, L = _layer(n_xy=8)
+    s0 = dict(s0, u=0.5 + 20.0 * s0["z"])
+    n = s0["x"].size
+    m, eos = _dicts(pd)
+    prm = _prm(pd)
+    nsteps, C = 12, 4
+    rng = np.random.default_rng(3)
+    w = {k: rng.standard_normal(n) for k in capi.FIELDS}
+    ctx = capi.Context(n, cap=64)
+    init = {k: T(s0[k], dev) for k in capi.FIELDS}
+    seed = {k: T(w[k], dev) for k in capi.FIELDS}
+    dmui, gi = capi.lp_step_adjoint(ctx, init, m, eos, prm, pd["dt"], nsteps, C, seed,
+                                    want_initial=True)
+    got = dmui.cpu().numpy()
+    _, tan = orc.step_tangent(s0, _opar(orc, pd), nsteps, rebuild_every=C)
+    ref = np.array([sum((w[k] * tan[t, f]).sum() for f, k in enumerate(capi.FIELDS))
+                    for t in range(3)])
+    print("periodic adjoint", got, "tangent", ref)
+    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max(), (got, ref)
+
+    def loss(state):
+        st = {k: T(state[k], dev) for k in capi.FIELDS}
+        capi.lp_step(ctx, st, m, eos, dict(prm, rebuild_every=C), pd["dt"], nsteps)
+        ctx.sync()
+        return sum(float((st[k].cpu().numpy() * w[k]).sum()) for k in capi.FIELDS)
+
+    h = pd["h"]
+    edge = np.flatnonzero((s0["x"] < 0.3 * h) | (s0["x"] > L - 0.3 * h))
+    for i in edge[:2]:
+        for k, eps in (("u", 1e-7), ("x", 1e-9), ("y", 1e-9)):
+            sp = {q: v.copy() for q, v in s0.items()}
+            sm = {q: v.copy() for q, v in s0.items()}
+            sp[k][i] += eps
+            sm[k][i] -= eps
+            fd = (loss(sp) - loss(sm)) / (2 * eps)
+            a = float(gi[k][i].item())
+            assert abs(fd - a) <= 1e-5 * abs(a) + 1e-6, (i, k, fd, a)

@@ -129,3 +129,29 @@ def test_periodic_sides_carry_no_ghosts(orc):
     has = np.array([(nbr[i, :cnt[i]].astype(np.int64) & GB).any() for i in range(x.size)])
     assert has[iz == 5].all()
     assert not has[iz < 5].any()
+
+
+def test_tangent_linear_with_periods_matches_central_differences(orc):
+    """The dual-number tangent run (the reference of the GPU adjoint) with
+    periodic x and y, on a sheared layer sliding across the edges."""
+    import math
+    h = 1e-3
+    x, y, z, L = _layer(8, 30, h, 0.05, 5)
+    x, y = np.mod(x + 0.5 * h, L), np.mod(y + 0.3 * h, L)
+    st = _state(x, y, z, u=0.5 + 20.0 * z)
+    th = math.radians(30)
+    kw = dict(gx=9.81 * math.sin(th), gz=-9.81 * math.cos(th))
+    p = _p(orc, L, **kw)
+    nst = reb = 8
+    _, tan = orc.step_tangent(st, p, nst, rebuild_every=reb)
+    for kix, name in enumerate(("mu_s", "mu_2", "I0")):
+        eps = 1e-5
+        sp_, _ = orc.step(st, _p(orc, L, **dict(kw, **{name: getattr(p, name) + eps})), nst,
+                          rebuild_every=reb)
+        sm_, _ = orc.step(st, _p(orc, L, **dict(kw, **{name: getattr(p, name) - eps})), nst,
+                          rebuild_every=reb)
+        for f, key in enumerate(("u", "v", "w", "V")):
+            fd = (sp_[key] - sm_[key]) / (2 * eps)
+            t = tan[kix, 3 + f]
+            assert np.abs(t).max() > 0
+            assert np.abs(fd - t).max() <= 1e-5 * np.abs(t).max(), (name, key)
