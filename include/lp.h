@@ -154,7 +154,8 @@ typedef struct {
                           * phi_min (1 - 1e-3) and the |gdot| that keeps the
                           * inertial pressure continuous. Stencil entries plus
                           * ghosts must fit in cap (else LP_ERR_STENCIL_OVERFLOW).
-                          * lp_step_adjoint: LP_ERR_UNIMPLEMENTED.              */
+                          * lp_step_adjoint covers them (flags frozen like the
+                          * stencils, ghost regime frozen).                     */
   int32_t time_scheme;   /* LP_TIME_PAPER: the paper's step (Sec. 3.1 items 8,
                           * 10: V first, momentum with V^{n+1}, x with the mean
                           * velocity; first order). LP_TIME_HEUN: Heun's method

@@ -12,6 +12,12 @@
 // Least-squares adjoint, for c = G^{-1} A^T b with residual r = b - A c:
 //   z = G^{-1} cbar,  bbar = A z,  Abar = r z^T - (A z) c^T,
 // and Abar reaches the positions through the offsets d_k = (p_k - p_i)/h.
+// Free-surface ghosts: a flagged entry k also stands for the row a_G =
+// T(-d_k) of its point reflection. Its pass-1 right-hand sides are 0 (the
+// ghost carries the particle's velocity); its pass-2 ones depend only on the
+// particle's own |gdot| and V^{n+1} (the ghost state, regime frozen), so their
+// adjoints return to the particle; its offset adjoint enters d_k with a minus
+// sign. The flags are frozen like the stencils.
 // Along a periodic axis an offset is the nearest image of p_k - p_i, a
 // constant shift of it, and the position update wraps by whole periods: both
 // leave the derivatives as they are.
@@ -91,11 +97,13 @@ __global__ void __launch_bounds__(kBlock) k_adj_prepare(const AdjArgs A) {
       M.zero();
       for (int k = 0; k < m; ++k) {
         const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-        const int j = code & ~kMirrorBit;
+        const int j = code & kIndexMask;
         if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
         const double zj = (code >> 31) ? f2 - A.z[j] : A.z[j];
-        M.add(min_image(A.x[j] - xi, A.K.Lx) * ih, min_image(A.y[j] - yi, A.K.Ly) * ih,
-              (zj - zi) * ih);
+        const double dx = min_image(A.x[j] - xi, A.K.Lx) * ih;
+        const double dy = min_image(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
+        M.add(dx, dy, dz);
+        if (code & kGhostBit) M.add(-dx, -dy, -dz);  // the ghost's row
       }
       double L[kTri];
       M.gram(L);
@@ -256,9 +264,24 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
   const double gni = Gn[s], Vi = Vn[s];
   const int m = min(A.cnt[s], A.cap);
   double sg = 0.0, sV = 0.0, sp[3] = {0.0, 0.0, 0.0};
+  // ghost rows (free surface): right-hand sides bg_G = |gdot|_G - gni and
+  // bv_G = V_G - Vi with |gdot|_G = gni k / (phi_c - phi) in the inertial
+  // regime; their derivatives with respect to gni and Vi (phi = 1/Vi)
+  double bgG = 0.0, bvG = 0.0, dbg_dg = 0.0, dbg_dV = 0.0;
+  if (A.K.free_surface) {
+    const double phi = 1.0 / Vi;
+    bvG = A.K.ghost_V - Vi;
+    if (phi > A.K.phi_min && phi <= A.K.phi_max) {
+      const double w = A.K.phi_c - phi;
+      bgG = gni * (A.K.ghost_num / w) - gni;
+      dbg_dg = A.K.ghost_num / w - 1.0;
+      dbg_dV = -gni * A.K.ghost_num / (w * w * Vi * Vi);
+    }
+  }
+  double og = 0.0, oV = 0.0;  // adjoints of the particle's own gni, Vi from ghost rows
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-    const int j = code & ~kMirrorBit;
+    const int j = code & kIndexMask;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
     const double zj = mir ? f2 - A.z[j] : A.z[j];
@@ -280,13 +303,29 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
     double ab[kNB], db[3];
     for (int q = 0; q < kNB; ++q) ab[q] = rg * zg[q] - bg * cg[q] + rV * zV[q] - bV * cV[q];
     row_adjoint(dx, dy, dz, ab, db);
+    if (code & kGhostBit) {  // the ghost's row T(-d)
+      taylor_row(-dx, -dy, -dz, a);
+      double rgG = bgG, rVG = bvG, bgb = 0.0, bVb = 0.0;
+      for (int q = 0; q < kNB; ++q) {
+        rgG -= a[q] * cg[q];
+        rVG -= a[q] * cV[q];
+        bgb += a[q] * zg[q];
+        bVb += a[q] * zV[q];
+      }
+      og += bgb * dbg_dg;
+      oV += bgb * dbg_dV - bVb;
+      for (int q = 0; q < kNB; ++q) ab[q] = rgG * zg[q] - bgb * cg[q] + rVG * zV[q] - bVb * cV[q];
+      double dbG[3];
+      row_adjoint(-dx, -dy, -dz, ab, dbG);
+      for (int c = 0; c < 3; ++c) db[c] -= dbG[c];
+    }
     atomicAdd(&A.l0[0][j], db[0] * ih);
     atomicAdd(&A.l0[1][j], db[1] * ih);
     atomicAdd(&A.l0[2][j], (mir ? -db[2] : db[2]) * ih);
     for (int c = 0; c < 3; ++c) sp[c] += db[c] * ih;
   }
-  atomicAdd(&A.lGn[s], -sg);
-  atomicAdd(&A.lVn[s], -sV);
+  atomicAdd(&A.lGn[s], og - sg);
+  atomicAdd(&A.lVn[s], oV - sV);
   for (int c = 0; c < 3; ++c) atomicAdd(&A.l0[c][s], -sp[c]);
 }
 
@@ -355,7 +394,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass1(const AdjArgs A) {
   double su[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
-    const int j = code & ~kMirrorBit;
+    const int j = code & kIndexMask;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
     const double zj = mir ? f2 - A.z[j] : A.z[j];
@@ -378,6 +417,21 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass1(const AdjArgs A) {
     }
     double db[3];
     row_adjoint(dx, dy, dz, ab, db);
+    if (code & kGhostBit) {  // the ghost's row T(-d), right-hand sides 0
+      taylor_row(-dx, -dy, -dz, a);
+      for (int q = 0; q < kNB; ++q) ab[q] = 0.0;
+      for (int f = 0; f < 3; ++f) {
+        double r = 0.0, b = 0.0;
+        for (int q = 0; q < kNB; ++q) {
+          r -= a[q] * c[f][q];
+          b += a[q] * lc[f][q];
+        }
+        for (int q = 0; q < kNB; ++q) ab[q] += r * lc[f][q] - b * c[f][q];
+      }
+      double dbG[3];
+      row_adjoint(-dx, -dy, -dz, ab, dbG);
+      for (int q = 0; q < 3; ++q) db[q] -= dbG[q];
+    }
     atomicAdd(&A.l0[0][j], db[0] * ih);
     atomicAdd(&A.l0[1][j], db[1] * ih);
     atomicAdd(&A.l0[2][j], (mir ? -db[2] : db[2]) * ih);

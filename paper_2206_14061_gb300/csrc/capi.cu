@@ -1190,7 +1190,6 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, initial, offs, true));
   if (!valid_params(q, eos, dt) || q->precision != LP_FP64) return LP_ERR_INVALID_ARG;
-  if (q->free_surface) return LP_ERR_UNIMPLEMENTED;  // adjoint of the ghost rows not built
   if (q->time_scheme != LP_TIME_PAPER) return LP_ERR_UNIMPLEMENTED;
   if (seed->n != initial->n || (initial->n > 0 && (!seed->x || !seed->y || !seed->z || !seed->u ||
                                                    !seed->v || !seed->w || !seed->V)))
@@ -1325,6 +1324,9 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
                        c->cells + 2 * c->cell_capacity, nullptr, K.radius, K.mirror_mode,
                        K.floor_z, c->cap, c->nbr, c->cnt, c->dg, st, kBlock, nullptr, nullptr,
                        K.periodic != 0);
+      if (K.free_surface)  // the same ghost flags as the forward run
+        launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
+                      c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, kBlock);
       for (int f = 0; f < 7; ++f)
         cudaMemcpyAsync(tab[tseg + f], c->X[c->cx][f], sizeof(double) * N,
                         cudaMemcpyDeviceToDevice, st);

@@ -167,13 +167,48 @@ def test_ghosts_extend_the_stable_horizon(dev, capi):
     assert d["n_nonfinite"] == 0 and sp.max() < 0.1, sp.max()
 
 
-def test_adjoint_with_ghosts_is_unimplemented(dev, capi):
-    wl = W.cube(6)
+def test_adjoint_with_ghosts_matches_oracle_tangent(dev, capi, orc):
+    """lp_step_adjoint with ghosts (sheared 8^3 cube, 12 FP64 steps, stencils
+    and ghost flags rebuilt every 4) against the oracle's tangent-linear run,
+    and dL/d(initial state) of surface particles that carry ghosts against
+    central differences of lp_step."""
+    wl = W.cube(8)
+    s0 = dict(wl.state)
+    s0["u"] = 20.0 * s0["z"]
     pd = W.param_dict(wl)
     m, eos = _dicts(pd)
+    prm = _prm(pd)
+    nsteps, C = 12, 4
+    rng = np.random.default_rng(3)
+    w = {k: rng.standard_normal(wl.n) for k in capi.FIELDS}
     ctx = capi.Context(wl.n, cap=64)
-    st = {k: T(wl.state[k], dev) for k in capi.FIELDS}
-    seed = {k: torch.ones_like(v) for k, v in st.items()}
-    with pytest.raises(capi.LpError) as ei:
-        capi.lp_step_adjoint(ctx, st, m, eos, _prm(pd), pd["dt"], 4, 2, seed)
-    assert ei.value.status == capi.LP_ERR_UNIMPLEMENTED
+    init = {k: T(s0[k], dev) for k in capi.FIELDS}
+    seed = {k: T(w[k], dev) for k in capi.FIELDS}
+    dmui, gi = capi.lp_step_adjoint(ctx, init, m, eos, prm, pd["dt"], nsteps, C, seed,
+                                    want_initial=True)
+    got = dmui.cpu().numpy()
+    _, tan = orc.step_tangent(s0, _orc_params(orc, pd), nsteps, rebuild_every=C)
+    ref = np.array([sum((w[k] * tan[t, f]).sum() for f, k in enumerate(capi.FIELDS))
+                    for t in range(3)])
+    print("ghost adjoint", got, "tangent", ref)
+    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max(), (got, ref)
+
+    def loss(state):
+        st = {k: T(state[k], dev) for k in capi.FIELDS}
+        capi.lp_step(ctx, st, m, eos, dict(prm, rebuild_every=C), pd["dt"], nsteps)
+        ctx.sync()
+        return sum(float((st[k].cpu().numpy() * w[k]).sum()) for k in capi.FIELDS)
+
+    nbr, cnt, _ = orc.step_stencils(s0["x"], s0["y"], s0["z"], _orc_params(orc, pd), brute=True)
+    flagged = [i for i in range(wl.n) if (nbr[i, :cnt[i]].astype(np.int64) & GB).any()]
+    assert len(flagged) > 0
+    for i in flagged[:2]:
+        # (V terms dominate the loss: a step of 1e-9 would be round-off)
+        for k, eps in (("u", 1e-7), ("z", 1e-9), ("V", 1e-7)):
+            sp = {q: v.copy() for q, v in s0.items()}
+            sm = {q: v.copy() for q, v in s0.items()}
+            sp[k][i] += eps
+            sm[k][i] -= eps
+            fd = (loss(sp) - loss(sm)) / (2 * eps)
+            a = float(gi[k][i].item())
+            assert abs(fd - a) <= 1e-5 * abs(a) + 1e-6, (i, k, fd, a)
