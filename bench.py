@@ -517,8 +517,9 @@ def e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world):
         with torch.cuda.stream(stream):
             for k in capi.FIELDS:
                 dst[k].copy_(host[k], non_blocking=True)
-            capi.lp_step(ctx, dst, mui, eos, params(args.precision, graph=0), pd["dt"], 1,
-                         stream=stream)
+            # one call per step; the Verlet lists stay on the context between calls
+            capi.lp_step(ctx, dst, mui, eos, dict(params(args.precision, graph=0), keep_lists=1),
+                         pd["dt"], 1, stream=stream)
             for k in capi.FIELDS:
                 host[k].copy_(dst[k], non_blocking=True)
         stream.synchronize()

@@ -177,6 +177,20 @@ typedef struct {
                           * and lp_fit_derivatives are not periodic;
                           * lp_step_adjoint is (offsets shift by whole
                           * periods, so the derivatives are unchanged).        */
+  int32_t keep_lists;    /* 1 (with skin > 0, rebuild_every == 1): the Verlet
+                          * candidate lists, their reference positions and the
+                          * sorted order of this call are kept on the context
+                          * for the next lp_step call, which then searches only
+                          * if some particle moved more than skin/2 since the
+                          * last search (checked on the device; stencils are
+                          * those of a full search either way). They are kept
+                          * while the particle count, the column offsets,
+                          * radius, skin, floor, mirror mode and periods stay
+                          * the same and no other entry point uses the
+                          * context. Results then depend on the earlier calls
+                          * only through the summation order of the stencils.
+                          * 0: lists live for one call.                        */
+  int32_t pad;
 } lp_params;
 
 /* Stencils produced by lp_build_neighbors: library-owned device memory, valid

@@ -65,7 +65,7 @@ class LpParams(ctypes.Structure):
         (k, ctypes.c_int32) for k in ("mirror_mode", "precision", "rebuild_every", "launch_mode")] + [
         ("skin", ctypes.c_double), ("free_surface", ctypes.c_int32),
         ("time_scheme", ctypes.c_int32), ("period_x", ctypes.c_double),
-        ("period_y", ctypes.c_double)]
+        ("period_y", ctypes.c_double), ("keep_lists", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class LpNeighbors(ctypes.Structure):
@@ -216,7 +216,8 @@ def params_struct(q) -> LpParams:
                     int(q.get("precision", LP_FP64)), int(q.get("rebuild_every", 1)),
                     int(q.get("launch_mode", LP_LAUNCH_KERNELS)), float(q.get("skin", 0.0)),
                     int(q.get("free_surface", 0)), int(q.get("time_scheme", 0)),
-                    float(q.get("period_x", 0.0)), float(q.get("period_y", 0.0)))
+                    float(q.get("period_x", 0.0)), float(q.get("period_y", 0.0)),
+                    int(q.get("keep_lists", 0)), 0)
 
 
 class Context:

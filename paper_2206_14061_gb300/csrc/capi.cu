@@ -49,6 +49,9 @@ void launch_copy_state(int n, double* const* dst, double* const* src, cudaStream
 void launch_heun_combine(int n, double* const* y, double* const* y0, double Lx, double Ly,
                          cudaStream_t st);
 void launch_wrap_positions(int n, double* x, double* y, double Lx, double Ly, cudaStream_t st);
+void launch_need_search(int n, const double* x, const double* y, const double* z,
+                        const double* xref, double half_skin2, double Lx, double Ly, int* flag,
+                        cudaStream_t st);
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st);
 // fit.cu
@@ -111,6 +114,14 @@ struct lp_ctx {
   DevDiag* dg = nullptr;
   DevDiag* h_dg = nullptr;
   double** d_tab = nullptr;  // [2 dir][2 kind][2 src/dst][8]
+  // Verlet lists kept across lp_step calls (lp_params.keep_lists): the
+  // candidate lists, their reference positions and the sorted order of the
+  // last call stay valid for the same particle count, columns and search
+  // parameters until another entry point uses the context
+  bool lists_valid = false;
+  int64_t lists_n = 0;
+  std::vector<int32_t> lists_offs;
+  double lists_sig[6] = {};
   double** d_ptr = nullptr;  // caller pointers for the final scatter
   double** h_ptr = nullptr;  // pinned staging of d_ptr
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
@@ -261,14 +272,35 @@ lp_status setup_grids(lp_ctx* c, int ncol, double rmax, cudaStream_t st, double 
   return LP_OK;
 }
 
+// True if every column's bounding box (h_bbox) lies inside its current grid
+// with at least one cell to spare on each non-periodic side.
+bool grids_cover(const lp_ctx* c, int ncol) {
+  if ((int)c->h_grids.size() < ncol) return false;
+  for (int k = 0; k < ncol; ++k) {
+    const GridCol& g = c->h_grids[k];
+    const double* b = c->h_bbox + 7 * k;
+    const double org[3] = {g.ox, g.oy, g.oz}, ic[3] = {g.icx, g.icy, g.icz};
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    const double per[3] = {g.Lx, g.Ly, 0.0};
+    for (int a = 0; a < 3; ++a) {
+      if (per[a] > 0.0) continue;
+      if (!(b[a] <= b[3 + a])) continue;  // empty column
+      const double lo = (b[a] - org[a]) * ic[a], hi = (b[3 + a] - org[a]) * ic[a];
+      if (!(lo >= 1.0 && hi <= dims[a] - 1.0)) return false;
+    }
+  }
+  return true;
+}
+
 // Upload offsets and column ids; compute the bounding boxes (synchronises).
+// (fill_colid false: the slots keep the column ids of the previous call)
 lp_status begin_columns(lp_ctx* c, const lp_particles* p, const double* radius_dev, int buf,
-                        std::vector<int32_t>& offs, cudaStream_t st) {
+                        std::vector<int32_t>& offs, cudaStream_t st, bool fill_colid = true) {
   const int ncol = p->ncolumns;
   if (cudaMemcpyAsync(c->d_offs, offs.data(), sizeof(int32_t) * (ncol + 1), cudaMemcpyHostToDevice,
                       st) != cudaSuccess)
     return LP_ERR_CUDA;
-  launch_fill_colid((int)p->n, c->d_offs, ncol, c->colid[c->ci], st);
+  if (fill_colid) launch_fill_colid((int)p->n, c->d_offs, ncol, c->colid[c->ci], st);
   launch_bbox((int)p->n, ncol, c->X[buf][0], c->X[buf][1], c->X[buf][2], radius_dev,
               c->colid[c->ci], (unsigned long long*)c->d_bbox, st);
   if (cudaMemcpyAsync(c->h_bbox, c->d_bbox, sizeof(double) * 7 * ncol, cudaMemcpyDeviceToHost,
@@ -806,6 +838,7 @@ lp_status lp_build_neighbors(lp_ctx* c, const lp_particles* p, const double* rad
                              double r_const, int32_t mirror_mode, double floor_z, int32_t cap,
                              int32_t keep_nearest, lp_neighbors* out, void* stream) {
   if (!c || !out) return LP_ERR_INVALID_ARG;
+  c->lists_valid = false;  // uses the buffers the kept Verlet lists live in
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, p, offs, false));
   if (cap < 1 || cap > c->cap || mirror_mode < 0 || mirror_mode > 2 || !std::isfinite(floor_z))
@@ -885,6 +918,7 @@ lp_status lp_fit_derivatives(lp_ctx* c, const lp_particles* p, const lp_neighbor
                              double h, double floor_z, double* coeffs, int32_t precision,
                              void* stream) {
   if (!c || !nb || !fields || !mirror_sign || !coeffs) return LP_ERR_INVALID_ARG;
+  c->lists_valid = false;  // uses the buffers the kept Verlet lists live in
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, p, offs, false));
   if (nf < 1 || nf > kMaxFields || !finite_pos(h) || !std::isfinite(floor_z) ||
@@ -965,9 +999,10 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
 }
 
 // caller state -> internal buffer in caller order; per-column mu(I) upload
-// (periods Lx, Ly > 0: positions along those axes mapped into [0, L))
+// (periods Lx, Ly > 0: positions along those axes mapped into [0, L);
+// gather: into the sorted order of the previous call, kept in ids)
 lp_status load_state(lp_ctx* c, const lp_particles* p, const lp_mui* mui, cudaStream_t st,
-                     double Lx = 0.0, double Ly = 0.0) {
+                     double Lx = 0.0, double Ly = 0.0, bool gather = false) {
   const int n = (int)p->n;
   std::vector<ColMui> hm(p->ncolumns);
   for (int k = 0; k < p->ncolumns; ++k)
@@ -977,10 +1012,19 @@ lp_status load_state(lp_ctx* c, const lp_particles* p, const lp_mui* mui, cudaSt
     return LP_ERR_CUDA;
   const int d = c->cx;
   double* const src[7] = {p->x, p->y, p->z, p->u, p->v, p->w, p->V};
-  for (int f = 0; f < 7; ++f)
-    cudaMemcpyAsync(c->X[d][f], src[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (gather) {
+    std::memcpy(c->h_ptr, src, sizeof(src));
+    if (cudaMemcpyAsync(c->d_ptr, c->h_ptr, sizeof(src), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return LP_ERR_CUDA;
+    launch_gather_fields(n, c->ids[c->ci], (const double* const*)c->d_ptr,
+                         c->d_tab + ((d * 2 + 0) * 2 + 0) * kTabFields, 7, st);
+  } else {
+    for (int f = 0; f < 7; ++f)
+      cudaMemcpyAsync(c->X[d][f], src[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    launch_iota(n, c->ids[c->ci], st);
+  }
   if (Lx > 0.0 || Ly > 0.0) launch_wrap_positions(n, c->X[d][0], c->X[d][1], Lx, Ly, st);
-  launch_iota(n, c->ids[c->ci], st);
   // mu(I) parameters are read back from pageable memory only once the copy ran
   return cudaStreamSynchronize(st) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
 }
@@ -1004,20 +1048,40 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   const int n = (int)p->n;
   if (n == 0 || nsteps == 0) return LP_OK;
   const StepConsts K = step_consts(eos, q, dt, c->cap);
-  LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y));
-  const int d = c->cx;
   // Verlet candidate lists: the grid must hold radius + skin in one cell. The
-  // lists live for one call, and the wider first search only pays off from
-  // about three steps on; fewer steps search with the radius alone (the
-  // stencils are the same either way).
-  const double skin = (q->skin > 0.0 && q->rebuild_every == 1 && nsteps >= 3) ? q->skin : 0.0;
-  LP_TRY(begin_columns(c, p, nullptr, d, offs, st));
-  LP_TRY(setup_grids(c, p->ncolumns, q->radius + skin, st, q->period_x, q->period_y));
+  // lists live for one call unless keep_lists asks to keep them for the next
+  // one; without that, the wider first search only pays off from about three
+  // steps on and fewer steps search with the radius alone (the stencils are
+  // the same either way).
+  const bool keep = q->keep_lists != 0 && q->skin > 0.0 && q->rebuild_every == 1;
+  const double skin =
+      (q->skin > 0.0 && q->rebuild_every == 1 && (nsteps >= 3 || keep)) ? q->skin : 0.0;
+  const double sig[6] = {q->radius, q->skin, q->floor_z, (double)q->mirror_mode, q->period_x,
+                         q->period_y};
+  const bool reuse = keep && c->lists_valid && c->lists_n == n && c->lists_offs == offs &&
+                     std::memcmp(sig, c->lists_sig, sizeof(sig)) == 0;
+  c->lists_valid = false;  // until this call has completed
+  LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y, reuse));
+  const int d = c->cx;
+  LP_TRY(begin_columns(c, p, nullptr, d, offs, st, !reuse));
+  // kept lists keep their grid while the particles fit in it (the split
+  // positions of the float-float fits are taken relative to its origin)
+  if (!reuse || !grids_cover(c, p->ncolumns))
+    LP_TRY(setup_grids(c, p->ncolumns, q->radius + skin, st, q->period_x, q->period_y));
   LP_TRY(ensure_twin_buffers(c, q));
   if (skin > 0.0) {
-    const int one = 1;
-    if (cudaMemcpyAsync(c->d_search, &one, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    // a search on the first step, or (kept lists) only if some particle moved
+    // more than skin/2 since the last one
+    const int first = reuse ? 0 : 1;
+    if (cudaMemcpyAsync(c->d_search, &first, sizeof(int), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
       return LP_ERR_CUDA;
+    if (reuse) {
+      const double hs = 0.5 * skin;
+      launch_need_search(n, c->X[d][0], c->X[d][1], c->X[d][2], c->xref,
+                         hs * hs * (1.0 - 0x1p-20), q->period_x, q->period_y, c->d_search, st);
+      c->launches += 2;  // gather, displacement test
+    }
   }
   c->skin = skin;
   const lp_status rs = run_steps(c, n, K, q->precision, q->rebuild_every, q->launch_mode, nsteps,
@@ -1034,6 +1098,12 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
       return LP_ERR_CUDA;
     flags = c->h_dg->flags;
     if (flags & LP_FLAG_TIMEOUT) return LP_OK;
+  }
+  if (keep && skin > 0.0) {  // lists, reference positions and order stay for the next call
+    c->lists_valid = true;
+    c->lists_n = n;
+    c->lists_offs = offs;
+    std::memcpy(c->lists_sig, sig, sizeof(sig));
   }
   // internal state -> caller arrays (original order)
   {
@@ -1064,6 +1134,7 @@ lp_status lp_autotune(lp_ctx* c, const lp_particles* p, const lp_mui* mui, const
                       const char* table_path, lp_tuning* out, void* stream) {
   if (!c || !mui || !out || steps_per_trial < 1 || steps_per_trial > 1000)
     return LP_ERR_INVALID_ARG;
+  c->lists_valid = false;  // uses the buffers the kept Verlet lists live in
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, p, offs, true));
   if (!valid_params(q, eos, dt) || p->n < 1) return LP_ERR_INVALID_ARG;
@@ -1187,6 +1258,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
                           lp_particles* dL_dinitial, void* stream) {
   if (!c || !mui || !seed || !dL_dmui || nsteps < 0 || checkpoint_every < 1)
     return LP_ERR_INVALID_ARG;
+  c->lists_valid = false;  // uses the buffers the kept Verlet lists live in
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, initial, offs, true));
   if (!valid_params(q, eos, dt) || q->precision != LP_FP64) return LP_ERR_INVALID_ARG;
