@@ -130,7 +130,7 @@ struct lp_ctx {
   int32_t* gcnt = nullptr;    // ghost entries per stencil
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
   double* Y0[7] = {};                  // Heun: state at the start of the step (on first use)
-  float* Lff = nullptr;      // float-float Cholesky factors (LP_MIXED_FF)
+  float2* Lff = nullptr;     // float-float Cholesky factors (LP_MIXED_FF), (hi, lo) pairs
   // Verlet candidate lists (lp_params.skin)
   int32_t* cand = nullptr;   // capc x n, k-major
   int32_t* ccnt = nullptr;
@@ -694,7 +694,7 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->Uh, n);
   if (s == LP_OK) s = dalloc(c, &c->Ul, n);
   if (s == LP_OK) s = dalloc(c, &c->GVff, n);
-  if (s == LP_OK) s = dalloc(c, &c->Lff, n * 2 * kTri);
+  if (s == LP_OK) s = dalloc(c, &c->Lff, n * kTri);
   if (s == LP_OK) s = dalloc(c, &c->Xfix, n);
   if (s == LP_OK) s = dalloc(c, &c->gcnt, n);
   c->capc = std::min(c->cap + 32, 96);

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_pass2(const StepArgs A) {
 }
 
 template <bool PER>
-__global__ void __launch_bounds__(kFFBlock, 5) k_pass2_ff(const StepArgs A) {
+__global__ void __launch_bounds__(kFFBlock, 4) k_pass2_ff(const StepArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   pass2_body<LP_MIXED_FF, PER>(A, s, s < A.n);
 }

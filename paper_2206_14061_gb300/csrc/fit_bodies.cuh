@@ -496,17 +496,20 @@ __device__ __forceinline__ bool ff_chol9(ff* a, float rel_tol) {
 template <int NF>
 __device__ __forceinline__ void ff_chol_solve(const StepArgs& A, int s, ff (*r)[kNB]) {
   const int64_t n = A.n;
-  const float* Lh = A.Lff + s;
-  const float* Ll = A.Lff + (int64_t)kTri * n + s;
+  const float2* L = A.Lff + s;  // one 8-byte load per entry
+  auto at = [&](int k) {
+    const float2 v = L[k * n];
+    return ff{v.x, v.y};
+  };
 #pragma unroll
   for (int i = 0; i < kNB; ++i) {
 #pragma unroll
     for (int k = 0; k < i; ++k) {
-      const ff l = {Lh[tri(i, k) * n], Ll[tri(i, k) * n]};
+      const ff l = at(tri(i, k));
 #pragma unroll
       for (int f = 0; f < NF; ++f) ff_acc(r[f][i], l, ff_neg(r[f][k]));
     }
-    const ff inv = {Lh[tri(i, i) * n], Ll[tri(i, i) * n]};
+    const ff inv = at(tri(i, i));
 #pragma unroll
     for (int f = 0; f < NF; ++f) r[f][i] = ff_mul(ff_norm(r[f][i]), inv);
   }
@@ -514,11 +517,11 @@ __device__ __forceinline__ void ff_chol_solve(const StepArgs& A, int s, ff (*r)[
   for (int i = kNB - 1; i >= 0; --i) {
 #pragma unroll
     for (int k = i + 1; k < kNB; ++k) {
-      const ff l = {Lh[tri(k, i) * n], Ll[tri(k, i) * n]};
+      const ff l = at(tri(k, i));
 #pragma unroll
       for (int f = 0; f < NF; ++f) ff_acc(r[f][i], l, ff_neg(r[f][k]));
     }
-    const ff inv = {Lh[tri(i, i) * n], Ll[tri(i, i) * n]};
+    const ff inv = at(tri(i, i));
 #pragma unroll
     for (int f = 0; f < NF; ++f) r[f][i] = ff_mul(ff_norm(r[f][i]), inv);
   }
@@ -650,8 +653,7 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
   A.fbslot[s] = -1;
 #pragma unroll
   for (int k = 0; k < kTri; ++k) {
-    A.Lff[(int64_t)k * n + s] = G[k].h;
-    A.Lff[(int64_t)(kTri + k) * n + s] = G[k].l;
+    A.Lff[(int64_t)k * n + s] = make_float2(G[k].h, G[k].l);
   }
 }
 

@@ -207,8 +207,8 @@ struct StepArgs {
   int32_t* gcnt;    // free surface: entries with a ghost, at the end of each stencil
   float *Tg, *T2;   // free surface: sums over those entries and their ghosts
                     // (Gram moments 62 x n, pass-2 right-hand sides 36 x n)
-  float* Lff;       // 90 * n: float-float Cholesky factor of the Gram matrix,
-                    // hi (45) then lo (45), k-major; the diagonal holds 1/L_jj
+  float2* Lff;      // 45 * n: float-float Cholesky factor of the Gram matrix,
+                    // (hi, lo) pairs, k-major; the diagonal holds 1/L_jj
   // Verlet candidate lists: positions at the last search and the flag that
   // requests a new search when a particle has moved more than skin/2
   const double* xref;  // 3 * n, or NULL when candidate lists are off
