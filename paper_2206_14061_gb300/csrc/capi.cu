@@ -125,7 +125,7 @@ struct lp_ctx {
   double** d_ptr = nullptr;  // caller pointers for the final scatter
   double** h_ptr = nullptr;  // pinned staging of d_ptr
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
-  float4 *Xh = nullptr, *Xl = nullptr, *Uh = nullptr, *Ul = nullptr, *GVff = nullptr;
+  FF8* XU = nullptr;  // split positions and velocities (LP_MIXED_FF)
   int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
   int32_t* gcnt = nullptr;    // ghost entries per stencil
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
@@ -393,7 +393,7 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.p1 = c->p1; A.fbgrad = c->fbgrad; A.dg = c->dg;
   A.K = K;
   A.grids = c->d_grids;
-  A.Xh = c->Xh; A.Xl = c->Xl; A.Uh = c->Uh; A.Ul = c->Ul; A.GVff = c->GVff; A.Lff = c->Lff;
+  A.XU = c->XU; A.Lff = c->Lff;
   A.Xfix = c->Xfix;
   A.gcnt = c->gcnt;
   A.Tg = c->Tg; A.T2 = c->T2;
@@ -689,11 +689,7 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->d_tab, 2 * 2 * 2 * kTabFields);
   if (s == LP_OK) s = dalloc(c, &c->d_ptr, kTabFields);
   if (s == LP_OK) s = dalloc(c, &c->bar, 2);
-  if (s == LP_OK) s = dalloc(c, &c->Xh, n);
-  if (s == LP_OK) s = dalloc(c, &c->Xl, n);
-  if (s == LP_OK) s = dalloc(c, &c->Uh, n);
-  if (s == LP_OK) s = dalloc(c, &c->Ul, n);
-  if (s == LP_OK) s = dalloc(c, &c->GVff, n);
+  if (s == LP_OK) s = dalloc(c, &c->XU, n);
   if (s == LP_OK) s = dalloc(c, &c->Lff, n * kTri);
   if (s == LP_OK) s = dalloc(c, &c->Xfix, n);
   if (s == LP_OK) s = dalloc(c, &c->gcnt, n);

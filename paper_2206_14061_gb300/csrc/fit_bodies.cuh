@@ -330,18 +330,20 @@ __device__ __forceinline__ void split_state_body(const StepArgs& A, int s) {
   const ff fx = ff_of((A.x[s] - g.ox) * ih), fy = ff_of((A.y[s] - g.oy) * ih);
   const ff fz = ff_of((A.z[s] - g.oz) * ih);
   const ff fm = ff_of((2.0 * A.K.floor_z - A.z[s] - g.oz) * ih);
-  A.Xh[s] = make_float4(fx.h, fy.h, fz.h, fm.h);
-  A.Xl[s] = make_float4(fx.l, fy.l, fz.l, fm.l);
+  FF8 r;
+  r.xh = make_float4(fx.h, fy.h, fz.h, fm.h);
+  r.xl = make_float4(fx.l, fy.l, fz.l, fm.l);
   const ff fu = ff_of(A.u[s]), fv = ff_of(A.v[s]), fw = ff_of(A.w[s]);
-  A.Uh[s] = make_float4(fu.h, fv.h, fw.h, 0.f);
-  A.Ul[s] = make_float4(fu.l, fv.l, fw.l, 0.f);
+  r.uh = make_float4(fu.h, fv.h, fw.h, 0.f);
+  r.ul = make_float4(fu.l, fv.l, fw.l, 0.f);
+  A.XU[s] = r;
 }
 
 // split |gdot|^n and V^{n+1} (pass-1 outputs, FP64) for pass 2
 __device__ __forceinline__ void split_p1_body(const StepArgs& A, int s) {
   const ff g = ff_of(A.p1[P1_GN * A.n + s]);
   const ff v = ff_of(A.K.euler ? A.V[s] : A.p1[P1_VN * A.n + s]);  // V of the pass-2 fit
-  A.GVff[s] = make_float4(g.h, g.l, v.h, v.l);
+  A.XU[s].uh = make_float4(g.h, g.l, v.h, v.l);  // the velocity half is no longer read
 }
 
 // float-float offset between two split coordinates
@@ -359,8 +361,8 @@ __device__ __forceinline__ void ff_gather(const StepArgs& A, int s, uint32_t cod
                                           float4& jl) {
   int j = code & kIndexMask;
   if ((unsigned)j >= (unsigned)A.n) j = s;  // never read outside the arrays (zero row)
-  jh = A.Xh[j];
-  jl = A.Xl[j];
+  jh = A.XU[j].xh;
+  jl = A.XU[j].xl;
 }
 // offset along an axis of period Lh (units of h, float-float; Lh = 0: not
 // periodic), taken as its nearest image
@@ -540,7 +542,7 @@ __device__ __forceinline__ void gram_twins_body(const StepArgs& A, int s) {
   const int m = min(A.cnt[s], A.cap);
   const int mr = m - ghost_count(A, s, m);
   if (mr == m) return;
-  const float4 hi = A.Xh[s], lo = A.Xl[s];
+  const float4 hi = A.XU[s].xh, lo = A.XU[s].xl;
   ff t[31];
 #pragma unroll
   for (int q = 0; q < 31; ++q) t[q] = {0.f, 0.f};
@@ -558,15 +560,15 @@ __device__ __forceinline__ void gram_twins_body(const StepArgs& A, int s) {
 // Pass-2 right-hand-side terms of the entries with a ghost and their ghosts
 // (reflected row, right-hand sides fixed by the particle): b_j a + b_G a~,
 // a~ the row with its linear terms negated. T2: 2 x 9 float-float, hi then
-// lo, k-major. Needs the pass-1 outputs and their split copy (GVff).
+// lo, k-major. Needs the pass-1 outputs and their split copy (XU[].uh).
 template <bool PER>
 __device__ __forceinline__ void pass2_twins_body(const StepArgs& A, int s) {
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);
   const int mr = m - ghost_count(A, s, m);
   if (mr == m || A.fbslot[s] != -1) return;
-  const float4 hi = A.Xh[s], lo = A.Xl[s];
-  const float4 gvi = A.GVff[s];
+  const float4 hi = A.XU[s].xh, lo = A.XU[s].xl;
+  const float4 gvi = A.XU[s].uh;
   double bgd, bvd;
   ghost_rhs2(A, A.p1[P1_GN * n + s], A.K.euler ? A.V[s] : A.p1[P1_VN * n + s], &bgd, &bvd);
   const ff bgg = ff_of(bgd), bvg = ff_of(bvd);
@@ -582,7 +584,7 @@ __device__ __forceinline__ void pass2_twins_body(const StepArgs& A, int s) {
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     ff a[kNB];
     ff_taylor(ff_entry_row<PER>(A, s, hi, lo, c0), a);
-    const float4 gvj = A.GVff[j];
+    const float4 gvj = A.XU[j].uh;
     const ff bg = (c0 >> 31) ? ff{-gvi.x, -gvi.y} : ff_diff(gvj.x, gvj.y, gvi.x, gvi.y);
     const ff bv = ff_diff(gvj.z, gvj.w, gvi.z, gvi.w);
     const ff lin[2] = {ff_sub(bg, bgg), ff_sub(bv, bvg)};
@@ -611,7 +613,7 @@ template <bool PER>
 __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);
-  const float4 hi = A.Xh[s], lo = A.Xl[s];
+  const float4 hi = A.XU[s].xh, lo = A.XU[s].xl;
   // entries with a ghost (at the end of the stencil): their moments, with
   // their ghosts', come from gram_twins_body and seed the sums
   const int mr = m - ghost_count(A, s, m);
@@ -710,8 +712,8 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   if (A.fbslot[s] != -1) return;  // queued for the pivoted-QR fit
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);  // ghost rows carry b = 0: no right-hand side
-  const float4 hi = A.Xh[s], lo = A.Xl[s];
-  const float4 uh = A.Uh[s], ul = A.Ul[s];
+  const float4 hi = A.XU[s].xh, lo = A.XU[s].xl;
+  const float4 uh = A.XU[s].uh, ul = A.XU[s].ul;
   const int mm = A.K.mirror_mode;
   const float sg[3] = {mm == LP_MIRROR_NOSLIP ? -1.f : 1.f, mm == LP_MIRROR_NOSLIP ? -1.f : 1.f,
                        mm != LP_MIRROR_NONE ? -1.f : 1.f};
@@ -726,7 +728,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   if (m > 0) {
     ff_gather(A, s, code, xh, xl);
     const unsigned jj = min(code & kIndexMask, (unsigned)(n - 1));
-    vh = A.Uh[jj]; vl = A.Ul[jj];
+    vh = A.XU[jj].uh; vl = A.XU[jj].ul;
   }
   for (int k = 0; k < m; ++k) {
     const uint32_t c0 = code;
@@ -735,7 +737,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
       code = nxt;
       ff_gather(A, s, code, xh, xl);
       const unsigned jj = min(code & kIndexMask, (unsigned)(n - 1));
-      vh = A.Uh[jj]; vl = A.Ul[jj];
+      vh = A.XU[jj].uh; vl = A.XU[jj].ul;
       if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
     const FFRow r = ff_row_of<PER>(hi, lo, h0, l0, c0, A.K);
@@ -763,8 +765,8 @@ template <bool PER>
 __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, double gni,
                                                double Vi, double* gg, double* gV) {
   const int n = A.n;
-  const float4 hi = A.Xh[s], lo = A.Xl[s];
-  const float4 gvi = A.GVff[s];
+  const float4 hi = A.XU[s].xh, lo = A.XU[s].xl;
+  const float4 gvi = A.XU[s].uh;
   // entries with a ghost (at the end of the stencil): their terms, with their
   // ghosts', come from pass2_twins_body and seed the sums
   const int mg = ghost_count(A, s, m);
@@ -787,7 +789,7 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
   float4 jh = make_float4(0.f, 0.f, 0.f, 0.f), jl = jh, jg = jh;
   if (m > 0) {
     ff_gather(A, s, code, jh, jl);
-    jg = A.GVff[min(code & kIndexMask, (unsigned)(n - 1))];
+    jg = A.XU[min(code & kIndexMask, (unsigned)(n - 1))].uh;
   }
   for (int k = 0; k < m; ++k) {
     const uint32_t c0 = code;
@@ -795,7 +797,7 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
     if (k + 1 < m) {
       code = nxt;
       ff_gather(A, s, code, jh, jl);
-      jg = A.GVff[min(code & kIndexMask, (unsigned)(n - 1))];
+      jg = A.XU[min(code & kIndexMask, (unsigned)(n - 1))].uh;
       if (k + 2 < m) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
     const FFRow r = ff_row_of<PER>(hi, lo, h0, l0, c0, A.K);

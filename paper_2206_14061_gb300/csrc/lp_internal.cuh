@@ -94,6 +94,15 @@ __device__ __forceinline__ double wrap_pos(double x, double L) {
   return x;
 }
 
+// split position (x, y, z, mirror height) and velocity of one particle, hi
+// and lo, in one 64-byte record: a row of pass 1 gathers one cache line, the
+// Gram kernel the first 32-byte sector. Once pass 1 is done the velocity half
+// is dead and uh holds the split |gdot|^n and V of pass 2 instead (gv: hi,
+// lo, hi, lo), so a row of pass 2 gathers one line as well.
+struct __align__(64) FF8 {
+  float4 xh, xl, uh, ul;
+};
+
 // ------------------------------------------------------------ float-float
 // Unevaluated sums hi + lo of two floats (about 48 significant bits), built
 // from the error-free transformations TwoSum (Knuth) and TwoProduct (an FMA
@@ -201,7 +210,8 @@ struct StepArgs {
   // into hi and lo floats (w = mirror height), velocities split likewise,
   // |gdot| and V^{n+1} split (hi, lo, hi, lo), Gram matrices in float-float
   const GridCol* grids;
-  float4 *Xh, *Xl, *Uh, *Ul, *GVff;
+  FF8* XU;  // split positions and velocities
+
   int4* Xfix;       // free surface: round(K (x, y, z, 2 floor_z - z)) per particle,
                     // relative to the column's fixed-point origin
   int32_t* gcnt;    // free surface: entries with a ghost, at the end of each stencil
