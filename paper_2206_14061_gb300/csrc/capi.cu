@@ -126,6 +126,7 @@ struct lp_ctx {
   double** h_ptr = nullptr;  // pinned staging of d_ptr
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
   FF8* XU = nullptr;  // split positions and velocities (LP_MIXED_FF)
+  float2* P1s = nullptr;  // float-float gdot and ld of pass 1 (LP_MIXED_FF)
   int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
   int32_t* gcnt = nullptr;    // ghost entries per stencil
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
@@ -393,7 +394,7 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.p1 = c->p1; A.fbgrad = c->fbgrad; A.dg = c->dg;
   A.K = K;
   A.grids = c->d_grids;
-  A.XU = c->XU; A.Lff = c->Lff;
+  A.XU = c->XU; A.Lff = c->Lff; A.P1s = c->P1s;
   A.Xfix = c->Xfix;
   A.gcnt = c->gcnt;
   A.Tg = c->Tg; A.T2 = c->T2;
@@ -690,6 +691,7 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->d_ptr, kTabFields);
   if (s == LP_OK) s = dalloc(c, &c->bar, 2);
   if (s == LP_OK) s = dalloc(c, &c->XU, n);
+  if (s == LP_OK) s = dalloc(c, &c->P1s, n * 9);
   if (s == LP_OK) s = dalloc(c, &c->Lff, n * kTri);
   if (s == LP_OK) s = dalloc(c, &c->Xfix, n);
   if (s == LP_OK) s = dalloc(c, &c->gcnt, n);
@@ -975,6 +977,7 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
   const double ih2 = K.inv_h * K.inv_h;
   K.ih_h = (float)K.inv_h; K.ih_l = (float)(K.inv_h - (double)K.ih_h);
   K.ih2_h = (float)ih2; K.ih2_l = (float)(ih2 - (double)K.ih2_h);
+  K.phic_h = (float)K.phi_c; K.phic_l = (float)(K.phi_c - (double)K.phic_h);
   if (K.free_surface) {
     // ghost particles (Sec. 3.1 items 6 and 9): fixed-point grid K r <= 8192
     double g = 1.0;
@@ -995,14 +998,30 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
 }
 
 // caller state -> internal buffer in caller order; per-column mu(I) upload
+// Column record: the mu(I) parameters and the float-float constants of the
+// inertial closure used by pass 2 of LP_MIXED_FF (a = phi_c - phi_min).
+ColMui col_mui(const lp_mui& m, const lp_eos* e) {
+  ColMui r{m.mu_s, m.mu_2, m.I0, m.d, m.rho_s};
+  auto split = [](double v, float* f) {
+    f[0] = (float)v;
+    f[1] = (float)(v - (double)f[0]);
+  };
+  const double a = e->phi_c - e->phi_min;
+  split(4.0 * a * a * m.d * m.d, r.kf);
+  split(a * m.I0, r.aI0f);
+  split(a * m.mu_s * m.I0, r.bf);
+  split(m.mu_2, r.mu2f);
+  split(a * m.I0 * (m.mu_2 - m.mu_s), r.cf);
+  return r;
+}
+
 // (periods Lx, Ly > 0: positions along those axes mapped into [0, L);
 // gather: into the sorted order of the previous call, kept in ids)
-lp_status load_state(lp_ctx* c, const lp_particles* p, const lp_mui* mui, cudaStream_t st,
-                     double Lx = 0.0, double Ly = 0.0, bool gather = false) {
+lp_status load_state(lp_ctx* c, const lp_particles* p, const lp_mui* mui, const lp_eos* eos,
+                     cudaStream_t st, double Lx = 0.0, double Ly = 0.0, bool gather = false) {
   const int n = (int)p->n;
   std::vector<ColMui> hm(p->ncolumns);
-  for (int k = 0; k < p->ncolumns; ++k)
-    hm[k] = ColMui{mui[k].mu_s, mui[k].mu_2, mui[k].I0, mui[k].d, mui[k].rho_s};
+  for (int k = 0; k < p->ncolumns; ++k) hm[k] = col_mui(mui[k], eos);
   if (cudaMemcpyAsync(c->d_mui, hm.data(), sizeof(ColMui) * p->ncolumns, cudaMemcpyHostToDevice,
                       st) != cudaSuccess)
     return LP_ERR_CUDA;
@@ -1057,7 +1076,7 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   const bool reuse = keep && c->lists_valid && c->lists_n == n && c->lists_offs == offs &&
                      std::memcmp(sig, c->lists_sig, sizeof(sig)) == 0;
   c->lists_valid = false;  // until this call has completed
-  LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y, reuse));
+  LP_TRY(load_state(c, p, mui, eos, st, q->period_x, q->period_y, reuse));
   const int d = c->cx;
   LP_TRY(begin_columns(c, p, nullptr, d, offs, st, !reuse));
   // kept lists keep their grid while the particles fit in it (the split
@@ -1169,11 +1188,11 @@ lp_status lp_autotune(lp_ctx* c, const lp_particles* p, const lp_mui* mui, const
   const int R = q->rebuild_every;
   // every trial starts from the caller's state (which is never modified)
   auto restart = [&]() -> lp_status {
-    LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y));
+    LP_TRY(load_state(c, p, mui, eos, st, q->period_x, q->period_y));
     launch_fill_colid(n, c->d_offs, p->ncolumns, c->colid[c->ci], st);
     return LP_OK;
   };
-  LP_TRY(load_state(c, p, mui, st, q->period_x, q->period_y));
+  LP_TRY(load_state(c, p, mui, eos, st, q->period_x, q->period_y));
   LP_TRY(begin_columns(c, p, nullptr, c->cx, offs, st));
   LP_TRY(setup_grids(c, p->ncolumns, q->radius, st, q->period_x, q->period_y));
   LP_TRY(ensure_twin_buffers(c, q));

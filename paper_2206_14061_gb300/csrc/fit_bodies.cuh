@@ -691,6 +691,9 @@ __device__ __forceinline__ void pass1_finish_ff(const StepArgs& A, int s, const 
 #pragma unroll
   for (int q = 0; q < 6; ++q) p[(P1_GD + q) * n + s] = ff_to_double(gd[q]);
   p[P1_GN * n + s] = gn;
+  if (A.P1s)  // the float-float copy for the acceleration of pass 2
+#pragma unroll
+    for (int q = 0; q < 6; ++q) A.P1s[(int64_t)q * n + s] = make_float2(gd[q].h, gd[q].l);
   // Hessian columns: 3 xx, 4 yy, 5 zz, 6 xy, 7 xz, 8 yz
   const ff dd[3] = {ff_add(ff_add(c[0][3], c[1][6]), c[2][7]),
                     ff_add(ff_add(c[0][6], c[1][4]), c[2][8]),
@@ -700,6 +703,7 @@ __device__ __forceinline__ void pass1_finish_ff(const StepArgs& A, int s, const 
     const ff lap = ff_add(ff_add(c[a][3], c[a][4]), c[a][5]);
     const ff ld = ff_mul(ff_add(ff_scale(lap, 0.5f), ff_mul(dd[a], sixth)), ih2);
     p[(P1_LD + a) * n + s] = ff_to_double(ld);
+    if (A.P1s) A.P1s[(int64_t)(6 + a) * n + s] = make_float2(ld.h, ld.l);
   }
   const double Vi = A.V[s], dv = ff_to_double(div);
   p[P1_VN * n + s] = Vi + A.K.dt * (Vi * dv);
@@ -762,8 +766,8 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
 
 // pass-2 fits in float-float: gradients of |gdot|^n and V^{n+1}
 template <bool PER>
-__device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, double gni,
-                                               double Vi, double* gg, double* gV) {
+__device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, ff* gg,
+                                               ff* gV) {
   const int n = A.n;
   const float4 hi = A.XU[s].xh, lo = A.XU[s].xl;
   const float4 gvi = A.XU[s].uh;
@@ -815,11 +819,63 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
     }
   }
   ff_chol_solve<2>(A, s, R);
-  const double ih = A.K.inv_h;
+  const ff ih{A.K.ih_h, A.K.ih_l};
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    gg[q] = ff_to_double(R[0][q]) * ih;
-    gV[q] = ff_to_double(R[1][q]) * ih;
+    gg[q] = ff_mul(R[0][q], ih);
+    gV[q] = ff_mul(R[1][q], ih);
+  }
+}
+
+// Acceleration of the inertial regime (Sec. 2.3) in float-float, for a
+// particle fitted in float-float: V [ -(|g|/V^2)(S |g| V_c + R g_cj V_j) +
+// 2 M |g| |g|_c + N g_cj |g|_j + N |g| ld_c ] + g_c with the closure M, N,
+// S, R at phi = 1/V formed in float-float from the column's constants.
+// |g| and V come from the split record, gdot and ld from pass 1's
+// float-float copy; the result is rounded to FP64 once per component.
+__device__ __forceinline__ void accel_ff(const StepArgs& A, int s, const ff* gg, const ff* gV,
+                                         double* acc) {
+  const int64_t n = A.n;
+  const float4 gv = A.XU[s].uh;
+  const ff G{gv.x, gv.y}, V{gv.z, gv.w};
+  const ColMui& cm = A.mui[A.colid[s]];
+  const ff k{cm.kf[0], cm.kf[1]}, aI0{cm.aI0f[0], cm.aI0f[1]}, b{cm.bf[0], cm.bf[1]};
+  const ff mu2{cm.mu2f[0], cm.mu2f[1]}, c{cm.cf[0], cm.cf[1]};
+  const ff phi = ff_recip(V);
+  const ff w = ff_sub(ff{A.K.phic_h, A.K.phic_l}, phi);
+  const ff iw = ff_recip(w), iw2 = ff_mul(iw, iw);
+  const ff iden = ff_recip(ff_add(aI0, w));
+  const ff M = ff_neg(ff_mul(k, iw2));
+  const ff mu = ff_mul(ff_add(b, ff_mul(mu2, w)), iden);
+  const ff N = ff_neg(ff_mul(M, mu));
+  const ff S = ff_scale(ff_mul(ff_mul(k, iw2), iw), -2.f);
+  const ff dmu = ff_neg(ff_mul(c, ff_mul(iden, iden)));
+  const ff R = ff_neg(ff_add(ff_mul(S, mu), ff_mul(M, dmu)));
+  ff g3[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float2 v = A.P1s[(int64_t)q * n + s];
+    g3[q] = ff{v.x, v.y};
+  }
+  // rows of the symmetric gdot: (xx, xy, xz), (xy, yy, yz), (xz, yz, zz)
+  const int ix[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+  const ff GV2 = ff_mul(G, ff_mul(phi, phi));  // |g| / V^2
+  const ff SG = ff_mul(S, G), MG2 = ff_scale(ff_mul(M, G), 2.f), NG = ff_mul(N, G);
+  const double gvec[3] = {A.K.gx, A.K.gy, A.K.gz};
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) {
+    ff gjV = ff_mul(g3[ix[cc][0]], gV[0]), gjG = ff_mul(g3[ix[cc][0]], gg[0]);
+#pragma unroll
+    for (int d = 1; d < 3; ++d) {
+      gjV = ff_add(gjV, ff_mul(g3[ix[cc][d]], gV[d]));
+      gjG = ff_add(gjG, ff_mul(g3[ix[cc][d]], gg[d]));
+    }
+    const float2 l = A.P1s[(int64_t)(6 + cc) * n + s];
+    const ff t1 = ff_neg(ff_mul(GV2, ff_add(ff_mul(SG, gV[cc]), ff_mul(R, gjV))));
+    const ff t2 = ff_mul(MG2, gg[cc]);
+    const ff t3 = ff_mul(N, gjG);
+    const ff t4 = ff_mul(NG, ff{l.x, l.y});
+    acc[cc] = ff_to_double(ff_mul(V, ff_add(ff_add(ff_add(t1, t2), t3), t4))) + gvec[cc];
   }
 }
 
@@ -841,6 +897,8 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     const double gni = gn[s], Vi = Vn[s];
     const double Vnext = A.p1[P1_VN * n + s];
     double gg[3], gV[3];
+    ff ggf[3], gVf[3];  // float-float fit (LP_MIXED_FF, no fallback)
+    bool ffit = false;
     const int slot = A.fbslot[s];
     if (slot >= 0) {
 #pragma unroll
@@ -851,7 +909,10 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
     } else if (slot == -1) {
       const int m = min(A.cnt[s], A.cap);
       if (PREC == LP_MIXED_FF) {
-        pass2_ff_grads<PER>(A, s, m, gni, Vi, gg, gV);
+        pass2_ff_grads<PER>(A, s, m, ggf, gVf);
+        ffit = true;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) gg[q] = gV[q] = 0.0;  // set below where needed
       } else if (PREC == LP_FP64) {
         double R[2][kNB];
 #pragma unroll
@@ -986,6 +1047,9 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
       regime = 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[c] = gvec[c];
+    } else if (phi <= A.K.phi_max && PREC == LP_MIXED_FF && ffit) {
+      regime = 1;
+      accel_ff(A, s, ggf, gVf, acc);
     } else if (phi <= A.K.phi_max) {
       regime = 1;
       const Closure cl = closure_at(phi, A.mui[A.colid[s]], A.K.phi_c, A.K.phi_min);
@@ -1009,6 +1073,9 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
       }
     } else {
       regime = 2;
+      if (PREC == LP_MIXED_FF && ffit)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) gV[q] = ff_to_double(gVf[q]);
       // sigma = -phi_s (alpha + beta phi) I  =>  a = beta grad V / V + g
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[c] = (A.K.beta * gV[c]) / Vi + gvec[c];

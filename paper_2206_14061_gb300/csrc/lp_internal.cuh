@@ -40,6 +40,10 @@ struct GridCol {
 // per-column material parameters
 struct ColMui {
   double mu_s, mu_2, I0, d, rho_s;
+  // float-float (hi, lo) constants of the inertial closure for pass 2 of
+  // LP_MIXED_FF, a = phi_c - phi_min: k = 4 a^2 d^2, a I0, a mu_s I0, mu_2,
+  // a I0 (mu_2 - mu_s)
+  float kf[2], aI0f[2], bf[2], mu2f[2], cf[2];
 };
 
 // constants of one step
@@ -59,6 +63,7 @@ struct StepConsts {
   double Lx, Ly;
   float Lhx_h, Lhx_l, Lhy_h, Lhy_l;
   float ih_h, ih_l, ih2_h, ih2_l;  // 1/h and 1/h^2 as float-float
+  float phic_h, phic_l;            // phi_c as float-float
   long long ghost_PX, ghost_PY;
   double ghost_grid, ghost_hk, ghost_V, ghost_num;
   long long ghost_R2, ghost_clear2;
@@ -162,6 +167,14 @@ __device__ __forceinline__ ff ff_rsqrt(ff d) {
   const float delta = __fsub_rn(__fsub_rn(1.f, t.h), t.l);
   return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), delta));
 }
+// 1/d in float-float: the rounded FP32 reciprocal refined by one Newton step
+// y + y (1 - d y), the residual formed in float-float
+__device__ __forceinline__ ff ff_recip(ff d) {
+  const float y = __frcp_rn(d.h);
+  const ff t = ff_mul(d, ff{y, 0.f});
+  const float e = __fsub_rn(__fsub_rn(1.f, t.h), t.l);
+  return fast_two_sum(y, __fmul_rn(y, e));
+}
 __device__ __forceinline__ ff ff_of(double d) {
   const float h = __double2float_rn(d);
   return {h, __double2float_rn(d - (double)h)};
@@ -211,6 +224,8 @@ struct StepArgs {
   // |gdot| and V^{n+1} split (hi, lo, hi, lo), Gram matrices in float-float
   const GridCol* grids;
   FF8* XU;  // split positions and velocities
+  float2* P1s;  // LP_MIXED_FF: gdot (6) and ld (3) of pass 1 as float-float, k-major
+                // (null in the other modes)
 
   int4* Xfix;       // free surface: round(K (x, y, z, 2 floor_z - z)) per particle,
                     // relative to the column's fixed-point origin
