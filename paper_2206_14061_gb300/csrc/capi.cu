@@ -978,6 +978,7 @@ StepConsts step_consts(const lp_eos* eos, const lp_params* q, double dt, int cap
   K.ih_h = (float)K.inv_h; K.ih_l = (float)(K.inv_h - (double)K.ih_h);
   K.ih2_h = (float)ih2; K.ih2_l = (float)(ih2 - (double)K.ih2_h);
   K.phic_h = (float)K.phi_c; K.phic_l = (float)(K.phi_c - (double)K.phic_h);
+  K.rho = (float)(q->radius / q->h * (1.0 + 0x1p-10));
   if (K.free_surface) {
     // ghost particles (Sec. 3.1 items 6 and 9): fixed-point grid K r <= 8192
     double g = 1.0;

@@ -440,6 +440,30 @@ __device__ __forceinline__ void ff_moments_add_twin(ff* mo, const FFRow& r) {
 }
 
 // packed Gram matrix from the moments (same entries as Moments::gram)
+// the same sums with the nine sums of terms that are never negative seeded
+// (ff_acc_seeded; see gram_ff_body) and the signed ones in plain float-float
+__device__ __forceinline__ void ff_moments_add_seeded(ff* mo, const FFRow& r) {
+  ff_acc1_seeded(mo[0], r.qxx); ff_acc1_seeded(mo[1], r.qyy); ff_acc1_seeded(mo[2], r.qzz);
+  ff_acc1(mo[3], r.qxy); ff_acc1(mo[4], r.qxz); ff_acc1(mo[5], r.qyz);
+  ff_acc(mo[6], r.dx, r.qxx);  ff_acc(mo[7], r.dy, r.qyy);  ff_acc(mo[8], r.dz, r.qzz);
+  ff_acc(mo[9], r.dy, r.qxx);  ff_acc(mo[10], r.dz, r.qxx); ff_acc(mo[11], r.dx, r.qyy);
+  ff_acc(mo[12], r.dz, r.qyy); ff_acc(mo[13], r.dx, r.qzz); ff_acc(mo[14], r.dy, r.qzz);
+  ff_acc(mo[15], r.dz, r.qxy);
+  ff_acc_seeded(mo[16], r.qxx, r.qxx); ff_acc_seeded(mo[17], r.qyy, r.qyy);
+  ff_acc_seeded(mo[18], r.qzz, r.qzz);
+  ff_acc(mo[19], r.qxx, r.qxy); ff_acc(mo[20], r.qxx, r.qxz); ff_acc(mo[21], r.qyy, r.qxy);
+  ff_acc(mo[22], r.qyy, r.qyz); ff_acc(mo[23], r.qzz, r.qxz); ff_acc(mo[24], r.qzz, r.qyz);
+  ff_acc_seeded(mo[25], r.qxx, r.qyy); ff_acc_seeded(mo[26], r.qxx, r.qzz);
+  ff_acc_seeded(mo[27], r.qyy, r.qzz);
+  ff_acc(mo[28], r.qxx, r.qyz); ff_acc(mo[29], r.qyy, r.qxz); ff_acc(mo[30], r.qzz, r.qxy);
+}
+// degree (2, 3 or 4) of the monomial summed in moment q
+__host__ __device__ constexpr int moment_degree(int q) { return q < 6 ? 2 : (q < 16 ? 3 : 4); }
+// moments whose terms are never negative (dx^2, dy^2, dz^2, dx^4, dy^4, dz^4,
+// dx^2 dy^2, dx^2 dz^2, dy^2 dz^2)
+__host__ __device__ constexpr bool moment_nonneg(int q) {
+  return q <= 2 || (q >= 16 && q <= 18) || (q >= 25 && q <= 27);
+}
 __device__ __forceinline__ void ff_gram(const ff* mo, ff* g) {
   const float h = 0.5f, q = 0.25f;
   g[tri(0, 0)] = mo[0];
@@ -617,14 +641,26 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
   // entries with a ghost (at the end of the stencil): their moments, with
   // their ghosts', come from gram_twins_body and seed the sums
   const int mr = m - ghost_count(A, s, m);
+  // The nine sums of terms that are never negative start at a power of two
+  // C >= rho^d (rho >= |offset| / h, d the degree): they only grow, so each
+  // row's term stays below the running sum and FastTwoSum is exact; C is
+  // small against the sums (no precision is lost) and comes off with an
+  // error-free TwoSum at the end. Signed sums keep TwoSum (a seed large
+  // enough for them would cost precision).
+  const float r2 = A.K.rho * A.K.rho, r4 = r2 * r2;
+  const float Cpos[2] = {pow2_ceil(r2), pow2_ceil(r4)};
+  auto seed = [&](int q) {
+    return moment_nonneg(q) ? Cpos[moment_degree(q) == 2 ? 0 : 1] : 0.f;
+  };
   ff mo[31];
   if (mr < m) {
 #pragma unroll
     for (int q = 0; q < 31; ++q)
-      mo[q] = ff{A.Tg[(int64_t)q * n + s], A.Tg[(int64_t)(31 + q) * n + s]};
+      mo[q] = ff_add(ff{seed(q), 0.f},
+                     ff{A.Tg[(int64_t)q * n + s], A.Tg[(int64_t)(31 + q) * n + s]});
   } else {
 #pragma unroll
-    for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+    for (int q = 0; q < 31; ++q) mo[q] = {seed(q), 0.f};
   }
   // software pipeline: stencil codes are loaded two rows ahead and the
   // neighbour's values one row ahead, so the dependent loads of a row
@@ -641,7 +677,12 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
       ff_gather(A, s, code, jh, jl);
       if (k + 2 < mr) nxt = (uint32_t)A.nbr[(int64_t)(k + 2) * n + s];
     }
-    ff_moments_add(mo, ff_row_of<PER>(hi, lo, h0, l0, c0, A.K));
+    ff_moments_add_seeded(mo, ff_row_of<PER>(hi, lo, h0, l0, c0, A.K));
+  }
+#pragma unroll
+  for (int q = 0; q < 31; ++q) {  // remove the seed (error-free)
+    const ff d = two_sum(mo[q].h, -seed(q));
+    mo[q] = fast_two_sum(d.h, __fadd_rn(d.l, mo[q].l));
   }
   ff G[kTri];
   ff_gram(mo, G);

@@ -64,6 +64,7 @@ struct StepConsts {
   float Lhx_h, Lhx_l, Lhy_h, Lhy_l;
   float ih_h, ih_l, ih2_h, ih2_l;  // 1/h and 1/h^2 as float-float
   float phic_h, phic_l;            // phi_c as float-float
+  float rho;                       // bound on |offset| / h of a stencil entry (r/h, rounded up)
   long long ghost_PX, ghost_PY;
   double ghost_grid, ghost_hk, ghost_V, ghost_num;
   long long ghost_R2, ghost_clear2;
@@ -148,6 +149,27 @@ __device__ __forceinline__ void ff_acc(ff& acc, ff a, ff b) {
   const ff s = two_sum(acc.h, p);
   acc.h = s.h;
   acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
+}
+// Seeded sums: when |acc.h| >= |a.h b.h| is known (the sum starts at a large
+// power of two, see gram_ff_body), the error of the high-part addition is
+// captured exactly by FastTwoSum (3 operations instead of TwoSum's 6).
+__device__ __forceinline__ void ff_acc_seeded(ff& acc, ff a, ff b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const ff s = fast_two_sum(acc.h, p);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
+}
+__device__ __forceinline__ void ff_acc1_seeded(ff& acc, ff a) {
+  const ff s = fast_two_sum(acc.h, a.h);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, a.l));
+}
+// smallest power of two >= v (v positive and normal)
+__device__ __forceinline__ float pow2_ceil(float v) {
+  return __int_as_float((__float_as_int(v) + 0x007fffff) & 0x7f800000);
 }
 // acc += a
 __device__ __forceinline__ void ff_acc1(ff& acc, ff a) {
