@@ -163,7 +163,8 @@ typedef struct {
                           * plans a second-order scheme): two stages on the
                           * step's stencils, y* = y + dt F(y), y** = y* +
                           * dt F(y*), y^{n+1} = (y + y**) / 2, F taking V at its
-                          * own time level. lp_step_adjoint: UNIMPLEMENTED.     */
+                          * own time level. lp_step_adjoint covers it (both
+                          * stages on the segment's stencils, then the average). */
   double period_x, period_y; /* > 0: periodic boundaries along x / y (Sec. 3.1
                           * item 9). lp_step first maps positions into [0, L)
                           * (values already there are kept bit for bit); every

@@ -12,6 +12,9 @@
 // Least-squares adjoint, for c = G^{-1} A^T b with residual r = b - A c:
 //   z = G^{-1} cbar,  bbar = A z,  Abar = r z^T - (A z) c^T,
 // and Abar reaches the positions through the offsets d_k = (p_k - p_i)/h.
+// Stage of Heun's method (K.euler): x' = x + dt u and the pass-2 fits and the
+// closure read V^n instead of V^{n+1}, so their V adjoint goes to V^n
+// directly (lVd) rather than through V^{n+1} = V + dt V div u.
 // Free-surface ghosts: a flagged entry k also stands for the row a_G =
 // T(-d_k) of its point reflection. Its pass-1 right-hand sides are 0 (the
 // ghost carries the particle's velocity); its pass-2 ones depend only on the
@@ -129,15 +132,18 @@ __global__ void __launch_bounds__(kBlock) k_adj_accel(const AdjArgs A) {
   if (s < A.n) {
     const int n = A.n;
     const double dt = A.K.dt, ih = A.K.inv_h;
+    const bool eu = A.K.euler;
     double lu1t[3], la[3];
     for (int c = 0; c < 3; ++c) {
-      lu1t[c] = A.l1[3 + c][s] + 0.5 * dt * A.l1[c][s];
+      // x' = x + (dt/2)(u + u') (the paper's step) or x + dt u (Euler stage)
+      lu1t[c] = A.l1[3 + c][s] + (eu ? 0.0 : 0.5 * dt * A.l1[c][s]);
       la[c] = dt * lu1t[c];
-      A.l0[c][s] = A.l1[c][s];                           // x' = x + ...
-      A.l0[3 + c][s] = lu1t[c] + 0.5 * dt * A.l1[c][s];  // u' = u + dt a, x' has u/2
+      A.l0[c][s] = A.l1[c][s];
+      A.l0[3 + c][s] = lu1t[c] + (eu ? dt : 0.5 * dt) * A.l1[c][s];  // u' = u + dt a
     }
-    double lVn = A.l1[6][s];  // V' = V^{n+1}
-    const double Vn = A.p1[P1_VN * n + s];
+    const double lV1 = A.l1[6][s];  // V' = V^{n+1}
+    double lVn = 0.0;               // adjoint of the V that the fits and the closure read
+    const double Vn = eu ? A.V[s] : A.p1[P1_VN * n + s];
     const double Gn = A.p1[P1_GN * n + s];
     const double phi = 1.0 / Vn;
     const int slot = A.fbslot[s];
@@ -204,7 +210,12 @@ __global__ void __launch_bounds__(kBlock) k_adj_accel(const AdjArgs A) {
       }
     }
     A.lGn[s] = lGn;
-    A.lVn[s] = lVn;
+    if (eu) {
+      A.lVn[s] = lV1;
+      A.lVd[s] = lVn;
+    } else {
+      A.lVn[s] = lV1 + lVn;
+    }
     A.lG6[0 * n + s] = lGam[0][0];
     A.lG6[1 * n + s] = lGam[1][1];
     A.lG6[2 * n + s] = lGam[2][2];
@@ -260,7 +271,9 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
   const double ih = A.K.inv_h, f2 = 2.0 * A.K.floor_z;
   const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
   const double* Gn = A.p1 + P1_GN * n;
-  const double* Vn = A.p1 + P1_VN * n;
+  // V of the pass-2 fit: V^{n+1}, or V^n in an Euler stage (whose adjoint is lVd)
+  const double* Vn = A.K.euler ? A.V : A.p1 + P1_VN * n;
+  double* const lVfit = A.K.euler ? A.lVd : A.lVn;
   const double gni = Gn[s], Vi = Vn[s];
   const int m = min(A.cnt[s], A.cap);
   double sg = 0.0, sV = 0.0, sp[3] = {0.0, 0.0, 0.0};
@@ -298,7 +311,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
     }
     if (!mir) atomicAdd(&A.lGn[j], bg);
     sg += bg;
-    atomicAdd(&A.lVn[j], bV);  // the mirror of j carries V^{n+1}_j
+    atomicAdd(&lVfit[j], bV);  // the mirror of j carries V_j
     sV += bV;
     double ab[kNB], db[3];
     for (int q = 0; q < kNB; ++q) ab[q] = rg * zg[q] - bg * cg[q] + rV * zV[q] - bV * cV[q];
@@ -325,7 +338,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
     for (int c = 0; c < 3; ++c) sp[c] += db[c] * ih;
   }
   atomicAdd(&A.lGn[s], og - sg);
-  atomicAdd(&A.lVn[s], oV - sV);
+  atomicAdd(&lVfit[s], oV - sV);
   for (int c = 0; c < 3; ++c) atomicAdd(&A.l0[c][s], -sp[c]);
 }
 
@@ -340,7 +353,8 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass1(const AdjArgs A) {
   const double lVn = A.lVn[s];
   const double div = A.p1[P1_DIV * n + s];
   const double Vi = A.V[s];
-  A.l0[6][s] = lVn * (1.0 + dt * div);  // V^{n+1} = V + dt V div
+  // V^{n+1} = V + dt V div; an Euler stage's fits and closure read V itself
+  A.l0[6][s] = lVn * (1.0 + dt * div) + (A.K.euler ? A.lVd[s] : 0.0);
   if (!A.ok[s]) return;
   const double ldiv = lVn * dt * Vi;
   const double Gn = A.p1[P1_GN * n + s];

@@ -49,6 +49,7 @@ void launch_copy_state(int n, double* const* dst, double* const* src, cudaStream
 void launch_heun_combine(int n, double* const* y, double* const* y0, double Lx, double Ly,
                          cudaStream_t st);
 void launch_wrap_positions(int n, double* x, double* y, double Lx, double Ly, cudaStream_t st);
+void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
 void launch_need_search(int n, const double* x, const double* y, const double* z,
                         const double* xref, double half_skin2, double Lx, double Ly, int* flag,
                         cudaStream_t st);
@@ -1278,7 +1279,6 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, initial, offs, true));
   if (!valid_params(q, eos, dt) || q->precision != LP_FP64) return LP_ERR_INVALID_ARG;
-  if (q->time_scheme != LP_TIME_PAPER) return LP_ERR_UNIMPLEMENTED;
   if (seed->n != initial->n || (initial->n > 0 && (!seed->x || !seed->y || !seed->z || !seed->u ||
                                                    !seed->v || !seed->w || !seed->V)))
     return LP_ERR_INVALID_ARG;
@@ -1304,17 +1304,21 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   const int C = checkpoint_every;
   const int nseg = (nsteps + C - 1) / C;
   std::vector<ColMui> hm(initial->ncolumns);
-  for (int k = 0; k < initial->ncolumns; ++k)
-    hm[k] = ColMui{mui[k].mu_s, mui[k].mu_2, mui[k].I0, mui[k].d, mui[k].rho_s};
+  for (int k = 0; k < initial->ncolumns; ++k) hm[k] = col_mui(mui[k], eos);
   if (cudaMemcpyAsync(c->d_mui, hm.data(), sizeof(ColMui) * initial->ncolumns,
                       cudaMemcpyHostToDevice, st) != cudaSuccess)
     return LP_ERR_CUDA;
-  const StepConsts K = step_consts(eos, q, dt, c->cap);  // periods included
+  const StepConsts K = step_consts(eos, q, dt, c->cap);  // periods, time scheme included
+  LP_TRY(ensure_twin_buffers(c, q));  // the saved state of Heun's method
+  // Heun's method: a segment keeps y^k and the first stage's y*_k of each step
+  const bool heun = q->time_scheme == LP_TIME_HEUN;
+  const int nkept = heun ? 2 * C + 1 : C + 1;
 
   // workspace of this call: checkpoints, segment states, coefficients, adjoints
   const size_t N = (size_t)n;
-  const size_t nd =
-      N * (7 * (size_t)nseg + 7 * (size_t)(C + 1) + 27 + 18 + 14 + 2 + 6 + 3 + 18 + 7 + 45 + 1) + 3;
+  const size_t nd = N * (7 * (size_t)nseg + 7 * (size_t)nkept + 27 + 18 + 14 + 2 + 6 + 3 + 18 +
+                         7 + 45 + 1 + 1 + (heun ? 14 : 0)) +
+                    3;
   double* W = nullptr;
   if (cudaMalloc(&W, nd * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -1323,12 +1327,15 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   double* p = W;
   auto take = [&](size_t k) { double* r = p; p += k; return r; };
   double* ckpt = take(7 * N * nseg);
-  double* seg = take(7 * N * (C + 1));
+  double* seg = take(7 * N * nkept);
   double* coef1 = take(27 * N);
   double* coef2 = take(18 * N);
   double* lam[2] = {take(7 * N), take(7 * N)};
   double* lGn = take(N);
   double* lVn = take(N);
+  double* lVd = take(N);
+  double* lamH = heun ? take(7 * N) : nullptr;  // Heun: half the adjoint, for y**
+  double* lamS = heun ? take(7 * N) : nullptr;  // Heun: adjoint of y*
   double* lG6 = take(6 * N);
   double* lld = take(3 * N);
   double* zz = take(18 * N);
@@ -1336,16 +1343,16 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   double* facx = take(45 * N);
   uint8_t* okf = (uint8_t*)take(N);  // N bytes used of N doubles
   double* dth = take(3);
-  // device pointer tables: checkpoints (nseg x 7), segment states ((C+1) x 7),
+  // device pointer tables: checkpoints (nseg x 7), segment states (nkept x 7),
   // lam[0], lam[1], seed, caller initial, dL_dinitial, internal X[0], X[1]
-  const int ntab = 7 * nseg + 7 * (C + 1) + 7 * 7;
+  const int ntab = 7 * nseg + 7 * nkept + 7 * 7;
   std::vector<double*> tab(ntab);
   for (int s2 = 0; s2 < nseg; ++s2)
     for (int f = 0; f < 7; ++f) tab[7 * s2 + f] = ckpt + (size_t)(7 * s2 + f) * N;
   const int tseg = 7 * nseg;
-  for (int k = 0; k <= C; ++k)
+  for (int k = 0; k < nkept; ++k)
     for (int f = 0; f < 7; ++f) tab[tseg + 7 * k + f] = seg + (size_t)(7 * k + f) * N;
-  const int tlam = tseg + 7 * (C + 1);
+  const int tlam = tseg + 7 * nkept;
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < 7; ++f) tab[tlam + 7 * b + f] = lam[b] + (size_t)f * N;
   const int tseed = tlam + 14;
@@ -1392,7 +1399,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
       if (k > 0 && k % C == 0)
         launch_scatter_state(n, c->ids[c->ci], (const double* const*)(dtab + tX + 7 * c->cx),
                              dtab + 7 * (k / C), 7, st);
-      run_step(c, n, K, LP_FP64, k % C == 0, st);
+      one_step(c, n, K, LP_FP64, k % C == 0, st);
     }
     // ---- reverse sweep
     int cur = 0;  // lam[cur] holds the adjoint (caller order between segments)
@@ -1418,32 +1425,40 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
       for (int f = 0; f < 7; ++f)
         cudaMemcpyAsync(tab[tseg + f], c->X[c->cx][f], sizeof(double) * N,
                         cudaMemcpyDeviceToDevice, st);
-      // re-run the segment, keeping every step's state
+      // re-run the segment, keeping every step's state (Heun's method: the
+      // state y^k at 2k, the first stage's y*_k at 2k + 1)
       StepArgs S = step_args(c, n, K);
-      for (int k = 0; k < steps; ++k) {
-        double* const* sk = &tab[tseg + 7 * k];
-        double* const* sk1 = &tab[tseg + 7 * (k + 1)];
-        S.x = sk[0]; S.y = sk[1]; S.z = sk[2]; S.u = sk[3]; S.v = sk[4]; S.w = sk[5]; S.V = sk[6];
-        S.xo = sk1[0]; S.yo = sk1[1]; S.zo = sk1[2]; S.uo = sk1[3]; S.vo = sk1[4]; S.wo = sk1[5];
-        S.Vo = sk1[6];
+      auto kept = [&](int i) { return &tab[tseg + 7 * i]; };
+      auto one_pass = [&](double* const* in, double* const* out) {
+        S.x = in[0]; S.y = in[1]; S.z = in[2]; S.u = in[3]; S.v = in[4]; S.w = in[5]; S.V = in[6];
+        S.xo = out[0]; S.yo = out[1]; S.zo = out[2]; S.uo = out[3]; S.vo = out[4]; S.wo = out[5];
+        S.Vo = out[6];
         cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
         launch_pass1(LP_FP64, S, st);
         launch_pass2(LP_FP64, S, st);
+      };
+      for (int k = 0; k < steps; ++k) {
+        if (!heun) {
+          one_pass(kept(k), kept(k + 1));
+        } else {  // two stages on the segment's stencils, then the average
+          one_pass(kept(2 * k), kept(2 * k + 1));
+          one_pass(kept(2 * k + 1), kept(2 * k + 2));
+          launch_heun_combine(n, kept(2 * k + 2), kept(2 * k), K.Lx, K.Ly, st);
+        }
       }
       // adjoint to the sorted order of this segment
       launch_gather_fields(n, c->ids[c->ci], (const double* const*)(dtab + tlam + 7 * cur),
                            dtab + tlam + 7 * (1 - cur), 7, st);
       cur = 1 - cur;
-      for (int k = steps - 1; k >= 0; --k) {
-        double* const* sk = &tab[tseg + 7 * k];
-        S.x = sk[0]; S.y = sk[1]; S.z = sk[2]; S.u = sk[3]; S.v = sk[4]; S.w = sk[5]; S.V = sk[6];
-        S.xo = scratch; S.yo = scratch + N; S.zo = scratch + 2 * N; S.uo = scratch + 3 * N;
-        S.vo = scratch + 4 * N; S.wo = scratch + 5 * N; S.Vo = scratch + 6 * N;
+      // adjoint of one step (the paper's) or one stage (Heun's method) from
+      // state `sk`: l0 = J^T l1, after recomputing that step's fits
+      auto adjoint_at = [&](double* const* sk, const double* l1, double* l0) {
+        double* const out[7] = {scratch,         scratch + N,     scratch + 2 * N,
+                                scratch + 3 * N, scratch + 4 * N, scratch + 5 * N,
+                                scratch + 6 * N};
         S.coef1 = coef1;
         S.coef2 = coef2;
-        cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
-        launch_pass1(LP_FP64, S, st);
-        launch_pass2(LP_FP64, S, st);
+        one_pass(sk, out);
         S.coef1 = S.coef2 = nullptr;
         AdjArgs J{};
         J.n = n; J.cap = c->cap;
@@ -1452,12 +1467,25 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
         J.mui = c->d_mui; J.fac = c->fac; J.p1 = c->p1; J.coef1 = coef1; J.coef2 = coef2;
         J.fbgrad = c->fbgrad; J.K = K;
         for (int f = 0; f < 7; ++f) {
-          J.l1[f] = lam[cur] + f * N;
-          J.l0[f] = lam[1 - cur] + f * N;
+          J.l1[f] = l1 + f * N;
+          J.l0[f] = l0 + f * N;
         }
-        J.lGn = lGn; J.lVn = lVn; J.lG6 = lG6; J.lld = lld; J.zz = zz; J.dtheta = dth;
-        J.dg = c->dg; J.ok = okf; J.facx = facx;
+        J.lGn = lGn; J.lVn = lVn; J.lVd = lVd; J.lG6 = lG6; J.lld = lld; J.zz = zz;
+        J.dtheta = dth; J.dg = c->dg; J.ok = okf; J.facx = facx;
         launch_adjoint_step(J, st);
+      };
+      for (int k = steps - 1; k >= 0; --k) {
+        if (!heun) {
+          adjoint_at(kept(k), lam[cur], lam[1 - cur]);
+        } else {
+          // y^{k+1} = (y^k + y**) / 2: half the adjoint to each; then the second
+          // stage (from y*) and the first (from y^k), and the direct half
+          launch_axpby((int64_t)(7 * N), 0.0, lam[cur], 0.5, lam[cur], st);
+          cudaMemcpyAsync(lamH, lam[cur], sizeof(double) * 7 * N, cudaMemcpyDeviceToDevice, st);
+          adjoint_at(kept(2 * k + 1), lamH, lamS);
+          adjoint_at(kept(2 * k), lamS, lam[1 - cur]);
+          launch_axpby((int64_t)(7 * N), 1.0, lam[cur], 1.0, lam[1 - cur], st);
+        }
         cur = 1 - cur;
       }
       // back to caller order

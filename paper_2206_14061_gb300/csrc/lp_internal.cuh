@@ -333,6 +333,8 @@ struct AdjArgs {
   double* l0[7];         // adjoint of the state at n (output)
   double* lGn;           // adjoint of |gdot|^n (accumulated)
   double* lVn;           // adjoint of V^{n+1} (accumulated)
+  double* lVd;           // Euler stage (K.euler): adjoint of the V^n that the fits and
+                         // the closure read (accumulated; added to l0 V directly)
   double* lG6;           // adjoint of gdot from the acceleration, 6 * n
   double* lld;           // adjoint of ld, 3 * n
   double* zz;            // G^{-1} cbar of pass 2 (|gdot|, V^{n+1}), 18 * n

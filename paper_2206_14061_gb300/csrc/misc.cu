@@ -92,6 +92,15 @@ void launch_wrap_positions(int n, double* x, double* y, double Lx, double Ly, cu
   k_wrap_positions<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, Lx, Ly);
 }
 
+// y = a x + b y over n doubles (the adjoint of Heun's average); x may be y
+__global__ void k_axpby(int64_t n, double a, const double* x, double b, double* y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st) {
+  k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, x, b, y);
+}
+
 void launch_iota(int n, int32_t* a, cudaStream_t st) {
   k_iota<<<(n + 255) / 256, 256, 0, st>>>(n, a);
 }

@@ -76,3 +76,26 @@ def test_heun_rest_and_rigid_translation(orc):
     for c, k in enumerate("xyz"):
         assert np.allclose(s2[k] - st[k], U[c] * t, rtol=1e-9, atol=1e-17)
     assert np.allclose(s2["u"], U[0], rtol=1e-13)
+
+
+def test_heun_tangent_linear_matches_central_differences(orc):
+    """The dual-number tangent run with Heun's method (the reference of the
+    GPU adjoint for that scheme) on a sheared 8^3 cube."""
+    wl = W.cube(8)
+    st = dict(wl.state)
+    st["u"] = 20.0 * st["z"]
+    pd = W.param_dict(wl)
+    nst = reb = 8
+    p = orc.params(**dict(pd, time_scheme=1))
+    _, tan = orc.step_tangent(st, p, nst, rebuild_every=reb)
+    for kix, name in enumerate(("mu_s", "mu_2", "I0")):
+        eps = 1e-5
+        sp_, _ = orc.step(st, orc.params(**dict(pd, time_scheme=1, **{name: pd[name] + eps})),
+                          nst, rebuild_every=reb)
+        sm_, _ = orc.step(st, orc.params(**dict(pd, time_scheme=1, **{name: pd[name] - eps})),
+                          nst, rebuild_every=reb)
+        for f, key in enumerate(("u", "v", "w", "V")):
+            fd = (sp_[key] - sm_[key]) / (2 * eps)
+            t = tan[kix, 3 + f]
+            assert np.abs(t).max() > 0
+            assert np.abs(fd - t).max() <= 1e-5 * np.abs(t).max(), (name, key)
