@@ -55,6 +55,8 @@ def parse():
                     help="skip the line with Heun's method")
     ap.add_argument("--no-periodic", action="store_true",
                     help="skip the periodic-layer line (Sec. 3.1 item 9, Sec. 4)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the lp_fit_derivatives line (derivative-operator sweep)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
@@ -354,6 +356,9 @@ def our_arm(args):
         ctx.close()
         line["batched"] = batched(args, dev, stream)
 
+    if not args.no_sweep and world == 1:
+        line["derivative_sweep"] = derivative_sweep(args, dev, stream)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, pd, budget_s=20.0)
 
@@ -494,6 +499,49 @@ def periodic_layer(args, dev, stream, world):
             "phase_ms_per_step": {k: v / max(prof["steps"], 1) for k, v in prof["ms"].items()},
             "ghost_entries_per_step": diag["n_ghosts"] / max(args.steps, 1),
             "n_nonfinite": diag["n_nonfinite"]}
+
+
+def derivative_sweep(args, dev, stream):
+    """lp_fit_derivatives on the derivative-operator sweep (jittered +-0.2h
+    lattice of 126^3 particles, per-particle radius U(1.8h, 2.6h), 48 nearest,
+    four smooth fields): stencils built once, then the fit timed in each
+    precision mode; throughput in particle-fields per second."""
+    import torch
+
+    from paper_2206_14061_gb300 import capi, workloads as W
+
+    x, y, z, rad, fields, _ = W.sweep_lattice(n_side=126)
+    n, nf = x.size, fields.shape[0]
+    ctx = capi.Context(n, cap=64)
+    X = [torch.tensor(a, device=dev) for a in (x, y, z)]
+    F = [torch.tensor(f, device=dev) for f in fields]
+    out = torch.empty((n, nf, 9), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        nb = capi.lp_build_neighbors(ctx, *X, radius=torch.tensor(rad, device=dev),
+                                     mirror_mode=0, cap=48, keep_nearest=True, stream=stream)
+    ctx.sync(stream)
+    res = {"workload": f"derivative sweep: {n} particles, {nf} fields, 48 nearest, "
+                       "jitter +-0.2h, radius U(1.8h, 2.6h)"}
+    reps = max(3, min(args.steps, 10))
+    for name in ("fp64", "mixed", "mixed_ff"):
+        def call():
+            capi.lp_fit_derivatives(ctx, *X, nb, F, [1.0] * nf, 1e-3, precision=PREC[name],
+                                    out=out, stream=stream)
+        with torch.cuda.stream(stream):
+            call()  # warm-up (and the float-float workspace)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_call": ms, "particle_fields_per_s": n * nf / (ms / 1e3)}
+    ctx.sync(stream)
+    ctx.close()
+    return res
 
 
 def e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world):

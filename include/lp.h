@@ -283,7 +283,10 @@ lp_status lp_neighbors_export(lp_ctx* ctx, const lp_neighbors* nb, int32_t* host
  * [dx, dy, dz, dx^2/2, dy^2/2, dz^2/2, dx dy, dx dz, dy dz], right-hand side
  * s_k - s_i. coeffs (device, n*nf*9 doubles, row-major [i][f][c]) receives
  * d/dx, d/dy, d/dz, d2/dx2, d2/dy2, d2/dz2, d2/dxdy, d2/dxdz, d2/dydz.
- * precision: LP_FP64 or LP_MIXED. 1 <= nf <= 16. */
+ * precision: LP_FP64, LP_MIXED or LP_MIXED_FF (moments, factor and
+ * right-hand sides in float-float on positions relative to the first
+ * particle; 8 B per particle and field of extra workspace, up to 16 fields,
+ * allocated on first use). 1 <= nf <= 16. */
 lp_status lp_fit_derivatives(lp_ctx* ctx, const lp_particles* p, const lp_neighbors* nb,
                              const double* const* fields, const double* mirror_sign, int32_t nf,
                              double h, double floor_z, double* coeffs, int32_t precision,

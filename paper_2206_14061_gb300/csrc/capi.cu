@@ -128,6 +128,7 @@ struct lp_ctx {
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
   FF8* XU = nullptr;  // split positions and velocities (LP_MIXED_FF)
   float2* P1s = nullptr;  // float-float gdot and ld of pass 1 (LP_MIXED_FF)
+  float2* fit_fs = nullptr;  // split fields of lp_fit_derivatives (LP_MIXED_FF), lazily
   int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
   int32_t* gcnt = nullptr;    // ghost entries per stencil
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
@@ -921,7 +922,8 @@ lp_status lp_fit_derivatives(lp_ctx* c, const lp_particles* p, const lp_neighbor
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, p, offs, false));
   if (nf < 1 || nf > kMaxFields || !finite_pos(h) || !std::isfinite(floor_z) ||
-      (precision != LP_FP64 && precision != LP_MIXED) || nb->n != p->n || !nb->nbr || !nb->cnt ||
+      (precision != LP_FP64 && precision != LP_MIXED && precision != LP_MIXED_FF) ||
+      nb->n != p->n || !nb->nbr || !nb->cnt ||
       nb->cap < 1 || nb->cap > LP_MAX_CAP)
     return LP_ERR_INVALID_ARG;
   for (int f = 0; f < nf; ++f)
@@ -941,6 +943,10 @@ lp_status lp_fit_derivatives(lp_ctx* c, const lp_particles* p, const lp_neighbor
   F.coeffs = coeffs;
   F.fb_list = c->fb_list; F.fb_count = c->fb_count; F.fb_cap = c->fb_cap;
   F.dg = c->dg;
+  if (precision == LP_MIXED_FF) {  // the step's split and factor buffers serve as scratch
+    if (!c->fit_fs) LP_TRY(dalloc(c, &c->fit_fs, (size_t)kMaxFields * c->cap_n));
+    F.xs = c->XU; F.fs = c->fit_fs; F.lf = c->Lff;
+  }
   cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
   launch_fit(precision, F, st);
   return cuda_status();

@@ -211,6 +211,104 @@ __global__ void __launch_bounds__(kBlock) k_fit(const FitArgs F) {
   }
 }
 
+// ---- lp_fit_derivatives in float-float (LP_MIXED_FF): positions relative
+// to the first particle in units of h (with the floor-mirror height) and the
+// fields are split once per particle; the moments, the Cholesky factor and
+// the right-hand sides then run on FP32 pairs as in the step's pass 1, with
+// the same pivot test and the same pivoted-QR fallback.
+__global__ void k_fit_split_ff(const FitArgs F) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= F.n) return;
+  const double ox = F.x[0], oy = F.y[0], oz = F.z[0], ih = F.inv_h;
+  const ff fx = ff_of((F.x[s] - ox) * ih), fy = ff_of((F.y[s] - oy) * ih);
+  const ff fz = ff_of((F.z[s] - oz) * ih), fm = ff_of((F.f2 - F.z[s] - oz) * ih);
+  F.xs[s].xh = make_float4(fx.h, fy.h, fz.h, fm.h);
+  F.xs[s].xl = make_float4(fx.l, fy.l, fz.l, fm.l);
+  for (int f = 0; f < F.nf; ++f) {
+    const ff v = ff_of(F.fields[f][s]);
+    F.fs[(int64_t)f * F.n + s] = make_float2(v.h, v.l);
+  }
+}
+
+__global__ void __launch_bounds__(128, 4) k_fit_gram_ff(const FitArgs F) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= F.n) return;
+  const int n = F.n;
+  const int m = min(F.cnt[s], F.cap);
+  const float4 hi = F.xs[s].xh, lo = F.xs[s].xl;
+  const StepConsts K0{};  // no periodic axes
+  ff mo[31];
+#pragma unroll
+  for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+  for (int k = 0; k < m; ++k) {
+    const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
+    const int j = code & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
+    ff_moments_add(mo, ff_row_of<false>(hi, lo, F.xs[j].xh, F.xs[j].xl, code, K0));
+  }
+  ff G[kTri];
+  ff_gram(mo, G);
+#pragma unroll
+  for (int k = 0; k < kTri; ++k) G[k] = ff_norm(G[k]);
+  if (!(ff_chol9(G, 1e-4f) && m >= kNB)) {
+    const int slot = atomicAdd(F.fb_count, 1);
+    if (slot < F.fb_cap) F.fb_list[slot] = s;
+    else atomicOr(&F.dg->flags, (unsigned)LP_FLAG_OVERFLOW);
+    F.lf[s] = make_float2(-1.f, 0.f);  // 1/L_00 > 0 for a factored stencil
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < kTri; ++k) F.lf[(int64_t)k * n + s] = make_float2(G[k].h, G[k].l);
+}
+
+__global__ void __launch_bounds__(128, 4) k_fit_rhs_ff(const FitArgs F) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= F.n) return;
+  if (!(F.lf[s].x > 0.f)) return;  // queued for the pivoted-QR fit
+  const int n = F.n;
+  const int m = min(F.cnt[s], F.cap);
+  const float4 hi = F.xs[s].xh, lo = F.xs[s].xl;
+  const StepConsts K0{};
+  const double ih = F.inv_h, ih2 = ih * ih;
+  for (int f0 = 0; f0 < F.nf; f0 += 3) {  // three fields per sweep
+    const int nf = min(3, F.nf - f0);
+    ff R[3][kNB], si[3];
+    float sg[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const float2 v = f < nf ? F.fs[(int64_t)(f0 + f) * n + s] : make_float2(0.f, 0.f);
+      si[f] = ff{v.x, v.y};
+      sg[f] = f < nf ? (float)F.msign[f0 + f] : 0.f;
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+    }
+    for (int k = 0; k < m; ++k) {
+      const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
+      const int j = code & ~kMirrorBit;
+      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
+      const bool mir = code >> 31;
+      ff a[kNB];
+      ff_taylor(ff_row_of<false>(hi, lo, F.xs[j].xh, F.xs[j].xl, code, K0), a);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        if (f < nf) {
+          const float2 v = F.fs[(int64_t)(f0 + f) * n + j];
+          const float sj = mir ? sg[f] : 1.f;  // the field at a floor mirror
+          const ff b = ff_diff(sj * v.x, sj * v.y, si[f].h, si[f].l);
+#pragma unroll
+          for (int q = 0; q < kNB; ++q) ff_acc(R[f][q], b, a[q]);
+        }
+      }
+    }
+    ff_chol_solve<3>(F.lf + s, n, R);
+    for (int f = 0; f < nf; ++f) {
+      double* o = F.coeffs + ((int64_t)s * F.nf + f0 + f) * kNB;
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) o[q] = ff_to_double(R[f][q]) * (q < 3 ? ih : ih2);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(64) k_fit_fallback(const FitArgs F) {
   const int cnt = min(*F.fb_count, F.fb_cap);
   double Am[LP_MAX_CAP * kNB], Bm[LP_MAX_CAP * 4], C[4 * kNB], Acopy[LP_MAX_CAP * kNB];
@@ -342,8 +440,16 @@ void launch_pass2(int prec, const StepArgs& A, cudaStream_t st, int bs) {
 }
 void launch_fit(int prec, const FitArgs& F, cudaStream_t st) {
   const int nb = (F.n + kBlock - 1) / kBlock;
-  if (prec == LP_FP64) k_fit<LP_FP64><<<nb, kBlock, 0, st>>>(F);
-  else k_fit<LP_MIXED><<<nb, kBlock, 0, st>>>(F);
+  if (prec == LP_FP64) {
+    k_fit<LP_FP64><<<nb, kBlock, 0, st>>>(F);
+  } else if (prec == LP_MIXED) {
+    k_fit<LP_MIXED><<<nb, kBlock, 0, st>>>(F);
+  } else {
+    const int nf = (F.n + 127) / 128;
+    k_fit_split_ff<<<(F.n + 255) / 256, 256, 0, st>>>(F);
+    k_fit_gram_ff<<<nf, 128, 0, st>>>(F);
+    k_fit_rhs_ff<<<nf, 128, 0, st>>>(F);
+  }
   k_fit_fallback<<<152, 64, 0, st>>>(F);
 }
 void launch_mui_stress(int64_t n, const ColMui& m, const lp_eos& e, const double* V,

@@ -519,10 +519,10 @@ __device__ __forceinline__ bool ff_chol9(ff* a, float rel_tol) {
 // gram_ff_body stored for particle s; each factor entry is loaded once per
 // sweep and used for every right-hand side. r (unnormalised accumulators on
 // entry) is overwritten by c.
+// (L: this particle's factor, entry k at L[k * n])
 template <int NF>
-__device__ __forceinline__ void ff_chol_solve(const StepArgs& A, int s, ff (*r)[kNB]) {
-  const int64_t n = A.n;
-  const float2* L = A.Lff + s;  // one 8-byte load per entry
+__device__ __forceinline__ void ff_chol_solve(const float2* L, int64_t n, ff (*r)[kNB]) {
+  // one 8-byte load per entry
   auto at = [&](int k) {
     const float2 v = L[k * n];
     return ff{v.x, v.y};
@@ -801,7 +801,7 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
       for (int q = 0; q < kNB; ++q) ff_acc(R[f][q], b, a[q]);
     }
   }
-  ff_chol_solve<3>(A, s, R);
+  ff_chol_solve<3>(A.Lff + s, A.n, R);
   pass1_finish_ff(A, s, R);
 }
 
@@ -859,7 +859,7 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
       ff_acc(R[1][q], bv, a[q]);
     }
   }
-  ff_chol_solve<2>(A, s, R);
+  ff_chol_solve<2>(A.Lff + s, A.n, R);
   const ff ih{A.K.ih_h, A.K.ih_l};
 #pragma unroll
   for (int q = 0; q < 3; ++q) {

@@ -271,6 +271,11 @@ struct FitArgs {
   double msign[kMaxFields];
   double inv_h, f2;
   double* coeffs;     // n x nf x 9
+  // LP_MIXED_FF: split positions (xh, xl of each record), split fields
+  // (nf x n, k-major) and the float-float factors (45 x n)
+  FF8* xs;
+  float2* fs;
+  float2* lf;
   int32_t* fb_list;
   int32_t* fb_count;
   int fb_cap;

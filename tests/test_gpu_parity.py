@@ -162,6 +162,39 @@ def test_fit_mixed_error_bound(dev, capi, sweep):
     assert err <= 1e-5, err
 
 
+def test_fit_mixed_ff_error_bound(dev, capi, sweep):
+    """Float-float fit (moments, factor, right-hand sides on FP32 pairs): its
+    error is about 2^-44 kappa(G), far below the FP32-plus-refinement mode."""
+    F = [T(f, dev) for f in sweep["fields"]]
+    got = capi.lp_fit_derivatives(sweep["ctx"], *sweep["X"], sweep["nb"], F, [1.0] * 4, 1e-3,
+                                  precision=capi.LP_MIXED_FF)
+    sweep["ctx"].sync()
+    err = _class_err(got.cpu().numpy(), sweep["ref"])
+    print(f"float-float fit: max class error vs FP64 oracle = {err:.3e}")
+    assert err <= 1e-8, err
+
+
+def test_fit_mixed_ff_mirrors_and_field_groups(dev, capi, orc):
+    """Floor mirrors with even, odd and zero mirror signs, five fields (a full
+    and a partial group of three): float-float against the oracle."""
+    x, y, z, rad, fields, spec = W.sweep_lattice(n_side=14, nfields=5, index=7)
+    ctx = capi.Context(x.size, cap=64)
+    X = [T(a, dev) for a in (x, y, z)]
+    nb = capi.lp_build_neighbors(ctx, *X, radius=T(rad, dev), mirror_mode=1, floor_z=0.0, cap=48,
+                                 keep_nearest=True)
+    ctx.sync()
+    nbr, cnt = nb.export()
+    assert (nbr < 0).any()  # some entries are floor mirrors (bit 31)
+    ms = [1.0, -1.0, 0.0, 1.0, -1.0]
+    ref, _ = orc.fit(x, y, z, nbr, cnt, fields, ms, 1e-3)
+    got = capi.lp_fit_derivatives(ctx, *X, nb, [T(f, dev) for f in fields], ms, 1e-3,
+                                  precision=capi.LP_MIXED_FF).cpu().numpy()
+    ctx.sync()
+    err = _class_err(got, ref)
+    print(f"float-float fit with mirrors: max class error = {err:.3e}")
+    assert err <= 1e-8, err
+
+
 def test_fit_fallback_matches_oracle_projection(dev, capi, orc):
     """Sparse clouds (m < 9) and planar stencils take the pivoted-QR path; the
     fitted values A c (unique even when the basic solution is not) match."""
@@ -178,10 +211,16 @@ def test_fit_fallback_matches_oracle_projection(dev, capi, orc):
     ctx.sync()
     nbr, cnt = nb.export()
     assert (cnt < 9).any()
-    got = capi.lp_fit_derivatives(ctx, *X, nb, [T(a, dev) for a in f], [1, 1], 1e-3).cpu().numpy()
-    d = ctx.sync()
-    assert d["n_fallback"] > 0
     ref, rank = orc.fit(x, y, z, nbr, cnt, f, [1, 1], 1e-3)
+    for prec in (capi.LP_FP64, capi.LP_MIXED_FF):
+        got = capi.lp_fit_derivatives(ctx, *X, nb, [T(a, dev) for a in f], [1, 1], 1e-3,
+                                      precision=prec).cpu().numpy()
+        d = ctx.sync()
+        assert d["n_fallback"] > 0
+        _check_projection(x, y, z, f, nbr, cnt, got, ref, n, 1e-9 if prec == capi.LP_FP64 else 1e-7)
+
+
+def _check_projection(x, y, z, f, nbr, cnt, got, ref, n, tol):
     h = 1e-3
     for i in range(n):
         m = cnt[i]
@@ -196,7 +235,7 @@ def test_fit_fallback_matches_oracle_projection(dev, capi, orc):
             fa = A @ (got[i, q] * sc)
             fb = A @ (ref[i, q] * sc)
             b = f[q, j] - f[q, i]
-            assert np.abs(fa - fb).max() <= 1e-9 * (np.abs(b).max() + 1e-30), (i, q)
+            assert np.abs(fa - fb).max() <= tol * (np.abs(b).max() + 1e-30), (i, q)
 
 
 # ----------------------------------------------------------------- mu(I) ---
