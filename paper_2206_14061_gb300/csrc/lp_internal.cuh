@@ -21,6 +21,10 @@ constexpr int kTri = 45;          // packed lower triangle of a 9x9 matrix
 constexpr int kMaxColumns = 4096;
 constexpr int kBlock = 128;       // default threads per block of the per-particle kernels
 constexpr int kMaxBlock = 256;    // largest block size the tuner may pick
+#ifndef LP_FILTER_CHUNK
+#define LP_FILTER_CHUNK 8
+#endif
+constexpr int kFilterChunk = LP_FILTER_CHUNK;  // candidates whose gathers the filter issues together
 constexpr int kMaxFields = 16;    // lp_fit_derivatives
 constexpr int kMaxCand = 128;     // candidate buffer of the keep-nearest search
 

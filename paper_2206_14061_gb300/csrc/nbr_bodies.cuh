@@ -323,40 +323,54 @@ __device__ __forceinline__ void filter_body(
     const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
     const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
     const int m = min(ccnt[s], capc);
-    // software pipeline: candidate codes two ahead, their positions one ahead
-    uint32_t nc = m > 0 ? (uint32_t)cand[s] : 0u;
-    uint32_t nn = m > 1 ? (uint32_t)cand[(int64_t)n + s] : 0u;
-    float4 np = m > 0 ? pf[min(nc & ~kMirrorBit, (uint32_t)(n - 1))] : pi;
-    for (int k = 0; k < m; ++k) {
-      const uint32_t code = nc;
-      const float4 pj = np;
-      if (k + 1 < m) {
-        nc = nn;
-        np = pf[min(nc & ~kMirrorBit, (uint32_t)(n - 1))];
-        if (k + 2 < m) nn = (uint32_t)cand[(int64_t)(k + 2) * n + s];
+    // Candidates in chunks of kFilterChunk: the chunk's position gathers are
+    // issued together and the next chunk's codes load while this one is
+    // tested, so each thread keeps several gathers in flight. The stencil
+    // keeps the candidates' order.
+    uint32_t code[kFilterChunk];
+#pragma unroll
+    for (int t = 0; t < kFilterChunk; ++t)
+      code[t] = t < m ? (uint32_t)cand[(int64_t)t * n + s] : 0u;
+    for (int k0 = 0; k0 < m; k0 += kFilterChunk) {
+      float4 pj[kFilterChunk];
+#pragma unroll
+      for (int t = 0; t < kFilterChunk; ++t)
+        pj[t] = k0 + t < m ? pf[min(code[t] & ~kMirrorBit, (uint32_t)(n - 1))] : pi;
+      uint32_t next[kFilterChunk];
+#pragma unroll
+      for (int t = 0; t < kFilterChunk; ++t) {
+        const int k = k0 + kFilterChunk + t;
+        next[t] = k < m ? (uint32_t)cand[(int64_t)k * n + s] : 0u;
       }
-      const int j = code & ~kMirrorBit;
-      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
-      const bool mir = code >> 31;
-      float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
-      if (PER) {  // nearest image (exact no-op for a period of 0)
-        dxf = min_image_f(dxf, Lxf);
-        dyf = min_image_f(dyf, Lyf);
+#pragma unroll
+      for (int t = 0; t < kFilterChunk; ++t) {
+        const uint32_t cd = code[t];
+        const int j = cd & ~kMirrorBit;
+        // past the list, or a stale or corrupt stencil entry
+        if (k0 + t >= m || (unsigned)j >= (unsigned)n) continue;
+        const bool mir = cd >> 31;
+        float dxf = pj[t].x - pi.x, dyf = pj[t].y - pi.y;
+        if (PER) {  // nearest image (exact no-op for a period of 0)
+          dxf = min_image_f(dxf, Lxf);
+          dyf = min_image_f(dyf, Lyf);
+        }
+        const float dzf = (mir ? fz2 - pj[t].z : pj[t].z) - pi.z;
+        const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+        if (!exact_only && d2f > hi) continue;
+        bool in;
+        if (!exact_only && d2f < lo) {
+          in = true;
+        } else {
+          double d2;
+          const double zj = mir ? __dsub_rn(2.0 * floor_z, z[j]) : z[j];
+          in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2, PER ? g.Lx : 0.0, PER ? g.Ly : 0.0);
+        }
+        if (!in) continue;
+        if (c < cap) nbr[(int64_t)c * n + s] = (int32_t)cd;
+        ++c;
       }
-      const float dzf = (mir ? fz2 - pj.z : pj.z) - pi.z;
-      const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
-      if (!exact_only && d2f > hi) continue;
-      bool in;
-      if (!exact_only && d2f < lo) {
-        in = true;
-      } else {
-        double d2;
-        const double zj = mir ? __dsub_rn(2.0 * floor_z, z[j]) : z[j];
-        in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2, PER ? g.Lx : 0.0, PER ? g.Ly : 0.0);
-      }
-      if (!in) continue;
-      if (c < cap) nbr[(int64_t)c * n + s] = (int32_t)code;
-      ++c;
+#pragma unroll
+      for (int t = 0; t < kFilterChunk; ++t) code[t] = next[t];
     }
     over = c > cap || ccnt[s] > capc;
     cnt[s] = c;
