@@ -25,6 +25,10 @@ constexpr int kMaxBlock = 256;    // largest block size the tuner may pick
 #define LP_FILTER_CHUNK 8
 #endif
 constexpr int kFilterChunk = LP_FILTER_CHUNK;  // candidates whose gathers the filter issues together
+#ifndef LP_SEARCH_CHUNK
+#define LP_SEARCH_CHUNK 4
+#endif
+constexpr int kSearchChunk = LP_SEARCH_CHUNK;  // cell-range entries the search loads together
 constexpr int kMaxFields = 16;    // lp_fit_derivatives
 constexpr int kMaxCand = 128;     // candidate buffer of the keep-nearest search
 

@@ -203,9 +203,16 @@ __device__ __forceinline__ void neighbors_body(
             const int64_t c0 = cell_id(g, sx ? xw : xa0, ky, kz);
             const int64_t c1 = cell_id(g, sx ? xw : xb0, ky, kz);
             const uint32_t b = start[c0], e = start[c1 + 1];
-            for (uint32_t j = b; j < e; ++j) {
-              if (pass == 0 && (int)j == s) continue;
-              const float4 pj = pf[j];
+            // the range in chunks of kSearchChunk: their loads issue together
+            for (uint32_t j0 = b; j0 < e; j0 += kSearchChunk) {
+              float4 pc[kSearchChunk];
+#pragma unroll
+              for (int t = 0; t < kSearchChunk; ++t) pc[t] = j0 + t < e ? pf[j0 + t] : pi;
+#pragma unroll
+              for (int t = 0; t < kSearchChunk; ++t) {
+              const uint32_t j = j0 + t;
+              if (j >= e || (pass == 0 && (int)j == s)) continue;
+              const float4 pj = pc[t];
               float dxf = pj.x - pi.x, dyf = pj.y - pi.y;
               if (PER) {  // nearest image (exact no-op for a period of 0)
                 dxf = min_image_f(dxf, Lxf);
@@ -236,6 +243,7 @@ __device__ __forceinline__ void neighbors_body(
                 nbr[(int64_t)c * n + s] = (int32_t)code;
               }
               ++c;
+              }
             }
           }
     }
