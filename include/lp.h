@@ -286,7 +286,8 @@ lp_status lp_neighbors_export(lp_ctx* ctx, const lp_neighbors* nb, int32_t* host
  * precision: LP_FP64, LP_MIXED or LP_MIXED_FF (moments, factor and
  * right-hand sides in float-float on positions relative to the first
  * particle; 8 B per particle and field of extra workspace, up to 16 fields,
- * allocated on first use). 1 <= nf <= 16. */
+ * allocated on first use). 1 <= nf <= 16. With n = 0 nothing is enqueued and
+ * the field and coeffs pointers may be NULL. */
 lp_status lp_fit_derivatives(lp_ctx* ctx, const lp_particles* p, const lp_neighbors* nb,
                              const double* const* fields, const double* mirror_sign, int32_t nf,
                              double h, double floor_z, double* coeffs, int32_t precision,

@@ -917,17 +917,18 @@ lp_status lp_fit_derivatives(lp_ctx* c, const lp_particles* p, const lp_neighbor
                              const double* const* fields, const double* mirror_sign, int32_t nf,
                              double h, double floor_z, double* coeffs, int32_t precision,
                              void* stream) {
-  if (!c || !nb || !fields || !mirror_sign || !coeffs) return LP_ERR_INVALID_ARG;
+  if (!c || !nb || !fields || !mirror_sign) return LP_ERR_INVALID_ARG;
   c->lists_valid = false;  // uses the buffers the kept Verlet lists live in
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, p, offs, false));
+  if (p->n > 0 && !coeffs) return LP_ERR_INVALID_ARG;  // (empty arrays may be NULL)
   if (nf < 1 || nf > kMaxFields || !finite_pos(h) || !std::isfinite(floor_z) ||
       (precision != LP_FP64 && precision != LP_MIXED && precision != LP_MIXED_FF) ||
       nb->n != p->n || !nb->nbr || !nb->cnt ||
       nb->cap < 1 || nb->cap > LP_MAX_CAP)
     return LP_ERR_INVALID_ARG;
   for (int f = 0; f < nf; ++f)
-    if (!fields[f] || !std::isfinite(mirror_sign[f])) return LP_ERR_INVALID_ARG;
+    if ((p->n > 0 && !fields[f]) || !std::isfinite(mirror_sign[f])) return LP_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   cudaSetDevice(c->device);
   if (p->n == 0) return LP_OK;

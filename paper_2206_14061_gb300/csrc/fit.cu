@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(128, 4) k_fit_gram_ff(const FitArgs F) {
     ff_moments_add(mo, ff_row_of<false>(hi, lo, F.xs[j].xh, F.xs[j].xl, code, K0));
   }
   ff G[kTri];
-  ff_gram(mo, G);
+  ff_gram_fo(mo, G);
 #pragma unroll
   for (int k = 0; k < kTri; ++k) G[k] = ff_norm(G[k]);
   if (!(ff_chol9(G, 1e-4f) && m >= kNB)) {

@@ -486,6 +486,25 @@ __device__ __forceinline__ void ff_gram(const ff* mo, ff* g) {
   g[tri(8, 6)] = mo[29];              g[tri(8, 7)] = mo[30];              g[tri(8, 8)] = mo[27];
 }
 
+// Order of the unknowns in the float-float factor: the six second-derivative
+// terms first, the gradient last (factor row i is unknown ff_unknown(i) of the
+// column order above), so that a solve that needs only the gradient stops its
+// back substitution after three rows.
+__host__ __device__ constexpr int ff_unknown(int i) { return i < 6 ? i + 3 : i - 6; }
+
+// packed Gram matrix in factor order
+__device__ __forceinline__ void ff_gram_fo(const ff* mo, ff* g) {
+  ff c[kTri];
+  ff_gram(mo, c);
+#pragma unroll
+  for (int i = 0; i < kNB; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const int a = ff_unknown(i), b = ff_unknown(j);
+      g[tri(i, j)] = c[a >= b ? tri(a, b) : tri(b, a)];
+    }
+}
+
 // In-place float-float Cholesky factor of a packed 9x9 Gram matrix (entries
 // normalised): the strictly lower entries become L and the diagonal 1/L_jj.
 // Same pivot test as chol9: the Schur complement of column j must stay above
@@ -516,11 +535,13 @@ __device__ __forceinline__ bool ff_chol9(ff* a, float rel_tol) {
 }
 
 // Solve L L^T c = r for NF right-hand sides at once with the factor that
-// gram_ff_body stored for particle s; each factor entry is loaded once per
-// sweep and used for every right-hand side. r (unnormalised accumulators on
-// entry) is overwritten by c.
+// gram_ff_body stored for particle s (unknowns in factor order; r and c in
+// column order); each factor entry is loaded once per sweep and used for
+// every right-hand side. r (unnormalised accumulators on entry) is
+// overwritten by c; with GRAD_ONLY only c[0..2] (the gradient), the other
+// entries are left holding intermediate values.
 // (L: this particle's factor, entry k at L[k * n])
-template <int NF>
+template <int NF, bool GRAD_ONLY = false>
 __device__ __forceinline__ void ff_chol_solve(const float2* L, int64_t n, ff (*r)[kNB]) {
   // one 8-byte load per entry
   auto at = [&](int k) {
@@ -529,27 +550,29 @@ __device__ __forceinline__ void ff_chol_solve(const float2* L, int64_t n, ff (*r
   };
 #pragma unroll
   for (int i = 0; i < kNB; ++i) {
+    const int qi = ff_unknown(i);
 #pragma unroll
     for (int k = 0; k < i; ++k) {
       const ff l = at(tri(i, k));
 #pragma unroll
-      for (int f = 0; f < NF; ++f) ff_acc(r[f][i], l, ff_neg(r[f][k]));
+      for (int f = 0; f < NF; ++f) ff_acc(r[f][qi], l, ff_neg(r[f][ff_unknown(k)]));
     }
     const ff inv = at(tri(i, i));
 #pragma unroll
-    for (int f = 0; f < NF; ++f) r[f][i] = ff_mul(ff_norm(r[f][i]), inv);
+    for (int f = 0; f < NF; ++f) r[f][qi] = ff_mul(ff_norm(r[f][qi]), inv);
   }
 #pragma unroll
-  for (int i = kNB - 1; i >= 0; --i) {
+  for (int i = kNB - 1; i >= (GRAD_ONLY ? kNB - 3 : 0); --i) {
+    const int qi = ff_unknown(i);
 #pragma unroll
     for (int k = i + 1; k < kNB; ++k) {
       const ff l = at(tri(k, i));
 #pragma unroll
-      for (int f = 0; f < NF; ++f) ff_acc(r[f][i], l, ff_neg(r[f][k]));
+      for (int f = 0; f < NF; ++f) ff_acc(r[f][qi], l, ff_neg(r[f][ff_unknown(k)]));
     }
     const ff inv = at(tri(i, i));
 #pragma unroll
-    for (int f = 0; f < NF; ++f) r[f][i] = ff_mul(ff_norm(r[f][i]), inv);
+    for (int f = 0; f < NF; ++f) r[f][qi] = ff_mul(ff_norm(r[f][qi]), inv);
   }
 }
 
@@ -685,7 +708,7 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
     mo[q] = fast_two_sum(d.h, __fadd_rn(d.l, mo[q].l));
   }
   ff G[kTri];
-  ff_gram(mo, G);
+  ff_gram_fo(mo, G);
 #pragma unroll
   for (int k = 0; k < kTri; ++k) G[k] = ff_norm(G[k]);
   const bool ok = ff_chol9(G, 1e-4f) && m >= kNB;
@@ -859,7 +882,7 @@ __device__ __forceinline__ void pass2_ff_grads(const StepArgs& A, int s, int m, 
       ff_acc(R[1][q], bv, a[q]);
     }
   }
-  ff_chol_solve<2>(A.Lff + s, A.n, R);
+  ff_chol_solve<2, true>(A.Lff + s, A.n, R);  // only the gradients are used
   const ff ih{A.K.ih_h, A.K.ih_l};
 #pragma unroll
   for (int q = 0; q < 3; ++q) {

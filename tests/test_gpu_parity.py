@@ -195,6 +195,36 @@ def test_fit_mixed_ff_mirrors_and_field_groups(dev, capi, orc):
     assert err <= 1e-8, err
 
 
+def test_fit_mixed_ff_limits(dev, capi, orc):
+    """Float-float fit at the field limit (16 fields: five groups of three and
+    one of one) against the oracle; 17 fields and an empty set."""
+    x, y, z, rad, fields, _ = W.sweep_lattice(n_side=10, nfields=16, index=9)
+    ctx = capi.Context(x.size, cap=64)
+    X = [T(a, dev) for a in (x, y, z)]
+    nb = capi.lp_build_neighbors(ctx, *X, radius=T(rad, dev), mirror_mode=0, cap=48,
+                                 keep_nearest=True)
+    ctx.sync()
+    nbr, cnt = nb.export()
+    ref, _ = orc.fit(x, y, z, nbr, cnt, fields, [1.0] * 16, 1e-3)
+    F = [T(f, dev) for f in fields]
+    got = capi.lp_fit_derivatives(ctx, *X, nb, F, [1.0] * 16, 1e-3,
+                                  precision=capi.LP_MIXED_FF).cpu().numpy()
+    ctx.sync()
+    err = _class_err(got, ref)
+    assert err <= 1e-8, err
+    with pytest.raises(capi.LpError) as e:
+        capi.lp_fit_derivatives(ctx, *X, nb, F + F[:1], [1.0] * 17, 1e-3,
+                                precision=capi.LP_MIXED_FF)
+    assert e.value.status == capi.LP_ERR_INVALID_ARG
+    # n = 0: nothing to do, no error
+    E = [torch.zeros(0, dtype=torch.float64, device=dev) for _ in range(3)]
+    nb0 = capi.lp_build_neighbors(ctx, *E, r_const=2.2e-3, mirror_mode=0, cap=48)
+    out = capi.lp_fit_derivatives(ctx, *E, nb0, [E[0]], [1.0], 1e-3,
+                                  precision=capi.LP_MIXED_FF)
+    ctx.sync()
+    assert out.shape == (0, 1, 9)
+
+
 def test_fit_fallback_matches_oracle_projection(dev, capi, orc):
     """Sparse clouds (m < 9) and planar stencils take the pivoted-QR path; the
     fitted values A c (unique even when the basic solution is not) match."""
@@ -539,8 +569,10 @@ def test_derivative_sweep_full_size(dev, capi, orc):
                                   precision=capi.LP_FP64).cpu().numpy()
     gmx = capi.lp_fit_derivatives(ctx, *X, nb, F, [1.0] * 4, 1e-3,
                                   precision=capi.LP_MIXED).cpu().numpy()
+    gff = capi.lp_fit_derivatives(ctx, *X, nb, F, [1.0] * 4, 1e-3,
+                                  precision=capi.LP_MIXED_FF).cpu().numpy()
     ctx.sync()
-    e64, emx = _class_err(g64, ref), _class_err(gmx, ref)
+    e64, emx, eff = _class_err(g64, ref), _class_err(gmx, ref), _class_err(gff, ref)
     # analytic derivatives of the seeded fields (interior particles)
     inner = ((x > 10e-3) & (x < 116e-3) & (y > 10e-3) & (y < 116e-3) & (z > 10e-3) & (z < 116e-3))
     ana = np.zeros((inner.sum(), 4, 9))
@@ -555,9 +587,10 @@ def test_derivative_sweep_full_size(dev, capi, orc):
                 ana[:, f, 3 + q] -= a[k] * kv[k, i1] * kv[k, i2] * s_
     ea = _class_err(ref[inner], ana)
     print(f"sweep 2,000,376: FP64 vs oracle {e64:.2e}, mixed vs oracle {emx:.2e}, "
-          f"oracle vs analytic {ea:.2e}")
+          f"float-float vs oracle {eff:.2e}, oracle vs analytic {ea:.2e}")
     assert e64 <= 1e-11, e64
     assert emx <= 1e-5, emx
+    assert eff <= 1e-8, eff
 
 
 def test_columns_smallest_four_match_oracle(dev, capi, orc):
