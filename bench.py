@@ -40,7 +40,7 @@ B_ALG = 128.0  # algorithmic bytes per particle update: read+write x,u,V (112) +
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("mixed_ff", "mixed", "fp64"), default="mixed_ff")
@@ -72,37 +72,64 @@ def dist_info():
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling during the timed region: sampling
+    starts (first line read) before the region opens; the samples kept are
+    those read between the host times that bracket it."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 20):
         self.gpu = gpu_index
+        self.interval = interval_ms
         self.proc = None
+        self.lines = []
+        self.reader = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line))
 
     def start(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                 "-lms", str(self.interval), "-i", str(self.gpu)], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        t = time.perf_counter()
+        while not self.lines and time.perf_counter() - t < 10.0 and self.proc.poll() is None:
+            time.sleep(0.005)
 
-    def stop(self) -> dict:
+    def stop(self, t0: float, t1: float) -> dict:
+        """Summary of the samples read between host times t0 and t1 (the
+        nearest one after t1 if none fell inside)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(2.5 * self.interval / 1e3)  # the sample in flight at t1
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        if self.reader is not None:
+            self.reader.join(timeout=5)
+        inside = [ln for ts, ln in self.lines if t0 <= ts <= t1]
+        window = "timed region"
+        if not inside:
+            after = [ln for ts, ln in self.lines if ts > t1]
+            inside = after[:1]
+            window = "first sample after the timed region"
         sm, smax, reasons, power = [], [], set(), []
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in out.strip().splitlines():
+        for line in inside:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -118,7 +145,8 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "interval_ms": self.interval, "window": window,
+                "reasons": sorted(reasons)}
 
 
 # ------------------------------------------------------------- our path
@@ -250,8 +278,9 @@ def our_arm(args):
         ctx.phase_times(stream)  # reset counters
         clocks = ClockSampler(local)
         clocks.start()
+        t0 = time.perf_counter()
         ms = timed(args.steps, prec)
-        ck = clocks.stop()
+        ck = clocks.stop(t0, time.perf_counter())
         pt = ctx.phase_times(stream)
         diag = ctx.sync(stream, raise_on_error=False)
         # per-kernel durations, measured with events on the launch stream
@@ -614,6 +643,9 @@ def cpu_baseline(wl, pd, budget_s=20.0, steps=None):
 
 # -------------------------------------------------------------- reference
 
+REF_BUDGET_S = 120.0
+
+
 def reference_arm(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -627,25 +659,31 @@ def reference_arm(args):
     p = O.params(**pd)
     # warm-up steps (from the initial state), then the timed sample
     t_w = time.perf_counter()
-    for _ in range(max(args.warmup, 0)):
+    for _ in range(max(args.warmup, 1)):
         O.step(wl.state, p, 1, brute=False)
     t_step = (time.perf_counter() - t_w) / max(args.warmup, 1)
+    # the timed sample is bounded to about REF_BUDGET_S seconds: at most K
+    # steps, fewer when K steps of the oracle would take longer
+    steps = max(1, min(args.steps, int(REF_BUDGET_S / max(t_step, 1e-9))))
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         O.step(wl.state, p, 1, brute=False)
     el = time.perf_counter() - t0
-    value = wl.n * args.steps / el
+    value = wl.n * steps / el
     cores = O.max_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "steps": steps, "steps_requested": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded jittered lattice column)",
             "config": {"workload": "cylindrical column collapse R=0.02 m H=2R h=R/50 "
                                    f"({wl.n} particles), FP64 CPU oracle",
                        "precision": "fp64"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} full LP steps of the {wl.n}-particle column "
-                                       f"from its initial state ({t_step:.2f} s per step)"},
+                             "sample": f"{steps} full LP steps of the {wl.n}-particle column "
+                                       f"from its initial state ({t_step:.2f} s per step; "
+                                       f"{args.steps} requested, bounded to about "
+                                       f"{REF_BUDGET_S:.0f} s)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -291,3 +291,25 @@ def test_periodic_adjoint_matches_oracle_tangent(dev, capi, orc):
             fd = (loss(sp) - loss(sm)) / (2 * eps)
             a = float(gi[k][i].item())
             assert abs(fd - a) <= 1e-5 * abs(a) + 1e-6, (i, k, fd, a)
+
+
+@pytest.mark.slow
+def test_periodic_layer_full_size(dev, capi, orc):
+    """The periodic layer at the benchmark's size (162 x 162 x 30 = 787,320
+    particles), periodic along x and y, free-surface ghosts, in the benchmark's
+    launch configuration (graph replay on a stream, Verlet skin 0.1 h), here
+    sliding down the incline so that every state component moves: three steps
+    against the oracle on every particle, FP64 within 1e-9 and float-float
+    within 1e-8."""
+    s0, pd, L = _layer(n_xy=162)
+    ref, rd = orc.step(s0, _opar(orc, pd, free_surface=1), 3, brute=False)
+    stream = torch.cuda.Stream()
+    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+        got, d = _run_gpu(capi, dev, s0, pd, 3, stream=stream, precision=prec,
+                          launch_mode=capi.LP_LAUNCH_GRAPH, skin=0.1 * pd["h"], free_surface=1)
+        e = _state_err(got, ref, s0, L)
+        print(f"periodic layer 787,320, precision {prec}, 3-step errors:",
+              {k: f"{v:.2e}" for k, v in e.items()})
+        assert max(e.values()) <= tol, (prec, e)
+        assert d["n_nonfinite"] == 0 and d["n_overflow"] == 0
+        assert d["n_ghosts"] == rd["n_ghosts"], (d["n_ghosts"], rd["n_ghosts"])
