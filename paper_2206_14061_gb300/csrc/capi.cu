@@ -131,6 +131,7 @@ struct lp_ctx {
   float2* fit_fs = nullptr;  // split fields of lp_fit_derivatives (LP_MIXED_FF), lazily
   int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
   int32_t* gcnt = nullptr;    // ghost entries per stencil
+  int32_t* perm = nullptr;    // fit thread -> particle (LP_MIXED_FF)
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
   double* Y0[7] = {};                  // Heun: state at the start of the step (on first use)
   float2* Lff = nullptr;     // float-float Cholesky factors (LP_MIXED_FF), (hi, lo) pairs
@@ -397,6 +398,7 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.K = K;
   A.grids = c->d_grids;
   A.XU = c->XU; A.Lff = c->Lff; A.P1s = c->P1s;
+  A.perm = LP_ROW_ORDER ? c->perm : nullptr;
   A.Xfix = c->Xfix;
   A.gcnt = c->gcnt;
   A.Tg = c->Tg; A.T2 = c->T2;
@@ -476,7 +478,7 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
   phase_mark(c, LP_PHASE_PASS2, true, st);
   launch_pass2(prec, A, st, c->bs_p2);
   phase_mark(c, LP_PHASE_PASS2, false, st);
-  c->launches += prec == LP_MIXED_FF ? (K.free_surface ? 9 : 7) : 4;
+  c->launches += prec == LP_MIXED_FF ? (K.free_surface ? 9 : 7) + (A.perm ? 1 : 0) : 4;
   c->steps += 1;
   c->cx ^= 1;
 }
@@ -697,6 +699,7 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->Lff, n * kTri);
   if (s == LP_OK) s = dalloc(c, &c->Xfix, n);
   if (s == LP_OK) s = dalloc(c, &c->gcnt, n);
+  if (s == LP_OK) s = dalloc(c, &c->perm, n);
   c->capc = std::min(c->cap + 32, 96);
   if (s == LP_OK) s = dalloc(c, &c->cand, n * c->capc);
   if (s == LP_OK) s = dalloc(c, &c->ccnt, n);

@@ -52,16 +52,48 @@ __global__ void __launch_bounds__(64) k_pass2_fallback(const StepArgs A) {
 // float-float kernels: 128 threads per block, at most 128 registers so that
 // 4 blocks (16 warps) share an SM
 constexpr int kFFBlock = 128;
+// Fit threads take the particles of each group of kRowGroup in order of
+// stencil size: a warp's lanes then have similar row counts and fewer idle
+// at the end of the row loops. perm[g kRowGroup + t] is the particle of rank
+// t in group g by (rows, index); the arithmetic of each particle is
+// unchanged, only the thread that does it.
+constexpr int kRowGroup = 128;
+__global__ void __launch_bounds__(kRowGroup) k_row_order(int n, const int32_t* __restrict__ cnt,
+                                                         int32_t* __restrict__ perm) {
+  __shared__ uint32_t key[kRowGroup];
+  const int base = blockIdx.x * kRowGroup, t = threadIdx.x, s = base + t;
+  key[t] = s < n ? ((uint32_t)min(max(cnt[s], 0), 0xffff) << 16) | (uint32_t)t : 0xffffffffu;
+  __syncthreads();
+  // bitonic sort of the 128 keys, ascending (past-the-end keys sort last)
+  for (int k = 2; k <= kRowGroup; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int p = t ^ j;
+      if (p > t) {
+        const uint32_t a = key[t], b = key[p];
+        if ((a > b) == ((t & k) == 0)) {
+          key[t] = b;
+          key[p] = a;
+        }
+      }
+      __syncthreads();
+    }
+  if (s < n) perm[s] = base + (int)(key[t] & 0xffffu);
+}
+__device__ __forceinline__ int fit_particle(const StepArgs& A) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  return (A.perm && t < A.n) ? A.perm[t] : t;
+}
+
 // (PER: periodic axes, offsets take their nearest image)
 template <bool PER>
 __global__ void __launch_bounds__(kFFBlock, 4) k_gram_ff(const StepArgs A) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = fit_particle(A);
   if (s < A.n) gram_ff_body<PER>(A, s);
 }
 
 template <bool PER>
 __global__ void __launch_bounds__(kFFBlock, 4) k_pass1_ff(const StepArgs A) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = fit_particle(A);
   if (s < A.n) pass1_body<LP_MIXED_FF, PER>(A, s);
 }
 
@@ -95,7 +127,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_pass2(const StepArgs A) {
 
 template <bool PER>
 __global__ void __launch_bounds__(kFFBlock, 4) k_pass2_ff(const StepArgs A) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = fit_particle(A);
   pass2_body<LP_MIXED_FF, PER>(A, s, s < A.n);
 }
 
@@ -401,6 +433,7 @@ void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs) {
     else k_pass1<LP_MIXED, false><<<nb, bs, 0, st>>>(A);
   } else {
     k_split_state<<<(A.n + 255) / 256, 256, 0, st>>>(A);
+    if (A.perm) k_row_order<<<(A.n + kRowGroup - 1) / kRowGroup, kRowGroup, 0, st>>>(A.n, A.cnt, const_cast<int32_t*>(A.perm));
     const int b = bs < kFFBlock ? bs : kFFBlock;
     const int ng = (A.n + 127) / 128, nf = (A.n + b - 1) / b;
     if (per) {

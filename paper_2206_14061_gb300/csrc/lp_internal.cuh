@@ -25,6 +25,9 @@ constexpr int kMaxBlock = 256;    // largest block size the tuner may pick
 #define LP_FILTER_CHUNK 8
 #endif
 constexpr int kFilterChunk = LP_FILTER_CHUNK;  // candidates whose gathers the filter issues together
+#ifndef LP_ROW_ORDER
+#define LP_ROW_ORDER 1  // fit threads take particles sorted by stencil size (k_row_order)
+#endif
 #ifndef LP_SEARCH_CHUNK
 #define LP_SEARCH_CHUNK 4
 #endif
@@ -264,6 +267,8 @@ struct StepArgs {
                     // (Gram moments 62 x n, pass-2 right-hand sides 36 x n)
   float2* Lff;      // 45 * n: float-float Cholesky factor of the Gram matrix,
                     // (hi, lo) pairs, k-major; the diagonal holds 1/L_jj
+  const int32_t* perm;  // LP_MIXED_FF: particle of each fit thread (stencil
+                        // sizes sorted within groups of 128), or NULL
   // Verlet candidate lists: positions at the last search and the flag that
   // requests a new search when a particle has moved more than skin/2
   const double* xref;  // 3 * n, or NULL when candidate lists are off
