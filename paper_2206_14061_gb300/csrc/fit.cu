@@ -57,7 +57,13 @@ constexpr int kFFBlock = 128;
 // at the end of the row loops. perm[g kRowGroup + t] is the particle of rank
 // t in group g by (rows, index); the arithmetic of each particle is
 // unchanged, only the thread that does it.
-constexpr int kRowGroup = 128;
+#ifndef LP_ROW_GROUP
+#define LP_ROW_GROUP 128
+#endif
+#ifndef LP_PASS2_BLOCKS
+#define LP_PASS2_BLOCKS 4
+#endif
+constexpr int kRowGroup = LP_ROW_GROUP;
 __global__ void __launch_bounds__(kRowGroup) k_row_order(int n, const int32_t* __restrict__ cnt,
                                                          int32_t* __restrict__ perm) {
   __shared__ uint32_t key[kRowGroup];
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_pass2(const StepArgs A) {
 }
 
 template <bool PER>
-__global__ void __launch_bounds__(kFFBlock, 4) k_pass2_ff(const StepArgs A) {
+__global__ void __launch_bounds__(kFFBlock, LP_PASS2_BLOCKS) k_pass2_ff(const StepArgs A) {
   const int s = fit_particle(A);
   pass2_body<LP_MIXED_FF, PER>(A, s, s < A.n);
 }

@@ -725,8 +725,11 @@ __device__ __forceinline__ void gram_ff_body(const StepArgs& A, int s) {
 
 // Derived values of pass 1 from float-float coefficients (as pass1_finish):
 // gdot, |gdot|, (1/2) Lap u + (1/6) grad div u and div u are formed in
-// float-float and rounded to FP64 once each, so the per-particle FP64 work is
-// the 11 conversions and V^{n+1} = V^n + dt V^n div u (FP64).
+// float-float. Pass 2 takes gdot and ld as float-float (P1s); of the FP64
+// outputs it reads |gdot| and V^{n+1} = V^n + dt V^n div u (FP64) only, since
+// the FP64 gdot, ld and div u of a particle are read only when it was fitted
+// by the QR fallback, whose kernel writes them. So the per-particle FP64 work
+// is two conversions and the V update.
 __device__ __forceinline__ void pass1_finish_ff(const StepArgs& A, int s, const ff (*c)[kNB]) {
   const int n = A.n;
   const ff ih{A.K.ih_h, A.K.ih_l}, ih2{A.K.ih2_h, A.K.ih2_l};
@@ -752,12 +755,10 @@ __device__ __forceinline__ void pass1_finish_ff(const StepArgs& A, int s, const 
     gn = half.h > 0.f ? sqrt(ff_to_double(half)) : 0.0;  // (1/x^2 would overflow)
   }
   double* p = A.p1;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) p[(P1_GD + q) * n + s] = ff_to_double(gd[q]);
   p[P1_GN * n + s] = gn;
-  if (A.P1s)  // the float-float copy for the acceleration of pass 2
+  // the float-float copy for the acceleration of pass 2
 #pragma unroll
-    for (int q = 0; q < 6; ++q) A.P1s[(int64_t)q * n + s] = make_float2(gd[q].h, gd[q].l);
+  for (int q = 0; q < 6; ++q) A.P1s[(int64_t)q * n + s] = make_float2(gd[q].h, gd[q].l);
   // Hessian columns: 3 xx, 4 yy, 5 zz, 6 xy, 7 xz, 8 yz
   const ff dd[3] = {ff_add(ff_add(c[0][3], c[1][6]), c[2][7]),
                     ff_add(ff_add(c[0][6], c[1][4]), c[2][8]),
@@ -766,12 +767,10 @@ __device__ __forceinline__ void pass1_finish_ff(const StepArgs& A, int s, const 
   for (int a = 0; a < 3; ++a) {
     const ff lap = ff_add(ff_add(c[a][3], c[a][4]), c[a][5]);
     const ff ld = ff_mul(ff_add(ff_scale(lap, 0.5f), ff_mul(dd[a], sixth)), ih2);
-    p[(P1_LD + a) * n + s] = ff_to_double(ld);
-    if (A.P1s) A.P1s[(int64_t)(6 + a) * n + s] = make_float2(ld.h, ld.l);
+    A.P1s[(int64_t)(6 + a) * n + s] = make_float2(ld.h, ld.l);
   }
   const double Vi = A.V[s], dv = ff_to_double(div);
   p[P1_VN * n + s] = Vi + A.K.dt * (Vi * dv);
-  p[P1_DIV * n + s] = dv;
 }
 
 // pass 1 in float-float: right-hand sides of u, v, w and the solves
