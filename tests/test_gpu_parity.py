@@ -530,10 +530,19 @@ def test_step_edge_cases(dev, capi, orc):
                V=np.array([1 / 0.585]))
     wl1 = W.Workload("one", pd["h"], pd["radius"], pd["dt"], one)
     ref, _ = orc.step(one, orc.params(**pd), 5)
-    got, d = _run_gpu(capi, dev, wl1, pd, 5)
-    assert d["n_fallback"] > 0
-    for k in capi.FIELDS:
-        assert np.allclose(got[k], ref[k], rtol=1e-12, atol=1e-18), k
+    for prec in (0, 2):
+        got, d = _run_gpu(capi, dev, wl1, pd, 5, prec=prec)
+        assert d["n_fallback"] > 0
+        for k in capi.FIELDS:
+            assert np.allclose(got[k], ref[k], rtol=1e-12, atol=1e-18), (prec, k)
+    # a few particles (one partial group of fit threads), float-float and FP64
+    few = W.cube(3)
+    pf = W.param_dict(few)
+    ref, _ = orc.step(few.state, orc.params(**pf), 3)
+    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+        got, _ = _run_gpu(capi, dev, few, pf, 3, prec=prec)
+        e = _state_err(got, ref, few.state)
+        assert max(e.values()) <= tol, (prec, e)
     # invalid arguments are rejected on the host
     with pytest.raises(capi.LpError) as e:
         capi.lp_step(ctx, {k: T(one[k], dev) for k in capi.FIELDS}, m, eos,
