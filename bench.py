@@ -71,6 +71,37 @@ def dist_info():
 
 # ------------------------------------------------------------------ clocks
 
+def clock_summary(lines, t0: float, t1: float, interval_ms: int) -> dict:
+    """Summary of nvidia-smi sample lines [(host time, csv line)] read between
+    host times t0 and t1 (the first one after t1 if none fell inside): median
+    and maximum SM clock, peak power, and the throttle reasons seen active."""
+    inside = [ln for ts, ln in lines if t0 <= ts <= t1]
+    window = "timed region"
+    if not inside:
+        inside = [ln for ts, ln in lines if ts > t1][:1]
+        window = "first sample after the timed region"
+    sm, smax, reasons, power = [], [], set(), []
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    for line in inside:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+            power.append(float(f[3]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "power_w_max": max(power) if power else None,
+            "samples": len(sm), "interval_ms": interval_ms, "window": window,
+            "reasons": sorted(reasons)}
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region: sampling
     starts (first line read) before the region opens; the samples kept are
@@ -121,32 +152,7 @@ class ClockSampler:
             self.proc.wait()
         if self.reader is not None:
             self.reader.join(timeout=5)
-        inside = [ln for ts, ln in self.lines if t0 <= ts <= t1]
-        window = "timed region"
-        if not inside:
-            after = [ln for ts, ln in self.lines if ts > t1]
-            inside = after[:1]
-            window = "first sample after the timed region"
-        sm, smax, reasons, power = [], [], set(), []
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in inside:
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-                power.append(float(f[3]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "power_w_max": max(power) if power else None,
-                "samples": len(sm), "interval_ms": self.interval, "window": window,
-                "reasons": sorted(reasons)}
+        return clock_summary(self.lines, t0, t1, self.interval)
 
 
 # ------------------------------------------------------------- our path
