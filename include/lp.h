@@ -56,9 +56,11 @@ typedef int32_t lp_status;
 #define LP_MIXED_FF 2 /* FP32 only on the stencil rows: offsets, moments and   */
                       /* right-hand sides accumulated as float-float (FP32     */
                       /* pairs, error-free transformations), the Gram matrix   */
-                      /* factored and solved in float-float (Cholesky); FP64   */
-                      /* per particle (derived values, closure, update) and in */
-                      /* the pivoted-QR fallback. lp_step only.                */
+                      /* factored and solved in float-float (Cholesky); the    */
+                      /* derived values and the inertial closure in            */
+                      /* float-float, rounded to FP64 once; FP64 for the       */
+                      /* regime test, the update and the pivoted-QR fallback.  */
+                      /* lp_step and lp_fit_derivatives.                       */
 
 /* time integration (lp_params.time_scheme) */
 #define LP_TIME_PAPER 0
