@@ -15,8 +15,9 @@
  * Conventions (all entry points):
  *   - Every call returns an lp_status. LP_OK is 0.
  *   - Particle arrays are CALLER-OWNED DEVICE pointers, FP64, structure of
- *     arrays, length n, in the caller's particle order. The library never
- *     frees them and never keeps them beyond the call.
+ *     arrays, length n, in the caller's particle order (lp_step also takes
+ *     HOST arrays, see there). The library never frees them and never keeps
+ *     them beyond the call.
  *   - The library owns its workspace through an opaque lp_ctx (one context
  *     per device; not thread-safe: serialise calls on one context).
  *   - Work is enqueued on the given CUDA stream (a cudaStream_t passed as
@@ -336,7 +337,14 @@ lp_status lp_mui_stress(lp_ctx* ctx, const lp_mui* mui, const lp_eos* eos, int64
  * and gives gdot, |gdot|, div u, (1/2) Lap u + (1/6) grad div u and
  * V^{n+1} = V^n + dt V^n div u^n; pass 2 fits |gdot| and V^{n+1} and gives the
  * acceleration from the pressure law and mu(I) stress at phi^{n+1}; then
- * u^{n+1} = u^n + dt a and x^{n+1} = x^n + dt (u^n + u^{n+1})/2. */
+ * u^{n+1} = u^n + dt a and x^{n+1} = x^n + dt (u^n + u^{n+1})/2.
+ * The seven state arrays are either all device arrays (stepped in place) or
+ * all HOST arrays: the call then copies them to a staging block of the
+ * context on the stream (one copy if they lie one after the other in the
+ * order x, y, z, u, v, w, V, each of n doubles), steps there and copies the
+ * result back on the stream; the arrays may be read once the stream has
+ * finished (pinned memory makes the copies asynchronous). A mix of host and
+ * device arrays is LP_ERR_INVALID_ARG. */
 lp_status lp_step(lp_ctx* ctx, lp_particles* p, const lp_mui* mui, const lp_eos* eos,
                   const lp_params* params, double dt, int32_t nsteps, void* stream);
 

@@ -180,12 +180,20 @@ def _ptr(t):
 FIELDS = ("x", "y", "z", "u", "v", "w", "V")
 
 
-def _particles(state: dict, column_offsets=None, need_state=True):
+def _host(t: torch.Tensor, name: str) -> torch.Tensor:
+    if (not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64
+            or not t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CPU tensor of torch.float64")
+    return t
+
+
+def _particles(state: dict, column_offsets=None, need_state=True, allow_host=False):
     n = state["x"].numel()
     p = LpParticles()
+    host = allow_host and not state["x"].is_cuda
     for k in FIELDS:
         if k in state and state[k] is not None:
-            t = _dev(state[k], k)
+            t = _host(state[k], k) if host else _dev(state[k], k)
             if t.numel() != n:
                 raise ValueError("all particle arrays must have the same length")
             setattr(p, k, t.data_ptr())
@@ -375,8 +383,11 @@ def _mui_array(mui, ncol):
 
 def lp_step(ctx: Context, state: dict, mui, eos: dict, params: dict, dt: float, nsteps: int,
             column_offsets=None, stream=None):
-    """nsteps LP steps in place on the CUDA tensors of `state`."""
-    p, keep = _particles(state, column_offsets)
+    """nsteps LP steps in place on the tensors of `state`: all CUDA tensors,
+    or all CPU tensors (pinned for asynchronous copies), which the library
+    copies to the device and back on `stream`; read them after the stream
+    has finished."""
+    p, keep = _particles(state, column_offsets, allow_host=True)
     ma = _mui_array(mui, p.ncolumns)
     e, q = eos_struct(eos), params_struct(params)
     _check(lib().lp_step(ctx.handle, ctypes.byref(p), ma, ctypes.byref(e), ctypes.byref(q),

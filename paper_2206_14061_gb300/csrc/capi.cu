@@ -134,6 +134,7 @@ struct lp_ctx {
   int32_t* perm = nullptr;    // fit thread -> particle (LP_MIXED_FF)
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
   double* Y0[7] = {};                  // Heun: state at the start of the step (on first use)
+  double* stage = nullptr;             // lp_step on host arrays: 7 x cap_n (on first use)
   float2* Lff = nullptr;     // float-float Cholesky factors (LP_MIXED_FF), (hi, lo) pairs
   // Verlet candidate lists (lp_params.skin)
   int32_t* cand = nullptr;   // capc x n, k-major
@@ -1063,6 +1064,19 @@ int log2_bucket(int64_t v) {
 }
 }  // namespace
 
+namespace {
+// 1: the kernels can read the array in place (device or managed memory);
+// 0: host memory (pinned, registered or pageable)
+int device_readable(const void* ptr) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+}  // namespace
+
 lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* eos,
                   const lp_params* q, double dt, int32_t nsteps, void* stream) {
   if (!c || !mui || nsteps < 0) return LP_ERR_INVALID_ARG;
@@ -1074,6 +1088,46 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   cudaSetDevice(c->device);
   const int n = (int)p->n;
   if (n == 0 || nsteps == 0) return LP_OK;
+  {
+    // Host arrays (all seven): copied in on the stream, stepped in the
+    // context's staging block, copied back. Seven host arrays laid out one
+    // after the other (x, y, z, u, v, w, V, each of n) move in one copy each
+    // way.
+    double* f7[7] = {p->x, p->y, p->z, p->u, p->v, p->w, p->V};
+    int on_device = 0;
+    for (int f = 0; f < 7; ++f) on_device += device_readable(f7[f]);
+    if (on_device != 0 && on_device != 7) return LP_ERR_INVALID_ARG;  // mixed
+    if (on_device == 0) {
+      if (!c->stage) LP_TRY(dalloc(c, &c->stage, (size_t)7 * c->cap_n));
+      bool packed = true;
+      for (int f = 1; f < 7; ++f) packed = packed && f7[f] == f7[0] + (size_t)f * n;
+      const size_t bytes = sizeof(double) * (size_t)n;
+      if (packed) {
+        if (cudaMemcpyAsync(c->stage, f7[0], 7 * bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+          return LP_ERR_CUDA;
+      } else {
+        for (int f = 0; f < 7; ++f)
+          if (cudaMemcpyAsync(c->stage + (size_t)f * n, f7[f], bytes, cudaMemcpyHostToDevice,
+                              st) != cudaSuccess)
+            return LP_ERR_CUDA;
+      }
+      lp_particles d = *p;
+      double** dp[7] = {&d.x, &d.y, &d.z, &d.u, &d.v, &d.w, &d.V};
+      for (int f = 0; f < 7; ++f) *dp[f] = c->stage + (size_t)f * n;
+      const lp_status r = lp_step(c, &d, mui, eos, q, dt, nsteps, stream);
+      if (r != LP_OK) return r;
+      if (packed) {
+        if (cudaMemcpyAsync(f7[0], c->stage, 7 * bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+          return LP_ERR_CUDA;
+      } else {
+        for (int f = 0; f < 7; ++f)
+          if (cudaMemcpyAsync(f7[f], c->stage + (size_t)f * n, bytes, cudaMemcpyDeviceToHost,
+                              st) != cudaSuccess)
+            return LP_ERR_CUDA;
+      }
+      return cuda_status();
+    }
+  }
   const StepConsts K = step_consts(eos, q, dt, c->cap);
   // Verlet candidate lists: the grid must hold radius + skin in one cell. The
   // lists live for one call unless keep_lists asks to keep them for the next
