@@ -360,6 +360,70 @@ def test_free_fall_and_rigid_translation(orc):
     assert np.allclose(s2["u"], U[0], rtol=1e-13)
 
 
+def test_mass_equation_under_uniform_dilation(orc):
+    """Sec. 2.1 Eq. 1 in V = 1/phi, discretised by the first difference
+    equation of Sec. 3.1 item 8: V^{n+1} = V^n + dt V^n DIV(u^n). Under the
+    uniform dilation u = c (x - x0) the fit of a linear field is exact, so
+    DIV u = 3c and one step gives V^n (1 + 3 c dt). The dilation has no
+    deviatoric part (gdot = 0), so no stress acts: u keeps its values and x
+    moves to x0 + (1 + c dt)(x - x0), where the same field is
+    u = c/(1 + c dt) (x - x0): the second step gives V^1 (1 + 3 c dt/(1 + c dt))."""
+    rng = np.random.default_rng(21)
+    h = 1e-3
+    x, y, z = W.lattice_box(7, 7, 7, h, 0.05, rng)
+    z = z + 0.01
+    c = 150.0
+    x0 = np.array([3.1e-3, 3.7e-3, 1.35e-2])
+    V0 = 1.0 / 0.585
+    st = _state(x, y, z, c * (x - x0[0]), c * (y - x0[1]), c * (z - x0[2]),
+                np.full(x.size, V0))
+    p = _p(orc, mirror_mode=0, gz=0.0)
+    cdt = c * p.dt
+    s1, d1 = orc.step(st, p, 1)
+    assert d1["n_inertial"] == x.size
+    V1 = V0 * (1.0 + 3.0 * cdt)
+    assert np.abs(s1["V"] / V1 - 1.0).max() <= 1e-14
+    for k, o in zip("uvw", range(3)):
+        assert np.abs(s1[k] - st[k]).max() <= 1e-12 * c * h
+    s2, _ = orc.step(s1, p, 1)
+    V2 = V1 * (1.0 + 3.0 * cdt / (1.0 + cdt))
+    assert np.abs(s2["V"] / V2 - 1.0).max() <= 1e-14
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_floor_mirror_velocity_signs(orc, mode):
+    """Solid boundary (Sec. 3.1 item 9) with the floor at z = 0: a mirror at
+    z* = -z_j carries u* = -u_j on every component for the no-slip floor
+    (mode 1) and only the normal component reversed for free slip (mode 2).
+    The field u = (G1 z, G2 z, G3 z) is zero on the floor, so its odd
+    extension is the same linear field and every no-slip stencil fits it
+    exactly: gdot_xz = G1/2, gdot_yz = G2/2 and dw/dz = gdot_zz + div/3 = G3
+    in the floor layer. Free slip reverses w alone: dw/dz stays exact, while
+    the even extension of G1 z and G2 z (|z|-shaped) spoils gdot_xz and
+    gdot_yz in stencils that hold mirrors."""
+    rng = np.random.default_rng(22)
+    h = 1e-3
+    x, y, z = W.lattice_box(7, 7, 5, h, 0.05, rng)
+    G = np.array([40.0, -25.0, 10.0])
+    st = _state(x, y, z, G[0] * z, G[1] * z, G[2] * z)
+    p = _p(orc, mirror_mode=mode, gz=0.0)
+    nbr, cnt, _ = orc.step_stencils(x, y, z, p)
+    has_mirror = np.array([(nbr[i, :cnt[i]].astype(np.int64) & MB).any() for i in range(x.size)])
+    assert has_mirror.sum() >= 49
+    det = orc.step_detail(st, p)
+    gd = det["gdot"][has_mirror]
+    scale = np.abs(G).max()
+    err_xz = np.abs(gd[:, 4] - G[0] / 2).max() / scale
+    err_yz = np.abs(gd[:, 5] - G[1] / 2).max() / scale
+    dwdz = gd[:, 2] + det["div"][has_mirror] / 3
+    assert np.abs(dwdz - G[2]).max() <= 1e-12 * scale
+    if mode == 1:
+        assert max(err_xz, err_yz) <= 1e-12
+        assert np.abs(det["div"][has_mirror] - G[2]).max() <= 1e-12 * scale
+    else:
+        assert min(err_xz, err_yz) > 1e-3
+
+
 def _analytic_accel(pts, prm, G, eps_u, kk, phi0, dphi, gvec):
     """a_i = (1/(phi_s phi)) d_j sigma_ij + g_i with sigma = -P I + tau built
     from the primitive relations of Sec. 2.2: gdot = D - div/3 I, P from the
