@@ -300,26 +300,37 @@ lp_status lp_fit_derivatives(lp_ctx* ctx, const lp_particles* p, const lp_neighb
 #define LP_NOALLOC_MAX_PARTICLES (1 << 20)
 
 /* lp_fit_derivatives for callers that cannot allocate device memory (code
- * running inside an allocator or memory-pool hook, plug-ins whose host owns
- * every device allocation, loops that forbid allocation after start-up). The
- * paper has no counterpart; this is a deployment variant of the same fit.
- * Needs no lp_ctx and calls no cudaMalloc/cudaFree or allocating routine: its
- * only scratch (the pivoted-QR fallback queue, its counter and a diagnostics
- * word, about 4 MB) is a file-scope __device__ array that every GPU loading
- * the library holds until the process exits. Inputs and output are as in
- * lp_fit_derivatives, with the stencils passed directly: nbr (device, k-major
- * nbr[k*n + i], k < min(cnt[i], cap), particle index j or j | 2^31 for the
- * floor mirror of j) and cnt (device, n). Works on the current CUDA device.
- * n > LP_NOALLOC_MAX_PARTICLES is rejected with LP_ERR_INVALID_ARG. The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. All calls share the array
- * and clear its counter and diagnostics on entry, so calls whose work overlaps
- * on the GPU (other streams, other host threads) race: serialise them. */
+ * running inside an allocator or memory-pool hook, which must not re-enter the
+ * allocator; plug-ins whose host application owns every device allocation;
+ * loops that forbid allocation after start-up). The paper has no counterpart;
+ * this is a deployment variant of the same fit. Needs no lp_ctx and calls no
+ * cudaMalloc/cudaFree or allocating routine: its only scratch (the
+ * pivoted-QR fallback queue, its counter and a diagnostics word, about 4 MB)
+ * is a file-scope __device__ array that every GPU loading the library holds
+ * until the process exits.
+ * Inputs and output are as in lp_fit_derivatives, with the stencils passed
+ * directly: nbr (device, k-major nbr[k*n + i], k < min(cnt[i], cap), particle
+ * index j or j | 2^31 for the floor mirror of j; an index outside [0, n) is
+ * skipped, as if the entry were absent) and cnt (device, n). Works on the
+ * current CUDA device. Accepted: precision LP_FP64 or LP_MIXED (LP_MIXED_FF
+ * needs per-particle workspace and is LP_ERR_INVALID_ARG here);
+ * n <= LP_NOALLOC_MAX_PARTICLES (larger n is LP_ERR_INVALID_ARG).
+ * diag (HOST, may be NULL): if non-NULL, the call waits for `stream` and
+ * fills diag->n_fallback (stencils solved by the pivoted-QR fallback) and
+ * diag->flags; the other fields are 0. With diag NULL the call is
+ * asynchronous and reports no device-side counts.
+ * First call on a device: it looks up the array's device address
+ * (cudaGetSymbolAddress), which under CUDA's lazy module loading may also
+ * load the library's module and place the array and kernels in device
+ * memory. Make that first call at start-up, outside any allocator hook and
+ * before any stream capture. All calls share the array and clear its counter
+ * and diagnostics on entry, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race: serialise them. */
 lp_status lp_fit_derivatives_noalloc(int64_t n, const double* x, const double* y, const double* z,
                                      const int32_t* nbr, const int32_t* cnt, int32_t cap,
                                      const double* const* fields, const double* mirror_sign,
                                      int32_t nf, double h, double floor_z, double* coeffs,
-                                     int32_t precision, void* stream);
+                                     int32_t precision, void* stream, lp_diag* diag);
 
 /* Pointwise mu(I) stress (Sec. 2.2, 2.2.1) from V and the velocity gradient
  * grad_u (device, n x 9 row-major, grad_u[9i + 3a + b] = d u_a / d x_b):

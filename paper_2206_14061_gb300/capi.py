@@ -120,7 +120,8 @@ _SIGS = {
                             _vp], ctypes.c_int32),
     "lp_fit_derivatives_noalloc": ([ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32,
                                     _P(_vp), _P(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
-                                    ctypes.c_double, _vp, ctypes.c_int32, _vp], ctypes.c_int32),
+                                    ctypes.c_double, _vp, ctypes.c_int32, _vp, _P(LpDiag)],
+                                   ctypes.c_int32),
     "lp_mui_stress": ([_vp, _P(LpMui), _P(LpEos), ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp,
                        _vp, _vp], ctypes.c_int32),
     "lp_step": ([_vp, _P(LpParticles), _P(LpMui), _P(LpEos), _P(LpParams), ctypes.c_double,
@@ -333,10 +334,12 @@ NOALLOC_MAX_PARTICLES = 1 << 20
 
 
 def lp_fit_derivatives_noalloc(x, y, z, nbr, cnt, cap, fields, mirror_sign, h, out,
-                               floor_z=0.0, precision=LP_FP64, stream=None) -> torch.Tensor:
+                               floor_z=0.0, precision=LP_FP64, stream=None, diag=False):
     """The fit without a context and without any device allocation by the
     library: stencils nbr (int32, k-major [cap, n] or flat) and cnt (int32, n)
-    and the output `out` ([n, nf, 9] float64) are all supplied by the caller."""
+    and the output `out` ([n, nf, 9] float64) are all supplied by the caller.
+    With diag=True the call waits for the stream and returns (out, counts),
+    counts holding n_fallback and flags; otherwise it returns out."""
     n = x.numel()
     for t, nm in ((x, "x"), (y, "y"), (z, "z")):
         _dev(t, nm)
@@ -348,10 +351,14 @@ def lp_fit_derivatives_noalloc(x, y, z, nbr, cnt, cap, fields, mirror_sign, h, o
         _dev(f, f"fields[{i}]")
     fp = (_vp * nf)(*[f.data_ptr() for f in fields])
     ms = (ctypes.c_double * nf)(*[float(v) for v in mirror_sign])
+    dg = LpDiag() if diag else None
     _check(lib().lp_fit_derivatives_noalloc(n, _ptr(x), _ptr(y), _ptr(z), _ptr(nbr), _ptr(cnt),
                                             int(cap), fp, ms, nf, float(h), float(floor_z),
-                                            _ptr(out), int(precision), _stream(stream)),
+                                            _ptr(out), int(precision), _stream(stream),
+                                            ctypes.byref(dg) if diag else None),
            "lp_fit_derivatives_noalloc")
+    if diag:
+        return out, {"n_fallback": dg.n_fallback, "flags": dg.flags}
     return out
 
 

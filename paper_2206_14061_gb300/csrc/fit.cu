@@ -158,16 +158,18 @@ __global__ void __launch_bounds__(kBlock) k_fit(const FitArgs F) {
   using T = typename std::conditional<PREC == LP_FP64, double, float>::type;
   Moments<T> M;
   M.zero();
+  int rows = 0;  // entries with an index in range
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
     const int j = code & ~kMirrorBit;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const double zj = (code >> 31) ? F.f2 - F.z[j] : F.z[j];
     M.add(T((F.x[j] - xi) * ih), T((F.y[j] - yi) * ih), T((zj - zi) * ih));
+    ++rows;
   }
   T L[kTri];
   M.gram(L);
-  const bool ok = chol9(L, PREC == LP_FP64 ? T(1e-9) : T(1e-4)) && m >= kNB;
+  const bool ok = chol9(L, PREC == LP_FP64 ? T(1e-9) : T(1e-4)) && rows >= kNB;
   if (!ok) {
     const int slot = atomicAdd(F.fb_count, 1);
     if (slot < F.fb_cap) F.fb_list[slot] = s;
@@ -278,17 +280,19 @@ __global__ void __launch_bounds__(128, 4) k_fit_gram_ff(const FitArgs F) {
   ff mo[31];
 #pragma unroll
   for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
+  int rows = 0;  // entries with an index in range
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
     const int j = code & ~kMirrorBit;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     ff_moments_add(mo, ff_row_of<false>(hi, lo, F.xs[j].xh, F.xs[j].xl, code, K0));
+    ++rows;
   }
   ff G[kTri];
   ff_gram_fo(mo, G);
 #pragma unroll
   for (int k = 0; k < kTri; ++k) G[k] = ff_norm(G[k]);
-  if (!(ff_chol9(G, 1e-4f) && m >= kNB)) {
+  if (!(ff_chol9(G, 1e-4f) && rows >= kNB)) {
     const int slot = atomicAdd(F.fb_count, 1);
     if (slot < F.fb_cap) F.fb_list[slot] = s;
     else atomicOr(&F.dg->flags, (unsigned)LP_FLAG_OVERFLOW);
@@ -355,29 +359,35 @@ __global__ void __launch_bounds__(64) k_fit_fallback(const FitArgs F) {
     const int n = F.n;
     const int m = min(F.cnt[s], F.cap);
     const double xi = F.x[s], yi = F.y[s], zi = F.z[s];
+    // rows are packed: an entry whose index is out of range is dropped, as in
+    // the Cholesky path, and the rows after it move up
+    int rows = 0;
     for (int k = 0; k < m; ++k) {
       const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
       const int j = code & ~kMirrorBit;
       if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
       const double zj = (code >> 31) ? F.f2 - F.z[j] : F.z[j];
       taylor_row((F.x[j] - xi) * F.inv_h, (F.y[j] - yi) * F.inv_h, (zj - zi) * F.inv_h,
-                 &Acopy[k * kNB]);
+                 &Acopy[rows * kNB]);
+      ++rows;
     }
     for (int f0 = 0; f0 < F.nf; f0 += 4) {
       const int nf = min(4, F.nf - f0);
+      int r = 0;
       for (int k = 0; k < m; ++k) {
         const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
         const int j = code & ~kMirrorBit;
         if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
         const bool mir = code >> 31;
-        for (int q = 0; q < kNB; ++q) Am[k * kNB + q] = Acopy[k * kNB + q];
+        for (int q = 0; q < kNB; ++q) Am[r * kNB + q] = Acopy[r * kNB + q];
         for (int f = 0; f < nf; ++f) {
           double vj = F.fields[f0 + f][j];
           if (mir) vj *= F.msign[f0 + f];
-          Bm[k * nf + f] = vj - F.fields[f0 + f][s];
+          Bm[r * nf + f] = vj - F.fields[f0 + f][s];
         }
+        ++r;
       }
-      qr_pivoted_solve(m, Am, nf, Bm, C);
+      qr_pivoted_solve(rows, Am, nf, Bm, C);
       for (int f = 0; f < nf; ++f) write_coeffs(F, s, f0 + f, C + f * kNB);
     }
   }

@@ -60,7 +60,8 @@ extern "C" lp_status lp_fit_derivatives_noalloc(int64_t n, const double* x, cons
                                                 const double* const* fields,
                                                 const double* mirror_sign, int32_t nf, double h,
                                                 double floor_z, double* coeffs,
-                                                int32_t precision, void* stream) {
+                                                int32_t precision, void* stream,
+                                                lp_diag* diag) {
   if (n < 0 || n > LP_NOALLOC_MAX_PARTICLES) return LP_ERR_INVALID_ARG;
   if (nf < 1 || nf > kMaxFields || cap < 1 || cap > LP_MAX_CAP || !fields || !mirror_sign ||
       !(h > 0.0) || !(h < INFINITY) || !(floor_z == floor_z) ||
@@ -100,5 +101,22 @@ extern "C" lp_status lp_fit_derivatives_noalloc(int64_t n, const double* x, cons
   F.fb_cap = LP_NOALLOC_MAX_PARTICLES;
   F.dg = (DevDiag*)(b + kDiagOff);
   launch_fit(precision, F, st);
-  return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return LP_ERR_CUDA;
+  if (!diag) return LP_OK;
+  // the caller asked for the device-side counts: wait for the fit and copy
+  // the diagnostics word (a plain copy into this stack frame; no allocation)
+  DevDiag d;
+  if (cudaMemcpyAsync(&d, b + kDiagOff, sizeof(DevDiag), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_ERR_CUDA;
+  }
+  std::memset(diag, 0, sizeof(*diag));
+  diag->flags = d.flags;
+  diag->n_fallback = (int64_t)d.n_fallback;
+  // more stencils needed the QR fallback than the queue holds (cannot happen
+  // while the queue holds LP_NOALLOC_MAX_PARTICLES >= n entries)
+  if (d.flags & LP_FLAG_OVERFLOW) return LP_ERR_STENCIL_OVERFLOW;
+  return LP_OK;
 }

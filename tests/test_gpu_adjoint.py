@@ -70,7 +70,7 @@ def test_adjoint_matches_oracle_tangent_small(dev, orc):
     ref = np.array([sum((w[k] * tan[t, f]).sum() for f, k in enumerate(capi.FIELDS))
                     for t in range(3)])
     print("adjoint", got, "tangent", ref)
-    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max(), (got, ref)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max(), (got, ref)
     # dL/d(initial u) of a few particles against central differences of lp_step
     L = lambda st: sum(float((st[k].cpu().numpy() * w[k]).sum()) for k in capi.FIELDS)
     for i in (0, 77, 300):
@@ -154,8 +154,8 @@ def test_adjoint_column_against_finite_differences(dev, orc):
     print("all fields:        adjoint", g_lin, "tangent", ref_lin)
     print("velocities:        adjoint", g_vel, "FD", fd_vel)
     print("runout+profile:    adjoint", g_run, "tangent", ref_run, "FD", fd_run)
-    assert np.abs(g_lin - ref_lin).max() <= 1e-6 * np.abs(ref_lin).max(), (g_lin, ref_lin)
-    assert np.abs(g_run - ref_run).max() <= 1e-6 * np.abs(ref_run).max(), (g_run, ref_run)
+    assert np.abs(g_lin - ref_lin).max() <= 1e-9 * np.abs(ref_lin).max(), (g_lin, ref_lin)
+    assert np.abs(g_run - ref_run).max() <= 1e-9 * np.abs(ref_run).max(), (g_run, ref_run)
     assert np.abs(g_vel - fd_vel).max() <= 1e-5 * np.abs(g_vel).max(), (g_vel, fd_vel)
     # FD of the runout+profile loss is limited by round-off of the positions
     # (about 2e-12 absolute at step 1e-6: ulp(0.02 m) accumulated over the run)

@@ -109,7 +109,7 @@ def test_ghosts_mixed_precision_bounds(dev, capi, orc):
     wl = W.cube(20)
     pd = W.param_dict(wl)
     ref, rd = orc.step(wl.state, _orc_params(orc, pd), 50, brute=False)
-    for prec, tol in ((1, 1e-6), (2, 1e-8)):
+    for prec, tol in ((1, 1e-9), (2, 1e-10)):
         got, d = _run_gpu(capi, dev, wl, pd, 50, prec=prec)
         assert d["n_ghosts"] == rd["n_ghosts"], prec
         e = _state_err(got, ref, wl.state)
@@ -145,7 +145,7 @@ def test_ghosts_cylinder_column(dev, capi, orc):
     pd = W.param_dict(wl)
     ref, rd = orc.step(wl.state, _orc_params(orc, pd), 3, brute=False)
     assert rd["n_ghosts"] > 0
-    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
         got, d = _run_gpu(capi, dev, wl, pd, 3, prec=prec)
         assert d["n_ghosts"] == rd["n_ghosts"], prec
         e = _state_err(got, ref, wl.state)
@@ -191,7 +191,7 @@ def test_adjoint_with_ghosts_matches_oracle_tangent(dev, capi, orc):
     ref = np.array([sum((w[k] * tan[t, f]).sum() for f, k in enumerate(capi.FIELDS))
                     for t in range(3)])
     print("ghost adjoint", got, "tangent", ref)
-    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max(), (got, ref)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max(), (got, ref)
 
     def loss(state):
         st = {k: T(state[k], dev) for k in capi.FIELDS}

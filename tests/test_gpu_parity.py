@@ -171,7 +171,7 @@ def test_fit_mixed_ff_error_bound(dev, capi, sweep):
     sweep["ctx"].sync()
     err = _class_err(got.cpu().numpy(), sweep["ref"])
     print(f"float-float fit: max class error vs FP64 oracle = {err:.3e}")
-    assert err <= 1e-8, err
+    assert err <= 1e-9, err
 
 
 def test_fit_mixed_ff_mirrors_and_field_groups(dev, capi, orc):
@@ -192,7 +192,7 @@ def test_fit_mixed_ff_mirrors_and_field_groups(dev, capi, orc):
     ctx.sync()
     err = _class_err(got, ref)
     print(f"float-float fit with mirrors: max class error = {err:.3e}")
-    assert err <= 1e-8, err
+    assert err <= 1e-9, err
 
 
 def test_fit_mixed_ff_limits(dev, capi, orc):
@@ -211,7 +211,7 @@ def test_fit_mixed_ff_limits(dev, capi, orc):
                                   precision=capi.LP_MIXED_FF).cpu().numpy()
     ctx.sync()
     err = _class_err(got, ref)
-    assert err <= 1e-8, err
+    assert err <= 1e-9, err
     with pytest.raises(capi.LpError) as e:
         capi.lp_fit_derivatives(ctx, *X, nb, F + F[:1], [1.0] * 17, 1e-3,
                                 precision=capi.LP_MIXED_FF)
@@ -248,6 +248,48 @@ def test_fit_fallback_matches_oracle_projection(dev, capi, orc):
         d = ctx.sync()
         assert d["n_fallback"] > 0
         _check_projection(x, y, z, f, nbr, cnt, got, ref, n, 1e-9 if prec == capi.LP_FP64 else 1e-7)
+
+
+def test_fit_skips_out_of_range_entries(dev, capi):
+    """A stencil entry whose index is outside [0, n) is skipped as if absent:
+    every precision mode gives the bits of the same stencil without it, both
+    in the Cholesky path and in the pivoted-QR fallback (sparse stencils)."""
+    rng = np.random.default_rng(23)
+    n = 600
+    x = rng.uniform(0, 0.03, n)
+    y = rng.uniform(0, 0.03, n)
+    z = np.where(rng.uniform(size=n) < 0.5, 0.005, rng.uniform(0, 0.03, n))
+    f = np.stack([np.sin(100 * x) + y * 50, np.cos(70 * y) * z * 30])
+    ctx = capi.Context(n, cap=64)
+    X = [T(a, dev) for a in (x, y, z)]
+    F = [T(a, dev) for a in f]
+    nb = capi.lp_build_neighbors(ctx, *X, r_const=0.0042, mirror_mode=0, cap=64)
+    ctx.sync()
+    nbr, cnt = nb.export()
+    bad = nbr.copy()
+    bcnt = cnt.copy()
+    hit = np.flatnonzero((np.arange(n) % 3 == 0) & (cnt < 64))
+    for i in hit:  # insert an out-of-range index in the middle of the stencil
+        k = cnt[i] // 2
+        bad[i, k + 1:cnt[i] + 1] = nbr[i, k:cnt[i]]
+        bad[i, k] = n + 7 + i
+        bcnt[i] += 1
+    assert (cnt[hit] < 9).any() and (cnt[hit] >= 9).any()
+
+    def own(nb_rows, c):
+        t = torch.tensor(np.ascontiguousarray(nb_rows.T).ravel(), dtype=torch.int32, device=dev)
+        tc = torch.tensor(c, dtype=torch.int32, device=dev)
+        return (t, tc), capi.Neighbors(ctx, capi.LpNeighbors(t.data_ptr(), tc.data_ptr(), n, 64,
+                                                              0))
+    keep_a, nb_a = own(nbr, cnt)
+    keep_b, nb_b = own(bad, bcnt)
+    for prec in (capi.LP_FP64, capi.LP_MIXED, capi.LP_MIXED_FF):
+        a = capi.lp_fit_derivatives(ctx, *X, nb_a, F, [1, 1], 1e-3, precision=prec).cpu().numpy()
+        da = ctx.sync()
+        b = capi.lp_fit_derivatives(ctx, *X, nb_b, F, [1, 1], 1e-3, precision=prec).cpu().numpy()
+        db = ctx.sync()
+        assert da["n_fallback"] == db["n_fallback"] > 0, prec
+        assert np.array_equal(a, b), prec
 
 
 def _check_projection(x, y, z, f, nbr, cnt, got, ref, n, tol):
@@ -336,7 +378,7 @@ def test_step_mixed_error_bound(dev, capi, orc):
     got, d = _run_gpu(capi, dev, wl, pd, 50, prec=1)
     e = _state_err(got, ref, wl.state)
     print("MIXED 50-step errors:", {k: f"{v:.2e}" for k, v in e.items()})
-    assert max(e.values()) <= 1e-6, e
+    assert max(e.values()) <= 1e-9, e
 
 
 def test_step_mixed_ff_error_bound(dev, capi, orc):
@@ -347,7 +389,7 @@ def test_step_mixed_ff_error_bound(dev, capi, orc):
     got, d = _run_gpu(capi, dev, wl, pd, 50, prec=2)
     e = _state_err(got, ref, wl.state)
     print("MIXED_FF 50-step errors:", {k: f"{v:.2e}" for k, v in e.items()})
-    assert max(e.values()) <= 1e-8, e
+    assert max(e.values()) <= 1e-10, e
     assert d["n_nonfinite"] == 0
 
 
@@ -539,7 +581,7 @@ def test_step_edge_cases(dev, capi, orc):
     few = W.cube(3)
     pf = W.param_dict(few)
     ref, _ = orc.step(few.state, orc.params(**pf), 3)
-    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
         got, _ = _run_gpu(capi, dev, few, pf, 3, prec=prec)
         e = _state_err(got, ref, few.state)
         assert max(e.values()) <= tol, (prec, e)
@@ -599,7 +641,7 @@ def test_derivative_sweep_full_size(dev, capi, orc):
           f"float-float vs oracle {eff:.2e}, oracle vs analytic {ea:.2e}")
     assert e64 <= 1e-11, e64
     assert emx <= 1e-5, emx
-    assert eff <= 1e-8, eff
+    assert eff <= 1e-9, eff
 
 
 def test_columns_smallest_four_match_oracle(dev, capi, orc):
@@ -619,7 +661,7 @@ def test_columns_smallest_four_match_oracle(dev, capi, orc):
         sc = {k: v[b:e] for k, v in wl.state.items()}
         refs.append((sc, orc.step(sc, orc.params(**dict(pd, mu_s=float(wl.mu_s_col[c]))), 30,
                                   brute=False)[0]))
-    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
         got, d = _run_gpu(capi, dev, wl, pd, 30, prec=prec, offsets=offs, mui=mui_c,
                           launch_mode=1, stream=torch.cuda.Stream())
         assert d["n_nonfinite"] == 0
@@ -644,8 +686,40 @@ def test_step_full_size_cylinder(dev, capi, orc):
     gotm, _ = _run_gpu(capi, dev, wl, pd, 3, prec=1)
     em = _state_err(gotm, ref, wl.state)
     print("cylinder 3-step MIXED errors:", {k: f"{v:.2e}" for k, v in em.items()})
-    assert max(em.values()) <= 1e-6, em
+    assert max(em.values()) <= 1e-9, em
     gotf, _ = _run_gpu(capi, dev, wl, pd, 3, prec=2)
     ef = _state_err(gotf, ref, wl.state)
     print("cylinder 3-step MIXED_FF errors:", {k: f"{v:.2e}" for k, v in ef.items()})
-    assert max(ef.values()) <= 1e-8, ef
+    assert max(ef.values()) <= 1e-10, ef
+
+
+@pytest.mark.slow
+def test_step_full_size_cylinder_bench_configuration(dev, capi, orc):
+    """The benchmark's exact launch configuration on the full column (785k
+    particles): float-float fits, graph replay, Verlet skin 0.1h, two lp_step
+    calls of 10 steps from the initial state (the benchmark's restart). Both
+    calls give the same bits, within 1e-10 of the oracle's 10-step run on
+    every particle."""
+    wl = W.cylinder()
+    pd = W.param_dict(wl)
+    ref, _ = orc.step(wl.state, orc.params(**pd), 10, brute=False)
+    ctx = capi.Context(wl.n, cap=64)
+    m, eos = _dicts(pd)
+    init = {k: T(wl.state[k], dev) for k in capi.FIELDS}
+    st = {k: v.clone() for k, v in init.items()}
+    stream = torch.cuda.Stream()
+    prm = _prm(pd, precision=2, launch_mode=1, skin=0.1 * pd["h"])
+    outs = []
+    with torch.cuda.stream(stream):
+        for call in range(2):
+            for k in capi.FIELDS:
+                st[k].copy_(init[k])
+            capi.lp_step(ctx, st, m, eos, prm, pd["dt"], 10, stream=stream)
+            d = ctx.sync(stream)
+            assert d["n_nonfinite"] == 0
+            outs.append({k: st[k].cpu().numpy() for k in capi.FIELDS})
+    for k in capi.FIELDS:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    e = _state_err(outs[0], ref, wl.state)
+    print("cylinder 10-step bench configuration errors:", {k: f"{v:.2e}" for k, v in e.items()})
+    assert max(e.values()) <= 1e-10, e

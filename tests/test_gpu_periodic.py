@@ -87,11 +87,17 @@ def _rel(diff, scale):
     return d / m
 
 
-def _state_err(got, ref, s0, L):
+def _state_err(got, ref, s0, L, joint=False):
+    """Per-field relative errors. joint=True scales the x, y and z
+    displacement errors by the largest displacement component of any axis
+    (the displacement as one vector), for runs where one axis barely moves."""
     e = {}
+    disp = {k: _img(ref[k] - s0[k], L) for k in "xy"}
+    disp["z"] = ref["z"] - s0["z"]
+    dscale = max(np.abs(v).max() for v in disp.values())
     for k in "xy":
-        e[k] = _rel(_img(got[k] - ref[k], L), _img(ref[k] - s0[k], L))
-    e["z"] = _rel(got["z"] - ref["z"], ref["z"] - s0["z"])
+        e[k] = _rel(_img(got[k] - ref[k], L), dscale if joint else disp[k])
+    e["z"] = _rel(got["z"] - ref["z"], dscale if joint else disp["z"])
     for k in "uvw":
         e[k] = _rel(got[k] - ref[k], ref[k])
     e["V"] = _rel(got["V"] - ref["V"], ref["V"] - s0["V"])
@@ -117,7 +123,7 @@ def test_periodic_stencils_and_parity_50_steps(dev, capi, orc):
     ref, _ = orc.step(s0, _opar(orc, pd), 50, brute=False)
     crossed = int((ref["x"] < s0["x"] - 0.5 * L).sum())
     assert crossed > 100
-    for prec, tol in ((0, 1e-9), (1, 1e-6), (2, 1e-8)):
+    for prec, tol in ((0, 1e-9), (1, 1e-9), (2, 1e-10)):
         got, d = _run_gpu(capi, dev, s0, pd, 50, precision=prec)
         e = _state_err(got, ref, s0, L)
         print(f"periodic precision {prec} 50-step errors:", {k: f"{v:.2e}" for k, v in e.items()})
@@ -137,7 +143,7 @@ def test_one_periodic_axis_parity(dev, capi, orc, axes):
     pd = dict(pd, period_x=L if axes == "x" else 0.0, period_y=L if axes == "y" else 0.0)
     op = _opar(orc, pd, free_surface=1)
     ref, rd = orc.step(s0, op, 30, brute=False)
-    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
         got, d = _run_gpu(capi, dev, s0, pd, 30, precision=prec, free_surface=1)
         assert d["n_ghosts"] == rd["n_ghosts"], (axes, prec)
         e = _state_err(got, ref, s0, L)
@@ -156,7 +162,7 @@ def test_periodic_ghost_counts_and_parity(dev, capi, orc):
     _, d1 = _run_gpu(capi, dev, s0, pd, 1, free_surface=1)
     assert ref1 > 0 and d1["n_ghosts"] == ref1, (d1["n_ghosts"], ref1)
     ref, rd = orc.step(s0, op, 30, brute=False)
-    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
         got, d = _run_gpu(capi, dev, s0, pd, 30, precision=prec, free_surface=1)
         assert d["n_ghosts"] == rd["n_ghosts"], (prec, d["n_ghosts"], rd["n_ghosts"])
         e = _state_err(got, ref, s0, L)
@@ -167,7 +173,7 @@ def test_periodic_ghost_counts_and_parity(dev, capi, orc):
 def test_periodic_heun_parity(dev, capi, orc):
     s0, pd, L = _layer()
     ref, _ = orc.step(s0, _opar(orc, pd, time_scheme=1), 30, brute=False)
-    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
         got, _ = _run_gpu(capi, dev, s0, pd, 30, precision=prec, time_scheme=1)
         e = _state_err(got, ref, s0, L)
         assert max(e.values()) <= tol, (prec, e)
@@ -272,7 +278,7 @@ def test_periodic_adjoint_matches_oracle_tangent(dev, capi, orc):
     ref = np.array([sum((w[k] * tan[t, f]).sum() for f, k in enumerate(capi.FIELDS))
                     for t in range(3)])
     print("periodic adjoint", got, "tangent", ref)
-    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max(), (got, ref)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max(), (got, ref)
 
     def loss(state):
         st = {k: T(state[k], dev) for k in capi.FIELDS}
@@ -300,14 +306,15 @@ def test_periodic_layer_full_size(dev, capi, orc):
     launch configuration (graph replay on a stream, Verlet skin 0.1 h), here
     sliding down the incline so that every state component moves: three steps
     against the oracle on every particle, FP64 within 1e-9 and float-float
-    within 1e-8."""
+    within 1e-10 (displacement errors scaled by the largest displacement
+    component: across the slope, y barely moves)."""
     s0, pd, L = _layer(n_xy=162)
     ref, rd = orc.step(s0, _opar(orc, pd, free_surface=1), 3, brute=False)
     stream = torch.cuda.Stream()
-    for prec, tol in ((0, 1e-9), (2, 1e-8)):
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
         got, d = _run_gpu(capi, dev, s0, pd, 3, stream=stream, precision=prec,
                           launch_mode=capi.LP_LAUNCH_GRAPH, skin=0.1 * pd["h"], free_surface=1)
-        e = _state_err(got, ref, s0, L)
+        e = _state_err(got, ref, s0, L, joint=True)
         print(f"periodic layer 787,320, precision {prec}, 3-step errors:",
               {k: f"{v:.2e}" for k, v in e.items()})
         assert max(e.values()) <= tol, (prec, e)
