@@ -160,17 +160,22 @@ static inline T wrap_t(const T& x, double L) {
 // Inclusion predicate: d^2 <= r^2, evaluated in FP64 left to right with no
 // contraction; r*r is formed once by the caller. Offsets along periodic axes
 // are nearest images.
+// *oct receives the octant of the offset: bit 0 set for dx >= 0, bit 1 for
+// dy >= 0, bit 2 for dz >= 0.
 static inline bool in_ball(double xi, double yi, double zi, double xj, double yj,
-                           double zj, double r2, double* d2out, const Periods& P = Periods()) {
+                           double zj, double r2, double* d2out, const Periods& P,
+                           uint8_t* oct) {
   double dx = min_image(xj - xi, P.Lx), dy = min_image(yj - yi, P.Ly), dz = zj - zi;
   double d2 = ((dx * dx) + (dy * dy)) + (dz * dz);
   *d2out = d2;
+  *oct = (uint8_t)((dx >= 0.0 ? 1 : 0) | (dy >= 0.0 ? 2 : 0) | (dz >= 0.0 ? 4 : 0));
   return d2 <= r2;
 }
 
 struct Cand {
   double d2;
   uint32_t code;  // j, with MIRROR_BIT for the floor mirror of j
+  uint8_t oct;    // octant of the offset x_j - x_i (see in_ball)
 };
 static bool cand_near_less(const Cand& a, const Cand& b) {
   // nearest first; ties by particle index, then real before mirror
@@ -186,14 +191,34 @@ static bool cand_canon_less(const Cand& a, const Cand& b) {
   return (a.code & ~MIRROR_BIT) < (b.code & ~MIRROR_BIT);
 }
 
-// Finalise a stencil: optional truncation to the `cap` nearest, canonical
-// order, store. Returns 1 if the list did not fit (and was not truncated).
+// Finalise a stencil: optional truncation to `cap` entries, canonical order,
+// store. Returns 1 if the list did not fit (and was not truncated).
+// keep_nearest 1: the cap nearest. keep_nearest 2: octant-balanced ordering
+// (Sec. 3.1 item 6: the first entries of a list should lie in all
+// directions, in every neighbouring octant, rather than be the nearest ones
+// only): each candidate's rank among the candidates of its own octant,
+// nearest first, is its round; the list takes round 0 (the nearest of every
+// octant), then round 1, and so on, nearest first within a round, and keeps
+// the first cap.
 static int store_stencil(std::vector<Cand>& c, int32_t cap, int keep_nearest,
                          int32_t* row, int32_t* cnt) {
   int over = 0;
   if (keep_nearest && (int64_t)c.size() > cap) {
     std::sort(c.begin(), c.end(), cand_near_less);
-    c.resize(cap);
+    if (keep_nearest == 2) {
+      std::vector<int32_t> round(c.size());
+      int32_t seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (size_t k = 0; k < c.size(); ++k) round[k] = seen[c[k].oct]++;
+      std::vector<size_t> ord(c.size());
+      for (size_t k = 0; k < ord.size(); ++k) ord[k] = k;
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](size_t a, size_t b) { return round[a] < round[b]; });
+      std::vector<Cand> kept;
+      for (int32_t k = 0; k < cap; ++k) kept.push_back(c[ord[k]]);
+      c.swap(kept);
+    } else {
+      c.resize(cap);
+    }
   }
   std::sort(c.begin(), c.end(), cand_canon_less);
   int64_t m = (int64_t)c.size();
@@ -215,15 +240,17 @@ static int neighbors_brute(int64_t n, const double* x, const double* y, const do
     double r2 = r * r;
     std::vector<Cand> c;
     double d2;
+    uint8_t oc;
     for (int64_t j = 0; j < n; ++j) {
       if (j == i) continue;
-      if (in_ball(x[i], y[i], z[i], x[j], y[j], z[j], r2, &d2, P)) c.push_back({d2, (uint32_t)j});
+      if (in_ball(x[i], y[i], z[i], x[j], y[j], z[j], r2, &d2, P, &oc))
+        c.push_back({d2, (uint32_t)j, oc});
     }
     if (mirror_mode != 0) {
       for (int64_t j = 0; j < n; ++j) {
         double zm = 2.0 * floor_z - z[j];
-        if (in_ball(x[i], y[i], z[i], x[j], y[j], zm, r2, &d2, P))
-          c.push_back({d2, (uint32_t)j | MIRROR_BIT});
+        if (in_ball(x[i], y[i], z[i], x[j], y[j], zm, r2, &d2, P, &oc))
+          c.push_back({d2, (uint32_t)j | MIRROR_BIT, oc});
       }
     }
     over += store_stencil(c, cap, keep_nearest, nbr + i * (int64_t)cap, cnt + i);
@@ -292,6 +319,7 @@ static int neighbors_grid(int64_t n, const double* x, const double* y, const dou
     double r2 = r * r;
     std::vector<Cand> c;
     double d2;
+    uint8_t oc;
     for (int pass = 0; pass < (mirror_mode ? 2 : 1); ++pass) {
       // pass 0: around x_i; pass 1: around the reflected point, for mirrors
       double qz = pass == 0 ? z[i] : 2.0 * floor_z - z[i];
@@ -311,12 +339,12 @@ static int neighbors_grid(int64_t n, const double* x, const double* y, const dou
               int64_t j = order[t];
               if (pass == 0) {
                 if (j == i) continue;
-                if (in_ball(x[i], y[i], z[i], x[j], y[j], z[j], r2, &d2, P))
-                  c.push_back({d2, (uint32_t)j});
+                if (in_ball(x[i], y[i], z[i], x[j], y[j], z[j], r2, &d2, P, &oc))
+                  c.push_back({d2, (uint32_t)j, oc});
               } else {
                 double zm = 2.0 * floor_z - z[j];
-                if (in_ball(x[i], y[i], z[i], x[j], y[j], zm, r2, &d2, P))
-                  c.push_back({d2, (uint32_t)j | MIRROR_BIT});
+                if (in_ball(x[i], y[i], z[i], x[j], y[j], zm, r2, &d2, P, &oc))
+                  c.push_back({d2, (uint32_t)j | MIRROR_BIT, oc});
               }
             }
           }
@@ -896,6 +924,7 @@ int orc_max_threads(void) {
 // Neighbour lists. nbr is n x cap (row-major), entries j or (j | 0x80000000)
 // for the floor mirror of j, real particles first, each group ascending.
 // cnt[i] = stencil size (may exceed cap when keep_nearest == 0: overflow).
+// keep_nearest: 0 all, 1 the cap nearest, 2 octant-balanced (store_stencil).
 // Returns the number of overflowing particles.
 int orc_neighbors(int64_t n, const double* x, const double* y, const double* z,
                   const double* radius, double r_const, int mirror_mode, double floor_z,

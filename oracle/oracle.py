@@ -118,14 +118,17 @@ def neighbors(x, y, z, radius=None, r_const=0.0, mirror_mode=0, floor_z=0.0, cap
     """Stencils (Sec. 3.1 items 5-6). Returns (nbr [n, cap] int32, cnt [n], n_overflow).
 
     Entries are particle indices j, or j | 0x80000000 for the floor mirror of j;
-    real particles come first, each group in ascending index order."""
+    real particles come first, each group in ascending index order.
+    keep_nearest: False / 0 keeps all (cnt may exceed cap: overflow), True / 1
+    the cap nearest, 2 the first cap of the octant-balanced ordering (Sec. 3.1
+    item 6)."""
     x, y, z = _f64(x), _f64(y), _f64(z)
     n = x.size
     rad = None if radius is None else _f64(radius)
     nbr = np.zeros((n, cap), dtype=np.int32)
     cnt = np.zeros(n, dtype=np.int32)
     over = lib().orc_neighbors(n, _p(x), _p(y), _p(z), _p(rad), float(r_const), int(mirror_mode),
-                               float(floor_z), int(cap), int(bool(keep_nearest)), int(bool(brute)),
+                               float(floor_z), int(cap), int(keep_nearest), int(bool(brute)),
                                _p(nbr), _p(cnt), int(nthreads))
     return nbr, cnt, over
 

@@ -78,6 +78,59 @@ def test_neighbors_keep_nearest_matches_sorting(orc):
         assert got == ref
 
 
+def _octant_reference(x, y, z, rad, i, cap):
+    """Octant-balanced selection for particle i written with numpy: all
+    candidates (real and floor mirrors) within rad[i]; each one's round is its
+    rank, nearest first (ties by index, real before mirror), among the
+    candidates in its own octant (bit 0: dx >= 0, bit 1: dy >= 0, bit 2:
+    dz >= 0); the first cap by (round, distance, index, mirror) are kept."""
+    j = np.arange(x.size)
+    rows = []
+    for mir, zz in ((0, z), (1, -z)):
+        dx, dy, dz = x - x[i], y - y[i], zz - z[i]
+        d2 = (dx * dx + dy * dy) + dz * dz
+        ok = d2 <= rad[i] ** 2
+        if mir == 0:
+            ok &= j != i
+        oc = (dx >= 0).astype(int) + 2 * (dy >= 0) + 4 * (dz >= 0)
+        rows += [(d2[k], k, mir, oc[k]) for k in np.flatnonzero(ok)]
+    rows.sort()
+    seen = [0] * 8
+    keyed = []
+    for d2, k, mir, oc in rows:
+        keyed.append((seen[oc], d2, k, mir, oc))
+        seen[oc] += 1
+    keyed.sort()
+    return keyed[:cap], rows
+
+
+def test_neighbors_octant_balanced_matches_numpy(orc):
+    """Sec. 3.1 item 6: the kept entries of a truncated stencil should lie in
+    all directions. Against a numpy restatement of the selection; every
+    octant that has candidates keeps at least min(its candidates,
+    floor(cap / 8)) of them, so a one-sided cut never starves a direction the
+    way a nearest-only cut does near a face."""
+    rng = np.random.default_rng(12)
+    h = 1e-3
+    x, y, z = W.lattice_box(10, 10, 10, h, 0.2, rng)
+    rad = rng.uniform(1.8 * h, 2.6 * h, size=x.size)
+    cap = 48
+    nbr, cnt, _ = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, cap=cap, keep_nearest=2)
+    near, _, _ = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, cap=cap, keep_nearest=True)
+    differs = 0
+    for i in range(0, x.size, 5):
+        kept, allc = _octant_reference(x, y, z, rad, i, cap)
+        ref = set(k | (MB if m else 0) for _, _, k, m, _ in kept)
+        got = set(int(v) & 0xFFFFFFFF for v in nbr[i, :cnt[i]])
+        assert cnt[i] == min(cap, len(allc))
+        assert got == ref, i
+        n_oct = np.bincount([r[3] for r in allc], minlength=8)
+        k_oct = np.bincount([r[4] for r in kept], minlength=8)
+        assert (k_oct >= np.minimum(n_oct, cap // 8)).all(), (i, n_oct, k_oct)
+        differs += got != set(int(v) & 0xFFFFFFFF for v in near[i, :cnt[i]])
+    assert differs > 0  # truncation happens and the two rules differ
+
+
 def test_grid_search_equals_brute_force(orc):
     rng = np.random.default_rng(3)
     n = 3000
@@ -87,6 +140,11 @@ def test_grid_search_equals_brute_force(orc):
     a = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, brute=True)
     b = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, brute=False)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[0], b[0])
+    for keep in (1, 2):
+        a = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, cap=16, keep_nearest=keep)
+        b = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, cap=16, keep_nearest=keep,
+                          brute=False)
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[0], b[0])
 
 
 # ------------------------------------------------------------- GFD fits ---
