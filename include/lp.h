@@ -260,15 +260,28 @@ lp_status lp_ctx_profile(lp_ctx* ctx, int32_t enable);
 lp_status lp_ctx_phase_times(lp_ctx* ctx, void* stream, double* ms, int64_t* launches,
                              int64_t* steps);
 
+/* truncation rules of lp_build_neighbors (keep_nearest) */
+#define LP_KEEP_ALL 0      /* every neighbour; longer than cap: overflow         */
+#define LP_KEEP_NEAREST 1  /* the cap nearest                                    */
+#define LP_KEEP_OCTANTS 2  /* the first cap of the octant-balanced ordering      */
+
 /* Neighbour search (Sec. 3.1 items 5-6, mirrors item 9). For every particle i:
  * all j != i of the same column with ((dx*dx)+(dy*dy))+(dz*dz) <= r_i*r_i in
  * FP64 without contraction (d = x_j - x_i), and, if mirror_mode != NONE, every
  * mirror j* (including i*) passing the same test. r_i = radius[i] if radius
- * (device, length n) is non-NULL, else r_const. If keep_nearest != 0, only
- * the min(cap, m_i) nearest are kept (ties by index, real before mirror) and
- * cnt[i] is that number; otherwise cnt[i] is the full count and stencils
- * longer than cap set LP_FLAG_OVERFLOW. Order within a stencil is
- * unspecified. Result in *out (library-owned). */
+ * (device, length n) is non-NULL, else r_const. keep_nearest:
+ *   LP_KEEP_ALL: cnt[i] is the full count and stencils longer than cap set
+ *     LP_FLAG_OVERFLOW;
+ *   LP_KEEP_NEAREST: only the min(cap, m_i) nearest are kept (ties by index,
+ *     real before mirror) and cnt[i] is that number;
+ *   LP_KEEP_OCTANTS: octant-balanced stencils (Sec. 3.1 item 6, the first
+ *     entries of a list lie in all neighbouring octants): a candidate's round
+ *     is its rank, in the nearest-first order above, among the candidates in
+ *     its own octant (bit 0: dx >= 0, bit 1: dy >= 0, bit 2: dz >= 0); the
+ *     min(cap, m_i) first by (round, nearest-first order) are kept.
+ * At most 128 candidates per particle are considered by the two truncating
+ * rules (more set LP_FLAG_OVERFLOW). Other values are LP_ERR_INVALID_ARG.
+ * Order within a stencil is unspecified. Result in *out (library-owned). */
 lp_status lp_build_neighbors(lp_ctx* ctx, const lp_particles* p, const double* radius,
                              double r_const, int32_t mirror_mode, double floor_z, int32_t cap,
                              int32_t keep_nearest, lp_neighbors* out, void* stream);

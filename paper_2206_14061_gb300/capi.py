@@ -33,6 +33,9 @@ LP_MIRROR_NONE = 0
 LP_MIRROR_NOSLIP = 1
 LP_MIRROR_FREESLIP = 2
 LP_MAX_CAP = 64
+LP_KEEP_ALL = 0
+LP_KEEP_NEAREST = 1
+LP_KEEP_OCTANTS = 2
 LP_LAUNCH_KERNELS = 0
 LP_LAUNCH_GRAPH = 1
 LP_LAUNCH_PERSISTENT = 2
@@ -302,13 +305,15 @@ class Neighbors:
 def lp_build_neighbors(ctx: Context, x, y, z, radius=None, r_const=0.0, mirror_mode=1,
                        floor_z=0.0, cap=LP_MAX_CAP, keep_nearest=False, column_offsets=None,
                        stream=None) -> Neighbors:
+    """keep_nearest: False / LP_KEEP_ALL, True / LP_KEEP_NEAREST or
+    LP_KEEP_OCTANTS (octant-balanced truncation)."""
     p, keep = _particles(dict(x=x, y=y, z=z), column_offsets, need_state=False)
     if radius is not None:
         _dev(radius, "radius")
     s = LpNeighbors()
     _check(lib().lp_build_neighbors(ctx.handle, ctypes.byref(p), _ptr(radius), float(r_const),
                                     int(mirror_mode), float(floor_z), int(cap),
-                                    int(bool(keep_nearest)), ctypes.byref(s), _stream(stream)),
+                                    int(keep_nearest), ctypes.byref(s), _stream(stream)),
            "lp_build_neighbors")
     return Neighbors(ctx, s)
 

@@ -29,7 +29,7 @@ void launch_gather(int n, const int32_t* tmp, const double* const* src, double* 
                    int nsrc, const int32_t* ids_in, int32_t* ids_out, const int32_t* col_in,
                    int32_t* col_out, const GridCol* grids, float4* pf, cudaStream_t st,
                    const int32_t* iota = nullptr, const int* search = nullptr);
-void launch_neighbors(bool keep, int n, const double* x, const double* y, const double* z,
+void launch_neighbors(int keep, int n, const double* x, const double* y, const double* z,
                       const float4* pf, const int32_t* colid, const int32_t* ids,
                       const GridCol* grids, const uint32_t* start, const double* radius,
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
@@ -845,7 +845,8 @@ lp_status lp_build_neighbors(lp_ctx* c, const lp_particles* p, const double* rad
   c->lists_valid = false;  // uses the buffers the kept Verlet lists live in
   std::vector<int32_t> offs;
   LP_TRY(check_particles(c, p, offs, false));
-  if (cap < 1 || cap > c->cap || mirror_mode < 0 || mirror_mode > 2 || !std::isfinite(floor_z))
+  if (cap < 1 || cap > c->cap || mirror_mode < 0 || mirror_mode > 2 || !std::isfinite(floor_z) ||
+      keep_nearest < LP_KEEP_ALL || keep_nearest > LP_KEEP_OCTANTS)
     return LP_ERR_INVALID_ARG;
   if (!radius && !finite_pos(r_const)) return LP_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -874,7 +875,7 @@ lp_status lp_build_neighbors(lp_ctx* c, const lp_particles* p, const double* rad
   LP_TRY(setup_grids(c, p->ncolumns, rmax, st));
   sort_particles(c, n, 1, radius ? 4 : 3, st);
   const int e = c->cx;
-  launch_neighbors(keep_nearest != 0, n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf,
+  launch_neighbors(keep_nearest, n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf,
                    c->colid[c->ci], c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity,
                    radius ? c->X[e][7] : nullptr, r_const, mirror_mode, floor_z, cap, c->nbr,
                    c->cnt, c->dg, st);

@@ -139,11 +139,21 @@ __device__ __forceinline__ bool cand_less(double da, uint32_t ka, double db, uin
   return ka < kb;  // ka = (orig id << 1) | mirror
 }
 
+// octant-balanced ordering (Sec. 3.1 item 6): round first (a candidate's
+// rank within its own octant), then the nearest-first order
+__device__ __forceinline__ bool cand_less_oct(int ra, double da, uint32_t ka, int rb, double db,
+                                              uint32_t kb) {
+  if (ra != rb) return ra < rb;
+  return cand_less(da, ka, db, kb);
+}
+
 __device__ __forceinline__ void stencil_stats(bool live, int c, int cap, DevDiag* dg);
 
 // Stencil of particle s; every lane of the warp must call it (live or not).
 // stats = false leaves the stencil-size statistics alone (candidate lists).
-// PER: the grid may have periodic axes (GridCol::Lx, Ly)
+// PER: the grid may have periodic axes (GridCol::Lx, Ly).
+// KEEP: truncate to cap entries; keep_mode 1 keeps the cap nearest,
+// keep_mode 2 the first cap of the octant-balanced ordering.
 template <bool KEEP, bool PER = false>
 __device__ __forceinline__ void neighbors_body(
     int s, bool live, int n, const double* __restrict__ x, const double* __restrict__ y,
@@ -152,7 +162,7 @@ __device__ __forceinline__ void neighbors_body(
     const GridCol* __restrict__ grids, const uint32_t* __restrict__ start,
     const double* __restrict__ radius, double r_const, int mirror_mode, double floor_z, int cap,
     int32_t* __restrict__ nbr, int32_t* __restrict__ cnt, DevDiag* __restrict__ dg,
-    bool stats = true) {
+    bool stats = true, int keep_mode = 1) {
   int c = 0;
   bool over = false;
   if (live) {
@@ -179,6 +189,7 @@ __device__ __forceinline__ void neighbors_body(
     const float Lxf = g.Lxf, Lyf = g.Lyf;
     double cd2[KEEP ? kMaxCand : 1];
     uint32_t cj[KEEP ? kMaxCand : 1];
+    uint8_t co[KEEP ? kMaxCand : 1];  // octant: bit 0 dx >= 0, bit 1 dy >= 0, bit 2 dz >= 0
     const int ncx = g.nx, ncy = g.ny, ncz = g.nz;
     // periodic axes wrap (>= 3 cells); float tests keep the FP64 pipe free
     const bool perx = PER && g.Lxf > 0.f, pery = PER && g.Lyf > 0.f;
@@ -223,12 +234,17 @@ __device__ __forceinline__ void neighbors_body(
               if (!exact_only && d2f > hi) continue;
               double d2 = 0.0;
               bool in;
+              uint8_t oct = 0;
               if (!exact_only && d2f < lo && !KEEP) {
                 in = true;
               } else {
                 const double zj = pass == 0 ? z[j] : __dsub_rn(2.0 * floor_z, z[j]);
                 in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2, PER ? g.Lx : 0.0,
                               PER ? g.Ly : 0.0);
+                // (caller stencils are never periodic: the sign of x_j - x_i
+                // in FP64 is that of the comparison)
+                if (KEEP)
+                  oct = (uint8_t)((x[j] >= xi ? 1 : 0) | (y[j] >= yi ? 2 : 0) | (zj >= zi ? 4 : 0));
               }
               if (!in) continue;
               const uint32_t code = j | (pass ? kMirrorBit : 0u);
@@ -236,6 +252,7 @@ __device__ __forceinline__ void neighbors_body(
                 if (c < kMaxCand) {
                   cd2[c] = d2;
                   cj[c] = code;
+                  co[c] = oct;
                 } else {
                   over = true;
                 }
@@ -250,16 +267,36 @@ __device__ __forceinline__ void neighbors_body(
     if (KEEP) {
       int m = c < kMaxCand ? c : kMaxCand;
       if (m > cap) {
-        // partial selection sort: the cap nearest to the front
+        auto key = [&](uint32_t code) {
+          return ((uint32_t)ids[code & ~kMirrorBit] << 1) | (code >> 31);
+        };
+        // octant-balanced: each candidate's round is its nearest-first rank
+        // among the candidates of its own octant (stored over co[])
+        if (keep_mode == 2) {
+          uint8_t rk[kMaxCand];
+          for (int t = 0; t < m; ++t) {
+            const uint32_t kt = key(cj[t]);
+            int r = 0;
+            for (int u = 0; u < m; ++u)
+              r += (u != t && co[u] == co[t] && cand_less(cd2[u], key(cj[u]), cd2[t], kt));
+            rk[t] = (uint8_t)r;
+          }
+          for (int t = 0; t < m; ++t) co[t] = rk[t];
+        }
+        // partial selection sort: the first cap of the ordering to the front
         for (int t = 0; t < cap; ++t) {
           int best = t;
-          uint32_t kb = ((uint32_t)ids[cj[t] & ~kMirrorBit] << 1) | (cj[t] >> 31);
+          uint32_t kb = key(cj[t]);
           for (int u = t + 1; u < m; ++u) {
-            const uint32_t ku = ((uint32_t)ids[cj[u] & ~kMirrorBit] << 1) | (cj[u] >> 31);
-            if (cand_less(cd2[u], ku, cd2[best], kb)) { best = u; kb = ku; }
+            const uint32_t ku = key(cj[u]);
+            const bool less = keep_mode == 2
+                                  ? cand_less_oct(co[u], cd2[u], ku, co[best], cd2[best], kb)
+                                  : cand_less(cd2[u], ku, cd2[best], kb);
+            if (less) { best = u; kb = ku; }
           }
           const double td = cd2[t]; cd2[t] = cd2[best]; cd2[best] = td;
           const uint32_t tj = cj[t]; cj[t] = cj[best]; cj[best] = tj;
+          const uint8_t to = co[t]; co[t] = co[best]; co[best] = to;
         }
         m = cap;
       }

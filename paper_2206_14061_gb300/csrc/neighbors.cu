@@ -200,7 +200,8 @@ k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
             const GridCol* __restrict__ grids, const uint32_t* __restrict__ start,
             const double* __restrict__ radius, double r_const, int mirror_mode, double floor_z,
             int cap, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt,
-            DevDiag* __restrict__ dg, const int* search, double* __restrict__ xref) {
+            DevDiag* __restrict__ dg, const int* search, double* __restrict__ xref,
+            int keep_mode) {
   if (!searching(search)) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (xref && s < n) {  // positions of this search, for the displacement test
@@ -209,7 +210,7 @@ k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
     xref[2 * n + s] = z[s];
   }
   neighbors_body<KEEP, PER>(s, s < n, n, x, y, z, pf, colid, ids, grids, start, radius, r_const,
-                            mirror_mode, floor_z, cap, nbr, cnt, dg, xref == nullptr);
+                            mirror_mode, floor_z, cap, nbr, cnt, dg, xref == nullptr, keep_mode);
 }
 
 // Verlet filter (filter_body). Thread 0 clears the search flag for the
@@ -294,7 +295,9 @@ void launch_gather(int n, const int32_t* tmp, const double* const* src, double* 
   k_gather<<<(n + 255) / 256, 256, 0, st>>>(n, tmp, src, dst, nsrc, ids_in, ids_out, col_in,
                                             col_out, grids, pf, iota, search);
 }
-void launch_neighbors(bool keep, int n, const double* x, const double* y, const double* z,
+// keep: 0 every neighbour (overflow past cap), 1 the cap nearest, 2 the first
+// cap of the octant-balanced ordering
+void launch_neighbors(int keep, int n, const double* x, const double* y, const double* z,
                       const float4* pf, const int32_t* colid, const int32_t* ids,
                       const GridCol* grids, const uint32_t* start, const double* radius,
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
@@ -304,15 +307,15 @@ void launch_neighbors(bool keep, int n, const double* x, const double* y, const 
   if (keep)  // (stencils for callers: never periodic)
     k_neighbors<true, false><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
                                                  r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
-                                                 search, xref);
+                                                 search, xref, keep);
   else if (periodic)
     k_neighbors<false, true><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
                                                  r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
-                                                 search, xref);
+                                                 search, xref, 0);
   else
     k_neighbors<false, false><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start,
                                                   radius, r_const, mirror_mode, floor_z, cap, nbr,
-                                                  cnt, dg, search, xref);
+                                                  cnt, dg, search, xref, 0);
 }
 void launch_filter(int n, const double* x, const double* y, const double* z, const float4* pf,
                    const int32_t* cand, const int32_t* ccnt, int capc, const GridCol* grids,

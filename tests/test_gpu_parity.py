@@ -81,6 +81,28 @@ def test_neighbors_keep_nearest_per_particle_radius(dev, capi, orc):
     assert gcnt.max() == 48 and gcnt.min() >= 1
 
 
+def test_neighbors_octant_balanced_per_particle_radius(dev, capi, orc):
+    """Octant-balanced truncation (Sec. 3.1 item 6) bit-exact against the
+    oracle, with floor mirrors and per-particle radii; an unknown rule is
+    rejected on the host."""
+    x, y, z, rad, _, _ = W.sweep_lattice(n_side=18, nfields=1)
+    ref, rcnt, _ = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, cap=48, keep_nearest=2)
+    near, _, _ = orc.neighbors(x, y, z, radius=rad, mirror_mode=1, cap=48, keep_nearest=1)
+    ctx = capi.Context(x.size, cap=64)
+    X = [T(a, dev) for a in (x, y, z)]
+    nb = capi.lp_build_neighbors(ctx, *X, radius=T(rad, dev), mirror_mode=1, cap=48,
+                                 keep_nearest=capi.LP_KEEP_OCTANTS)
+    ctx.sync()
+    got, gcnt = nb.export()
+    assert np.array_equal(gcnt, rcnt)
+    assert np.array_equal(got, ref[:, :48])
+    assert not np.array_equal(ref, near)
+    with pytest.raises(capi.LpError) as e:
+        capi.lp_build_neighbors(ctx, *X, radius=T(rad, dev), mirror_mode=1, cap=48,
+                                keep_nearest=3)
+    assert e.value.status == capi.LP_ERR_INVALID_ARG
+
+
 def test_neighbors_stay_within_columns(dev, capi, orc):
     wl = W.columns(ncol=5, n_lo=300, n_hi=1500, only=[0, 1, 2, 3, 4])
     x, y, z = (wl.state[k] for k in "xyz")
@@ -641,6 +663,57 @@ def test_derivative_sweep_full_size(dev, capi, orc):
           f"float-float vs oracle {eff:.2e}, oracle vs analytic {ea:.2e}")
     assert e64 <= 1e-11, e64
     assert emx <= 1e-5, emx
+    assert eff <= 1e-9, eff
+
+
+@pytest.mark.slow
+def test_derivative_sweep_octant_balanced_full_size(dev, capi, orc):
+    """The 2,000,376-particle sweep with octant-balanced stencils: bit-exact
+    against the oracle on every particle, FP64 derivatives within 1e-11 and
+    float-float within 1e-9 of the oracle on those stencils. The error of
+    both truncation rules against the analytic derivatives is reported, in
+    the interior and near the faces."""
+    x, y, z, rad, fields, spec = W.sweep_lattice(n_side=126)
+    ref_nbr, ref_cnt, _ = orc.neighbors(x, y, z, radius=rad, mirror_mode=0, cap=48,
+                                        keep_nearest=2, brute=False)
+    ctx = capi.Context(x.size, cap=64)
+    X = [T(a, dev) for a in (x, y, z)]
+    nb = capi.lp_build_neighbors(ctx, *X, radius=T(rad, dev), mirror_mode=0, cap=48,
+                                 keep_nearest=capi.LP_KEEP_OCTANTS)
+    ctx.sync()
+    got_nbr, got_cnt = nb.export()
+    assert np.array_equal(got_cnt, ref_cnt)
+    assert np.array_equal(got_nbr, ref_nbr[:, :48])
+    ref, _ = orc.fit(x, y, z, ref_nbr, ref_cnt, fields, [1.0] * 4, 1e-3)
+    F = [T(f, dev) for f in fields]
+    g64 = capi.lp_fit_derivatives(ctx, *X, nb, F, [1.0] * 4, 1e-3,
+                                  precision=capi.LP_FP64).cpu().numpy()
+    gff = capi.lp_fit_derivatives(ctx, *X, nb, F, [1.0] * 4, 1e-3,
+                                  precision=capi.LP_MIXED_FF).cpu().numpy()
+    ctx.sync()
+    e64, eff = _class_err(g64, ref), _class_err(gff, ref)
+    nb1 = capi.lp_build_neighbors(ctx, *X, radius=T(rad, dev), mirror_mode=0, cap=48,
+                                  keep_nearest=capi.LP_KEEP_NEAREST)
+    g1 = capi.lp_fit_derivatives(ctx, *X, nb1, F, [1.0] * 4, 1e-3,
+                                 precision=capi.LP_FP64).cpu().numpy()
+    ctx.sync()
+    ana = np.zeros((x.size, 4, 9))
+    for f, (a, kv, ph) in enumerate(spec):
+        for k in range(len(a)):
+            arg = kv[k, 0] * x + kv[k, 1] * y + kv[k, 2] * z + ph[k]
+            c, s_ = np.cos(arg), np.sin(arg)
+            for q in range(3):
+                ana[:, f, q] += a[k] * kv[k, q] * c
+            pairs = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+            for q, (i1, i2) in enumerate(pairs):
+                ana[:, f, 3 + q] -= a[k] * kv[k, i1] * kv[k, i2] * s_
+    L = 126e-3
+    dmin = np.minimum.reduce([x, y, z, L - x, L - y, L - z])
+    for name, sel in (("faces (< 2h)", dmin < 2e-3), ("interior", dmin > 5e-3)):
+        print(f"sweep vs analytic, {name}: nearest {_class_err(g1[sel], ana[sel]):.3e}, "
+              f"octant-balanced {_class_err(g64[sel], ana[sel]):.3e}")
+    print(f"octant-balanced sweep: FP64 vs oracle {e64:.2e}, float-float vs oracle {eff:.2e}")
+    assert e64 <= 1e-11, e64
     assert eff <= 1e-9, eff
 
 
