@@ -28,6 +28,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -387,9 +389,9 @@ def our_arm(args):
     if not args.no_e2e:
         line["e2e"] = e2e(args, ctx, wl, pd, mui, eos, params, dev, stream, world)
 
-    if not args.no_batched and world == 1:
+    if not args.no_batched:
         ctx.close()
-        line["batched"] = batched(args, dev, stream)
+        line["batched"] = batched(args, dev, stream, rank, world)
 
     if not args.no_sweep and world == 1:
         line["derivative_sweep"] = derivative_sweep(args, dev, stream)
@@ -403,28 +405,32 @@ def our_arm(args):
         dist.destroy_process_group()
 
 
-def batched(args, dev, stream):
+def batched(args, dev, stream, rank=0, world=1):
     """256 independent columns (log-uniform 2k-64k particles, aspect 0.5-6,
     mu_s 0.3-0.45) advanced together in one lp_step call per window, with the
-    autotuned launch configuration, against 256 sequential per-column lp_step
-    calls over the same steps."""
+    autotuned launch configuration, against per-column lp_step calls over the
+    same steps. With several ranks each one steps its shard of the columns
+    (dist.shard_state: contiguous columns balanced by particle count); nothing
+    is exchanged, and the step time is the maximum over ranks."""
     import torch
 
-    from paper_2206_14061_gb300 import capi, workloads as W
+    from paper_2206_14061_gb300 import capi, dist as D, workloads as W
 
     wl = W.columns()
     pd = W.param_dict(wl)
-    offs = wl.column_offsets
+    sh = D.shard_state(wl.state, wl.column_offsets, rank, world, wl.mu_s_col)
+    offs = sh["offsets"]
     ncol = len(offs) - 1
+    n_local = int(offs[-1])
     base = {k: pd[k] for k in ("mu_2", "I0", "d", "rho_s")}
-    mui_c = [dict(base, mu_s=float(m)) for m in wl.mu_s_col]
+    mui_c = [dict(base, mu_s=float(m)) for m in sh["per_column"]]
     eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max", "alpha", "beta")}
-    init = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
+    init = {k: torch.tensor(np.ascontiguousarray(v), device=dev) for k, v in sh["state"].items()}
     st = {k: v.clone() for k, v in init.items()}
     prm = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
                floor_z=0.0, mirror_mode=1, precision=PREC[args.precision], rebuild_every=1,
                launch_mode=capi.LP_LAUNCH_GRAPH, skin=args.skin * pd["h"])
-    ctx = capi.Context(wl.n, max_columns=ncol, cap=64)
+    ctx = capi.Context(max(n_local, 1), max_columns=max(ncol, 1), cap=64)
     tune = capi.lp_autotune(ctx, init, mui_c, eos, prm, pd["dt"], 3, column_offsets=offs,
                             stream=stream)
     steps = max(1, min(args.steps, args.restart_every))
@@ -433,19 +439,24 @@ def batched(args, dev, stream):
         for k in capi.FIELDS:
             st[k].copy_(init[k])
 
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
     def timed(fn):
         with torch.cuda.stream(stream):
             reset()
             fn()  # warm-up
             reset()
-        torch.cuda.synchronize()
+        barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         with torch.cuda.stream(stream):
             fn()
         e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+        barrier()
+        return D.max_over_ranks(e0.elapsed_time(e1), device=dev)
 
     modes = {}
     for name, mode in (("graph", capi.LP_LAUNCH_GRAPH), ("persistent", capi.LP_LAUNCH_PERSISTENT)):
@@ -464,9 +475,12 @@ def batched(args, dev, stream):
     ms_c = timed(per_column)
     ctx.sync(stream, raise_on_error=False)
     ctx.close()
-    upd = wl.n * steps
-    return {"workload": f"{ncol} columns, {wl.n} particles, {args.precision}, {steps} steps",
+    upd = wl.n * steps  # all ranks' particles
+    return {"workload": f"{len(wl.column_offsets) - 1} columns, {wl.n} particles, "
+                        f"{args.precision}, {steps} steps",
             "value": upd / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / steps,
+            "scaling": "strong",
+            "shard": {"ranks": world, "columns_rank0": ncol, "particles_rank0": n_local},
             "launch": chosen, "tuning": tune,
             "graph_ms_per_step": modes["graph"] / steps,
             "persistent_ms_per_step": modes["persistent"] / steps,

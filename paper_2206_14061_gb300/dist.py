@@ -33,6 +33,20 @@ def local_offsets(column_offsets, c0: int, c1: int):
     return (offs[c0:c1 + 1] - offs[c0]).astype(np.int32)
 
 
+def shard_state(state: dict, column_offsets, rank: int, world: int, per_column=None):
+    """This rank's share of a batch of independent columns: the particles of
+    columns [c0, c1) from shard_columns, their offsets relative to the first
+    of them and, if given, the per-column values (e.g. mu_s) of those
+    columns. Returns dict(state=..., offsets=..., per_column=..., c0=, c1=)."""
+    c0, c1 = shard_columns(column_offsets, rank, world)
+    offs = np.asarray(column_offsets, dtype=np.int64)
+    b, e = int(offs[c0]), int(offs[c1])
+    return dict(state={k: v[b:e] for k, v in state.items()},
+                offsets=local_offsets(column_offsets, c0, c1),
+                per_column=None if per_column is None else np.asarray(per_column)[c0:c1],
+                c0=c0, c1=c1)
+
+
 def max_over_ranks(value: float, device=None) -> float:
     """Largest value over all ranks of the default process group (identity
     when torch.distributed is not initialised)."""

@@ -1,6 +1,7 @@
 """Multi-rank host logic on CPU (gloo, world size 2): column sharding covers
-every column exactly once with balanced particle counts, and the timing
-reduction takes the maximum over ranks."""
+every column exactly once with balanced particle counts, the benchmark's
+per-rank share of the batched columns (dist.shard_state) reassembles into the
+whole batch, and the timing reduction takes the maximum over ranks."""
 import os
 import socket
 
@@ -21,14 +22,22 @@ def _free_port():
 def _worker(rank, world, port, offs, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    from paper_2206_14061_gb300.dist import max_over_ranks, shard_columns
+    from paper_2206_14061_gb300 import workloads as W
+    from paper_2206_14061_gb300.dist import max_over_ranks, shard_columns, shard_state
     c0, c1 = shard_columns(offs, rank, world)
     t = max_over_ranks(10.0 + rank)
     counts = torch.tensor([offs[c1] - offs[c0], c0, c1], dtype=torch.int64)
     gathered = [torch.zeros(3, dtype=torch.int64) for _ in range(world)]
     dist.all_gather(gathered, counts)
+    # the benchmark's sharding of the batched columns (smaller batch): each
+    # rank's x values and per-column mu_s, gathered on rank 0
+    wl = W.columns(ncol=16, n_lo=300, n_hi=1500)
+    sh = shard_state(wl.state, wl.column_offsets, rank, world, wl.mu_s_col)
+    parts = [None] * world
+    dist.all_gather_object(parts, (sh["state"]["x"], sh["offsets"], sh["per_column"],
+                                   sh["c0"], sh["c1"]))
     if rank == 0:
-        out.put((t, [g.tolist() for g in gathered]))
+        out.put((t, [g.tolist() for g in gathered], parts))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -44,7 +53,7 @@ def test_shard_columns_and_max_over_ranks_gloo():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, offs, q)) for r in range(2)]
     for p in procs:
         p.start()
-    t, parts = q.get(timeout=120)
+    t, parts, shards = q.get(timeout=120)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
@@ -53,7 +62,14 @@ def test_shard_columns_and_max_over_ranks_gloo():
     assert a0 == 0 and b0 == a1 and b1 == 256
     assert n0 + n1 == offs[-1]
     assert abs(n0 - n1) <= sizes.max()
-    assert W.columns  # the batched workload generator is importable on CPU
+    # the shards of the batched workload cover it exactly once, in order
+    wl = W.columns(ncol=16, n_lo=300, n_hi=1500)
+    assert np.array_equal(np.concatenate([s[0] for s in shards]), wl.state["x"])
+    assert np.array_equal(np.concatenate([s[2] for s in shards]), wl.mu_s_col)
+    assert shards[0][3] == 0 and shards[0][4] == shards[1][3] and shards[1][4] == 16
+    for x, lo, _, c0, c1 in shards:
+        assert lo[0] == 0 and lo[-1] == x.size and len(lo) == c1 - c0 + 1
+        assert np.array_equal(np.diff(lo), np.diff(wl.column_offsets)[c0:c1])
 
 
 def test_shard_columns_edge_cases():

@@ -160,3 +160,92 @@ def test_adjoint_column_against_finite_differences(dev, orc):
     # FD of the runout+profile loss is limited by round-off of the positions
     # (about 2e-12 absolute at step 1e-6: ulp(0.02 m) accumulated over the run)
     assert (np.abs(g_run - fd_run) <= 1e-5 * np.abs(g_run) + 5e-12).all(), (g_run, fd_run)
+
+
+def _runout_tangent(sf, tan, R, tg):
+    """d(runout + profile misfit)/d(mu_s, mu_2, I0) from the oracle's tangent
+    of the final positions, with the argmaxes of the final state."""
+    x, y, z = sf["x"], sf["y"], sf["z"]
+    r = np.sqrt(x * x + y * y)
+    i = int(np.argmax(r))
+    b = np.clip((r / (3 * R / 32)).astype(int), 0, 31)
+    out = np.zeros(3)
+    for t in range(3):
+        g = (x[i] * tan[t, 0, i] + y[i] * tan[t, 1, i]) / r[i]
+        for kb in range(32):
+            sel = np.flatnonzero(b == kb)
+            if sel.size:
+                j = sel[np.argmax(z[sel])]
+                g += 2.0 * (z[j] - tg[kb]) * tan[t, 2, j]
+        out[t] = g
+    return out
+
+
+@pytest.mark.slow
+def test_adjoint_column_200_steps(dev, orc):
+    """The adjoint column at its stated length: radius 0.02 m, H = 2R, spacing
+    R/25 (98,800 particles), 200 FP64 steps with a checkpoint every 20, loss =
+    runout + squared misfit of the 32-bin height profile to a seeded target.
+
+    The column starts at solid fraction 0.5 (the initial mean solid fraction
+    implied by the paper's layer test, Sec. 4.1: 0.03 m of material expected
+    to settle at phi_c = 0.6 into 0.025 m) with free-surface ghosts, which
+    keeps it inside its stable horizon (about 670 steps at this spacing from
+    rest, against about 50 at phi 0.585 without ghosts).
+
+    From rest the loss does not depend on (mu_s, mu_2, I0) at all over this
+    horizon: the stress is quadratic in the velocity gradient (P and tau both
+    scale with |gdot|^2), so the floor's disturbance dies out within a few
+    layers, and the runout particle and the top of every bin stay in exact
+    free fall. The adjoint and central differences both give exactly 0 there.
+    With a radial flow u_r = 0.5 m/s (r/R)(z/H) (zero at the no-slip floor)
+    the whole column shears: dL/d(mu_s, mu_2, I0) from lp_step_adjoint then
+    matches the oracle's tangent-linear run to 1e-9 and central differences of
+    lp_step (step 1e-6) to 1e-5. (At 0.02 m/s the gradient, about 4e-9, sits
+    only 200 times above the round-off of central differences, ulp(0.04 m)
+    accumulated over the run divided by 2e-6: they agree to 5e-3 there.)"""
+    from paper_2206_14061_gb300 import capi
+    from paper_2206_14061_gb300.autograd import lp_step_diff, runout_profile_loss
+    R = 0.02
+    nsteps, C, eps = 200, 20, 1e-6
+    for flow in (0.0, 0.5):
+        wl = _flowing_column(R, 2.0, 25, flow, index=4)
+        wl.state = dict(wl.state, V=np.full(wl.n, 1.0 / 0.5))
+        pd = W.param_dict(wl)
+        mui, eos, prm = _split(pd)
+        prm = dict(prm, free_surface=1)
+        ctx = capi.Context(wl.n, cap=64)
+        init = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
+        rest = {k: pd[k] for k in ("d", "rho_s")}
+        rng = np.random.default_rng(20220628 + 4)
+        _, h0 = runout_profile_loss(init, R, torch.zeros(32, dtype=torch.float64, device=dev))
+        target = h0 * (1.0 + 0.05 * torch.tensor(rng.standard_normal(32), device=dev))
+        theta = torch.tensor([pd[k] for k in NAMES], dtype=torch.float64, requires_grad=True)
+        fin = lp_step_diff(ctx, theta, init, rest, eos, prm, pd["dt"], nsteps, C)
+        d = ctx.sync()
+        assert d["n_nonfinite"] == 0
+        umax = float(torch.sqrt(fin["u"] ** 2 + fin["v"] ** 2 + fin["w"] ** 2).max())
+        assert umax < flow + 0.05, umax  # sane: gravity adds 0.02 m/s in 2 ms
+        Lr, _ = runout_profile_loss(fin, R, target)
+        (g_run,) = torch.autograd.grad(Lr, theta)
+        g_run = g_run.numpy()
+        fd_run = np.zeros(3)
+        for t, name in enumerate(NAMES):
+            vals = []
+            for sgn in (1.0, -1.0):
+                m = dict(mui, **{name: mui[name] + sgn * eps})
+                st = _gpu_final(capi, ctx, wl.state, m, eos, prm, pd["dt"], nsteps, C, dev)
+                vals.append(float(runout_profile_loss(st, R, target)[0]))
+            fd_run[t] = (vals[0] - vals[1]) / (2 * eps)
+        if flow == 0.0:
+            print("200-step column from rest: adjoint", g_run, "FD", fd_run)
+            assert (g_run == 0.0).all() and (fd_run == 0.0).all(), (g_run, fd_run)
+            continue
+        sf, tan = orc.step_tangent(wl.state, orc.params(**dict(pd, free_surface=1)), nsteps,
+                                   rebuild_every=C, brute=False)
+        ref_run = _runout_tangent(sf, tan, R, target.cpu().numpy())
+        print("200-step flowing column: adjoint", g_run, "tangent", ref_run, "FD", fd_run,
+              "FD relative", np.abs(g_run - fd_run) / np.abs(g_run))
+        assert (np.abs(g_run) > 0).all(), g_run
+        assert np.abs(g_run - ref_run).max() <= 1e-9 * np.abs(ref_run).max(), (g_run, ref_run)
+        assert (np.abs(g_run - fd_run) <= 1e-5 * np.abs(g_run) + 5e-12).all(), (g_run, fd_run)
