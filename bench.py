@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("mixed_ff", "mixed", "fp64"), default="mixed_ff")
     ap.add_argument("--restart-every", type=int, default=10)
+    ap.add_argument("--spacing-div", type=int, default=50,
+                    help="lattice spacing R/spacing_div of the cylinder (50: the benchmark's "
+                         "785k particles; smaller values give smaller cases for profiling)")
     ap.add_argument("--skin", type=float, default=0.1,
                     help="Verlet skin in lattice spacings (0: full search every step)")
     ap.add_argument("--free-surface", action="store_true",
@@ -245,7 +248,7 @@ def our_arm(args):
     dev = torch.device("cuda", local)
     capi.lib(build_if_missing=True)
 
-    wl = W.cylinder()
+    wl = W.cylinder(spacing_div=args.spacing_div)
     pd = W.param_dict(wl)
     n = wl.n
     mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
@@ -354,8 +357,9 @@ def our_arm(args):
                   "mixed": "f32+f64"}.get(args.precision, "f64"),
         "data": "synthetic (seeded jittered lattice column)",
         "config": {
-            "workload": "cylindrical column collapse R=0.02 m H=2R h=R/50 jitter 0.05h "
-                        f"({n} particles), mu_s 0.38 mu_2 0.64 I0 0.28 d 5e-4 rho 2500, "
+            "workload": f"cylindrical column collapse R=0.02 m H=2R h=R/{args.spacing_div} "
+                        f"jitter 0.05h ({n} particles), mu_s 0.38 mu_2 0.64 I0 0.28 d 5e-4 "
+                        "rho 2500, "
                         "dt 1e-5, stencil radius 2.2h, no-slip floor mirrors",
             "precision": args.precision, "graph": True, "restart_every": R,
             "verlet_skin_h": args.skin, "free_surface_ghosts": bool(args.free_surface),
