@@ -174,3 +174,74 @@ def test_tangent_linear_with_ghosts_matches_central_differences(orc):
             scale = np.abs(t).max()
             assert scale > 0
             assert np.abs(fd - t).max() <= 1e-5 * scale, (name, key)
+
+
+def _plain_ghost_decisions(x, y, z, nbr, cnt, h, r, mirror, tol):
+    """The free-boundary rule in plain FP64 on real-valued offsets (no
+    fixed-point grid): weights w = r^2 - |o|^2, S = sum w o; one-sided when
+    |S| > 0.22 h sum w; a ghost for every entry with o . S >= 0.5 h |S| whose
+    reflection has no entry within h/2 and, with floor mirrors, does not fall
+    below the floor. Returns {particle: set of flagged entry codes} and the
+    particles whose decisions lie within a relative `tol` of a threshold."""
+    flags, near = {}, set()
+    for i in range(x.size):
+        row = nbr[i, :cnt[i]].astype(np.int64) & 0xFFFFFFFF
+        row = row[(row & GB) == 0]
+        j = row & IDX
+        zj = np.where(row & MB, -z[j], z[j])
+        o = np.stack([x[j] - x[i], y[j] - y[i], zj - z[i]], 1)
+        w = np.maximum(0.0, r * r - (o * o).sum(1))
+        S = (w[:, None] * o).sum(0)
+        sn, lim = np.linalg.norm(S), 0.22 * h * w.sum()
+        if abs(sn - lim) <= tol * lim:
+            near.add(i)
+        if not sn > lim:
+            continue
+        dep = o @ S - 0.5 * h * sn
+        below = mirror and (2 * z[i] - zj < 0.0)
+        got = set()
+        for k in range(len(row)):
+            if abs(dep[k]) <= tol * h * sn:
+                near.add(i)
+            if dep[k] < 0 or below[k]:
+                continue
+            d2 = ((o + o[k]) ** 2).sum(1)
+            if (np.abs(d2 - 0.25 * h * h) <= tol * h * h).any():
+                near.add(i)
+            if (d2 >= 0.25 * h * h).all():
+                got.add(int(row[k]))
+        if got:
+            flags[i] = got
+    return flags, near
+
+
+def test_fixed_point_ghost_decisions_match_plain_fp64(orc):
+    """The oracle takes its ghost decisions on a fixed-point grid (reading
+    R23) so that a device can reproduce them bit for bit. Away from near-ties
+    (1e-3 relative of a threshold) they are the plain FP64 rule's decisions:
+    on a jittered cube with floor mirrors and on a cylinder, every particle's
+    set of flagged entries is the same."""
+    h, r = 1e-3, 2.2e-3
+    rng = np.random.default_rng(41)
+    cases = [W.lattice_box(9, 9, 9, h, 0.1, rng)]
+    cyl = W.cylinder(R=6e-3, aspect=1.5, spacing_div=6, jitter=0.1, index=41)
+    cases.append(tuple(cyl.state[k] for k in "xyz"))
+    compared = flagged = 0
+    for x, y, z in cases:
+        p = _p(orc)
+        nbr, cnt, over = orc.step_stencils(x, y, z, p)
+        assert over == 0
+        got = {}
+        for i in range(x.size):
+            row = nbr[i, :cnt[i]].astype(np.int64) & 0xFFFFFFFF
+            g = set(int(c) & ~GB for c in row if c & GB)
+            if g:
+                got[i] = g
+        ref, near = _plain_ghost_decisions(x, y, z, nbr, cnt, h, r, True, 1e-3)
+        for i in range(x.size):
+            if i in near:
+                continue
+            compared += 1
+            assert got.get(i, set()) == ref.get(i, set()), i
+            flagged += i in ref
+    assert compared > 1500 and flagged > 300, (compared, flagged)
