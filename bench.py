@@ -56,6 +56,8 @@ def parse():
                     help="ghost particles at free boundaries (Sec. 3.1 item 9)")
     ap.add_argument("--no-free-surface", action="store_true",
                     help="skip the line with free-surface ghosts")
+    ap.add_argument("--no-moving", action="store_true",
+                    help="skip the line with the column in a spreading flow")
     ap.add_argument("--no-heun", action="store_true",
                     help="skip the line with Heun's method")
     ap.add_argument("--no-periodic", action="store_true",
@@ -411,6 +413,24 @@ def our_arm(args):
             "ms_per_step": msh / args.steps,
             "phase_ms_per_step": {k: v / max(profh["steps"], 1) for k, v in profh["ms"].items()}}
 
+    if not args.no_moving:
+        # the same column in a spreading flow u_r = U (r/R)(z/H), U = 0.5 m/s
+        # (zero at the no-slip floor): particles move up to 0.0125 h per step,
+        # so the Verlet lists are searched every few steps instead of once per
+        # restart, as in a collapsing column
+        U, Rc, Hc = 0.5, wl.extra["R"], wl.extra["H"]
+        rest = {k: init[k] for k in ("u", "v")}
+        init["u"] = torch.tensor(U * wl.state["x"] / Rc * (wl.state["z"] / Hc), device=dev)
+        init["v"] = torch.tensor(U * wl.state["y"] / Rc * (wl.state["z"] / Hc), device=dev)
+        msv, _, _, dgv, profv, _ = bench(args.precision)
+        init.update(rest)
+        line["moving"] = {
+            "workload": "the same column in a spreading flow u_r = 0.5 m/s (r/R)(z/H)",
+            "value": n * args.steps * world / (msv / 1e3), "unit": UNIT,
+            "ms_per_step": msv / args.steps,
+            "phase_ms_per_step": {k: v / max(profv["steps"], 1) for k, v in profv["ms"].items()},
+            "n_nonfinite": dgv["n_nonfinite"]}
+
     if not args.no_periodic:
         line["periodic"] = periodic_layer(args, dev, stream, world)
 
@@ -502,6 +522,32 @@ def batched(args, dev, stream, rank=0, world=1):
 
     ms_c = timed(per_column)
     ctx.sync(stream, raise_on_error=False)
+
+    # the batch at its stated length: 500 steps in one lp_step call, no
+    # restart, from solid fraction 0.5 with free-surface ghosts (the start
+    # that keeps these columns inside their stable horizon)
+    full_steps = 500
+    p500 = dict(prm, launch_mode=tune["launch_mode"], free_surface=1)
+    v_half = torch.full_like(init["V"], 2.0)
+
+    def reset500():
+        reset()
+        st["V"].copy_(v_half)
+
+    with torch.cuda.stream(stream):
+        reset500()
+        capi.lp_step(ctx, st, mui_c, eos, p500, pd["dt"], 10, column_offsets=offs, stream=stream)
+        reset500()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    with torch.cuda.stream(stream):
+        capi.lp_step(ctx, st, mui_c, eos, p500, pd["dt"], full_steps, column_offsets=offs,
+                     stream=stream)
+    f1.record(stream)
+    barrier()
+    ms_f = D.max_over_ranks(f0.elapsed_time(f1), device=dev)
+    d500 = ctx.sync(stream, raise_on_error=False)
     ctx.close()
     upd = wl.n * steps  # all ranks' particles
     return {"workload": f"{len(wl.column_offsets) - 1} columns, {wl.n} particles, "
@@ -513,7 +559,12 @@ def batched(args, dev, stream, rank=0, world=1):
             "graph_ms_per_step": modes["graph"] / steps,
             "persistent_ms_per_step": modes["persistent"] / steps,
             "per_column_value": upd / (ms_c / 1e3), "per_column_ms_per_step": ms_c / steps,
-            "speedup_vs_per_column": ms_c / ms_b}
+            "speedup_vs_per_column": ms_c / ms_b,
+            "full_length": {"steps": full_steps, "phi0": 0.5, "free_surface_ghosts": True,
+                            "restart": None, "value": wl.n * full_steps / (ms_f / 1e3),
+                            "ms_per_step": ms_f / full_steps,
+                            "n_nonfinite": d500["n_nonfinite"],
+                            "ghost_entries_per_step": d500["n_ghosts"] / full_steps}}
 
 
 def periodic_layer(args, dev, stream, world):

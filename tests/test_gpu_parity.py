@@ -745,6 +745,42 @@ def test_columns_smallest_four_match_oracle(dev, capi, orc):
 
 
 @pytest.mark.slow
+def test_columns_smallest_four_500_steps(dev, capi, orc):
+    """The batched workload's stated length: its four smallest columns (about
+    2,100 particles each) advanced together for 500 steps on the GPU, from
+    solid fraction 0.5 with free-surface ghosts (the start that keeps this
+    spacing inside its stable horizon, about 700 steps), in FP64 and
+    float-float, against the oracle run column by column. A 1e-14 relative
+    perturbation of the start grows to about 2.5e-11 of the displacement over
+    these 500 steps on the oracle, so the bar stays 1e-9."""
+    full = W.columns()
+    sizes = np.diff(full.column_offsets)
+    four = sorted(np.argsort(sizes)[:4].tolist())
+    wl = W.columns(only=four)
+    wl.state = dict(wl.state, V=np.full(wl.n, 1.0 / 0.5))
+    pd = dict(W.param_dict(wl), free_surface=1)
+    mui_c = [dict(_dicts(pd)[0], mu_s=float(m)) for m in wl.mu_s_col]
+    offs = wl.column_offsets
+    refs = []
+    for c in range(4):
+        b, e = offs[c], offs[c + 1]
+        sc = {k: v[b:e] for k, v in wl.state.items()}
+        refs.append((sc, orc.step(sc, orc.params(**dict(pd, mu_s=float(wl.mu_s_col[c]))), 500,
+                                  brute=False)[0]))
+    for prec in (0, 2):
+        got, d = _run_gpu(capi, dev, wl, pd, 500, prec=prec, offsets=offs, mui=mui_c,
+                          launch_mode=1, skin=0.1 * pd["h"], free_surface=1,
+                          stream=torch.cuda.Stream())
+        assert d["n_nonfinite"] == 0 and d["n_ghosts"] > 0
+        for c in range(4):
+            b, e = offs[c], offs[c + 1]
+            err = _state_err({k: got[k][b:e] for k in got}, refs[c][1], refs[c][0])
+            print(f"column {c}, precision {prec}, 500-step errors:",
+                  {k: f"{v:.2e}" for k, v in err.items()})
+            assert max(err.values()) <= 1e-9, (prec, c, err)
+
+
+@pytest.mark.slow
 def test_step_full_size_cylinder(dev, capi, orc):
     """The column of radius 0.02 m at spacing R/50 (785k particles), three FP64
     steps in the launch configuration the benchmark uses, against the oracle on
