@@ -320,3 +320,48 @@ def test_periodic_layer_full_size(dev, capi, orc):
         assert max(e.values()) <= tol, (prec, e)
         assert d["n_nonfinite"] == 0 and d["n_overflow"] == 0
         assert d["n_ghosts"] == rd["n_ghosts"], (d["n_ghosts"], rd["n_ghosts"])
+
+
+def test_periodic_layer_matches_the_1d_reduction(dev, capi):
+    """Sec. 4.1's verification on the GPU path: the paper's layer on an
+    unjittered 16 x 16 x 30 periodic lattice (at rest, solid fraction 0.50 at
+    the floor to 0.48 at the top, free-surface ghosts, float-float fits,
+    graph replay) against the layer reduced to 1D (oracle/layer1d.py) over
+    600 steps: every level moves as one, the total compaction agrees to 5 %
+    and the velocities above the two floor levels to 1e-2 (0.2 % and 1e-4
+    after 200 steps; the floor levels split the compaction differently)."""
+    from oracle import layer1d as L1
+    wl = W.periodic_layer(n_xy=16, jitter=0.0)
+    L, h, nz = wl.extra["L"], wl.h, 30
+    pd = dict(W.param_dict(wl), period_x=L, period_y=L)
+    mui, eos = _dicts(pd)
+    s0 = wl.state
+    lev = np.rint(s0["z"] / h - 0.5).astype(int)
+    zl = (np.arange(nz) + 0.5) * h
+    z1, w1 = zl.copy(), np.zeros(nz)
+    V1 = np.array([s0["V"][lev == lv][0] for lv in range(nz)])
+    V0 = V1.copy()
+    ctx = capi.Context(wl.n, cap=64)
+    st = {k: T(s0[k], dev) for k in capi.FIELDS}
+    prm = _prm(pd, precision=capi.LP_MIXED_FF, launch_mode=capi.LP_LAUNCH_GRAPH,
+               skin=0.1 * h, free_surface=1)
+    done = 0
+    for steps, tol_c, tol_w in ((200, 2e-3, 1e-4), (600, 5e-2, 1e-2)):
+        capi.lp_step(ctx, st, mui, eos, prm, pd["dt"], steps - done)
+        d = ctx.sync()
+        assert d["n_nonfinite"] == 0
+        for _ in range(steps - done):
+            z1, w1, V1, _ = L1.step(z1, w1, V1, mui, eos, h, pd["radius"], pd["dt"])
+        done = steps
+        g = {k: st[k].cpu().numpy() for k in ("z", "w", "V")}
+        for f in ("z", "w", "V"):
+            spread = max(np.ptp(g[f][lev == lv]) for lv in range(nz))
+            assert spread <= 1e-12 * np.abs(g[f]).max(), (steps, f, spread)
+        w3 = np.array([g["w"][lev == lv][0] for lv in range(nz)])
+        V3 = np.array([g["V"][lev == lv][0] for lv in range(nz)])
+        c3, c1 = (V3 - V0).sum(), (V1 - V0).sum()
+        ew = np.abs(w3[2:] - w1[2:]).max() / np.abs(w1).max()
+        print(f"GPU layer, {steps} steps: compaction 3D {c3:.6e}, 1D {c1:.6e}; "
+              f"velocity above the floor levels {ew:.2e}")
+        assert abs(c3 - c1) <= tol_c * abs(c1), (steps, c3, c1)
+        assert ew <= tol_w, (steps, ew)
