@@ -744,6 +744,44 @@ def test_columns_smallest_four_match_oracle(dev, capi, orc):
             assert max(err.values()) <= tol, (prec, c, err)
 
 
+def test_ragged_columns_with_empty_and_single_particle_columns(dev, capi, orc):
+    """A batch whose columns include an empty one and a one-particle one (its
+    only stencil entry is its own floor mirror: the QR path), between two
+    ordinary columns: every launch mode gives the oracle's per-column result,
+    FP64 and float-float."""
+    wl = W.columns(ncol=3, n_lo=300, n_hi=900, only=[0, 1, 2])
+    offs0 = wl.column_offsets
+    one = dict(x=np.array([0.0]), y=np.array([0.0]), z=np.array([0.4e-3]), u=np.array([0.01]),
+               v=np.array([0.0]), w=np.array([-0.02]), V=np.array([1 / 0.585]))
+    parts = [{k: v[offs0[c]:offs0[c + 1]] for k, v in wl.state.items()} for c in range(3)]
+    cols = [parts[0], {k: np.zeros(0) for k in one}, one, parts[1], parts[2]]
+    state = {k: np.concatenate([c[k] for c in cols]) for k in capi.FIELDS}
+    offs = np.concatenate([[0], np.cumsum([c["x"].size for c in cols])]).astype(np.int32)
+    mus = [0.33, 0.38, 0.41, 0.36, 0.44]
+    pd = W.param_dict(wl)
+    mui_c = [dict(_dicts(pd)[0], mu_s=m) for m in mus]
+    nst = 6
+    refs = [orc.step(c, orc.params(**dict(pd, mu_s=mus[k])), nst, brute=False)[0]
+            if c["x"].size else None for k, c in enumerate(cols)]
+    wlr = W.Workload("ragged", pd["h"], pd["radius"], pd["dt"], state)
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
+        for mode in (0, 1, 2):
+            got, d = _run_gpu(capi, dev, wlr, pd, nst, prec=prec, offsets=offs, mui=mui_c,
+                              launch_mode=mode, stream=torch.cuda.Stream())
+            assert d["status"] == 0 and d["n_nonfinite"] == 0 and d["n_fallback"] > 0
+            for k, c in enumerate(cols):
+                if refs[k] is None:
+                    continue
+                b, e = offs[k], offs[k + 1]
+                if c["x"].size == 1:  # displacement of one particle: compare the values
+                    for f in capi.FIELDS:
+                        assert np.allclose(got[f][b:e], refs[k][f], rtol=1e-12, atol=1e-18), (
+                            prec, mode, f)
+                    continue
+                err = _state_err({f: got[f][b:e] for f in got}, refs[k], c)
+                assert max(err.values()) <= tol, (prec, mode, k, err)
+
+
 @pytest.mark.slow
 def test_columns_smallest_four_500_steps(dev, capi, orc):
     """The batched workload's stated length: its four smallest columns (about
