@@ -17,8 +17,11 @@ the time-n velocity quantities; w^{n+1} = w^n + dt a; z^{n+1} = z^n + dt
 item 7) with rows [dz/h, (dz/h)^2 / 2] over the particles within the stencil
 radius, floor mirrors (Sec. 3.1 item 9: mirror at -z with w* = -w, the same
 V, |gdot| = 0) and, at the free top, ghost particles with the free-boundary
-rule the 3D code uses (one-sided test and placement of readings R20-R22, here
-on real offsets): a ghost carries the particle's velocity, solid fraction
+rule the 3D code uses (a stencil is one-sided when its weighted mean offset,
+weights r^2 - d^2, exceeds 0.22 h; its entries at least h/2 on the inner side
+are reflected through the particle unless an entry lies within h/2 of the
+reflection or it falls below the floor), here on real offsets: a ghost
+carries the particle's velocity, solid fraction
 phi_G = phi_min (1 - 1e-3) and |gdot|_G = |gdot| (phi_c - phi_G)/(phi_c - phi)
 in the inertial regime.
 """
@@ -44,7 +47,7 @@ def stencils(z, r, h, floor_z=0.0):
     """Per particle: offsets of its entries (real particles j != i with
     |z_j - z_i| <= r, then floor mirrors j* at 2 floor_z - z_j passing the
     same test), their source index and mirror flag, and the ghost offsets of
-    the free-boundary rule (readings R20-R21 on real 1D offsets)."""
+    the free-boundary rule (module docstring) on real 1D offsets."""
     n = z.size
     out = []
     for i in range(n):

@@ -216,8 +216,9 @@ def _plain_ghost_decisions(x, y, z, nbr, cnt, h, r, mirror, tol):
 
 
 def test_fixed_point_ghost_decisions_match_plain_fp64(orc):
-    """The oracle takes its ghost decisions on a fixed-point grid (reading
-    R23) so that a device can reproduce them bit for bit. Away from near-ties
+    """The oracle takes its ghost decisions on a fixed-point grid (positions
+    rounded to multiples of a power of two, exact integer sums) so that a
+    device can reproduce them bit for bit. Away from near-ties
     (1e-3 relative of a threshold) they are the plain FP64 rule's decisions:
     on a jittered cube with floor mirrors and on a cylinder, every particle's
     set of flagged entries is the same."""
