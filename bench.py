@@ -514,6 +514,22 @@ def batched(args, dev, stream, rank=0, world=1):
     chosen = "persistent" if tune["launch_mode"] == capi.LP_LAUNCH_PERSISTENT else "graph"
     ms_b = modes[chosen]
 
+    def phases(mode):
+        """Per-phase device ms per step: CUDA events around the per-phase
+        kernels, or the persistent kernel's own marks after each barrier."""
+        ctx.profile(True)
+        ctx.phase_times(stream)  # reset
+        with torch.cuda.stream(stream):
+            reset()
+            capi.lp_step(ctx, st, mui_c, eos, dict(prm, launch_mode=mode), pd["dt"], steps,
+                         column_offsets=offs, stream=stream)
+        pt = ctx.phase_times(stream)
+        ctx.profile(False)
+        return {k: v / steps for k, v in pt["ms"].items()}
+
+    phase_kernels = phases(capi.LP_LAUNCH_KERNELS)
+    phase_persistent = phases(capi.LP_LAUNCH_PERSISTENT)
+
     def per_column():
         p = dict(prm, launch_mode=capi.LP_LAUNCH_GRAPH)
         for c in range(ncol):
@@ -558,6 +574,8 @@ def batched(args, dev, stream, rank=0, world=1):
             "launch": chosen, "tuning": tune,
             "graph_ms_per_step": modes["graph"] / steps,
             "persistent_ms_per_step": modes["persistent"] / steps,
+            "phase_ms_per_step_kernels": phase_kernels,
+            "phase_ms_per_step_persistent": phase_persistent,
             "per_column_value": upd / (ms_c / 1e3), "per_column_ms_per_step": ms_c / steps,
             "speedup_vs_per_column": ms_c / ms_b,
             "full_length": {"steps": full_steps, "phi0": 0.5, "free_surface_ghosts": True,

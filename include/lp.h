@@ -250,7 +250,10 @@ lp_status lp_ctx_set_wait_limit(lp_ctx* ctx, int64_t max_spins, int32_t extra_ar
 
 /* Per-phase timing (profiling aid, not in the paper). While enabled, lp_step
  * records a CUDA event pair around each phase of every step and does not use
- * graph replay. */
+ * graph replay. A persistent launch (one kernel per step) times its phases
+ * inside the kernel instead: thread 0 of block 0 reads the GPU's global timer
+ * after the grid barrier that closes each phase (two extra barriers while
+ * profiling). */
 lp_status lp_ctx_profile(lp_ctx* ctx, int32_t enable);
 /* Wait for `stream`; ms[LP_NPHASES] receives the device time of each phase
  * accumulated since the last call (0 where profiling was off); *launches

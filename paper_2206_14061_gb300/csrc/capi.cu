@@ -136,6 +136,7 @@ struct lp_ctx {
   double* Y0[7] = {};                  // Heun: state at the start of the step (on first use)
   double* stage = nullptr;             // lp_step on host arrays: 7 x cap_n (on first use)
   float2* Lff = nullptr;     // float-float Cholesky factors (LP_MIXED_FF), (hi, lo) pairs
+  unsigned long long* phase_ns = nullptr;  // persistent-launch phase times (profiling)
   // Verlet candidate lists (lp_params.skin)
   int32_t* cand = nullptr;   // capc x n, k-major
   int32_t* ccnt = nullptr;
@@ -543,6 +544,13 @@ lp_status run_step_persistent(lp_ctx* c, int n, const StepConsts& K, int prec, b
   P.bar = c->bar;
   P.max_spins = c->max_spins;  // default about 2 s of __nanosleep(64)
   P.extra_arrivals = c->extra_arrivals;
+  if (c->profile) {
+    if (!c->phase_ns) {
+      LP_TRY(dalloc(c, &c->phase_ns, (size_t)LP_NPHASES + 1));
+      cudaMemsetAsync(c->phase_ns, 0, sizeof(unsigned long long) * (LP_NPHASES + 1), st);
+    }
+    P.phase_ns = c->phase_ns;
+  }
   cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st);
   if (launch_persistent(prec, P, st) != cudaSuccess) {
     cudaGetLastError();
@@ -829,6 +837,14 @@ lp_status lp_ctx_phase_times(lp_ctx* c, void* stream, double* ms, int64_t* launc
       ms[c->ev_phase[r]] += t;
   }
   cudaGetLastError();
+  if (c->phase_ns) {  // phases of persistent launches (profiling)
+    unsigned long long ns[LP_NPHASES];
+    if (cudaMemcpy(ns, c->phase_ns, sizeof(ns), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        cudaMemset(c->phase_ns, 0, sizeof(ns)) == cudaSuccess) {
+      for (int k = 0; k < LP_NPHASES; ++k) ms[k] += 1e-6 * (double)ns[k];
+    }
+    cudaGetLastError();
+  }
   c->ev_phase.clear();
   c->ev_used = 0;
   if (launches) *launches = c->launches;

@@ -333,6 +333,10 @@ struct PersistArgs {
   unsigned* bar;
   unsigned long long max_spins;
   unsigned extra_arrivals;  // 0 in production; > 0 only to test the bounded wait
+  // profiling (lp_ctx_profile): nanoseconds per phase (LP_PHASE_*), added by
+  // thread 0 of block 0 after the grid barrier that closes each phase, and
+  // the last mark in [LP_NPHASES]; NULL when profiling is off
+  unsigned long long* phase_ns;
 };
 
 // arguments of the adjoint kernels (adjoint.cu)

@@ -56,6 +56,22 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long max_
     if (!grid_sync(P.bar, P.max_spins, P.extra_arrivals, P.S.dg)) return; \
   } while (0)
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Profiling only: thread 0 of block 0 adds the time since the last mark
+// (kept in phase_ns[LP_NPHASES]) to phase `ph`; called right after a grid
+// barrier, so the mark is the moment every block has finished the phase.
+__device__ __forceinline__ void phase_stamp(const PersistArgs& P, int ph) {
+  if (P.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long t = global_ns();
+    if (ph >= 0) P.phase_ns[ph] += t - P.phase_ns[LP_NPHASES];
+    P.phase_ns[LP_NPHASES] = t;
+  }
+}
+
 // float-float: at most 128 registers (4 blocks per SM), as the per-phase
 // float-float kernels; FP64 and MIXED at 3 blocks per SM (168 registers),
 // where their bodies do not spill much
@@ -66,6 +82,7 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
   const int nth = gridDim.x * blockDim.x;
   const int n = P.n;
   const StepArgs& S = P.S;
+  phase_stamp(P, -1);  // start mark
   // The search flag is read before the first barrier and cleared only by the
   // filter phase, after several barriers, so every block takes the same
   // branch. Without candidate lists every rebuild searches.
@@ -135,6 +152,7 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
         ghost_fix_body(t, S.x, S.y, S.z, S.colid, S.grids, S.K.ghost_grid, S.K.floor_z, S.Xfix);
     }
     LP_SYNC_OR_LEAVE();
+    phase_stamp(P, LP_PHASE_SORT);
   }
   if (srch) {
     // every lane of a warp runs the same number of rounds (warp-wide reductions)
@@ -174,6 +192,10 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
       ghost_body(s, s < n, n, S.z, S.Xfix, P.nbr, P.cnt, S.gcnt, S.K, S.dg);
     }
   }
+  if (P.phase_ns) {  // profiling: close the neighbour phase (same branch in every block)
+    LP_SYNC_OR_LEAVE();
+    phase_stamp(P, LP_PHASE_NEIGHBORS);
+  }
   if (tid == 0) *S.fb_count = 0;
   if (P.save_y0) {  // Heun's method: the state at the start of the step
     const double* src[7] = {S.x, S.y, S.z, S.u, S.v, S.w, S.V};
@@ -197,6 +219,7 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
   for (int t = tid; t < nfb; t += nth) pass1_fallback_item(S, t);
   if (tid == 0 && nfb > 0) atomicAdd(&S.dg->n_fallback, (unsigned long long)nfb);
   LP_SYNC_OR_LEAVE();
+  phase_stamp(P, LP_PHASE_PASS1);
   if (PREC == LP_MIXED_FF) {
     for (int s = tid; s < n; s += nth) split_p1_body(S, s);
     LP_SYNC_OR_LEAVE();
@@ -207,6 +230,10 @@ __global__ void __launch_bounds__(kBlock, PREC == LP_MIXED_FF ? 4 : 3)
     const int s = base + tid;
     if (PREC == LP_MIXED_FF && S.K.free_surface && s < n) pass2_twins_body<true>(S, s);
     pass2_body<PREC, true>(S, s, s < n);
+  }
+  if (P.phase_ns) {  // profiling: close pass 2
+    LP_SYNC_OR_LEAVE();
+    phase_stamp(P, LP_PHASE_PASS2);
   }
 }
 

@@ -458,6 +458,38 @@ def test_step_persistent_launch_is_bitwise_identical(dev, capi):
             assert np.array_equal(a[k], b[k]), ("skin", prec, k)
 
 
+def test_persistent_phase_times(dev, capi):
+    """With profiling on, a persistent launch times its own phases (marks
+    after the grid barriers): all four are positive, their sum stays within
+    the launch's wall time, and the state is still the per-phase kernels'."""
+    wc = W.columns(ncol=6, n_lo=3000, n_hi=9000, only=list(range(6)))
+    pc = W.param_dict(wc)
+    mui_c = [dict(_dicts(pc)[0], mu_s=float(m)) for m in wc.mu_s_col]
+    m, eos = _dicts(pc)
+    ctx = capi.Context(wc.n, max_columns=8, cap=64)
+    a, _ = _run_gpu(capi, dev, wc, pc, 4, prec=2, offsets=wc.column_offsets, mui=mui_c,
+                    launch_mode=0, skin=0.1 * pc["h"])
+    st = {k: T(wc.state[k], dev) for k in capi.FIELDS}
+    ctx.profile(True)
+    ctx.phase_times()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    capi.lp_step(ctx, st, mui_c, eos, _prm(pc, precision=2, launch_mode=2, skin=0.1 * pc["h"]),
+                 pc["dt"], 4, column_offsets=wc.column_offsets)
+    e1.record()
+    pt = ctx.phase_times()
+    ctx.profile(False)
+    d = ctx.sync()
+    assert d["status"] == 0 and d["flags"] == 0
+    wall = e0.elapsed_time(e1)
+    print("persistent phase ms:", pt["ms"], "wall ms:", wall)
+    assert all(v > 0.0 for v in pt["ms"].values()), pt
+    assert sum(pt["ms"].values()) <= wall * 1.001 + 0.05, (pt, wall)
+    for k in capi.FIELDS:
+        assert np.array_equal(st[k].cpu().numpy(), a[k]), k
+
+
 def test_autotune_choices_and_table(dev, capi, tmp_path):
     """The tuner returns valid block sizes and a launch mode, leaves the
     caller's particles unchanged, and the chosen block sizes do not change a
