@@ -96,3 +96,26 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_binding_signatures_match_the_header():
+    """Every function the binding declares takes as many arguments as its
+    prototype in include/lp.h, and returns lp_status (int32) unless the
+    header says otherwise."""
+    import os
+    import re
+    from paper_2206_14061_gb300 import capi
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                       "lp.h")
+    text = re.sub(r"/\*.*?\*/", " ", open(inc).read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"(\w[\w\s\*]*?)\b(lp_\w+)\s*\(([^;{]*?)\)\s*;", text):
+        ret, name, args = m.group(1).strip(), m.group(2), m.group(3).strip()
+        n = 0 if args in ("", "void") else args.count(",") + 1
+        protos[name] = (ret, n)
+    assert set(capi._SIGS) <= set(protos), set(capi._SIGS) - set(protos)
+    for name, (argtypes, restype) in capi._SIGS.items():
+        ret, n = protos[name]
+        assert len(argtypes) == n, (name, len(argtypes), n)
+        if ret.endswith("lp_status"):
+            assert restype is ctypes.c_int32, name
