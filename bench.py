@@ -58,6 +58,8 @@ def parse():
                     help="skip the line with free-surface ghosts")
     ap.add_argument("--no-moving", action="store_true",
                     help="skip the line with the column in a spreading flow")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint line (the 200-step adjoint column)")
     ap.add_argument("--no-heun", action="store_true",
                     help="skip the line with Heun's method")
     ap.add_argument("--no-periodic", action="store_true",
@@ -441,6 +443,9 @@ def our_arm(args):
         ctx.close()
         line["batched"] = batched(args, dev, stream, rank, world)
 
+    if not args.no_adjoint and world == 1:
+        line["adjoint"] = adjoint_line(dev, stream)
+
     if not args.no_sweep and world == 1:
         line["derivative_sweep"] = derivative_sweep(args, dev, stream)
 
@@ -583,6 +588,61 @@ def batched(args, dev, stream, rank=0, world=1):
                             "ms_per_step": ms_f / full_steps,
                             "n_nonfinite": d500["n_nonfinite"],
                             "ghost_entries_per_step": d500["n_ghosts"] / full_steps}}
+
+
+def adjoint_line(dev, stream):
+    """The adjoint column at its stated length: radius 0.02 m, H = 2R,
+    spacing R/25 (98,800 particles), 200 FP64 steps with a checkpoint every
+    20, from solid fraction 0.5 with free-surface ghosts and a radial flow of
+    0.5 m/s (r/R)(z/H). Times the forward run alone (lp_step, stencils
+    rebuilt every 20 steps) and the adjoint (lp_step_adjoint: segment
+    re-runs and the reverse sweep) for a seed on every state field."""
+    import torch
+
+    from paper_2206_14061_gb300 import capi, workloads as W
+
+    R, nsteps, C = 0.02, 200, 20
+    wl = W.cylinder(R=R, aspect=2.0, spacing_div=25, index=4)
+    s = dict(wl.state)
+    s["u"] = 0.5 * s["x"] / R * (s["z"] / (2 * R))
+    s["v"] = 0.5 * s["y"] / R * (s["z"] / (2 * R))
+    s["V"] = np.full(wl.n, 2.0)
+    pd = W.param_dict(wl)
+    mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
+    eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max", "alpha", "beta")}
+    prm = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
+               floor_z=0.0, mirror_mode=1, precision=PREC["fp64"], rebuild_every=C,
+               launch_mode=capi.LP_LAUNCH_KERNELS, free_surface=1)
+    init = {k: torch.tensor(v, device=dev) for k, v in s.items()}
+    rng = np.random.default_rng(20220628 + 4)
+    seed = {k: torch.tensor(rng.standard_normal(wl.n), device=dev) for k in capi.FIELDS}
+    ctx = capi.Context(wl.n, cap=64)
+    out = {}
+    for name in ("forward", "adjoint"):
+        with torch.cuda.stream(stream):
+            for rep in range(2):  # a warm-up, then the timed call
+                st = {k: v.clone() for k, v in init.items()}
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if name == "forward":
+                    capi.lp_step(ctx, st, mui, eos, prm, pd["dt"], nsteps, stream=stream)
+                else:
+                    dmui, _ = capi.lp_step_adjoint(ctx, st, mui, eos, prm, pd["dt"], nsteps, C,
+                                                   seed, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1)
+    d = ctx.sync(stream, raise_on_error=False)
+    ctx.close()
+    return {"workload": f"adjoint column R = 0.02 m, H = 2R, h = R/25 ({wl.n} particles), "
+                        "200 FP64 steps, checkpoint every 20, phi 0.5, free-surface ghosts, "
+                        "radial flow 0.5 m/s",
+            "forward_ms": out["forward"], "adjoint_ms": out["adjoint"],
+            "adjoint_over_forward": out["adjoint"] / out["forward"],
+            "value": wl.n * nsteps / (out["adjoint"] / 1e3),
+            "unit": "particle-steps/s differentiated (d/d(mu_s, mu_2, I0) of every state field)",
+            "dL_dmui": [float(v) for v in dmui.cpu()], "n_nonfinite": d["n_nonfinite"]}
 
 
 def periodic_layer(args, dev, stream, world):
