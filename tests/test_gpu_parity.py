@@ -851,6 +851,64 @@ def test_columns_smallest_four_500_steps(dev, capi, orc):
 
 
 @pytest.mark.slow
+def test_columns_full_batch_bench_configuration(dev, capi, orc):
+    """The batched workload at full size (256 columns, 4.79M particles) in the
+    benchmark's launch configuration: float-float fits, the autotuned
+    schedule, Verlet skin 0.1h, one lp_step call of 10 steps. Graph replay and
+    the persistent launch give the same bits. Six columns spread over the size
+    range (the two smallest, the quartiles and the largest) each match the
+    oracle run on that column alone within 1e-10, and each equals, bit for
+    bit, the same column stepped alone on the GPU: a column's result does not
+    depend on the batch around it."""
+    wl = W.columns()
+    pd = W.param_dict(wl)
+    offs = wl.column_offsets
+    ncol = len(offs) - 1
+    sizes = np.diff(offs)
+    order = np.argsort(sizes, kind="stable")
+    pick = sorted({int(order[0]), int(order[1]), int(order[ncol // 4]), int(order[ncol // 2]),
+                   int(order[3 * ncol // 4]), int(order[-1])})
+    m, eos = _dicts(pd)
+    mui_c = [dict(m, mu_s=float(mu)) for mu in wl.mu_s_col]
+    stream = torch.cuda.Stream()
+    nst = 10
+    prm = _prm(pd, precision=2, launch_mode=capi.LP_LAUNCH_GRAPH, skin=0.1 * pd["h"])
+    ctx = capi.Context(wl.n, max_columns=ncol, cap=64)
+    init = {k: T(wl.state[k], dev) for k in capi.FIELDS}
+    tune = capi.lp_autotune(ctx, init, mui_c, eos, prm, pd["dt"], 3, column_offsets=offs,
+                            stream=stream)
+    print("autotuned schedule:", tune)
+    outs = {}
+    for mode in (capi.LP_LAUNCH_GRAPH, capi.LP_LAUNCH_PERSISTENT):
+        st = {k: v.clone() for k, v in init.items()}
+        with torch.cuda.stream(stream):
+            capi.lp_step(ctx, st, mui_c, eos, dict(prm, launch_mode=mode), pd["dt"], nst,
+                         column_offsets=offs, stream=stream)
+        d = ctx.sync(stream)
+        assert d["n_nonfinite"] == 0 and d["n_overflow"] == 0, (mode, d)
+        outs[mode] = {k: st[k].cpu().numpy() for k in capi.FIELDS}
+    for k in capi.FIELDS:
+        assert np.array_equal(outs[capi.LP_LAUNCH_GRAPH][k], outs[capi.LP_LAUNCH_PERSISTENT][k]), k
+    got = outs[capi.LP_LAUNCH_GRAPH]
+    for c in pick:
+        b, e = int(offs[c]), int(offs[c + 1])
+        sc = {k: v[b:e] for k, v in wl.state.items()}
+        ref, _ = orc.step(sc, orc.params(**dict(pd, mu_s=float(wl.mu_s_col[c]))), nst,
+                          brute=False)
+        gc = {k: got[k][b:e] for k in got}
+        err = _state_err(gc, ref, sc)
+        print(f"column {c} ({e - b} particles) 10-step errors:",
+              {k: f"{v:.2e}" for k, v in err.items()})
+        assert max(err.values()) <= 1e-10, (c, err)
+        alone = W.Workload("column", pd["h"], pd["radius"], pd["dt"], sc)
+        ga, da = _run_gpu(capi, dev, alone, pd, nst, prec=2, mui=mui_c[c],
+                          launch_mode=capi.LP_LAUNCH_GRAPH, skin=0.1 * pd["h"], stream=stream)
+        assert da["n_nonfinite"] == 0
+        for k in capi.FIELDS:
+            assert np.array_equal(ga[k], gc[k]), (c, k)
+
+
+@pytest.mark.slow
 def test_step_full_size_cylinder(dev, capi, orc):
     """The column of radius 0.02 m at spacing R/50 (785k particles), three FP64
     steps in the launch configuration the benchmark uses, against the oracle on
