@@ -173,7 +173,7 @@ def _peaks():
         return {}
 
 
-KERNEL_SOURCES = ("fit.cu", "fit_bodies.cuh", "lp_internal.cuh")
+KERNEL_SOURCES = ("fit.cu", "fit_bodies.cuh", "lp_internal.cuh", "ff_split.cuh")
 
 
 def kernel_source_hash() -> str:

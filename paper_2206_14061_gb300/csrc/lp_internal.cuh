@@ -8,6 +8,7 @@
 #include <type_traits>
 
 #include "lp.h"
+#include "ff_split.cuh"
 
 namespace lp {
 
@@ -208,8 +209,12 @@ __device__ __forceinline__ ff ff_recip(ff d) {
   const float e = __fsub_rn(__fsub_rn(1.f, t.h), t.l);
   return fast_two_sum(y, __fmul_rn(y, e));
 }
+// (RN(d), RN(d - RN(d))): integer split on the fast range (ff_split.cuh), FP64
+// conversions elsewhere; the same bits either way
 __device__ __forceinline__ ff ff_of(double d) {
-  const float h = __double2float_rn(d);
+  float h, l;
+  if (ff_split_fast(d, &h, &l)) return {h, l};
+  h = __double2float_rn(d);
   return {h, __double2float_rn(d - (double)h)};
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.h + (double)a.l; }

@@ -931,6 +931,33 @@ def test_step_full_size_cylinder(dev, capi, orc):
 
 
 @pytest.mark.slow
+def test_step_full_size_cylinder_20_steps(dev, capi, orc):
+    """The full column (785k particles), 20 steps in one lp_step call (graph
+    replay, Verlet skin 0.1h), FP64 and float-float, against the oracle's
+    20-step run on every particle. Between steps 10 and 20 the column starts
+    to blow up: the inertial-regime equations grow short waves at this
+    spacing, and the largest speed goes from about 3e-4 to about 9 m/s at a
+    few particles (9 above 0.1 m/s; all still inertial, displacements below
+    0.01h). A 1e-15 relative perturbation of the start grows to about 1.5e-12
+    of each field's scale on the oracle over these 20 steps, so the bars stay
+    1e-9 (FP64) and 1e-10 (float-float)."""
+    wl = W.cylinder()
+    pd = W.param_dict(wl)
+    ref, rd = orc.step(wl.state, orc.params(**pd), 20, brute=False)
+    print(f"oracle after 20 steps: max|u| {np.abs(ref['u']).max():.3e} m/s, "
+          f"max|w| {np.abs(ref['w']).max():.3e} m/s")
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
+        got, d = _run_gpu(capi, dev, wl, pd, 20, prec=prec, launch_mode=capi.LP_LAUNCH_GRAPH,
+                          skin=0.1 * pd["h"], stream=torch.cuda.Stream())
+        assert d["n_nonfinite"] == 0
+        e = _state_err(got, ref, wl.state)
+        print(f"cylinder 20-step precision {prec} errors:",
+              {k: f"{v:.2e}" for k, v in e.items()},
+              {k: d[k] for k in ("n_gas", "n_quasistatic", "n_fallback")})
+        assert max(e.values()) <= tol, (prec, e)
+
+
+@pytest.mark.slow
 def test_step_full_size_cylinder_bench_configuration(dev, capi, orc):
     """The benchmark's exact launch configuration on the full column (785k
     particles): float-float fits, graph replay, Verlet skin 0.1h, two lp_step
