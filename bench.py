@@ -236,7 +236,7 @@ def pass1_work(prec: str, rows: float, n: int):
             "nominal FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)")
 
 
-PASS1_KERNELS = {"mixed_ff": "k_gram_ff + k_pass1_ff", "mixed": "k_pass1", "fp64": "k_pass1"}
+PASS1_KERNELS = {"mixed_ff": "k_gram_ff + k_pass1_ff_rows + k_pass1_ff_solve", "mixed": "k_pass1", "fp64": "k_pass1"}
 
 
 def our_arm(args):

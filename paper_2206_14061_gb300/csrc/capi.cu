@@ -128,6 +128,7 @@ struct lp_ctx {
   unsigned* bar = nullptr;   // grid barrier of the persistent kernel
   FF8* XU = nullptr;  // split positions and velocities (LP_MIXED_FF)
   float2* P1s = nullptr;  // float-float gdot and ld of pass 1 (LP_MIXED_FF)
+  float2* R1 = nullptr;   // float-float right-hand sides of pass 1 (LP_MIXED_FF)
   float2* fit_fs = nullptr;  // split fields of lp_fit_derivatives (LP_MIXED_FF), lazily
   int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
   int32_t* gcnt = nullptr;    // ghost entries per stencil
@@ -399,7 +400,7 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.p1 = c->p1; A.fbgrad = c->fbgrad; A.dg = c->dg;
   A.K = K;
   A.grids = c->d_grids;
-  A.XU = c->XU; A.Lff = c->Lff; A.P1s = c->P1s;
+  A.XU = c->XU; A.Lff = c->Lff; A.P1s = c->P1s; A.R1 = c->R1;
   A.perm = LP_ROW_ORDER ? c->perm : nullptr;
   A.Xfix = c->Xfix;
   A.gcnt = c->gcnt;
@@ -705,6 +706,7 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->bar, 2);
   if (s == LP_OK) s = dalloc(c, &c->XU, n);
   if (s == LP_OK) s = dalloc(c, &c->P1s, n * 9);
+  if (s == LP_OK) s = dalloc(c, &c->R1, n * 27);
   if (s == LP_OK) s = dalloc(c, &c->Lff, n * kTri);
   if (s == LP_OK) s = dalloc(c, &c->Xfix, n);
   if (s == LP_OK) s = dalloc(c, &c->gcnt, n);

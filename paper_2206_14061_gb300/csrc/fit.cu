@@ -98,9 +98,13 @@ __global__ void __launch_bounds__(kFFBlock, 4) k_gram_ff(const StepArgs A) {
 }
 
 template <bool PER>
-__global__ void __launch_bounds__(kFFBlock, 4) k_pass1_ff(const StepArgs A) {
+__global__ void __launch_bounds__(kFFBlock, 4) k_pass1_ff_rows(const StepArgs A) {
   const int s = fit_particle(A);
-  if (s < A.n) pass1_body<LP_MIXED_FF, PER>(A, s);
+  if (s < A.n) pass1_ff_rows_body<PER>(A, s);
+}
+__global__ void __launch_bounds__(kFFBlock) k_pass1_ff_solve(const StepArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) pass1_ff_solve_body(A, s);
 }
 
 __global__ void k_split_state(const StepArgs A) {
@@ -455,12 +459,13 @@ void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs) {
     if (per) {
       if (A.K.free_surface) k_gram_twins<true><<<ng, 128, 0, st>>>(A);
       k_gram_ff<true><<<nf, b, 0, st>>>(A);
-      k_pass1_ff<true><<<nf, b, 0, st>>>(A);
+      k_pass1_ff_rows<true><<<nf, b, 0, st>>>(A);
     } else {
       if (A.K.free_surface) k_gram_twins<false><<<ng, 128, 0, st>>>(A);
       k_gram_ff<false><<<nf, b, 0, st>>>(A);
-      k_pass1_ff<false><<<nf, b, 0, st>>>(A);
+      k_pass1_ff_rows<false><<<nf, b, 0, st>>>(A);
     }
+    k_pass1_ff_solve<<<(A.n + kFFBlock - 1) / kFFBlock, kFFBlock, 0, st>>>(A);
   }
   k_pass1_fallback<<<152, 64, 0, st>>>(A);
 }

@@ -773,10 +773,10 @@ __device__ __forceinline__ void pass1_finish_ff(const StepArgs& A, int s, const 
   p[P1_VN * n + s] = Vi + A.K.dt * (Vi * dv);
 }
 
-// pass 1 in float-float: right-hand sides of u, v, w and the solves
+// pass 1 in float-float, first half: the right-hand sides A^T b of u, v, w
+// (unnormalised float-float accumulators, left in R)
 template <bool PER>
-__device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
-  if (A.fbslot[s] != -1) return;  // queued for the pivoted-QR fit
+__device__ __forceinline__ void pass1_ff_rhs(const StepArgs& A, int s, ff (*R)[kNB]) {
   const int n = A.n;
   const int m = min(A.cnt[s], A.cap);  // ghost rows carry b = 0: no right-hand side
   const float4 hi = A.XU[s].xh, lo = A.XU[s].xl;
@@ -784,7 +784,6 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
   const int mm = A.K.mirror_mode;
   const float sg[3] = {mm == LP_MIRROR_NOSLIP ? -1.f : 1.f, mm == LP_MIRROR_NOSLIP ? -1.f : 1.f,
                        mm != LP_MIRROR_NONE ? -1.f : 1.f};
-  ff R[3][kNB];
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -823,7 +822,51 @@ __device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
       for (int q = 0; q < kNB; ++q) ff_acc(R[f][q], b, a[q]);
     }
   }
+}
+
+// pass 1 in float-float: right-hand sides, solves and derived values in one
+// thread (the persistent launch)
+template <bool PER>
+__device__ __forceinline__ void pass1_ff_body(const StepArgs& A, int s) {
+  if (A.fbslot[s] != -1) return;  // queued for the pivoted-QR fit
+  ff R[3][kNB];
+  pass1_ff_rhs<PER>(A, s, R);
   ff_chol_solve<3>(A.Lff + s, A.n, R);
+  pass1_finish_ff(A, s, R);
+}
+
+// The same work in two kernels (the per-phase launches): the row loop stores
+// its 27 accumulators as they stand (R1, hi and lo, k-major), and the solve
+// kernel reloads them, so the result is the same bits. Each kernel then keeps
+// one instruction stream: the unrolled row loop (about 530 instructions) or
+// the unrolled three-right-hand-side solve (about 3,100).
+template <bool PER>
+__device__ __forceinline__ void pass1_ff_rows_body(const StepArgs& A, int s) {
+  if (A.fbslot[s] != -1) return;
+  ff R[3][kNB];
+  pass1_ff_rhs<PER>(A, s, R);
+  const int64_t n = A.n;
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) A.R1[(int64_t)(f * kNB + q) * n + s] = make_float2(R[f][q].h, R[f][q].l);
+}
+__device__ __forceinline__ void pass1_ff_solve_body(const StepArgs& A, int s) {
+  if (A.fbslot[s] != -1) return;
+  const int64_t n = A.n;
+  ff R[3][kNB];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+      const float2 v = A.R1[(int64_t)(f * kNB + q) * n + s];
+      R[f][q] = ff{v.x, v.y};
+    }
+  // one field at a time (the same operations per field as the joint solve;
+  // the joint form makes the compiler keep R in local memory here)
+  ff_chol_solve<1>(A.Lff + s, A.n, R + 0);
+  ff_chol_solve<1>(A.Lff + s, A.n, R + 1);
+  ff_chol_solve<1>(A.Lff + s, A.n, R + 2);
   pass1_finish_ff(A, s, R);
 }
 

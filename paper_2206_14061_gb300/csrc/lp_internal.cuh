@@ -262,6 +262,7 @@ struct StepArgs {
   // |gdot| and V^{n+1} split (hi, lo, hi, lo), Gram matrices in float-float
   const GridCol* grids;
   FF8* XU;  // split positions and velocities
+  float2* R1;   // LP_MIXED_FF: pass 1's right-hand sides (27 float-float, k-major)
   float2* P1s;  // LP_MIXED_FF: gdot (6) and ld (3) of pass 1 as float-float, k-major
                 // (null in the other modes)
 
