@@ -285,11 +285,28 @@ __global__ void __launch_bounds__(128, 4) k_fit_gram_ff(const FitArgs F) {
 #pragma unroll
   for (int q = 0; q < 31; ++q) mo[q] = {0.f, 0.f};
   int rows = 0;  // entries with an index in range
+  // the neighbour's position one row ahead, its stencil code two rows ahead
+  float4 jh = make_float4(0.f, 0.f, 0.f, 0.f), jl = jh;
+  auto fetch = [&](uint32_t code) {
+    int j = code & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) j = s;  // never read outside the arrays (row skipped)
+    jh = F.xs[j].xh;
+    jl = F.xs[j].xl;
+  };
+  uint32_t code = m > 0 ? (uint32_t)F.nbr[s] : 0u;
+  uint32_t nxt = m > 1 ? (uint32_t)F.nbr[(int64_t)n + s] : 0u;
+  if (m > 0) fetch(code);
   for (int k = 0; k < m; ++k) {
-    const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
-    const int j = code & ~kMirrorBit;
+    const uint32_t c0 = code;
+    const float4 h0 = jh, l0 = jl;
+    if (k + 1 < m) {
+      code = nxt;
+      fetch(code);
+      if (k + 2 < m) nxt = (uint32_t)F.nbr[(int64_t)(k + 2) * n + s];
+    }
+    const int j = c0 & ~kMirrorBit;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
-    ff_moments_add(mo, ff_row_of<false>(hi, lo, F.xs[j].xh, F.xs[j].xl, code, K0));
+    ff_moments_add(mo, ff_row_of<false>(hi, lo, h0, l0, c0, K0));
     ++rows;
   }
   ff G[kTri];
@@ -307,47 +324,79 @@ __global__ void __launch_bounds__(128, 4) k_fit_gram_ff(const FitArgs F) {
   for (int k = 0; k < kTri; ++k) F.lf[(int64_t)k * n + s] = make_float2(G[k].h, G[k].l);
 }
 
-__global__ void __launch_bounds__(128, 4) k_fit_rhs_ff(const FitArgs F) {
+// Right-hand sides and solves of the float-float fit for the field group
+// f0 .. f0 + NG - 1 (one launch per group): the group's NG x 9 sums stay in
+// registers, and the neighbour's position and field values are loaded one
+// row ahead of the arithmetic (its stencil code two rows ahead), as in the
+// step's row kernels.
+template <int NG>  // 1 or 2; 3 blocks of 168 registers (at 128 the sums spill)
+__global__ void __launch_bounds__(128, 3) k_fit_rhs_ff(const FitArgs F, int f0) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= F.n) return;
   if (!(F.lf[s].x > 0.f)) return;  // queued for the pivoted-QR fit
   const int n = F.n;
   const int m = min(F.cnt[s], F.cap);
+  const int ng = min(NG, F.nf - f0);
   const float4 hi = F.xs[s].xh, lo = F.xs[s].xl;
   const StepConsts K0{};
-  const double ih = F.inv_h, ih2 = ih * ih;
-  for (int f0 = 0; f0 < F.nf; f0 += 3) {  // three fields per sweep
-    const int nf = min(3, F.nf - f0);
-    ff R[3][kNB], si[3];
-    float sg[3];
+  ff R[NG][kNB], si[NG];
+  float sg[NG];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      const float2 v = f < nf ? F.fs[(int64_t)(f0 + f) * n + s] : make_float2(0.f, 0.f);
-      si[f] = ff{v.x, v.y};
-      sg[f] = f < nf ? (float)F.msign[f0 + f] : 0.f;
+  for (int f = 0; f < NG; ++f) {
+    const float2 v = f < ng ? F.fs[(int64_t)(f0 + f) * n + s] : make_float2(0.f, 0.f);
+    si[f] = ff{v.x, v.y};
+    sg[f] = f < ng ? (float)F.msign[f0 + f] : 0.f;
 #pragma unroll
-      for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+    for (int q = 0; q < kNB; ++q) R[f][q] = {0.f, 0.f};
+  }
+  float4 jh = make_float4(0.f, 0.f, 0.f, 0.f), jl = jh;
+  float2 jv[NG];
+  auto fetch = [&](uint32_t code) {
+    int j = code & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) j = s;  // never read outside the arrays (row skipped)
+    jh = F.xs[j].xh;
+    jl = F.xs[j].xl;
+#pragma unroll
+    for (int f = 0; f < NG; ++f)
+      jv[f] = f < ng ? F.fs[(int64_t)(f0 + f) * n + j] : make_float2(0.f, 0.f);
+  };
+  uint32_t code = m > 0 ? (uint32_t)F.nbr[s] : 0u;
+  uint32_t nxt = m > 1 ? (uint32_t)F.nbr[(int64_t)n + s] : 0u;
+  if (m > 0) fetch(code);
+  for (int k = 0; k < m; ++k) {
+    const uint32_t c0 = code;
+    const float4 h0 = jh, l0 = jl;
+    float2 v0[NG];
+#pragma unroll
+    for (int f = 0; f < NG; ++f) v0[f] = jv[f];
+    if (k + 1 < m) {
+      code = nxt;
+      fetch(code);
+      if (k + 2 < m) nxt = (uint32_t)F.nbr[(int64_t)(k + 2) * n + s];
     }
-    for (int k = 0; k < m; ++k) {
-      const uint32_t code = (uint32_t)F.nbr[(int64_t)k * n + s];
-      const int j = code & ~kMirrorBit;
-      if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
-      const bool mir = code >> 31;
-      ff a[kNB];
-      ff_taylor(ff_row_of<false>(hi, lo, F.xs[j].xh, F.xs[j].xl, code, K0), a);
+    const int j = c0 & ~kMirrorBit;
+    if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
+    const bool mir = c0 >> 31;
+    ff a[kNB];
+    ff_taylor(ff_row_of<false>(hi, lo, h0, l0, c0, K0), a);
 #pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        if (f < nf) {
-          const float2 v = F.fs[(int64_t)(f0 + f) * n + j];
-          const float sj = mir ? sg[f] : 1.f;  // the field at a floor mirror
-          const ff b = ff_diff(sj * v.x, sj * v.y, si[f].h, si[f].l);
+    for (int f = 0; f < NG; ++f) {
+      if (f < ng) {
+        const float sj = mir ? sg[f] : 1.f;  // the field at a floor mirror
+        const ff b = ff_diff(sj * v0[f].x, sj * v0[f].y, si[f].h, si[f].l);
 #pragma unroll
-          for (int q = 0; q < kNB; ++q) ff_acc(R[f][q], b, a[q]);
-        }
+        for (int q = 0; q < kNB; ++q) ff_acc(R[f][q], b, a[q]);
       }
     }
-    ff_chol_solve<3>(F.lf + s, n, R);
-    for (int f = 0; f < nf; ++f) {
+  }
+  // one field at a time: the joint solve of a 2-D array of sums makes the
+  // compiler keep them in local memory
+  ff_chol_solve<1>(F.lf + s, n, R + 0);
+  if (NG > 1) ff_chol_solve<1>(F.lf + s, n, R + 1);
+  const double ih = F.inv_h, ih2 = ih * ih;
+#pragma unroll
+  for (int f = 0; f < NG; ++f) {
+    if (f < ng) {
       double* o = F.coeffs + ((int64_t)s * F.nf + f0 + f) * kNB;
 #pragma unroll
       for (int q = 0; q < kNB; ++q) o[q] = ff_to_double(R[f][q]) * (q < 3 ? ih : ih2);
@@ -502,7 +551,7 @@ void launch_fit(int prec, const FitArgs& F, cudaStream_t st) {
     const int nf = (F.n + 127) / 128;
     k_fit_split_ff<<<(F.n + 255) / 256, 256, 0, st>>>(F);
     k_fit_gram_ff<<<nf, 128, 0, st>>>(F);
-    k_fit_rhs_ff<<<nf, 128, 0, st>>>(F);
+    for (int f0 = 0; f0 < F.nf; f0 += 2) k_fit_rhs_ff<2><<<nf, 128, 0, st>>>(F, f0);
   }
   k_fit_fallback<<<152, 64, 0, st>>>(F);
 }
