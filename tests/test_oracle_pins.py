@@ -566,6 +566,36 @@ def test_quasistatic_and_gas_accelerations(orc):
     assert np.array_equal(det2["acc"], np.tile([0.0, 0.0, p.gz], (x.size, 1)))
 
 
+def test_hydrostatic_layer_is_at_rest_to_second_order(orc):
+    """A quasi-static layer in hydrostatic balance (Sec. 2.2.1 with Eq. 2-4):
+    with a = beta grad V / V + g, the profile V(z) = V_b exp(-g_z z / beta)
+    makes a = 0 exactly. On the lattice the quadratic fit of V leaves a
+    residual acceleration that falls as h^2 (order > 1.7 from h to h/2), and
+    every particle stays quasi-static. beta = 1 m^2/s^2 gives the profile
+    enough curvature (k h = 0.01) for the truncation error to stand above
+    rounding; interior particles only (the faces have one-sided stencils)."""
+    beta = 1.0
+    k = 9.81 / beta
+    res = []
+    for nside, h in ((8, 1e-3), (16, 5e-4)):
+        rng = np.random.default_rng(21)
+        x, y, z = W.lattice_box(nside, nside, nside, h, 0.05, rng)
+        z = z + 0.02
+        V = (1 / 0.64) * np.exp(k * (z - 0.02))
+        assert (1 / V).min() > 0.59  # quasi-static throughout
+        p = _p(orc, h=h, radius=2.2 * h, mirror_mode=0, beta=beta, alpha=-beta * 0.59)
+        det = orc.step_detail(_state(x, y, z, V=V), p)
+        assert (det["regime"] == 2).all()
+        L = nside * h
+        inner = ((x > 2.2 * h) & (x < L - 2.2 * h) & (y > 2.2 * h) & (y < L - 2.2 * h)
+                 & (z > 0.02 + 2.2 * h) & (z < 0.02 + L - 2.2 * h))
+        assert inner.sum() >= 8
+        res.append(np.abs(det["acc"][inner]).max())
+    # the residual is 1e-4 of g at h = 1e-3 (3.9e-4 m/s^2), and it falls as h^2
+    assert res[0] < 1e-3, res
+    assert math.log2(res[0] / res[1]) > 1.7, res
+
+
 def test_rotation_covariance(orc):
     """Rotating the column by 90 degrees about z rotates every output."""
     rng = np.random.default_rng(13)
