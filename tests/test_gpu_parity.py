@@ -612,6 +612,38 @@ def test_step_columns_match_oracle_per_column(dev, capi, orc):
         assert max(err.values()) <= 1e-9, (c, err)
 
 
+def test_step_all_three_regimes(dev, capi, orc):
+    """A sheared 12^3 cube on the no-slip floor whose solid fraction
+    0.47 + 0.14 sin(2 pi x/L) cos(2 pi y/L + 0.3) spans the gas (phi <= 0.35),
+    inertial and quasi-static (phi > 0.59) regimes: every branch of the
+    acceleration (Sec. 2.2-2.3) and the regime decision run in one step. A
+    soft quasi-static law (beta = 0.1 m^2/s^2, alpha = -beta phi_max) keeps the
+    regime boundaries sane over the 30 steps (a 1e-15 perturbation of the
+    start grows to about 3e-13 on the oracle). FP64 and float-float, kernels
+    and graph replay, against the oracle on every particle."""
+    h = 1e-3
+    x, y, z = W.lattice_box(12, 12, 12, h, 0.05, np.random.default_rng(31))
+    L = 12 * h
+    phi = 0.47 + 0.14 * np.sin(2 * np.pi * x / L) * np.cos(2 * np.pi * y / L + 0.3)
+    st = dict(x=x, y=y, z=z, u=z * (1 + 0.2 * np.sin(2 * np.pi * y / L)),
+              v=0.4 * z * np.cos(2 * np.pi * x / L), w=np.zeros(x.size), V=1 / phi)
+    pd = dict(W.param_dict(W.cube(12)), beta=0.1, alpha=-0.1 * 0.59)
+    ref, rd = orc.step(st, orc.params(**pd), 30, brute=False)
+    assert rd["n_gas"] > 0 and rd["n_quasistatic"] > 0 and rd["n_inertial"] > 0
+    wl = W.Workload("three_regimes", h, pd["radius"], pd["dt"], st)
+    for prec, tol in ((0, 1e-9), (2, 1e-10)):
+        for mode in (capi.LP_LAUNCH_KERNELS, capi.LP_LAUNCH_GRAPH):
+            got, d = _run_gpu(capi, dev, wl, pd, 30, prec=prec, launch_mode=mode,
+                              stream=torch.cuda.Stream())
+            assert d["n_nonfinite"] == 0
+            assert d["n_gas"] == rd["n_gas"] and d["n_quasistatic"] == rd["n_quasistatic"], (
+                prec, mode, d["n_gas"], d["n_quasistatic"], rd["n_gas"], rd["n_quasistatic"])
+            e = _state_err(got, ref, st)
+            print(f"three regimes, precision {prec}, mode {mode}:",
+                  {k: f"{v:.2e}" for k, v in e.items()})
+            assert max(e.values()) <= tol, (prec, mode, e)
+
+
 def test_step_edge_cases(dev, capi, orc):
     pd = W.param_dict(W.cube(2))
     # empty set: no work, no error
