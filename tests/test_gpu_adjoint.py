@@ -86,6 +86,55 @@ def test_adjoint_matches_oracle_tangent_small(dev, orc):
             assert abs(fd - a) <= 1e-5 * abs(a) + 1e-6, (i, k, fd, a)
 
 
+def test_adjoint_across_all_three_regimes(dev, orc):
+    """The adjoint on a sheared cube that spans the gas, inertial and
+    quasi-static regimes (solid fraction 0.47 + 0.14 sin(2 pi x/L)
+    cos(2 pi y/L + 0.3), soft quasi-static law beta = 0.1 m^2/s^2), 12 FP64
+    steps with stencils rebuilt every 4: dL/d(mu_s, mu_2, I0) equals the
+    oracle's tangent-linear run, and dL/d(initial u, V) of the most
+    compacted (quasi-static), the loosest (gas) and a mid-range (inertial)
+    particle match central differences of lp_step. Regimes are frozen at
+    their forward values, so the steps of the differences change none."""
+    from paper_2206_14061_gb300 import capi
+    h = 1e-3
+    x, y, z = W.lattice_box(12, 12, 12, h, 0.05, np.random.default_rng(31))
+    L = 12 * h
+    phi = 0.47 + 0.14 * np.sin(2 * np.pi * x / L) * np.cos(2 * np.pi * y / L + 0.3)
+    s0 = dict(x=x, y=y, z=z, u=z * (1 + 0.2 * np.sin(2 * np.pi * y / L)),
+              v=0.4 * z * np.cos(2 * np.pi * x / L), w=np.zeros(x.size), V=1 / phi)
+    pd = dict(W.param_dict(W.cube(12)), beta=0.1, alpha=-0.1 * 0.59)
+    mui, eos, prm = _split(pd)
+    nsteps, C = 12, 4
+    n = x.size
+    rng = np.random.default_rng(5)
+    w = {k: rng.standard_normal(n) for k in capi.FIELDS}
+    ctx = capi.Context(n, cap=64)
+    init = {k: torch.tensor(s0[k], device=dev) for k in capi.FIELDS}
+    seed = {k: torch.tensor(w[k], device=dev) for k in capi.FIELDS}
+    dmui, gi = capi.lp_step_adjoint(ctx, init, mui, eos, prm, pd["dt"], nsteps, C, seed,
+                                    want_initial=True)
+    got = dmui.cpu().numpy()
+    _, tan = orc.step_tangent(s0, orc.params(**pd), nsteps, rebuild_every=C)
+    ref = np.array([sum((w[k] * tan[t, f]).sum() for f, k in enumerate(capi.FIELDS))
+                    for t in range(3)])
+    print("three regimes: adjoint", got, "tangent", ref)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max(), (got, ref)
+    Lf = lambda st: sum(float((st[k].cpu().numpy() * w[k]).sum()) for k in capi.FIELDS)
+    picks = (int(np.argmax(phi)), int(np.argmin(phi)), int(np.argmin(np.abs(phi - 0.47))))
+    assert phi[picks[0]] > 0.6 and phi[picks[1]] < 0.34
+    for i in picks:
+        for k, eps in (("u", 1e-7), ("V", 1e-8)):
+            sp = {q: v.copy() for q, v in s0.items()}
+            sm = {q: v.copy() for q, v in s0.items()}
+            sp[k][i] += eps
+            sm[k][i] -= eps
+            fd = (Lf(_gpu_final(capi, ctx, sp, mui, eos, prm, pd["dt"], nsteps, C, dev)) -
+                  Lf(_gpu_final(capi, ctx, sm, mui, eos, prm, pd["dt"], nsteps, C, dev))) / (2 * eps)
+            a = float(gi[k][i].item())
+            print(f"particle {i} (phi {phi[i]:.3f}) dL/d{k}: adjoint {a:.9e}, differences {fd:.9e}")
+            assert abs(fd - a) <= 1e-5 * abs(a) + 1e-6, (i, k, fd, a)
+
+
 def test_adjoint_column_against_finite_differences(dev, orc):
     """Column of radius 0.02 m at spacing R/25 (98,800 particles), 30 FP64
     steps, stencils rebuilt every 10 steps (the stable horizon of this column
