@@ -409,7 +409,12 @@ lp_status lp_autotune(lp_ctx* ctx, const lp_particles* p, const lp_mui* mui, con
  * |gdot| = 0. seed holds dL/d(final x, y, z, u, v, w, V) (device). On return
  * dL_dmui (device, 3 doubles) holds dL/d(mu_s, mu_2, I0) summed over all
  * columns, and if dL_dinitial is non-NULL its arrays receive dL/d(initial
- * state). Synchronises. Requires p->ncolumns == 1 in this version. */
+ * state). Synchronises. Requires p->ncolumns == 1 in this version.
+ * Workspace (allocated and freed by the call): the checkpoints and one
+ * segment's states and adjoints, plus, for the paper's step, each segment
+ * step's fit data (about 860 bytes per particle and step) so that the reverse
+ * sweep need not recompute it; when that part cannot be allocated the steps
+ * are recomputed instead, with the same result. */
 lp_status lp_step_adjoint(lp_ctx* ctx, const lp_particles* initial, const lp_mui* mui,
                           const lp_eos* eos, const lp_params* params, double dt, int32_t nsteps,
                           int32_t checkpoint_every, const lp_particles* seed, double* dL_dmui,

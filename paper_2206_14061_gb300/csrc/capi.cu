@@ -1456,6 +1456,32 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
     cudaFree(W);
     return LP_ERR_OOM;
   }
+  // Per-step fit data of one segment (the paper's step; Heun's method keeps
+  // recomputing): the segment's re-run keeps each step's factors, pass-1
+  // outputs, coefficients and QR-fallback slots and gradients, so the reverse
+  // sweep reads them instead of computing each step a third time. Without
+  // room for them the step is recomputed as before.
+  const size_t per_step = N * (size_t)(P1_N + kTri + 27 + 18) + (size_t)c->fb_cap * 6;
+  double* Wk = nullptr;
+  int32_t* Fk = nullptr;
+  if (!heun) {
+    if (cudaMalloc(&Wk, per_step * (size_t)C * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&Fk, N * (size_t)C * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(Wk);
+      Wk = nullptr;
+      Fk = nullptr;
+    }
+  }
+  struct StepData {
+    double *p1, *fac, *coef1, *coef2, *fbgrad;
+    int32_t* fbslot;
+  };
+  auto step_data = [&](int k) {
+    double* b = Wk + per_step * (size_t)k;
+    return StepData{b, b + N * P1_N, b + N * (P1_N + kTri), b + N * (P1_N + kTri + 27),
+                    b + N * (P1_N + kTri + 45), Fk + N * (size_t)k};
+  };
   lp_status rs = LP_OK;
   do {
     if (cudaMemcpy(dtab, tab.data(), sizeof(double*) * ntab, cudaMemcpyHostToDevice) !=
@@ -1522,6 +1548,11 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
       };
       for (int k = 0; k < steps; ++k) {
         if (!heun) {
+          if (Wk) {
+            const StepData d = step_data(k);
+            S.p1 = d.p1; S.fac = d.fac; S.coef1 = d.coef1; S.coef2 = d.coef2;
+            S.fbslot = d.fbslot; S.fbgrad = d.fbgrad;
+          }
           one_pass(kept(k), kept(k + 1));
         } else {  // two stages on the segment's stencils, then the average
           one_pass(kept(2 * k), kept(2 * k + 1));
@@ -1529,26 +1560,37 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
           launch_heun_combine(n, kept(2 * k + 2), kept(2 * k), K.Lx, K.Ly, st);
         }
       }
+      S.p1 = c->p1; S.fac = c->fac; S.coef1 = S.coef2 = nullptr;
+      S.fbslot = c->fbslot; S.fbgrad = c->fbgrad;
       // adjoint to the sorted order of this segment
       launch_gather_fields(n, c->ids[c->ci], (const double* const*)(dtab + tlam + 7 * cur),
                            dtab + tlam + 7 * (1 - cur), 7, st);
       cur = 1 - cur;
       // adjoint of one step (the paper's) or one stage (Heun's method) from
       // state `sk`: l0 = J^T l1, after recomputing that step's fits
-      auto adjoint_at = [&](double* const* sk, const double* l1, double* l0) {
-        double* const out[7] = {scratch,         scratch + N,     scratch + 2 * N,
-                                scratch + 3 * N, scratch + 4 * N, scratch + 5 * N,
-                                scratch + 6 * N};
-        S.coef1 = coef1;
-        S.coef2 = coef2;
-        one_pass(sk, out);
-        S.coef1 = S.coef2 = nullptr;
+      // (k_stored >= 0: the step's fit data kept by the segment's re-run)
+      auto adjoint_at = [&](double* const* sk, const double* l1, double* l0, int k_stored) {
         AdjArgs J{};
         J.n = n; J.cap = c->cap;
-        J.x = S.x; J.y = S.y; J.z = S.z; J.u = S.u; J.v = S.v; J.w = S.w; J.V = S.V;
-        J.nbr = c->nbr; J.cnt = c->cnt; J.colid = c->colid[c->ci]; J.fbslot = c->fbslot;
-        J.mui = c->d_mui; J.fac = c->fac; J.p1 = c->p1; J.coef1 = coef1; J.coef2 = coef2;
-        J.fbgrad = c->fbgrad; J.K = K;
+        J.x = sk[0]; J.y = sk[1]; J.z = sk[2]; J.u = sk[3]; J.v = sk[4]; J.w = sk[5];
+        J.V = sk[6];
+        J.nbr = c->nbr; J.cnt = c->cnt; J.colid = c->colid[c->ci]; J.mui = c->d_mui;
+        if (k_stored >= 0) {
+          const StepData d = step_data(k_stored);
+          J.fbslot = d.fbslot; J.fac = d.fac; J.p1 = d.p1; J.coef1 = d.coef1;
+          J.coef2 = d.coef2; J.fbgrad = d.fbgrad;
+        } else {
+          double* const out[7] = {scratch,         scratch + N,     scratch + 2 * N,
+                                  scratch + 3 * N, scratch + 4 * N, scratch + 5 * N,
+                                  scratch + 6 * N};
+          S.coef1 = coef1;
+          S.coef2 = coef2;
+          one_pass(sk, out);
+          S.coef1 = S.coef2 = nullptr;
+          J.fbslot = c->fbslot; J.fac = c->fac; J.p1 = c->p1; J.coef1 = coef1; J.coef2 = coef2;
+          J.fbgrad = c->fbgrad;
+        }
+        J.K = K;
         for (int f = 0; f < 7; ++f) {
           J.l1[f] = l1 + f * N;
           J.l0[f] = l0 + f * N;
@@ -1559,14 +1601,14 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
       };
       for (int k = steps - 1; k >= 0; --k) {
         if (!heun) {
-          adjoint_at(kept(k), lam[cur], lam[1 - cur]);
+          adjoint_at(kept(k), lam[cur], lam[1 - cur], Wk ? k : -1);
         } else {
           // y^{k+1} = (y^k + y**) / 2: half the adjoint to each; then the second
           // stage (from y*) and the first (from y^k), and the direct half
           launch_axpby((int64_t)(7 * N), 0.0, lam[cur], 0.5, lam[cur], st);
           cudaMemcpyAsync(lamH, lam[cur], sizeof(double) * 7 * N, cudaMemcpyDeviceToDevice, st);
-          adjoint_at(kept(2 * k + 1), lamH, lamS);
-          adjoint_at(kept(2 * k), lamS, lam[1 - cur]);
+          adjoint_at(kept(2 * k + 1), lamH, lamS, -1);
+          adjoint_at(kept(2 * k), lamS, lam[1 - cur], -1);
           launch_axpby((int64_t)(7 * N), 1.0, lam[cur], 1.0, lam[1 - cur], st);
         }
         cur = 1 - cur;
@@ -1585,6 +1627,8 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
     if (rs == LP_OK) rs = cuda_status();
   } while (0);
   cudaFree(dtab);
+  cudaFree(Wk);
+  cudaFree(Fk);
   cudaFree(W);
   return rs;
 }
