@@ -267,37 +267,56 @@ __device__ __forceinline__ void neighbors_body(
     if (KEEP) {
       int m = c < kMaxCand ? c : kMaxCand;
       if (m > cap) {
-        auto key = [&](uint32_t code) {
-          return ((uint32_t)ids[code & ~kMirrorBit] << 1) | (code >> 31);
-        };
+        // tie-break keys (original index, then real before mirror), read once
+        uint32_t kk[kMaxCand];
+        for (int t = 0; t < m; ++t)
+          kk[t] = ((uint32_t)ids[cj[t] & ~kMirrorBit] << 1) | (cj[t] >> 31);
         // octant-balanced: each candidate's round is its nearest-first rank
         // among the candidates of its own octant (stored over co[])
         if (keep_mode == 2) {
           uint8_t rk[kMaxCand];
           for (int t = 0; t < m; ++t) {
-            const uint32_t kt = key(cj[t]);
             int r = 0;
             for (int u = 0; u < m; ++u)
-              r += (u != t && co[u] == co[t] && cand_less(cd2[u], key(cj[u]), cd2[t], kt));
+              r += (u != t && co[u] == co[t] && cand_less(cd2[u], kk[u], cd2[t], kk[t]));
             rk[t] = (uint8_t)r;
           }
           for (int t = 0; t < m; ++t) co[t] = rk[t];
         }
-        // partial selection sort: the first cap of the ordering to the front
-        for (int t = 0; t < cap; ++t) {
-          int best = t;
-          uint32_t kb = key(cj[t]);
-          for (int u = t + 1; u < m; ++u) {
-            const uint32_t ku = key(cj[u]);
-            const bool less = keep_mode == 2
-                                  ? cand_less_oct(co[u], cd2[u], ku, co[best], cd2[best], kb)
-                                  : cand_less(cd2[u], ku, cd2[best], kb);
-            if (less) { best = u; kb = ku; }
+        // the first cap of the ordering (keys are unique, so it is one set in
+        // one order): a max-heap of cap candidate indices, in which a
+        // candidate that precedes the top replaces it; then heapsort, so that
+        // hp[0 .. cap-1] lists them in ascending order
+        auto before = [&](int a, int b) {
+          return keep_mode == 2 ? cand_less_oct(co[a], cd2[a], kk[a], co[b], cd2[b], kk[b])
+                                : cand_less(cd2[a], kk[a], cd2[b], kk[b]);
+        };
+        uint8_t hp[LP_MAX_CAP];
+        auto sift_down = [&](int i, int len) {
+          for (;;) {
+            const int l = 2 * i + 1;
+            if (l >= len) break;
+            int big = l;
+            if (l + 1 < len && before(hp[l], hp[l + 1])) big = l + 1;
+            if (!before(hp[i], hp[big])) break;
+            const uint8_t t = hp[i]; hp[i] = hp[big]; hp[big] = t;
+            i = big;
           }
-          const double td = cd2[t]; cd2[t] = cd2[best]; cd2[best] = td;
-          const uint32_t tj = cj[t]; cj[t] = cj[best]; cj[best] = tj;
-          const uint8_t to = co[t]; co[t] = co[best]; co[best] = to;
+        };
+        for (int t = 0; t < cap; ++t) hp[t] = (uint8_t)t;
+        for (int i = cap / 2 - 1; i >= 0; --i) sift_down(i, cap);
+        for (int t = cap; t < m; ++t)
+          if (before(t, hp[0])) {
+            hp[0] = (uint8_t)t;
+            sift_down(0, cap);
+          }
+        for (int e = cap - 1; e > 0; --e) {
+          const uint8_t t = hp[0]; hp[0] = hp[e]; hp[e] = t;
+          sift_down(0, e);
         }
+        uint32_t kept[LP_MAX_CAP];
+        for (int t = 0; t < cap; ++t) kept[t] = cj[hp[t]];
+        for (int t = 0; t < cap; ++t) cj[t] = kept[t];
         m = cap;
       }
       for (int t = 0; t < m; ++t) nbr[(int64_t)t * n + s] = (int32_t)cj[t];
