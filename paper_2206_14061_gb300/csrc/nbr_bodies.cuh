@@ -132,17 +132,19 @@ __device__ __forceinline__ bool exact_in(double xi, double yi, double zi, double
   return d2 <= r2;
 }
 
-// ordering of keep-nearest candidates: nearest first, then original index,
-// then real before mirror
-__device__ __forceinline__ bool cand_less(double da, uint32_t ka, double db, uint32_t kb) {
+// Candidate order of the truncating searches: squared distance, then the key
+// (orig id << 1) | mirror. Squared distances are never negative (nor NaN:
+// such pairs fail the radius test), so the bit patterns of the doubles order
+// as their values and are compared as integers, off the FP64 pipe.
+__device__ __forceinline__ bool cand_less(uint64_t da, uint32_t ka, uint64_t db, uint32_t kb) {
   if (da != db) return da < db;
-  return ka < kb;  // ka = (orig id << 1) | mirror
+  return ka < kb;
 }
 
 // octant-balanced ordering (Sec. 3.1 item 6): round first (a candidate's
 // rank within its own octant), then the nearest-first order
-__device__ __forceinline__ bool cand_less_oct(int ra, double da, uint32_t ka, int rb, double db,
-                                              uint32_t kb) {
+__device__ __forceinline__ bool cand_less_oct(int ra, uint64_t da, uint32_t ka, int rb,
+                                              uint64_t db, uint32_t kb) {
   if (ra != rb) return ra < rb;
   return cand_less(da, ka, db, kb);
 }
@@ -187,7 +189,7 @@ __device__ __forceinline__ void neighbors_body(
     const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
     const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
     const float Lxf = g.Lxf, Lyf = g.Lyf;
-    double cd2[KEEP ? kMaxCand : 1];
+    uint64_t cd2[KEEP ? kMaxCand : 1];  // bit patterns of the squared distances
     uint32_t cj[KEEP ? kMaxCand : 1];
     uint8_t co[KEEP ? kMaxCand : 1];  // octant: bit 0 dx >= 0, bit 1 dy >= 0, bit 2 dz >= 0
     const int ncx = g.nx, ncy = g.ny, ncz = g.nz;
@@ -243,14 +245,14 @@ __device__ __forceinline__ void neighbors_body(
                               PER ? g.Ly : 0.0);
                 // (caller stencils are never periodic: the sign of x_j - x_i
                 // in FP64 is that of the comparison)
-                if (KEEP)
+                if (KEEP && keep_mode == 2)
                   oct = (uint8_t)((x[j] >= xi ? 1 : 0) | (y[j] >= yi ? 2 : 0) | (zj >= zi ? 4 : 0));
               }
               if (!in) continue;
               const uint32_t code = j | (pass ? kMirrorBit : 0u);
               if (KEEP) {
                 if (c < kMaxCand) {
-                  cd2[c] = d2;
+                  cd2[c] = (uint64_t)__double_as_longlong(d2);
                   cj[c] = code;
                   co[c] = oct;
                 } else {
