@@ -818,14 +818,21 @@ def cpu_baseline(wl, pd, budget_s=20.0, steps=None):
     cores = O.max_threads()
     done, t0 = 0, time.perf_counter()
     while True:
-        O.step(wl.state, p, 1, brute=False)
+        O.step(wl.state, p, 1, brute=False, nthreads=cores)
         done += 1
         el = time.perf_counter() - t0
         if (steps is not None and done >= steps) or (steps is None and el >= budget_s):
             break
-    return {"value": wl.n * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} full LP step(s) of the {wl.n}-particle column from its initial "
-                      f"state, grid neighbour search, OpenMP over particles ({el:.1f} s)"}
+    out = {"value": wl.n * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{done} full LP step(s) of the {wl.n}-particle column from its initial "
+                     f"state, grid neighbour search, OpenMP over particles ({el:.1f} s)"}
+    if steps is None:  # one step on one core as well (about 10 s here)
+        t1 = time.perf_counter()
+        O.step(wl.state, p, 1, brute=False, nthreads=1)
+        e1 = time.perf_counter() - t1
+        out["single_thread"] = {"value": wl.n / e1, "unit": UNIT, "cores": 1,
+                                "sample": f"1 full LP step of the same column ({e1:.1f} s)"}
+    return out
 
 
 # -------------------------------------------------------------- reference
