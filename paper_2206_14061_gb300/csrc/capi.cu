@@ -1567,8 +1567,9 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
                            dtab + tlam + 7 * (1 - cur), 7, st);
       cur = 1 - cur;
       // adjoint of one step (the paper's) or one stage (Heun's method) from
-      // state `sk`: l0 = J^T l1, after recomputing that step's fits
-      // (k_stored >= 0: the step's fit data kept by the segment's re-run)
+      // state `sk`: l0 = J^T l1, with the step's fit data kept by the
+      // segment's re-run (k_stored >= 0: its step within the segment) or
+      // recomputed here
       auto adjoint_at = [&](double* const* sk, const double* l1, double* l0, int k_stored) {
         AdjArgs J{};
         J.n = n; J.cap = c->cap;

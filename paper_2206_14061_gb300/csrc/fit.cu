@@ -329,7 +329,9 @@ __global__ void __launch_bounds__(128, 4) k_fit_gram_ff(const FitArgs F) {
 // registers, and the neighbour's position and field values are loaded one
 // row ahead of the arithmetic (its stencil code two rows ahead), as in the
 // step's row kernels.
-template <int NG>  // 1 or 2; 3 blocks of 168 registers (at 128 the sums spill)
+// (NG = 2: a last group of an odd field count holds one field, and its second
+// solve runs on zero sums; 3 blocks of 168 registers, as at 128 the sums spill)
+template <int NG>
 __global__ void __launch_bounds__(128, 3) k_fit_rhs_ff(const FitArgs F, int f0) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= F.n) return;
