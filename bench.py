@@ -60,6 +60,8 @@ def parse():
                     help="skip the line with the column in a spreading flow")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint line (the 200-step adjoint column)")
+    ap.add_argument("--no-collapse", action="store_true",
+                    help="skip the column-collapse validation line (a = 0.6 column, Sec. 4.2.1)")
     ap.add_argument("--no-heun", action="store_true",
                     help="skip the line with Heun's method")
     ap.add_argument("--no-periodic", action="store_true",
@@ -445,6 +447,8 @@ def our_arm(args):
 
     if not args.no_adjoint and world == 1:
         line["adjoint"] = adjoint_line(dev, stream)
+    if not args.no_collapse and world == 1:
+        line["column_collapse"] = collapse_line(dev, stream)
 
     if not args.no_sweep and world == 1:
         line["derivative_sweep"] = derivative_sweep(args, dev, stream)
@@ -588,6 +592,69 @@ def batched(args, dev, stream, rank=0, world=1):
                             "ms_per_step": ms_f / full_steps,
                             "n_nonfinite": d500["n_nonfinite"],
                             "ghost_entries_per_step": d500["n_ghosts"] / full_steps}}
+
+
+def collapse_line(dev, stream):
+    """The column collapse of the paper's validation (Sec. 4.2.1): the
+    a = 0.6 column, r_i = 0.05 m, h_i = a r_i = 0.03 m, 10 particles per
+    radius (h = 5 mm), the paper's mu(I) set (Sec. 4), solid fraction 0.5,
+    free-surface ghosts, float-float with graph replay, run in chunks of 100
+    steps to the fits' t_inf = 3 (h_i/g)^(1/2) or until it blows up (a
+    non-finite value or a speed above 3 m/s), for the benchmark's stiff
+    quasi-static law (beta = 400 m^2/s^2) and a soft one (beta = 1 m^2/s^2).
+    Reports the time reached and the front radius and height over r_i and h_i
+    at each tenth of the run, against the fits of Sec. 4.2 (r_inf/r_i =
+    1 + 1.24 a, h_inf/h_i = 1 for a < 1.7)."""
+    import torch
+
+    from paper_2206_14061_gb300 import capi, workloads as W
+
+    ri, a, g = 0.05, 0.6, 9.81
+    hi = a * ri
+    t_inf = 3.0 * math.sqrt(hi / g)
+    wl = W.cylinder(R=ri, aspect=a, spacing_div=10, jitter=0.05, index=7)
+    pd = dict(W.param_dict(wl), **W.PAPER_MUI)
+    mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
+    dt, chunk = 1e-5, 100
+    nmax = int(math.ceil(t_inf / dt / chunk)) * chunk
+    out = {"workload": f"a = 0.6 column, r_i = 0.05 m, h_i = 0.03 m, h = r_i/10 ({wl.n} "
+                       "particles), paper mu(I) set, phi 0.5, free-surface ghosts, mixed_ff",
+           "t_inf_s": t_inf, "fit_r_inf_over_ri": 1.0 + 1.24 * a, "fit_h_inf_over_hi": 1.0,
+           "runs": []}
+    for beta in (400.0, 1.0):
+        eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max")}
+        eos.update(alpha=-beta * pd["phi_max"], beta=beta)
+        st = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
+        st["V"].fill_(2.0)
+        ctx = capi.Context(wl.n, cap=64)
+        prm = dict(h=wl.h, radius=2.2 * wl.h, gx=0.0, gy=0.0, gz=-g, floor_z=0.0, mirror_mode=1,
+                   precision=PREC["mixed_ff"], rebuild_every=1,
+                   launch_mode=capi.LP_LAUNCH_GRAPH, skin=0.1 * wl.h, free_surface=1)
+        traj, steps, status = [], 0, "reached t_inf"
+        t0 = time.perf_counter()
+        while steps < nmax:
+            with torch.cuda.stream(stream):
+                capi.lp_step(ctx, st, mui, eos, prm, dt, chunk, stream=stream)
+            d = ctx.sync(stream, raise_on_error=False)
+            steps += chunk
+            x, y, z = (st[k].cpu().numpy() for k in "xyz")
+            sp = np.sqrt(sum(st[k].cpu().numpy() ** 2 for k in "uvw"))
+            traj.append((steps * dt, float(np.sqrt(x * x + y * y).max()) / ri,
+                         float(z.max()) / hi, float(sp.max())))
+            if not np.isfinite(sp).all() or sp.max() > 3.0:
+                status = "blew up"
+                break
+            if d["status"] != 0:
+                status = "stopped: " + capi.lib().lp_status_string(int(d["status"])).decode()
+                break
+        wall = time.perf_counter() - t0
+        ctx.close()
+        keep = traj[::max(1, len(traj) // 10)] + traj[-1:]
+        out["runs"].append({"beta": beta, "status": status, "t_reached_s": steps * dt,
+                            "steps": steps, "wall_s": wall,
+                            "trajectory": [{"t_s": t, "r_front_over_ri": r, "h_max_over_hi": h,
+                                            "max_speed": v} for t, r, h, v in keep]})
+    return out
 
 
 def adjoint_line(dev, stream):
