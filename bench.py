@@ -62,6 +62,8 @@ def parse():
                     help="skip the adjoint line (the 200-step adjoint column)")
     ap.add_argument("--no-collapse", action="store_true",
                     help="skip the column-collapse validation line (a = 0.6 column, Sec. 4.2.1)")
+    ap.add_argument("--no-layer", action="store_true",
+                    help="skip the layer-compaction validation line (periodic layer, Sec. 4.1)")
     ap.add_argument("--no-heun", action="store_true",
                     help="skip the line with Heun's method")
     ap.add_argument("--no-periodic", action="store_true",
@@ -449,6 +451,8 @@ def our_arm(args):
         line["adjoint"] = adjoint_line(dev, stream)
     if not args.no_collapse and world == 1:
         line["column_collapse"] = collapse_line(dev, stream)
+    if not args.no_layer and world == 1:
+        line["layer_compaction"] = layer_line(dev, stream)
 
     if not args.no_sweep and world == 1:
         line["derivative_sweep"] = derivative_sweep(args, dev, stream)
@@ -654,6 +658,65 @@ def collapse_line(dev, stream):
                             "steps": steps, "wall_s": wall,
                             "trajectory": [{"t_s": t, "r_front_over_ri": r, "h_max_over_hi": h,
                                             "max_speed": v} for t, r, h, v in keep]})
+    return out
+
+
+def layer_line(dev, stream):
+    """The layer compaction of the paper's verification (Sec. 4.1): the
+    periodic layer, 0.03 m high, 8 x 8 particles across (period 8 mm along x
+    and y), h = 1e-3, at rest, solid fraction 0.50 at the floor to 0.48 at the
+    top, free-surface ghosts, no-slip floor, float-float with graph replay, run
+    in chunks of 100 steps to 0.3 s or until it blows up, for the benchmark's
+    stiff quasi-static law (beta = 400 m^2/s^2) and a soft one (1 m^2/s^2).
+    Reports the time reached, the top height (the highest particle) and the
+    mean solid fraction against the expected settled height of 0.025 m (the
+    paper's own run ends at 0.02 m)."""
+    import torch
+
+    from paper_2206_14061_gb300 import capi, workloads as W
+
+    wl = W.periodic_layer(n_xy=8)
+    L, H = wl.extra["L"], wl.extra["H"]
+    pd = W.param_dict(wl)
+    mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
+    dt, chunk, t_end = 1e-5, 100, 0.3
+    nmax = int(round(t_end / dt))
+    out = {"workload": f"periodic layer {wl.n} particles (8 x 8 x 30), H = 0.03 m, h = 1e-3, "
+                       "phi 0.50 to 0.48, free-surface ghosts, mixed_ff",
+           "expected_settled_height_m": 0.025, "paper_simulated_height_m": 0.02, "runs": []}
+    for beta in (400.0, 1.0):
+        eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max")}
+        eos.update(alpha=-beta * pd["phi_max"], beta=beta)
+        st = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
+        ctx = capi.Context(wl.n, cap=64)
+        prm = dict(h=wl.h, radius=wl.radius, gx=0.0, gy=0.0, gz=-9.81, floor_z=0.0,
+                   mirror_mode=1, precision=PREC["mixed_ff"], rebuild_every=1,
+                   launch_mode=capi.LP_LAUNCH_GRAPH, skin=0.1 * wl.h, free_surface=1,
+                   period_x=L, period_y=L)
+        traj, steps, status = [], 0, "reached 0.3 s"
+        t0 = time.perf_counter()
+        while steps < nmax:
+            with torch.cuda.stream(stream):
+                capi.lp_step(ctx, st, mui, eos, prm, dt, chunk, stream=stream)
+            d = ctx.sync(stream, raise_on_error=False)
+            steps += chunk
+            z = st["z"].cpu().numpy()
+            V = st["V"].cpu().numpy()
+            sp = np.sqrt(sum(st[k].cpu().numpy() ** 2 for k in "uvw"))
+            traj.append((steps * dt, float(z.max()), float(np.mean(1.0 / V)), float(sp.max())))
+            if not (np.isfinite(sp).all() and np.isfinite(V).all()) or sp.max() > 3.0:
+                status = "blew up"
+                break
+            if d["status"] != 0:
+                status = "stopped: " + capi.lib().lp_status_string(int(d["status"])).decode()
+                break
+        wall = time.perf_counter() - t0
+        ctx.close()
+        keep = traj[::max(1, len(traj) // 10)] + traj[-1:]
+        out["runs"].append({"beta": beta, "status": status, "t_reached_s": steps * dt,
+                            "steps": steps, "wall_s": wall,
+                            "trajectory": [{"t_s": t, "top_height_m": zt, "mean_phi": ph,
+                                            "max_speed": v} for t, zt, ph, v in keep]})
     return out
 
 
