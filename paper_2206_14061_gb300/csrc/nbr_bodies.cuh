@@ -141,14 +141,6 @@ __device__ __forceinline__ bool cand_less(uint64_t da, uint32_t ka, uint64_t db,
   return ka < kb;
 }
 
-// octant-balanced ordering (Sec. 3.1 item 6): round first (a candidate's
-// rank within its own octant), then the nearest-first order
-__device__ __forceinline__ bool cand_less_oct(int ra, uint64_t da, uint32_t ka, int rb,
-                                              uint64_t db, uint32_t kb) {
-  if (ra != rb) return ra < rb;
-  return cand_less(da, ka, db, kb);
-}
-
 __device__ __forceinline__ void stencil_stats(bool live, int c, int cap, DevDiag* dg);
 
 // Stencil of particle s; every lane of the warp must call it (live or not).
@@ -189,7 +181,7 @@ __device__ __forceinline__ void neighbors_body(
     const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
     const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
     const float Lxf = g.Lxf, Lyf = g.Lyf;
-    uint64_t cd2[KEEP ? kMaxCand : 1];  // bit patterns of the squared distances
+    float cdf[KEEP ? kMaxCand : 1];  // FP32 squared distances (the ordering's screen)
     uint32_t cj[KEEP ? kMaxCand : 1];
     uint8_t co[KEEP ? kMaxCand : 1];  // octant: bit 0 dx >= 0, bit 1 dy >= 0, bit 2 dz >= 0
     const int ncx = g.nx, ncy = g.ny, ncz = g.nz;
@@ -237,7 +229,9 @@ __device__ __forceinline__ void neighbors_body(
               double d2 = 0.0;
               bool in;
               uint8_t oct = 0;
-              if (!exact_only && d2f < lo && !KEEP) {
+              // (the octant rule forms octants from the FP64 offsets, so its
+              // candidates all take the FP64 test)
+              if (!exact_only && d2f < lo && !(KEEP && keep_mode == 2)) {
                 in = true;
               } else {
                 const double zj = pass == 0 ? z[j] : __dsub_rn(2.0 * floor_z, z[j]);
@@ -252,7 +246,7 @@ __device__ __forceinline__ void neighbors_body(
               const uint32_t code = j | (pass ? kMirrorBit : 0u);
               if (KEEP) {
                 if (c < kMaxCand) {
-                  cd2[c] = (uint64_t)__double_as_longlong(d2);
+                  cdf[c] = d2f;
                   cj[c] = code;
                   co[c] = oct;
                 } else {
@@ -273,6 +267,25 @@ __device__ __forceinline__ void neighbors_body(
         uint32_t kk[kMaxCand];
         for (int t = 0; t < m; ++t)
           kk[t] = ((uint32_t)ids[cj[t] & ~kMirrorBit] << 1) | (cj[t] >> 31);
+        // The order is by the FP64 squared distance, then the key. The FP32
+        // distances are within band r^2 of it (the prefilter's bound, for
+        // every pair within the radius), so two candidates whose FP32
+        // distances differ by more than twice that are in that order; only
+        // closer pairs recompute their FP64 distances (as the test above)
+        // and compare them exactly.
+        const float gap = exact_only ? INFINITY : 2.0f * band * r2f;
+        auto exact_bits = [&](uint32_t code) {
+          const int j = code & ~kMirrorBit;
+          const double zj = (code >> 31) ? __dsub_rn(2.0 * floor_z, z[j]) : z[j];
+          double d2 = 0.0;
+          exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2);
+          return (uint64_t)__double_as_longlong(d2);
+        };
+        auto d_less = [&](int a, int b) {
+          if (cdf[a] + gap < cdf[b]) return true;
+          if (cdf[b] + gap < cdf[a]) return false;
+          return cand_less(exact_bits(cj[a]), kk[a], exact_bits(cj[b]), kk[b]);
+        };
         // octant-balanced: each candidate's round is its nearest-first rank
         // among the candidates of its own octant (stored over co[])
         if (keep_mode == 2) {
@@ -280,7 +293,7 @@ __device__ __forceinline__ void neighbors_body(
           for (int t = 0; t < m; ++t) {
             int r = 0;
             for (int u = 0; u < m; ++u)
-              r += (u != t && co[u] == co[t] && cand_less(cd2[u], kk[u], cd2[t], kk[t]));
+              r += (u != t && co[u] == co[t] && d_less(u, t));
             rk[t] = (uint8_t)r;
           }
           for (int t = 0; t < m; ++t) co[t] = rk[t];
@@ -290,8 +303,8 @@ __device__ __forceinline__ void neighbors_body(
         // candidate that precedes the top replaces it; then heapsort, so that
         // hp[0 .. cap-1] lists them in ascending order
         auto before = [&](int a, int b) {
-          return keep_mode == 2 ? cand_less_oct(co[a], cd2[a], kk[a], co[b], cd2[b], kk[b])
-                                : cand_less(cd2[a], kk[a], cd2[b], kk[b]);
+          if (keep_mode == 2 && co[a] != co[b]) return co[a] < co[b];  // round first
+          return d_less(a, b);
         };
         uint8_t hp[LP_MAX_CAP];
         auto sift_down = [&](int i, int len) {
