@@ -44,7 +44,7 @@ void launch_filter(int n, const double* x, const double* y, const double* z, con
 void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
                    const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
-                   cudaStream_t st, int bs);
+                   cudaStream_t st, int bs, int32_t* glist, int* gcount);
 void launch_copy_state(int n, double* const* dst, double* const* src, cudaStream_t st);
 void launch_heun_combine(int n, double* const* y, double* const* y0, double Lx, double Ly,
                          cudaStream_t st);
@@ -132,6 +132,8 @@ struct lp_ctx {
   float2* fit_fs = nullptr;  // split fields of lp_fit_derivatives (LP_MIXED_FF), lazily
   int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
   int32_t* gcnt = nullptr;    // ghost entries per stencil
+  int32_t* glist = nullptr;   // particles with ghost entries (compact, any order)
+  int* gcount = nullptr;      // their number
   int32_t* perm = nullptr;    // fit thread -> particle (LP_MIXED_FF)
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
   double* Y0[7] = {};                  // Heun: state at the start of the step (on first use)
@@ -404,6 +406,7 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   A.perm = LP_ROW_ORDER ? c->perm : nullptr;
   A.Xfix = c->Xfix;
   A.gcnt = c->gcnt;
+  A.glist = c->glist; A.gcount = c->gcount;
   A.Tg = c->Tg; A.T2 = c->T2;
   if (c->skin > 0.0) {
     A.xref = c->xref;
@@ -447,7 +450,7 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
                   c->dg, c->d_search, st, c->bs_nbr, K.periodic != 0);
     if (K.free_surface) {
       launch_ghosts(n, c->X[e][0], c->X[e][1], c->X[e][2], c->colid[c->ci], c->d_grids, c->Xfix,
-                    c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr);
+                    c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr, c->glist, c->gcount);
       c->launches += 2;
     }
     phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
@@ -463,7 +466,8 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
                      st, c->bs_nbr, nullptr, nullptr, K.periodic != 0);
     if (K.free_surface) {
       launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
-                    c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr);
+                    c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr,
+                    c->glist, c->gcount);
       c->launches += 2;
     }
     phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
@@ -710,6 +714,8 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->Lff, n * kTri);
   if (s == LP_OK) s = dalloc(c, &c->Xfix, n);
   if (s == LP_OK) s = dalloc(c, &c->gcnt, n);
+  if (s == LP_OK) s = dalloc(c, &c->glist, n);
+  if (s == LP_OK) s = dalloc(c, &c->gcount, 1);
   if (s == LP_OK) s = dalloc(c, &c->perm, n);
   c->capc = std::min(c->cap + 32, 96);
   if (s == LP_OK) s = dalloc(c, &c->cand, n * c->capc);
@@ -727,6 +733,7 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
     cudaMemset(c->colid[1], 0, n * sizeof(int32_t));
     cudaMemset(c->cnt, 0, n * sizeof(int32_t));
     cudaMemset(c->nbr, 0, n * c->cap * sizeof(int32_t));
+    cudaMemset(c->gcount, 0, sizeof(int));  // no particle with ghosts yet
     cudaMemset(c->ccnt, 0, n * sizeof(int32_t));
     cudaMemset(c->cand, 0, n * c->capc * sizeof(int32_t));
     cudaMemset(c->key, 0, n * sizeof(uint32_t));
@@ -1530,7 +1537,8 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
                        K.periodic != 0);
       if (K.free_surface)  // the same ghost flags as the forward run
         launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
-                      c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, kBlock);
+                      c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, kBlock,
+                      c->glist, c->gcount);
       for (int f = 0; f < 7; ++f)
         cudaMemcpyAsync(tab[tseg + f], c->X[c->cx][f], sizeof(double) * N,
                         cudaMemcpyDeviceToDevice, st);

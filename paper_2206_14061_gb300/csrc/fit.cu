@@ -112,16 +112,21 @@ __global__ void k_split_state(const StepArgs A) {
   if (s < A.n) split_state_body(A, s);
 }
 
-// rows of the entries with a ghost (free surface), ahead of the main kernels
+// rows of the entries with a ghost (free surface), ahead of the main kernels:
+// a fixed grid strides over the list of particles that have such entries
+// (only they have work), so that a warp's lanes are all busy
+constexpr int kTwinBlocks = 4 * 152;
 template <bool PER>
 __global__ void k_gram_twins(const StepArgs A) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < A.n) gram_twins_body<PER>(A, s);
+  const int cnt = min(*A.gcount, A.n);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x)
+    gram_twins_body<PER>(A, A.glist[t]);
 }
 template <bool PER>
 __global__ void k_pass2_twins(const StepArgs A) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < A.n) pass2_twins_body<PER>(A, s);
+  const int cnt = min(*A.gcount, A.n);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x)
+    pass2_twins_body<PER>(A, A.glist[t]);
 }
 
 __global__ void k_split_p1(const StepArgs A) {
@@ -506,13 +511,13 @@ void launch_pass1(int prec, const StepArgs& A, cudaStream_t st, int bs) {
     k_split_state<<<(A.n + 255) / 256, 256, 0, st>>>(A);
     if (A.perm) k_row_order<<<(A.n + kRowGroup - 1) / kRowGroup, kRowGroup, 0, st>>>(A.n, A.cnt, const_cast<int32_t*>(A.perm));
     const int b = bs < kFFBlock ? bs : kFFBlock;
-    const int ng = (A.n + 127) / 128, nf = (A.n + b - 1) / b;
+    const int nf = (A.n + b - 1) / b;
     if (per) {
-      if (A.K.free_surface) k_gram_twins<true><<<ng, 128, 0, st>>>(A);
+      if (A.K.free_surface) k_gram_twins<true><<<kTwinBlocks, 128, 0, st>>>(A);
       k_gram_ff<true><<<nf, b, 0, st>>>(A);
       k_pass1_ff_rows<true><<<nf, b, 0, st>>>(A);
     } else {
-      if (A.K.free_surface) k_gram_twins<false><<<ng, 128, 0, st>>>(A);
+      if (A.K.free_surface) k_gram_twins<false><<<kTwinBlocks, 128, 0, st>>>(A);
       k_gram_ff<false><<<nf, b, 0, st>>>(A);
       k_pass1_ff_rows<false><<<nf, b, 0, st>>>(A);
     }
@@ -524,8 +529,8 @@ void launch_pass2(int prec, const StepArgs& A, cudaStream_t st, int bs) {
   if (prec == LP_MIXED_FF) {
     k_split_p1<<<(A.n + 255) / 256, 256, 0, st>>>(A);
     if (A.K.free_surface) {
-      if (A.K.periodic) k_pass2_twins<true><<<(A.n + 127) / 128, 128, 0, st>>>(A);
-      else k_pass2_twins<false><<<(A.n + 127) / 128, 128, 0, st>>>(A);
+      if (A.K.periodic) k_pass2_twins<true><<<kTwinBlocks, 128, 0, st>>>(A);
+      else k_pass2_twins<false><<<kTwinBlocks, 128, 0, st>>>(A);
     }
   }
   k_pass2_fallback<<<152, 64, 0, st>>>(A);

@@ -269,6 +269,8 @@ struct StepArgs {
   int4* Xfix;       // free surface: round(K (x, y, z, 2 floor_z - z)) per particle,
                     // relative to the column's fixed-point origin
   int32_t* gcnt;    // free surface: entries with a ghost, at the end of each stencil
+  const int32_t* glist;  // free surface: the particles with ghost entries (compact), and
+  const int* gcount;     // their number (set by the ghost kernel of the same stencils)
   float *Tg, *T2;   // free surface: sums over those entries and their ghosts
                     // (Gram moments 62 x n, pass-2 right-hand sides 36 x n)
   float2* Lff;      // 45 * n: float-float Cholesky factor of the Gram matrix,

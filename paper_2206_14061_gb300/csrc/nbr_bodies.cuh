@@ -508,11 +508,15 @@ __device__ __forceinline__ void ghost_fix_body(int s, const double* __restrict__
 
 // Flags the entries of particle s whose reflections are ghosts; every lane of
 // the warp must call it (live or not).
+// glist (optional): every particle with ghosts is appended, in no set order,
+// at glist[(*gcount)++], so that the twin kernels need visit only those.
 __device__ __forceinline__ void ghost_body(int s, bool live, int n, const double* __restrict__ z,
                                            const int4* __restrict__ X,
                                            int32_t* __restrict__ nbr, const int32_t* __restrict__ cnt,
                                            int32_t* __restrict__ gcnt, const StepConsts& K,
-                                           DevDiag* __restrict__ dg) {
+                                           DevDiag* __restrict__ dg,
+                                           int32_t* __restrict__ glist = nullptr,
+                                           int* __restrict__ gcount = nullptr) {
   int twins = 0;
   bool over = false;
   if (live) {
@@ -587,6 +591,16 @@ __device__ __forceinline__ void ghost_body(int s, bool live, int n, const double
       }
     }
     gcnt[s] = twins;
+  }
+  if (glist) {  // one atomic per warp for the warp's particles with ghosts
+    const unsigned has = __ballot_sync(0xffffffffu, live && twins > 0);
+    if (has) {
+      const int lane = threadIdx.x & 31;
+      int base = 0;
+      if (lane == 0) base = atomicAdd(gcount, __popc(has));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (live && twins > 0) glist[base + __popc(has & ((1u << lane) - 1u))] = s;
+    }
   }
   unsigned long long a = (unsigned long long)twins;
   for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);

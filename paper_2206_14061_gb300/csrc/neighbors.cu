@@ -234,17 +234,19 @@ k_filter(int n, const double* __restrict__ x, const double* __restrict__ y,
 __global__ void k_ghost_fix(int n, const double* __restrict__ x, const double* __restrict__ y,
                             const double* __restrict__ z, const int32_t* __restrict__ colid,
                             const GridCol* __restrict__ grids, double grid, double floor_z,
-                            int4* __restrict__ X) {
+                            int4* __restrict__ X, int* __restrict__ gcount) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) *gcount = 0;  // the list k_ghosts fills next
   if (s < n) ghost_fix_body(s, x, y, z, colid, grids, grid, floor_z, X);
 }
 
 __global__ void __launch_bounds__(kMaxBlock)
 k_ghosts(int n, const double* __restrict__ z, const int4* __restrict__ X,
          int32_t* __restrict__ nbr, const int32_t* __restrict__ cnt, int32_t* __restrict__ gcnt,
-         const StepConsts K, DevDiag* __restrict__ dg) {
+         const StepConsts K, DevDiag* __restrict__ dg, int32_t* __restrict__ glist,
+         int* __restrict__ gcount) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  ghost_body(s, s < n, n, z, X, nbr, cnt, gcnt, K, dg);
+  ghost_body(s, s < n, n, z, X, nbr, cnt, gcnt, K, dg, glist, gcount);
 }
 
 // Stencils from sorted indices to caller indices.
@@ -333,10 +335,10 @@ void launch_filter(int n, const double* x, const double* y, const double* z, con
 void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
                    const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
-                   cudaStream_t st, int bs) {
+                   cudaStream_t st, int bs, int32_t* glist, int* gcount) {
   k_ghost_fix<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, z, colid, grids, K.ghost_grid, K.floor_z,
-                                               X);
-  k_ghosts<<<(n + bs - 1) / bs, bs, 0, st>>>(n, z, X, nbr, cnt, gcnt, K, dg);
+                                               X, gcount);
+  k_ghosts<<<(n + bs - 1) / bs, bs, 0, st>>>(n, z, X, nbr, cnt, gcnt, K, dg, glist, gcount);
 }
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st) {
