@@ -44,7 +44,7 @@ void launch_filter(int n, const double* x, const double* y, const double* z, con
 void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
                    const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
-                   cudaStream_t st, int bs, int32_t* glist, int* gcount);
+                   cudaStream_t st, int bs, int32_t* glist, int* gcount, int32_t* olist);
 void launch_copy_state(int n, double* const* dst, double* const* src, cudaStream_t st);
 void launch_heun_combine(int n, double* const* y, double* const* y0, double Lx, double Ly,
                          cudaStream_t st);
@@ -133,7 +133,8 @@ struct lp_ctx {
   int4* Xfix = nullptr;       // fixed-point positions of the free-surface test
   int32_t* gcnt = nullptr;    // ghost entries per stencil
   int32_t* glist = nullptr;   // particles with ghost entries (compact, any order)
-  int* gcount = nullptr;      // their number
+  int32_t* olist = nullptr;   // particles with one-sided stencils (compact, any order)
+  int* gcount = nullptr;      // the two lists' lengths
   int32_t* perm = nullptr;    // fit thread -> particle (LP_MIXED_FF)
   float *Tg = nullptr, *T2 = nullptr;  // twin sums (allocated on first free-surface step)
   double* Y0[7] = {};                  // Heun: state at the start of the step (on first use)
@@ -450,8 +451,8 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
                   c->dg, c->d_search, st, c->bs_nbr, K.periodic != 0);
     if (K.free_surface) {
       launch_ghosts(n, c->X[e][0], c->X[e][1], c->X[e][2], c->colid[c->ci], c->d_grids, c->Xfix,
-                    c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr, c->glist, c->gcount);
-      c->launches += 2;
+                    c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr, c->glist, c->gcount, c->olist);
+      c->launches += 3;
     }
     phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
     c->launches += 2;
@@ -467,8 +468,8 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
     if (K.free_surface) {
       launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
                     c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr,
-                    c->glist, c->gcount);
-      c->launches += 2;
+                    c->glist, c->gcount, c->olist);
+      c->launches += 3;
     }
     phase_mark(c, LP_PHASE_NEIGHBORS, false, st);
     c->launches += 1;
@@ -715,7 +716,8 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->Xfix, n);
   if (s == LP_OK) s = dalloc(c, &c->gcnt, n);
   if (s == LP_OK) s = dalloc(c, &c->glist, n);
-  if (s == LP_OK) s = dalloc(c, &c->gcount, 1);
+  if (s == LP_OK) s = dalloc(c, &c->olist, n);
+  if (s == LP_OK) s = dalloc(c, &c->gcount, 2);
   if (s == LP_OK) s = dalloc(c, &c->perm, n);
   c->capc = std::min(c->cap + 32, 96);
   if (s == LP_OK) s = dalloc(c, &c->cand, n * c->capc);
@@ -733,7 +735,7 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
     cudaMemset(c->colid[1], 0, n * sizeof(int32_t));
     cudaMemset(c->cnt, 0, n * sizeof(int32_t));
     cudaMemset(c->nbr, 0, n * c->cap * sizeof(int32_t));
-    cudaMemset(c->gcount, 0, sizeof(int));  // no particle with ghosts yet
+    cudaMemset(c->gcount, 0, 2 * sizeof(int));  // no particle with ghosts yet
     cudaMemset(c->ccnt, 0, n * sizeof(int32_t));
     cudaMemset(c->cand, 0, n * c->capc * sizeof(int32_t));
     cudaMemset(c->key, 0, n * sizeof(uint32_t));
@@ -1538,7 +1540,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
       if (K.free_surface)  // the same ghost flags as the forward run
         launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
                       c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, kBlock,
-                      c->glist, c->gcount);
+                      c->glist, c->gcount, c->olist);
       for (int f = 0; f < 7; ++f)
         cudaMemcpyAsync(tab[tseg + f], c->X[c->cx][f], sizeof(double) * N,
                         cudaMemcpyDeviceToDevice, st);

@@ -508,6 +508,86 @@ __device__ __forceinline__ void ghost_fix_body(int s, const double* __restrict__
 
 // Flags the entries of particle s whose reflections are ghosts; every lane of
 // the warp must call it (live or not).
+// The sums of the one-sided test over the entries of particle s (weights
+// r^2 - d^2 in fixed point): S = sum w o, W = sum w; with STORE the offsets o
+// are kept for the clearance check. False if an entry is out of range or
+// already carries a ghost (the stencil is then left alone).
+template <bool STORE>
+__device__ __forceinline__ bool ghost_sums(int s, int n, const int4* __restrict__ X,
+                                           const int32_t* __restrict__ nbr, int m, int4 xi,
+                                           const StepConsts& K, short (*o)[LP_MAX_CAP],
+                                           long long& S0, long long& S1, long long& S2,
+                                           long long& W) {
+  S0 = S1 = S2 = W = 0;
+  const int R2 = (int)K.ghost_R2;
+  const int PX = (int)K.ghost_PX, PY = (int)K.ghost_PY;  // integer periods (0: none)
+  bool ok = m > 0;
+  // software pipeline: codes two entries ahead, positions one ahead
+  uint32_t nc = m > 0 ? (uint32_t)nbr[s] : 0u;
+  uint32_t nn = m > 1 ? (uint32_t)nbr[(int64_t)n + s] : 0u;
+  int4 nx = m > 0 ? X[min(nc & kIndexMask, (uint32_t)(n - 1))] : xi;
+  for (int k = 0; k < m; ++k) {
+    const uint32_t code = nc;
+    const int4 xj = nx;
+    if (k + 1 < m) {
+      nc = nn;
+      nx = X[min(nc & kIndexMask, (uint32_t)(n - 1))];
+      if (k + 2 < m) nn = (uint32_t)nbr[(int64_t)(k + 2) * n + s];
+    }
+    if ((code & kIndexMask) >= (uint32_t)n || (code & kGhostBit)) { ok = false; break; }
+    const int o0 = wrap_fix(xj.x - xi.x, PX), o1 = wrap_fix(xj.y - xi.y, PY);
+    const int o2 = ((code & kMirrorBit) ? xj.w : xj.z) - xi.z;
+    if (STORE) { o[0][k] = (short)o0; o[1][k] = (short)o1; o[2][k] = (short)o2; }
+    const int q = (o0 * o0 + o1 * o1) + o2 * o2;
+    const int w = q < R2 ? R2 - q : 0;
+    S0 += (long long)w * o0;
+    S1 += (long long)w * o1;
+    S2 += (long long)w * o2;
+    W += w;
+  }
+  return ok;
+}
+// the one-sided test: |S| > 0.22 h W (in the fixed-point units)
+__device__ __forceinline__ bool ghost_one_sided(long long S0, long long S1, long long S2,
+                                                long long W, const StepConsts& K,
+                                                double* s2out) {
+  const double sx = (double)S0, sy = (double)S1, sz = (double)S2;
+  const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
+  const double lim = __dmul_rn(__dmul_rn(0.22, K.ghost_hk), (double)W);
+  *s2out = s2;
+  return s2 > __dmul_rn(lim, lim);
+}
+
+// First half of the ghost kernels (every particle): the one-sided test
+// alone. A one-sided particle is appended, in no set order, at
+// olist[(*ocount)++] for ghost_body; the others get no ghosts (gcnt 0). Every
+// lane of the warp must call it (live or not).
+__device__ __forceinline__ void ghost_scan_body(int s, bool live, int n,
+                                                const int4* __restrict__ X,
+                                                const int32_t* __restrict__ nbr,
+                                                const int32_t* __restrict__ cnt,
+                                                int32_t* __restrict__ gcnt, const StepConsts& K,
+                                                int32_t* __restrict__ olist,
+                                                int* __restrict__ ocount) {
+  bool side = false;
+  if (live) {
+    const int m = min(cnt[s], K.cap);
+    long long S0, S1, S2, W;
+    double s2;
+    side = ghost_sums<false>(s, n, X, nbr, m, X[s], K, nullptr, S0, S1, S2, W) &&
+           ghost_one_sided(S0, S1, S2, W, K, &s2);
+    if (!side) gcnt[s] = 0;
+  }
+  const unsigned has = __ballot_sync(0xffffffffu, side);
+  if (has) {
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ocount, __popc(has));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (side) olist[base + __popc(has & ((1u << lane) - 1u))] = s;
+  }
+}
+
 // glist (optional): every particle with ghosts is appended, in no set order,
 // at glist[(*gcount)++], so that the twin kernels need visit only those.
 __device__ __forceinline__ void ghost_body(int s, bool live, int n, const double* __restrict__ z,
@@ -523,37 +603,11 @@ __device__ __forceinline__ void ghost_body(int s, bool live, int n, const double
     const int m = min(cnt[s], K.cap);
     const int4 xi = X[s];
     short o[3][LP_MAX_CAP];  // offsets of the entries (|o| <= 8193)
-    long long S0 = 0, S1 = 0, S2 = 0, W = 0;
-    const int R2 = (int)K.ghost_R2;
-    const int PX = (int)K.ghost_PX, PY = (int)K.ghost_PY;  // integer periods (0: none)
-    bool ok = m > 0;
-    // software pipeline: codes two entries ahead, positions one ahead
-    uint32_t nc = m > 0 ? (uint32_t)nbr[s] : 0u;
-    uint32_t nn = m > 1 ? (uint32_t)nbr[(int64_t)n + s] : 0u;
-    int4 nx = m > 0 ? X[min(nc & kIndexMask, (uint32_t)(n - 1))] : xi;
-    for (int k = 0; k < m; ++k) {
-      const uint32_t code = nc;
-      const int4 xj = nx;
-      if (k + 1 < m) {
-        nc = nn;
-        nx = X[min(nc & kIndexMask, (uint32_t)(n - 1))];
-        if (k + 2 < m) nn = (uint32_t)nbr[(int64_t)(k + 2) * n + s];
-      }
-      if ((code & kIndexMask) >= (uint32_t)n || (code & kGhostBit)) { ok = false; break; }
-      const int o0 = wrap_fix(xj.x - xi.x, PX), o1 = wrap_fix(xj.y - xi.y, PY);
-      const int o2 = ((code & kMirrorBit) ? xj.w : xj.z) - xi.z;
-      o[0][k] = (short)o0; o[1][k] = (short)o1; o[2][k] = (short)o2;
-      const int q = (o0 * o0 + o1 * o1) + o2 * o2;
-      const int w = q < R2 ? R2 - q : 0;
-      S0 += (long long)w * o0;
-      S1 += (long long)w * o1;
-      S2 += (long long)w * o2;
-      W += w;
-    }
-    const double sx = (double)S0, sy = (double)S1, sz = (double)S2;
-    const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
-    const double lim = __dmul_rn(__dmul_rn(0.22, K.ghost_hk), (double)W);
-    if (ok && s2 > __dmul_rn(lim, lim)) {
+    long long S0, S1, S2, W;
+    const bool ok = ghost_sums<true>(s, n, X, nbr, m, xi, K, o, S0, S1, S2, W);
+    double s2;
+    const bool side = ghost_one_sided(S0, S1, S2, W, K, &s2);
+    if (ok && side) {
       const double dep = __dmul_rn(0.5, K.ghost_hk);
       const double dep2s2 = __dmul_rn(__dmul_rn(dep, dep), s2);
       const double zi = z[s];

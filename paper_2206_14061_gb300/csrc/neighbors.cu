@@ -236,17 +236,35 @@ __global__ void k_ghost_fix(int n, const double* __restrict__ x, const double* _
                             const GridCol* __restrict__ grids, double grid, double floor_z,
                             int4* __restrict__ X, int* __restrict__ gcount) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s == 0) *gcount = 0;  // the list k_ghosts fills next
+  if (s == 0) gcount[0] = gcount[1] = 0;  // the two lists the ghost kernels fill next
   if (s < n) ghost_fix_body(s, x, y, z, colid, grids, grid, floor_z, X);
 }
 
+// first half: the one-sided test of every particle (gcount[1]: one-sided ones)
 __global__ void __launch_bounds__(kMaxBlock)
+k_ghost_scan(int n, const int4* __restrict__ X, const int32_t* __restrict__ nbr,
+             const int32_t* __restrict__ cnt, int32_t* __restrict__ gcnt, const StepConsts K,
+             int32_t* __restrict__ olist, int* __restrict__ gcount) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  ghost_scan_body(s, s < n, n, X, nbr, cnt, gcnt, K, olist, gcount + 1);
+}
+
+// second half: the one-sided particles of the list, in full warps (a fixed
+// grid strides over the list a warp at a time, so every lane calls the body)
+constexpr int kGhostBlocks = 4 * 152;
+__global__ void __launch_bounds__(128)
 k_ghosts(int n, const double* __restrict__ z, const int4* __restrict__ X,
          int32_t* __restrict__ nbr, const int32_t* __restrict__ cnt, int32_t* __restrict__ gcnt,
          const StepConsts K, DevDiag* __restrict__ dg, int32_t* __restrict__ glist,
-         int* __restrict__ gcount) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  ghost_body(s, s < n, n, z, X, nbr, cnt, gcnt, K, dg, glist, gcount);
+         int* __restrict__ gcount, const int32_t* __restrict__ olist) {
+  const int m = min(gcount[1], n);
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < m; base += stride) {
+    const int t = base + lane;
+    const bool live = t < m;
+    ghost_body(live ? olist[t] : 0, live, n, z, X, nbr, cnt, gcnt, K, dg, glist, gcount);
+  }
 }
 
 // Stencils from sorted indices to caller indices.
@@ -335,10 +353,11 @@ void launch_filter(int n, const double* x, const double* y, const double* z, con
 void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
                    const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
-                   cudaStream_t st, int bs, int32_t* glist, int* gcount) {
+                   cudaStream_t st, int bs, int32_t* glist, int* gcount, int32_t* olist) {
   k_ghost_fix<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, z, colid, grids, K.ghost_grid, K.floor_z,
                                                X, gcount);
-  k_ghosts<<<(n + bs - 1) / bs, bs, 0, st>>>(n, z, X, nbr, cnt, gcnt, K, dg, glist, gcount);
+  k_ghost_scan<<<(n + bs - 1) / bs, bs, 0, st>>>(n, X, nbr, cnt, gcnt, K, olist, gcount);
+  k_ghosts<<<kGhostBlocks, 128, 0, st>>>(n, z, X, nbr, cnt, gcnt, K, dg, glist, gcount, olist);
 }
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st) {
