@@ -62,6 +62,8 @@ def parse():
                     help="skip the adjoint line (the 200-step adjoint column)")
     ap.add_argument("--no-collapse", action="store_true",
                     help="skip the column-collapse validation line (a = 0.6 column, Sec. 4.2.1)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large-column line (21M particles at the headline spacing)")
     ap.add_argument("--no-layer", action="store_true",
                     help="skip the layer-compaction validation line (periodic layer, Sec. 4.1)")
     ap.add_argument("--no-heun", action="store_true",
@@ -449,6 +451,8 @@ def our_arm(args):
 
     if not args.no_adjoint and world == 1:
         line["adjoint"] = adjoint_line(dev, stream)
+    if not args.no_large:
+        line["large_column"] = large_line(args, dev, stream, world)
     if not args.no_collapse and world == 1:
         line["column_collapse"] = collapse_line(dev, stream)
     if not args.no_layer and world == 1:
@@ -596,6 +600,62 @@ def batched(args, dev, stream, rank=0, world=1):
                             "ms_per_step": ms_f / full_steps,
                             "n_nonfinite": d500["n_nonfinite"],
                             "ghost_entries_per_step": d500["n_ghosts"] / full_steps}}
+
+
+def large_line(args, dev, stream, world):
+    """The headline column scaled up at the same spacing: R = 0.06 m, H = 2R,
+    h = R/150 = 4e-4 m (about 21.2M particles, 27 times the headline's), the
+    same parameters, float-float with graph replay and Verlet skin 0.1h, calls
+    of 10 steps from the initial state (a warm-up call, then two timed ones).
+    Reports the throughput and the device memory the context and the state
+    take (cudaMemGetInfo before and after)."""
+    import torch
+
+    from paper_2206_14061_gb300 import capi, workloads as W
+
+    wl = W.cylinder(R=0.06, spacing_div=150, index=2)
+    pd = W.param_dict(wl)
+    mui = {k: pd[k] for k in ("mu_s", "mu_2", "I0", "d", "rho_s")}
+    eos = {k: pd[k] for k in ("phi_c", "phi_min", "phi_max", "alpha", "beta")}
+    prm = dict(h=pd["h"], radius=pd["radius"], gx=pd["gx"], gy=pd["gy"], gz=pd["gz"],
+               floor_z=0.0, mirror_mode=1, precision=PREC["mixed_ff"], rebuild_every=1,
+               launch_mode=capi.LP_LAUNCH_GRAPH, skin=args.skin * pd["h"])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    init = {k: torch.tensor(wl.state[k], device=dev) for k in capi.FIELDS}
+    st = {k: v.clone() for k, v in init.items()}
+    ctx = capi.Context(wl.n, cap=64)
+    steps, calls = 10, 2
+
+    def run():
+        with torch.cuda.stream(stream):
+            for k in capi.FIELDS:
+                st[k].copy_(init[k])
+            capi.lp_step(ctx, st, mui, eos, prm, pd["dt"], steps, stream=stream)
+
+    run()  # warm-up
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    if world > 1:
+        torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(calls):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (steps * calls)
+    if world > 1:
+        from paper_2206_14061_gb300 import dist as D
+        ms = D.max_over_ranks(ms, device=dev)
+    d = ctx.sync(stream, raise_on_error=False)
+    ctx.close()
+    return {"workload": f"cylindrical column R = 0.06 m, H = 2R, h = R/150 ({wl.n} particles), "
+                        "the headline's parameters, mixed_ff, graph replay",
+            "value": wl.n * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "steps": steps * calls, "restart_every": steps,
+            "device_bytes": int(used), "bytes_per_particle": used / wl.n,
+            "n_nonfinite": d["n_nonfinite"]}
 
 
 def collapse_line(dev, stream):
