@@ -986,6 +986,55 @@ def test_columns_full_batch_500_steps(dev, capi, orc):
 
 
 @pytest.mark.slow
+def test_large_column_sampled_particles(dev, capi, orc):
+    """The headline column scaled up at the same spacing (R = 0.06 m, h = R/150,
+    21.2M particles: indices past 2^24), 10 float-float steps with graph replay
+    and Verlet skin 0.1h, as the benchmark's large-column line runs them, from
+    the spreading flow u_r = 0.5 m/s (r/R)(z/H) (at rest only the particles
+    near the floor would leave free fall within 10 steps). A
+    particle's state after 10 steps depends only on particles within
+    10 x 2 x 2.2h = 44h of it (each step's two fit passes reach 2.2h each), so
+    the oracle computes sampled particles one by one: on the ball of radius 50h
+    around each, 10 steps. Their displacements, velocities and changes of V
+    match within 1e-9 of the ball's largest."""
+    wl = W.cylinder(R=0.06, spacing_div=150, index=2)
+    pd = W.param_dict(wl)
+    assert wl.n > (1 << 24)
+    H, R, h = 0.12, 0.06, pd["h"]
+    st = dict(wl.state)
+    st["u"] = 0.5 * st["x"] / R * (st["z"] / H)
+    st["v"] = 0.5 * st["y"] / R * (st["z"] / H)
+    wl.state = st
+    got, d = _run_gpu(capi, dev, wl, pd, 10, prec=2, launch_mode=capi.LP_LAUNCH_GRAPH,
+                      skin=0.1 * pd["h"], stream=torch.cuda.Stream())
+    assert d["n_nonfinite"] == 0
+    s0 = wl.state
+    x, y, z = s0["x"], s0["y"], s0["z"]
+    r = np.sqrt(x * x + y * y)
+    picks = [int(np.argmin((x - 0.0) ** 2 + (y - 0.0) ** 2 + (z - 0.5 * H) ** 2)),  # centre
+             int(np.argmin(x * x + y * y + z * z)),                               # floor
+             int(np.argmin((r - R) ** 2 + (z - H) ** 2)),                         # top rim
+             wl.n - 1, (1 << 24) + 12345]                                         # late indices
+    for i in picks:
+        ball = np.nonzero((x - x[i]) ** 2 + (y - y[i]) ** 2 + (z - z[i]) ** 2
+                          <= (50 * h) ** 2)[0]
+        sub = {k: v[ball] for k, v in s0.items()}
+        ref, _ = orc.step(sub, orc.params(**pd), 10, brute=False)
+        j = int(np.nonzero(ball == i)[0][0])
+        # (far from the floor the ball is still in exact free fall: no change
+        # of x, y or V anywhere in it, and then none is allowed here either)
+        rel = lambda a, sc: 0.0 if a == 0.0 else (a / sc if sc > 0.0 else np.inf)
+        err = {}
+        for k in "xyzV":
+            scale = np.abs(ref[k] - sub[k]).max()
+            err[k] = rel(abs((got[k][i] - s0[k][i]) - (ref[k][j] - sub[k][j])), scale)
+        for k in "uvw":
+            err[k] = rel(abs(got[k][i] - ref[k][j]), np.abs(ref[k]).max())
+        print(f"particle {i} ({ball.size} in its ball):", {k: f"{v:.2e}" for k, v in err.items()})
+        assert max(err.values()) <= 1e-9, (i, err)
+
+
+@pytest.mark.slow
 def test_step_full_size_cylinder(dev, capi, orc):
     """The column of radius 0.02 m at spacing R/50 (785k particles), three FP64
     steps in the launch configuration the benchmark uses, against the oracle on
