@@ -32,7 +32,7 @@
 // forward path's conditioning threshold. Rank-deficient stencils (fewer than
 // 9 rows, or a non-positive pivot) carry no fit adjoint and are counted in
 // n_fallback.
-#include "lp_internal.cuh"
+#include "fit_bodies.cuh"
 
 namespace lp {
 
@@ -80,6 +80,23 @@ __device__ __forceinline__ void row_adjoint(double dx, double dy, double dz, con
   db[0] = ab[0] + dx * ab[3] + dy * ab[6] + dz * ab[7];
   db[1] = ab[1] + dy * ab[4] + dx * ab[6] + dz * ab[8];
   db[2] = ab[2] + dz * ab[5] + dx * ab[7] + dy * ab[8];
+}
+// the same in float-float
+__device__ __forceinline__ void ff_row_adjoint(ff dx, ff dy, ff dz, const ff* ab, ff* db) {
+  db[0] = ab[0];
+  ff_acc(db[0], dx, ab[3]);
+  ff_acc(db[0], dy, ab[6]);
+  ff_acc(db[0], dz, ab[7]);
+  db[1] = ab[1];
+  ff_acc(db[1], dy, ab[4]);
+  ff_acc(db[1], dx, ab[6]);
+  ff_acc(db[1], dz, ab[8]);
+  db[2] = ab[2];
+  ff_acc(db[2], dz, ab[5]);
+  ff_acc(db[2], dx, ab[7]);
+  ff_acc(db[2], dy, ab[8]);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) db[q] = ff_norm(db[q]);
 }
 
 // ---------------------------------------------------------------- R0
@@ -343,8 +360,17 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
 }
 
 // ---------------------------------------------------------------- R3
+// the state of step n split into float-float pairs for the pass-1 adjoint's
+// rows: positions relative to the column's grid origin in units of h (with
+// the floor-mirror height), and velocities, as the forward step splits them
+__global__ void k_adj_split(const AdjArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.n) split_state_body(A, s);
+}
+
 // pass-1 adjoint: |gdot| and ld to the velocity gradient and Hessians, then
 // the least-squares rows to the neighbours' velocities and the positions
+template <bool PER>
 __global__ void __launch_bounds__(kBlock) k_adj_pass1(const AdjArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= A.n) return;
@@ -389,70 +415,107 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass1(const AdjArgs A) {
   for (int f = 0; f < 3; ++f)
     for (int q = 0; q < kNB; ++q) any = any || lc[f][q] != 0.0;
   if (!any) return;
-  const double* F = factor_of(A, s);
-  double L[kTri];
+  {
+    const double* F = factor_of(A, s);
+    double L[kTri];
 #pragma unroll
-  for (int k = 0; k < kTri; ++k) L[k] = F[(int64_t)k * n + s];
-  double c[3][kNB];
-  for (int f = 0; f < 3; ++f) {
-    chol9_solve(L, lc[f]);  // lc becomes z_f
-    for (int q = 0; q < kNB; ++q) c[f][q] = A.coef1[(int64_t)(f * kNB + q) * n + s];
+    for (int k = 0; k < kTri; ++k) L[k] = F[(int64_t)k * n + s];
+    for (int f = 0; f < 3; ++f) chol9_solve(L, lc[f]);  // lc becomes z_f
   }
-  const double f2 = 2.0 * A.K.floor_z;
+  // The rows in float-float (the forward step's coefficients c_f and the z_f
+  // split once; the offsets and velocity differences from the split state):
+  // the rows' residuals, b = a . z and the row adjoints run on the FP32 pipe,
+  // and only the scattered sums are FP64, converted exactly from float-float.
+  ff cf[3][kNB], zf[3][kNB];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+      cf[f][q] = ff_of(A.coef1[(int64_t)(f * kNB + q) * n + s]);
+      zf[f][q] = ff_of(lc[f][q]);
+    }
   const int mm = A.K.mirror_mode;
-  const double sgn[3] = {usign_adj(mm, 0), usign_adj(mm, 1), usign_adj(mm, 2)};
-  const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
-  const double* uf[3] = {A.u, A.v, A.w};
-  double ui[3] = {A.u[s], A.v[s], A.w[s]};
+  const float sgn[3] = {(float)usign_adj(mm, 0), (float)usign_adj(mm, 1),
+                        (float)usign_adj(mm, 2)};
+  const float4 hi = A.XU[s].xh, lo = A.XU[s].xl, uh = A.XU[s].uh, ul = A.XU[s].ul;
+  const float uih[3] = {uh.x, uh.y, uh.z}, uil[3] = {ul.x, ul.y, ul.z};
+  const ff ihf{A.K.ih_h, A.K.ih_l};
   const int m = min(A.cnt[s], A.cap);
-  double su[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
+  ff su[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, sp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
     const int j = code & kIndexMask;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
-    const double zj = mir ? f2 - A.z[j] : A.z[j];
-    const double dx = min_image(A.x[j] - xi, A.K.Lx) * ih;
-    const double dy = min_image(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
-    double a[kNB];
-    taylor_row(dx, dy, dz, a);
-    double ab[kNB];
-    for (int q = 0; q < kNB; ++q) ab[q] = 0.0;
+    const FF8& rj = A.XU[j];
+    const FFRow row = ff_row_of<PER>(hi, lo, rj.xh, rj.xl, code, A.K);
+    ff a[kNB];
+    ff_taylor(row, a);
+    const float ujh[3] = {rj.uh.x, rj.uh.y, rj.uh.z}, ujl[3] = {rj.ul.x, rj.ul.y, rj.ul.z};
+    ff ab[kNB];
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) ab[q] = {0.f, 0.f};
+#pragma unroll
     for (int f = 0; f < 3; ++f) {
-      const double sj = mir ? sgn[f] : 1.0;
-      double r = sj * uf[f][j] - ui[f], b = 0.0;
+      const float sj = mir ? sgn[f] : 1.f;
+      ff r = ff_diff(sj * ujh[f], sj * ujl[f], uih[f], uil[f]), b = {0.f, 0.f};
+#pragma unroll
       for (int q = 0; q < kNB; ++q) {
-        r -= a[q] * c[f][q];
-        b += a[q] * lc[f][q];
+        ff_acc(r, a[q], ff_neg(cf[f][q]));
+        ff_acc(b, a[q], zf[f][q]);
       }
-      atomicAdd(&A.l0[3 + f][j], sj * b);
-      su[f] += b;
-      for (int q = 0; q < kNB; ++q) ab[q] += r * lc[f][q] - b * c[f][q];
+      r = ff_norm(r);
+      b = ff_norm(b);
+      atomicAdd(&A.l0[3 + f][j], ffs_to_double(sj * b.h) + ffs_to_double(sj * b.l));
+      su[f] = ff_add(su[f], b);
+      const ff nb = ff_neg(b);
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) {
+        ff_acc(ab[q], r, zf[f][q]);
+        ff_acc(ab[q], nb, cf[f][q]);
+      }
     }
-    double db[3];
-    row_adjoint(dx, dy, dz, ab, db);
+    ff db[3];
+    ff_row_adjoint(row.dx, row.dy, row.dz, ab, db);
     if (code & kGhostBit) {  // the ghost's row T(-d), right-hand sides 0
-      taylor_row(-dx, -dy, -dz, a);
-      for (int q = 0; q < kNB; ++q) ab[q] = 0.0;
+      const ff ndx = ff_neg(row.dx), ndy = ff_neg(row.dy), ndz = ff_neg(row.dz);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) a[q] = ff_neg(a[q]);  // T(-d): linear terms flip
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) ab[q] = {0.f, 0.f};
+#pragma unroll
       for (int f = 0; f < 3; ++f) {
-        double r = 0.0, b = 0.0;
+        ff r = {0.f, 0.f}, b = {0.f, 0.f};
+#pragma unroll
         for (int q = 0; q < kNB; ++q) {
-          r -= a[q] * c[f][q];
-          b += a[q] * lc[f][q];
+          ff_acc(r, a[q], ff_neg(cf[f][q]));
+          ff_acc(b, a[q], zf[f][q]);
         }
-        for (int q = 0; q < kNB; ++q) ab[q] += r * lc[f][q] - b * c[f][q];
+        r = ff_norm(r);
+        b = ff_norm(b);
+        const ff nb = ff_neg(b);
+#pragma unroll
+        for (int q = 0; q < kNB; ++q) {
+          ff_acc(ab[q], r, zf[f][q]);
+          ff_acc(ab[q], nb, cf[f][q]);
+        }
       }
-      double dbG[3];
-      row_adjoint(-dx, -dy, -dz, ab, dbG);
-      for (int q = 0; q < 3; ++q) db[q] -= dbG[q];
+      ff dbG[3];
+      ff_row_adjoint(ndx, ndy, ndz, ab, dbG);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) db[q] = ff_sub(db[q], dbG[q]);
     }
-    atomicAdd(&A.l0[0][j], db[0] * ih);
-    atomicAdd(&A.l0[1][j], db[1] * ih);
-    atomicAdd(&A.l0[2][j], (mir ? -db[2] : db[2]) * ih);
-    for (int q = 0; q < 3; ++q) sp[q] += db[q] * ih;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const ff g = ff_mul(q == 2 && mir ? ff_neg(db[q]) : db[q], ihf);
+      atomicAdd(&A.l0[q][j], ffs_to_double(g.h) + ffs_to_double(g.l));
+      sp[q] = ff_add(sp[q], ff_mul(db[q], ihf));
+    }
   }
-  for (int f = 0; f < 3; ++f) atomicAdd(&A.l0[3 + f][s], -su[f]);
-  for (int q = 0; q < 3; ++q) atomicAdd(&A.l0[q][s], -sp[q]);
+  for (int f = 0; f < 3; ++f)
+    atomicAdd(&A.l0[3 + f][s], -(ffs_to_double(su[f].h) + ffs_to_double(su[f].l)));
+  for (int q = 0; q < 3; ++q)
+    atomicAdd(&A.l0[q][s], -(ffs_to_double(sp[q].h) + ffs_to_double(sp[q].l)));
 }
 
 // dst[f][s] = src[f][idx[s]] (caller order to sorted order)
@@ -476,7 +539,9 @@ void launch_adjoint_step(const AdjArgs& A, cudaStream_t st) {
   k_adj_prepare<<<nb, kBlock, 0, st>>>(A);
   k_adj_accel<<<nb, kBlock, 0, st>>>(A);
   k_adj_pass2<<<nb, kBlock, 0, st>>>(A);
-  k_adj_pass1<<<nb, kBlock, 0, st>>>(A);
+  k_adj_split<<<nb, kBlock, 0, st>>>(A);
+  if (A.K.periodic) k_adj_pass1<true><<<nb, kBlock, 0, st>>>(A);
+  else k_adj_pass1<false><<<nb, kBlock, 0, st>>>(A);
 }
 
 }  // namespace lp

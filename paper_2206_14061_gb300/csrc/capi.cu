@@ -1586,6 +1586,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
         J.x = sk[0]; J.y = sk[1]; J.z = sk[2]; J.u = sk[3]; J.v = sk[4]; J.w = sk[5];
         J.V = sk[6];
         J.nbr = c->nbr; J.cnt = c->cnt; J.colid = c->colid[c->ci]; J.mui = c->d_mui;
+        J.grids = c->d_grids; J.XU = c->XU;  // (free: the FP64 re-runs do not split)
         if (k_stored >= 0) {
           const StepData d = step_data(k_stored);
           J.fbslot = d.fbslot; J.fac = d.fac; J.p1 = d.p1; J.coef1 = d.coef1;

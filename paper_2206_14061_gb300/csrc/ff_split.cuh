@@ -86,3 +86,31 @@ LP_FFS_FN bool ff_split_fast(double d, float* h, float* l) {
   *l = fa * ffs_float_of(ls | (((uint32_t)(e - 52 + 127)) << 23));  // exact: 2^(e-52) >= 2^-112
   return true;
 }
+
+// float -> double, exactly, with integer operations (the conversion
+// instruction runs on the FP64 pipe): a normal float's exponent is re-biased
+// and its significand shifted into place; zeros keep their sign; subnormal,
+// infinite and NaN floats take the conversion instruction.
+LP_FFS_FN double ffs_double_of_bits(uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  memcpy(&d, &b, sizeof d);
+  return d;
+#endif
+}
+LP_FFS_FN double ffs_to_double(float f) {
+  uint32_t b;
+#ifdef __CUDA_ARCH__
+  b = __float_as_uint(f);
+#else
+  memcpy(&b, &f, sizeof b);
+#endif
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+  if ((b & 0x7fffffffu) == 0u) return ffs_double_of_bits(sign);
+  if (e == 0u || e == 0xffu) return (double)f;
+  return ffs_double_of_bits(sign | ((uint64_t)(e + 896u) << 52) |
+                            ((uint64_t)(b & 0x007fffffu) << 29));
+}

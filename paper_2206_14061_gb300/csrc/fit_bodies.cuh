@@ -324,7 +324,9 @@ static __device__ __noinline__ void pass2_fallback_item(const StepArgs& A, int t
 // about 2^-44 cond(G) relative error, the accuracy of the float-float G.
 
 // scaled, split positions and velocities of the current state
-__device__ __forceinline__ void split_state_body(const StepArgs& A, int s) {
+// (StepArgs, or the adjoint's AdjArgs for the step it differentiates)
+template <class Args>
+__device__ __forceinline__ void split_state_body(const Args& A, int s) {
   const GridCol g = A.grids[A.colid[s]];
   const double ih = A.K.inv_h;
   const ff fx = ff_of((A.x[s] - g.ox) * ih), fy = ff_of((A.y[s] - g.oy) * ih);

@@ -351,6 +351,8 @@ struct PersistArgs {
 struct AdjArgs {
   int n, cap;
   const double *x, *y, *z, *u, *v, *w, *V;  // forward state at step n (sorted order)
+  const GridCol* grids;  // the columns' cell grids (origins of the split positions)
+  FF8* XU;               // the state of step n split into float-float pairs
   const int32_t *nbr, *cnt, *colid, *fbslot;
   const ColMui* mui;
   const double* fac;     // FP64 Cholesky factors, 45 * n

@@ -1,10 +1,12 @@
-"""The integer split of a double into a float-float pair
-(paper_2206_14061_gb300/csrc/ff_split.cuh), compiled as plain C++ on the host,
-against the FP64 conversion it replaces in the kernels: RN(d) to float, then
-RN(d - RN(d)) to float. Both parts must agree bit for bit over random doubles
-of every exponent in the fast range, the tie and carry cases of the rounding,
-signed zeros and the edges of the range; outside the range the split must
-decline (the kernels then convert with FP64 operations)."""
+"""The integer split of a double into a float-float pair and the exact
+float-to-double conversion (paper_2206_14061_gb300/csrc/ff_split.cuh), compiled
+as plain C++ on the host, against the conversions they replace in the
+kernels. The split must give RN(d) to float, then RN(d - RN(d)) to float, bit
+for bit over random doubles of every exponent in the fast range, the tie and
+carry cases of the rounding, signed zeros and the edges of the range; outside
+the range it must decline (the kernels then convert with FP64 operations). The
+float-to-double conversion must equal the cast on random bit patterns and on
+zeros, subnormals and the largest float."""
 import os
 import subprocess
 
@@ -84,8 +86,27 @@ int main(void) {
   check(1e300, 0);
   check(of_bits(0x7ff0000000000000ull), 0);
   check(of_bits(0x7ff8000000000000ull), 0);
-  printf("fast %ld declined %ld bad %ld\n", fast, declined, bad);
-  return bad != 0;
+  // the exact float -> double conversion, against the cast
+  long bad2 = 0;
+  for (long k = 0; k < 4000000; ++k) {
+    uint32_t b = (uint32_t)next();
+    float f;
+    memcpy(&f, &b, 4);
+    const double got = ffs_to_double(f), ref = (double)f;
+    uint64_t gb, rb;
+    memcpy(&gb, &got, 8);
+    memcpy(&rb, &ref, 8);
+    if (gb != rb && !(f != f)) ++bad2;
+  }
+  const float specials[] = {0.0f, -0.0f, 1.0f, -1.0f, 1e-45f, -1e-45f, 1.17549435e-38f,
+                            3.4028235e38f};
+  for (unsigned i = 0; i < sizeof specials / sizeof specials[0]; ++i)
+    if (ffs_to_double(specials[i]) != (double)specials[i] ||
+        (ffs_to_double(specials[i]) == 0.0 &&
+         (1.0 / ffs_to_double(specials[i]) != 1.0 / (double)specials[i])))
+      ++bad2;
+  printf("fast %ld declined %ld bad %ld to_double bad %ld\n", fast, declined, bad, bad2);
+  return bad != 0 || bad2 != 0;
 }
 """
 
