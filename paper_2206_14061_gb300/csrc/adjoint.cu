@@ -271,29 +271,29 @@ __global__ void __launch_bounds__(kBlock) k_adj_accel(const AdjArgs A) {
 // ---------------------------------------------------------------- R2
 // rows of the pass-2 adjoint: to the neighbours' |gdot| and V^{n+1}, and to
 // the positions
+template <bool PER>
 __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= A.n || !A.ok[s]) return;
   const int n = A.n;
-  double zg[kNB], zV[kNB], cg[kNB], cV[kNB];
+  // z and the forward coefficients c of the two pass-2 fits (|gdot|, V), split once
+  ff zg[kNB], zV[kNB], cg[kNB], cV[kNB];
   bool any = false;
+#pragma unroll
   for (int q = 0; q < kNB; ++q) {
-    zg[q] = A.zz[(int64_t)q * n + s];
-    zV[q] = A.zz[(int64_t)(kNB + q) * n + s];
-    cg[q] = A.coef2[(int64_t)q * n + s];
-    cV[q] = A.coef2[(int64_t)(kNB + q) * n + s];
-    any = any || zg[q] != 0.0 || zV[q] != 0.0;
+    const double zgq = A.zz[(int64_t)q * n + s], zVq = A.zz[(int64_t)(kNB + q) * n + s];
+    any = any || zgq != 0.0 || zVq != 0.0;
+    zg[q] = ff_of(zgq);
+    zV[q] = ff_of(zVq);
+    cg[q] = ff_of(A.coef2[(int64_t)q * n + s]);
+    cV[q] = ff_of(A.coef2[(int64_t)(kNB + q) * n + s]);
   }
   if (!any) return;
-  const double ih = A.K.inv_h, f2 = 2.0 * A.K.floor_z;
-  const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
   const double* Gn = A.p1 + P1_GN * n;
   // V of the pass-2 fit: V^{n+1}, or V^n in an Euler stage (whose adjoint is lVd)
   const double* Vn = A.K.euler ? A.V : A.p1 + P1_VN * n;
   double* const lVfit = A.K.euler ? A.lVd : A.lVn;
   const double gni = Gn[s], Vi = Vn[s];
-  const int m = min(A.cnt[s], A.cap);
-  double sg = 0.0, sV = 0.0, sp[3] = {0.0, 0.0, 0.0};
   // ghost rows (free surface): right-hand sides bg_G = |gdot|_G - gni and
   // bv_G = V_G - Vi with |gdot|_G = gni k / (phi_c - phi) in the inertial
   // regime; their derivatives with respect to gni and Vi (phi = 1/Vi)
@@ -308,64 +308,111 @@ __global__ void __launch_bounds__(kBlock) k_adj_pass2(const AdjArgs A) {
       dbg_dV = -gni * A.K.ghost_num / (w * w * Vi * Vi);
     }
   }
+  const ff bgGf = ff_of(bgG), bvGf = ff_of(bvG);
+  // the rows in float-float, as in the pass-1 adjoint: positions and the
+  // neighbours' |gdot|^n and V from the split state
+  const float4 hi = A.XU[s].xh, lo = A.XU[s].xl, gvi = A.XU[s].uh;
+  const ff ihf{A.K.ih_h, A.K.ih_l};
+  const int m = min(A.cnt[s], A.cap);
+  ff sg = {0.f, 0.f}, sV = {0.f, 0.f};
+  ff sp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   double og = 0.0, oV = 0.0;  // adjoints of the particle's own gni, Vi from ghost rows
   for (int k = 0; k < m; ++k) {
     const uint32_t code = (uint32_t)A.nbr[(int64_t)k * n + s];
     const int j = code & kIndexMask;
     if ((unsigned)j >= (unsigned)n) continue;  // stale or corrupt stencil entry
     const bool mir = code >> 31;
-    const double zj = mir ? f2 - A.z[j] : A.z[j];
-    const double dx = min_image(A.x[j] - xi, A.K.Lx) * ih;
-    const double dy = min_image(A.y[j] - yi, A.K.Ly) * ih, dz = (zj - zi) * ih;
-    double a[kNB];
-    taylor_row(dx, dy, dz, a);
-    double rg = (mir ? 0.0 : Gn[j]) - gni, rV = Vn[j] - Vi, bg = 0.0, bV = 0.0;
+    const FF8& rj = A.XU[j];
+    const FFRow row = ff_row_of<PER>(hi, lo, rj.xh, rj.xl, code, A.K);
+    ff a[kNB];
+    ff_taylor(row, a);
+    const float4 gvj = rj.uh;
+    ff rg = mir ? ff{-gvi.x, -gvi.y} : ff_diff(gvj.x, gvj.y, gvi.x, gvi.y);
+    ff rV = ff_diff(gvj.z, gvj.w, gvi.z, gvi.w), bg = {0.f, 0.f}, bV = {0.f, 0.f};
+#pragma unroll
     for (int q = 0; q < kNB; ++q) {
-      rg -= a[q] * cg[q];
-      rV -= a[q] * cV[q];
-      bg += a[q] * zg[q];
-      bV += a[q] * zV[q];
+      ff_acc(rg, a[q], ff_neg(cg[q]));
+      ff_acc(rV, a[q], ff_neg(cV[q]));
+      ff_acc(bg, a[q], zg[q]);
+      ff_acc(bV, a[q], zV[q]);
     }
-    if (!mir) atomicAdd(&A.lGn[j], bg);
-    sg += bg;
-    atomicAdd(&lVfit[j], bV);  // the mirror of j carries V_j
-    sV += bV;
-    double ab[kNB], db[3];
-    for (int q = 0; q < kNB; ++q) ab[q] = rg * zg[q] - bg * cg[q] + rV * zV[q] - bV * cV[q];
-    row_adjoint(dx, dy, dz, ab, db);
+    rg = ff_norm(rg);
+    rV = ff_norm(rV);
+    bg = ff_norm(bg);
+    bV = ff_norm(bV);
+    if (!mir) atomicAdd(&A.lGn[j], ffs_to_double(bg.h) + ffs_to_double(bg.l));
+    sg = ff_add(sg, bg);
+    atomicAdd(&lVfit[j], ffs_to_double(bV.h) + ffs_to_double(bV.l));  // the mirror of j carries V_j
+    sV = ff_add(sV, bV);
+    ff ab[kNB];
+    const ff nbg = ff_neg(bg), nbV = ff_neg(bV);
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+      ab[q] = {0.f, 0.f};
+      ff_acc(ab[q], rg, zg[q]);
+      ff_acc(ab[q], nbg, cg[q]);
+      ff_acc(ab[q], rV, zV[q]);
+      ff_acc(ab[q], nbV, cV[q]);
+    }
+    ff db[3];
+    ff_row_adjoint(row.dx, row.dy, row.dz, ab, db);
     if (code & kGhostBit) {  // the ghost's row T(-d)
-      taylor_row(-dx, -dy, -dz, a);
-      double rgG = bgG, rVG = bvG, bgb = 0.0, bVb = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) a[q] = ff_neg(a[q]);  // T(-d): linear terms flip
+      ff rgG = bgGf, rVG = bvGf, bgb = {0.f, 0.f}, bVb = {0.f, 0.f};
+#pragma unroll
       for (int q = 0; q < kNB; ++q) {
-        rgG -= a[q] * cg[q];
-        rVG -= a[q] * cV[q];
-        bgb += a[q] * zg[q];
-        bVb += a[q] * zV[q];
+        ff_acc(rgG, a[q], ff_neg(cg[q]));
+        ff_acc(rVG, a[q], ff_neg(cV[q]));
+        ff_acc(bgb, a[q], zg[q]);
+        ff_acc(bVb, a[q], zV[q]);
       }
-      og += bgb * dbg_dg;
-      oV += bgb * dbg_dV - bVb;
-      for (int q = 0; q < kNB; ++q) ab[q] = rgG * zg[q] - bgb * cg[q] + rVG * zV[q] - bVb * cV[q];
-      double dbG[3];
-      row_adjoint(-dx, -dy, -dz, ab, dbG);
-      for (int c = 0; c < 3; ++c) db[c] -= dbG[c];
+      rgG = ff_norm(rgG);
+      rVG = ff_norm(rVG);
+      bgb = ff_norm(bgb);
+      bVb = ff_norm(bVb);
+      const double bgbd = ffs_to_double(bgb.h) + ffs_to_double(bgb.l);
+      og += bgbd * dbg_dg;
+      oV += bgbd * dbg_dV - (ffs_to_double(bVb.h) + ffs_to_double(bVb.l));
+      const ff nbgb = ff_neg(bgb), nbVb = ff_neg(bVb);
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) {
+        ab[q] = {0.f, 0.f};
+        ff_acc(ab[q], rgG, zg[q]);
+        ff_acc(ab[q], nbgb, cg[q]);
+        ff_acc(ab[q], rVG, zV[q]);
+        ff_acc(ab[q], nbVb, cV[q]);
+      }
+      ff dbG[3];
+      ff_row_adjoint(ff_neg(row.dx), ff_neg(row.dy), ff_neg(row.dz), ab, dbG);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) db[c] = ff_sub(db[c], dbG[c]);
     }
-    atomicAdd(&A.l0[0][j], db[0] * ih);
-    atomicAdd(&A.l0[1][j], db[1] * ih);
-    atomicAdd(&A.l0[2][j], (mir ? -db[2] : db[2]) * ih);
-    for (int c = 0; c < 3; ++c) sp[c] += db[c] * ih;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const ff g = ff_mul(q == 2 && mir ? ff_neg(db[q]) : db[q], ihf);
+      atomicAdd(&A.l0[q][j], ffs_to_double(g.h) + ffs_to_double(g.l));
+      sp[q] = ff_add(sp[q], ff_mul(db[q], ihf));
+    }
   }
-  atomicAdd(&A.lGn[s], og - sg);
-  atomicAdd(&lVfit[s], oV - sV);
-  for (int c = 0; c < 3; ++c) atomicAdd(&A.l0[c][s], -sp[c]);
+  atomicAdd(&A.lGn[s], og - (ffs_to_double(sg.h) + ffs_to_double(sg.l)));
+  atomicAdd(&lVfit[s], oV - (ffs_to_double(sV.h) + ffs_to_double(sV.l)));
+  for (int c = 0; c < 3; ++c)
+    atomicAdd(&A.l0[c][s], -(ffs_to_double(sp[c].h) + ffs_to_double(sp[c].l)));
 }
 
 // ---------------------------------------------------------------- R3
-// the state of step n split into float-float pairs for the pass-1 adjoint's
-// rows: positions relative to the column's grid origin in units of h (with
-// the floor-mirror height), and velocities, as the forward step splits them
+// the state of step n split into float-float pairs for the adjoint's rows:
+// positions relative to the column's grid origin in units of h (with the
+// floor-mirror height), and velocities, as the forward step splits them (GV:
+// the velocity half then holds |gdot|^n and the V of the pass-2 fit, as the
+// forward step's pass 2 reads them)
+template <bool GV>
 __global__ void k_adj_split(const AdjArgs A) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < A.n) split_state_body(A, s);
+  if (s >= A.n) return;
+  split_state_body(A, s);
+  if (GV) split_p1_body(A, s);
 }
 
 // pass-1 adjoint: |gdot| and ld to the velocity gradient and Hessians, then
@@ -538,8 +585,10 @@ void launch_adjoint_step(const AdjArgs& A, cudaStream_t st) {
   const int nb = (A.n + kBlock - 1) / kBlock;
   k_adj_prepare<<<nb, kBlock, 0, st>>>(A);
   k_adj_accel<<<nb, kBlock, 0, st>>>(A);
-  k_adj_pass2<<<nb, kBlock, 0, st>>>(A);
-  k_adj_split<<<nb, kBlock, 0, st>>>(A);
+  k_adj_split<true><<<nb, kBlock, 0, st>>>(A);
+  if (A.K.periodic) k_adj_pass2<true><<<nb, kBlock, 0, st>>>(A);
+  else k_adj_pass2<false><<<nb, kBlock, 0, st>>>(A);
+  k_adj_split<false><<<nb, kBlock, 0, st>>>(A);
   if (A.K.periodic) k_adj_pass1<true><<<nb, kBlock, 0, st>>>(A);
   else k_adj_pass1<false><<<nb, kBlock, 0, st>>>(A);
 }

@@ -342,7 +342,8 @@ __device__ __forceinline__ void split_state_body(const Args& A, int s) {
 }
 
 // split |gdot|^n and V^{n+1} (pass-1 outputs, FP64) for pass 2
-__device__ __forceinline__ void split_p1_body(const StepArgs& A, int s) {
+template <class Args>
+__device__ __forceinline__ void split_p1_body(const Args& A, int s) {
   const ff g = ff_of(A.p1[P1_GN * A.n + s]);
   const ff v = ff_of(A.K.euler ? A.V[s] : A.p1[P1_VN * A.n + s]);  // V of the pass-2 fit
   A.XU[s].uh = make_float4(g.h, g.l, v.h, v.l);  // the velocity half is no longer read
