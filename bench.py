@@ -785,8 +785,11 @@ def adjoint_line(dev, stream):
     spacing R/25 (98,800 particles), 200 FP64 steps with a checkpoint every
     20, from solid fraction 0.5 with free-surface ghosts and a radial flow of
     0.5 m/s (r/R)(z/H). Times the forward run alone (lp_step, stencils
-    rebuilt every 20 steps) and the adjoint (lp_step_adjoint: segment
-    re-runs and the reverse sweep) for a seed on every state field."""
+    rebuilt every 20 steps) and the adjoint (lp_step_adjoint) for a seed on
+    every state field: by default the forward sweep keeps the whole run's
+    data (about 19 GB here) and the reverse sweep reads it; `adjoint_rerun_ms`
+    is the same call with no room for that (each segment re-run from its
+    checkpoint)."""
     import torch
 
     from paper_2206_14061_gb300 import capi, workloads as W
@@ -808,7 +811,8 @@ def adjoint_line(dev, stream):
     seed = {k: torch.tensor(rng.standard_normal(wl.n), device=dev) for k in capi.FIELDS}
     ctx = capi.Context(wl.n, cap=64)
     out = {}
-    for name in ("forward", "adjoint"):
+    for name in ("forward", "adjoint_rerun", "adjoint"):
+        ctx.set_adjoint_memory(0 if name == "adjoint_rerun" else -1)
         with torch.cuda.stream(stream):
             for rep in range(2):  # a warm-up, then the timed call
                 st = {k: v.clone() for k, v in init.items()}
@@ -823,6 +827,8 @@ def adjoint_line(dev, stream):
                 e1.record(stream)
                 torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1)
+        if name == "adjoint_rerun":
+            dmui_rerun = dmui
     d = ctx.sync(stream, raise_on_error=False)
     ctx.close()
     return {"workload": f"adjoint column R = 0.02 m, H = 2R, h = R/25 ({wl.n} particles), "
@@ -830,6 +836,8 @@ def adjoint_line(dev, stream):
                         "radial flow 0.5 m/s",
             "forward_ms": out["forward"], "adjoint_ms": out["adjoint"],
             "adjoint_over_forward": out["adjoint"] / out["forward"],
+            "adjoint_rerun_ms": out["adjoint_rerun"],
+            "dL_dmui_rerun": [float(v) for v in dmui_rerun.cpu()],
             "value": wl.n * nsteps / (out["adjoint"] / 1e3),
             "unit": "particle-steps/s differentiated (d/d(mu_s, mu_2, I0) of every state field)",
             "dL_dmui": [float(v) for v in dmui.cpu()], "n_nonfinite": d["n_nonfinite"]}

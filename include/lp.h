@@ -248,6 +248,12 @@ lp_status lp_ctx_sync(lp_ctx* ctx, void* stream, lp_diag* diag);
  * a test aid only (0 restores normal operation). */
 lp_status lp_ctx_set_wait_limit(lp_ctx* ctx, int64_t max_spins, int32_t extra_arrivals);
 
+/* Device memory that lp_step_adjoint may use to keep a whole run's states,
+ * fit data and stencils (not in the paper): max_bytes < 0 (the default) means
+ * half of the device memory free at the call, 0 means never (re-run each
+ * checkpoint segment). About 930 bytes per particle and step. */
+lp_status lp_ctx_set_adjoint_memory(lp_ctx* ctx, int64_t max_bytes);
+
 /* Per-phase timing (profiling aid, not in the paper). While enabled, lp_step
  * records a CUDA event pair around each phase of every step and does not use
  * graph replay. A persistent launch (one kernel per step) times its phases
@@ -410,11 +416,17 @@ lp_status lp_autotune(lp_ctx* ctx, const lp_particles* p, const lp_mui* mui, con
  * dL_dmui (device, 3 doubles) holds dL/d(mu_s, mu_2, I0) summed over all
  * columns, and if dL_dinitial is non-NULL its arrays receive dL/d(initial
  * state). Synchronises. Requires p->ncolumns == 1 in this version.
- * Workspace (allocated and freed by the call): the checkpoints and one
- * segment's states and adjoints, plus, for the paper's step, each segment
- * step's fit data (about 860 bytes per particle and step) so that the reverse
- * sweep need not recompute it; when that part cannot be allocated the steps
- * are recomputed instead, with the same result. */
+ * Workspace (allocated and freed by the call): the checkpoints, the
+ * adjoints and, for the paper's step, each step's fit data (about 860 bytes
+ * per particle and step) so that the reverse sweep need not compute it again:
+ *  - when every segment's states, fit data and stencils fit in the limit set
+ *    by lp_ctx_set_adjoint_memory, the forward sweep keeps them all and the
+ *    reverse sweep recomputes nothing (one forward run in all);
+ *  - otherwise the reverse sweep re-runs each segment from its checkpoint and
+ *    keeps that segment's data (two forward runs); when even that cannot be
+ *    allocated, each reverse step recomputes its own.
+ * The three give the same result to rounding. Heun's method always takes the
+ * last. */
 lp_status lp_step_adjoint(lp_ctx* ctx, const lp_particles* initial, const lp_mui* mui,
                           const lp_eos* eos, const lp_params* params, double dt, int32_t nsteps,
                           int32_t checkpoint_every, const lp_particles* seed, double* dL_dmui,

@@ -109,6 +109,7 @@ _SIGS = {
     "lp_ctx_sync": ([_vp, _vp, _P(LpDiag)], ctypes.c_int32),
     "lp_ctx_profile": ([_vp, ctypes.c_int32], ctypes.c_int32),
     "lp_ctx_set_wait_limit": ([_vp, ctypes.c_int64, ctypes.c_int32], ctypes.c_int32),
+    "lp_ctx_set_adjoint_memory": ([_vp, ctypes.c_int64], ctypes.c_int32),
     "lp_ctx_phase_times": ([_vp, _vp, _P(ctypes.c_double), _P(ctypes.c_int64),
                             _P(ctypes.c_int64)], ctypes.c_int32),
     "lp_ctx_set_tuning": ([_vp, _P(LpTuning)], ctypes.c_int32),
@@ -259,6 +260,12 @@ class Context:
     def set_wait_limit(self, max_spins: int = 1 << 25, extra_arrivals: int = 0):
         _check(lib().lp_ctx_set_wait_limit(self.handle, int(max_spins), int(extra_arrivals)),
                "lp_ctx_set_wait_limit")
+
+    def set_adjoint_memory(self, max_bytes: int = -1):
+        """Device memory lp_step_adjoint may keep for a whole run's data
+        (-1: half of the free memory; 0: re-run each checkpoint segment)."""
+        _check(lib().lp_ctx_set_adjoint_memory(self.handle, int(max_bytes)),
+               "lp_ctx_set_adjoint_memory")
 
     def profile(self, enable: bool = True):
         _check(lib().lp_ctx_profile(self.handle, int(bool(enable))), "lp_ctx_profile")

@@ -163,6 +163,9 @@ struct lp_ctx {
   // bounded waits of the persistent kernel (lp_ctx_set_wait_limit)
   unsigned long long max_spins = 1ull << 25;
   unsigned extra_arrivals = 0;
+  // device memory lp_step_adjoint may keep for whole-run data (< 0: half of
+  // the free memory; 0: always recompute from checkpoints)
+  int64_t adj_keep_bytes = -1;
   // launch configuration (lp_ctx_set_tuning / lp_autotune)
   int bs_nbr = kBlock, bs_p1 = kBlock, bs_p2 = kBlock;
 };
@@ -819,6 +822,12 @@ lp_status lp_ctx_sync(lp_ctx* c, void* stream, lp_diag* diag) {
   return LP_OK;
 }
 
+lp_status lp_ctx_set_adjoint_memory(lp_ctx* c, int64_t max_bytes) {
+  if (!c) return LP_ERR_INVALID_ARG;
+  c->adj_keep_bytes = max_bytes < 0 ? -1 : max_bytes;
+  return LP_OK;
+}
+
 lp_status lp_ctx_set_wait_limit(lp_ctx* c, int64_t max_spins, int32_t extra_arrivals) {
   if (!c || max_spins < 1 || extra_arrivals < 0 || extra_arrivals > 1024)
     return LP_ERR_INVALID_ARG;
@@ -1405,21 +1414,87 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   // Heun's method: a segment keeps y^k and the first stage's y*_k of each step
   const bool heun = q->time_scheme == LP_TIME_HEUN;
   const int nkept = heun ? 2 * C + 1 : C + 1;
+  const size_t N = (size_t)n;
+
+  // Per-step fit data (the paper's step; Heun's method keeps recomputing):
+  // each step's factors, pass-1 outputs, coefficients and QR-fallback slots
+  // and gradients, so that the reverse sweep reads them instead of computing
+  // each step again. Two ways to get them:
+  //  - keep: with room for every segment's states, fit data and stencils
+  //    (within the context's adjoint memory limit), the forward sweep runs
+  //    each segment as below and keeps it all; the reverse sweep recomputes
+  //    nothing;
+  //  - recompute: the forward sweep keeps only the checkpoints, and the
+  //    reverse sweep re-runs each segment from its checkpoint, keeping that
+  //    segment's data; without room even for that, each reverse step
+  //    recomputes its own.
+  const size_t per_step = N * (size_t)(P1_N + kTri + 27 + 18) + (size_t)c->fb_cap * 6;
+  const size_t nsnap = (size_t)c->cap + 3;  // a segment's stencils: nbr, cnt, ids, colid
+  bool keep = false;
+  if (!heun && c->adj_keep_bytes != 0) {
+    const size_t need =
+        sizeof(double) * (7 * N * (size_t)(nseg - 1) * nkept + per_step * (size_t)nsteps) +
+        sizeof(int32_t) * N * ((size_t)nsteps + nsnap * nseg);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+      const size_t lim =
+          c->adj_keep_bytes < 0 ? fr / 2 : std::min((size_t)c->adj_keep_bytes, fr);
+      keep = need <= lim;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  double* Wk = nullptr;
+  int32_t* Fk = nullptr;
+  auto alloc_fit_data = [&](int steps_kept, size_t extra_i32) {
+    if (cudaMalloc(&Wk, per_step * (size_t)steps_kept * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&Fk, (N * (size_t)steps_kept + extra_i32) * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(Wk);
+      Wk = nullptr;
+      Fk = nullptr;
+      return false;
+    }
+    return true;
+  };
+  if (keep) keep = alloc_fit_data(nsteps, nsnap * N * (size_t)nseg);
+  if (!heun && !keep) alloc_fit_data(C, 0);
+  const int nsegk = keep ? nseg : 1;  // segments whose states the workspace holds
+  struct StepData {
+    double *p1, *fac, *coef1, *coef2, *fbgrad;
+    int32_t* fbslot;
+  };
+  // fit data of step k of segment s2
+  auto step_data = [&](int s2, int k) {
+    const size_t i = keep ? (size_t)s2 * C + k : (size_t)k;
+    double* b = Wk + per_step * i;
+    return StepData{b, b + N * P1_N, b + N * (P1_N + kTri), b + N * (P1_N + kTri + 27),
+                    b + N * (P1_N + kTri + 45), Fk + N * i};
+  };
+  // stencils of segment s2 (keep) in the segment's sorted order
+  struct Stencils {
+    const int32_t *nbr, *cnt, *ids, *colid;
+  };
+  auto snapshot = [&](int s2) {
+    int32_t* b = Fk + N * (size_t)nsteps + nsnap * N * (size_t)s2;
+    return b;
+  };
 
   // workspace of this call: checkpoints, segment states, coefficients, adjoints
-  const size_t N = (size_t)n;
-  const size_t nd = N * (7 * (size_t)nseg + 7 * (size_t)nkept + 27 + 18 + 14 + 2 + 6 + 3 + 18 +
-                         7 + 45 + 1 + 1 + (heun ? 14 : 0)) +
+  const size_t nd = N * (7 * (size_t)nseg + 7 * (size_t)nkept * nsegk + 27 + 18 + 14 + 2 + 6 +
+                         3 + 18 + 7 + 45 + 1 + 1 + (heun ? 14 : 0)) +
                     3;
   double* W = nullptr;
   if (cudaMalloc(&W, nd * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
+    cudaFree(Wk);
+    cudaFree(Fk);
     return LP_ERR_OOM;
   }
   double* p = W;
   auto take = [&](size_t k) { double* r = p; p += k; return r; };
   double* ckpt = take(7 * N * nseg);
-  double* seg = take(7 * N * nkept);
+  double* seg = take(7 * N * nkept * nsegk);
   double* coef1 = take(27 * N);
   double* coef2 = take(18 * N);
   double* lam[2] = {take(7 * N), take(7 * N)};
@@ -1435,16 +1510,18 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   double* facx = take(45 * N);
   uint8_t* okf = (uint8_t*)take(N);  // N bytes used of N doubles
   double* dth = take(3);
-  // device pointer tables: checkpoints (nseg x 7), segment states (nkept x 7),
-  // lam[0], lam[1], seed, caller initial, dL_dinitial, internal X[0], X[1]
-  const int ntab = 7 * nseg + 7 * nkept + 7 * 7;
+  // device pointer tables: checkpoints (nseg x 7), segment states (nsegk x
+  // nkept x 7), lam[0], lam[1], seed, caller initial, dL_dinitial, internal
+  // X[0], X[1]
+  const int nstates = nkept * nsegk;
+  const int ntab = 7 * nseg + 7 * nstates + 7 * 7;
   std::vector<double*> tab(ntab);
   for (int s2 = 0; s2 < nseg; ++s2)
     for (int f = 0; f < 7; ++f) tab[7 * s2 + f] = ckpt + (size_t)(7 * s2 + f) * N;
   const int tseg = 7 * nseg;
-  for (int k = 0; k < nkept; ++k)
+  for (int k = 0; k < nstates; ++k)
     for (int f = 0; f < 7; ++f) tab[tseg + 7 * k + f] = seg + (size_t)(7 * k + f) * N;
-  const int tlam = tseg + 7 * nkept;
+  const int tlam = tseg + 7 * nstates;
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < 7; ++f) tab[tlam + 7 * b + f] = lam[b] + (size_t)f * N;
   const int tseed = tlam + 14;
@@ -1463,33 +1540,63 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
   if (cudaMalloc(&dtab, sizeof(double*) * ntab) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(W);
+    cudaFree(Wk);
+    cudaFree(Fk);
     return LP_ERR_OOM;
   }
-  // Per-step fit data of one segment (the paper's step; Heun's method keeps
-  // recomputing): the segment's re-run keeps each step's factors, pass-1
-  // outputs, coefficients and QR-fallback slots and gradients, so the reverse
-  // sweep reads them instead of computing each step a third time. Without
-  // room for them the step is recomputed as before.
-  const size_t per_step = N * (size_t)(P1_N + kTri + 27 + 18) + (size_t)c->fb_cap * 6;
-  double* Wk = nullptr;
-  int32_t* Fk = nullptr;
-  if (!heun) {
-    if (cudaMalloc(&Wk, per_step * (size_t)C * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&Fk, N * (size_t)C * sizeof(int32_t)) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(Wk);
-      Wk = nullptr;
-      Fk = nullptr;
-    }
-  }
-  struct StepData {
-    double *p1, *fac, *coef1, *coef2, *fbgrad;
-    int32_t* fbslot;
+  // state i of segment s2 (host table; the device copy at the same offset)
+  auto kept_at = [&](int s2, int i) { return tseg + 7 * ((keep ? s2 : 0) * nkept + i); };
+  StepArgs S{};
+  auto one_pass = [&](double* const* in, double* const* out) {
+    S.x = in[0]; S.y = in[1]; S.z = in[2]; S.u = in[3]; S.v = in[4]; S.w = in[5]; S.V = in[6];
+    S.xo = out[0]; S.yo = out[1]; S.zo = out[2]; S.uo = out[3]; S.vo = out[4]; S.wo = out[5];
+    S.Vo = out[6];
+    cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
+    launch_pass1(LP_FP64, S, st);
+    launch_pass2(LP_FP64, S, st);
   };
-  auto step_data = [&](int k) {
-    double* b = Wk + per_step * (size_t)k;
-    return StepData{b, b + N * P1_N, b + N * (P1_N + kTri), b + N * (P1_N + kTri + 27),
-                    b + N * (P1_N + kTri + 45), Fk + N * (size_t)k};
+  // segment s2 from its checkpoint: the stencils rebuilt exactly as the
+  // forward run built them, then every step, keeping each state (Heun's
+  // method: the state y^k at 2k, the first stage's y*_k at 2k + 1) and, with
+  // room for it, each step's fit data
+  auto run_segment = [&](int s2) {
+    const int steps = std::min(C, nsteps - s2 * C);
+    for (int f = 0; f < 7; ++f)
+      cudaMemcpyAsync(c->X[c->cx][f], tab[7 * s2 + f], sizeof(double) * N,
+                      cudaMemcpyDeviceToDevice, st);
+    launch_iota(n, c->ids[c->ci], st);
+    launch_fill_colid(n, c->d_offs, initial->ncolumns, c->colid[c->ci], st);
+    sort_particles(c, n, 0, 7, st);
+    launch_neighbors(false, n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->pf,
+                     c->colid[c->ci], c->ids[c->ci], c->d_grids,
+                     c->cells + 2 * c->cell_capacity, nullptr, K.radius, K.mirror_mode,
+                     K.floor_z, c->cap, c->nbr, c->cnt, c->dg, st, kBlock, nullptr, nullptr,
+                     K.periodic != 0);
+    if (K.free_surface)  // the same ghost flags as the forward run
+      launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
+                    c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, kBlock,
+                    c->glist, c->gcount, c->olist);
+    for (int f = 0; f < 7; ++f)
+      cudaMemcpyAsync(tab[kept_at(s2, 0) + f], c->X[c->cx][f], sizeof(double) * N,
+                      cudaMemcpyDeviceToDevice, st);
+    S = step_args(c, n, K);
+    auto kept = [&](int i) { return &tab[kept_at(s2, i)]; };
+    for (int k = 0; k < steps; ++k) {
+      if (!heun) {
+        if (Wk) {
+          const StepData d = step_data(s2, k);
+          S.p1 = d.p1; S.fac = d.fac; S.coef1 = d.coef1; S.coef2 = d.coef2;
+          S.fbslot = d.fbslot; S.fbgrad = d.fbgrad;
+        }
+        one_pass(kept(k), kept(k + 1));
+      } else {  // two stages on the segment's stencils, then the average
+        one_pass(kept(2 * k), kept(2 * k + 1));
+        one_pass(kept(2 * k + 1), kept(2 * k + 2));
+        launch_heun_combine(n, kept(2 * k + 2), kept(2 * k), K.Lx, K.Ly, st);
+      }
+    }
+    S.p1 = c->p1; S.fac = c->fac; S.coef1 = S.coef2 = nullptr;
+    S.fbslot = c->fbslot; S.fbgrad = c->fbgrad;
   };
   lp_status rs = LP_OK;
   do {
@@ -1513,11 +1620,31 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
     if (rs != LP_OK) break;
     rs = setup_grids(c, initial->ncolumns, q->radius, st, q->period_x, q->period_y);
     if (rs != LP_OK) break;
-    for (int k = 0; k < nsteps; ++k) {
-      if (k > 0 && k % C == 0)
-        launch_scatter_state(n, c->ids[c->ci], (const double* const*)(dtab + tX + 7 * c->cx),
-                             dtab + 7 * (k / C), 7, st);
-      one_step(c, n, K, LP_FP64, k % C == 0, st);
+    if (keep) {
+      // every segment as the reverse sweep's re-run would run it, kept whole:
+      // its stencils, and its last state (caller order) as the next checkpoint
+      for (int s2 = 0; s2 < nseg; ++s2) {
+        run_segment(s2);
+        int32_t* sn = snapshot(s2);
+        cudaMemcpyAsync(sn, c->nbr, sizeof(int32_t) * N * c->cap, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(sn + N * c->cap, c->cnt, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice,
+                        st);
+        cudaMemcpyAsync(sn + N * (c->cap + 1), c->ids[c->ci], sizeof(int32_t) * N,
+                        cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(sn + N * (c->cap + 2), c->colid[c->ci], sizeof(int32_t) * N,
+                        cudaMemcpyDeviceToDevice, st);
+        if (s2 + 1 < nseg)
+          launch_scatter_state(n, c->ids[c->ci],
+                               (const double* const*)(dtab + kept_at(s2, std::min(C, nsteps - s2 * C))),
+                               dtab + 7 * (s2 + 1), 7, st);
+      }
+    } else {
+      for (int k = 0; k < nsteps; ++k) {
+        if (k > 0 && k % C == 0)
+          launch_scatter_state(n, c->ids[c->ci], (const double* const*)(dtab + tX + 7 * c->cx),
+                               dtab + 7 * (k / C), 7, st);
+        one_step(c, n, K, LP_FP64, k % C == 0, st);
+      }
     }
     // ---- reverse sweep
     int cur = 0;  // lam[cur] holds the adjoint (caller order between segments)
@@ -1525,70 +1652,31 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
       cudaMemcpyAsync(lam[cur] + f * N, sd[f], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     for (int s2 = nseg - 1; s2 >= 0; --s2) {
       const int steps = std::min(C, nsteps - s2 * C);
-      // restore the checkpoint, rebuild the stencils exactly as the forward run did
-      for (int f = 0; f < 7; ++f)
-        cudaMemcpyAsync(c->X[c->cx][f], tab[7 * s2 + f], sizeof(double) * N,
-                        cudaMemcpyDeviceToDevice, st);
-      launch_iota(n, c->ids[c->ci], st);
-      launch_fill_colid(n, c->d_offs, initial->ncolumns, c->colid[c->ci], st);
-      sort_particles(c, n, 0, 7, st);
-      launch_neighbors(false, n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->pf,
-                       c->colid[c->ci], c->ids[c->ci], c->d_grids,
-                       c->cells + 2 * c->cell_capacity, nullptr, K.radius, K.mirror_mode,
-                       K.floor_z, c->cap, c->nbr, c->cnt, c->dg, st, kBlock, nullptr, nullptr,
-                       K.periodic != 0);
-      if (K.free_surface)  // the same ghost flags as the forward run
-        launch_ghosts(n, c->X[c->cx][0], c->X[c->cx][1], c->X[c->cx][2], c->colid[c->ci],
-                      c->d_grids, c->Xfix, c->nbr, c->cnt, c->gcnt, K, c->dg, st, kBlock,
-                      c->glist, c->gcount, c->olist);
-      for (int f = 0; f < 7; ++f)
-        cudaMemcpyAsync(tab[tseg + f], c->X[c->cx][f], sizeof(double) * N,
-                        cudaMemcpyDeviceToDevice, st);
-      // re-run the segment, keeping every step's state (Heun's method: the
-      // state y^k at 2k, the first stage's y*_k at 2k + 1)
-      StepArgs S = step_args(c, n, K);
-      auto kept = [&](int i) { return &tab[tseg + 7 * i]; };
-      auto one_pass = [&](double* const* in, double* const* out) {
-        S.x = in[0]; S.y = in[1]; S.z = in[2]; S.u = in[3]; S.v = in[4]; S.w = in[5]; S.V = in[6];
-        S.xo = out[0]; S.yo = out[1]; S.zo = out[2]; S.uo = out[3]; S.vo = out[4]; S.wo = out[5];
-        S.Vo = out[6];
-        cudaMemsetAsync(c->fb_count, 0, sizeof(int32_t), st);
-        launch_pass1(LP_FP64, S, st);
-        launch_pass2(LP_FP64, S, st);
-      };
-      for (int k = 0; k < steps; ++k) {
-        if (!heun) {
-          if (Wk) {
-            const StepData d = step_data(k);
-            S.p1 = d.p1; S.fac = d.fac; S.coef1 = d.coef1; S.coef2 = d.coef2;
-            S.fbslot = d.fbslot; S.fbgrad = d.fbgrad;
-          }
-          one_pass(kept(k), kept(k + 1));
-        } else {  // two stages on the segment's stencils, then the average
-          one_pass(kept(2 * k), kept(2 * k + 1));
-          one_pass(kept(2 * k + 1), kept(2 * k + 2));
-          launch_heun_combine(n, kept(2 * k + 2), kept(2 * k), K.Lx, K.Ly, st);
-        }
+      Stencils sten{c->nbr, c->cnt, c->ids[c->ci], c->colid[c->ci]};
+      if (keep) {
+        const int32_t* sn = snapshot(s2);
+        sten = Stencils{sn, sn + N * c->cap, sn + N * (c->cap + 1), sn + N * (c->cap + 2)};
+      } else {
+        run_segment(s2);
+        sten = Stencils{c->nbr, c->cnt, c->ids[c->ci], c->colid[c->ci]};
       }
-      S.p1 = c->p1; S.fac = c->fac; S.coef1 = S.coef2 = nullptr;
-      S.fbslot = c->fbslot; S.fbgrad = c->fbgrad;
+      auto kept = [&](int i) { return &tab[kept_at(s2, i)]; };
       // adjoint to the sorted order of this segment
-      launch_gather_fields(n, c->ids[c->ci], (const double* const*)(dtab + tlam + 7 * cur),
+      launch_gather_fields(n, sten.ids, (const double* const*)(dtab + tlam + 7 * cur),
                            dtab + tlam + 7 * (1 - cur), 7, st);
       cur = 1 - cur;
       // adjoint of one step (the paper's) or one stage (Heun's method) from
-      // state `sk`: l0 = J^T l1, with the step's fit data kept by the
-      // segment's re-run (k_stored >= 0: its step within the segment) or
-      // recomputed here
+      // state `sk`: l0 = J^T l1, with the step's kept fit data (k_stored >= 0:
+      // its step within the segment) or recomputed here
       auto adjoint_at = [&](double* const* sk, const double* l1, double* l0, int k_stored) {
         AdjArgs J{};
         J.n = n; J.cap = c->cap;
         J.x = sk[0]; J.y = sk[1]; J.z = sk[2]; J.u = sk[3]; J.v = sk[4]; J.w = sk[5];
         J.V = sk[6];
-        J.nbr = c->nbr; J.cnt = c->cnt; J.colid = c->colid[c->ci]; J.mui = c->d_mui;
+        J.nbr = sten.nbr; J.cnt = sten.cnt; J.colid = sten.colid; J.mui = c->d_mui;
         J.grids = c->d_grids; J.XU = c->XU;  // (free: the FP64 re-runs do not split)
         if (k_stored >= 0) {
-          const StepData d = step_data(k_stored);
+          const StepData d = step_data(s2, k_stored);
           J.fbslot = d.fbslot; J.fac = d.fac; J.p1 = d.p1; J.coef1 = d.coef1;
           J.coef2 = d.coef2; J.fbgrad = d.fbgrad;
         } else {
@@ -1626,7 +1714,7 @@ lp_status lp_step_adjoint(lp_ctx* c, const lp_particles* initial, const lp_mui* 
         cur = 1 - cur;
       }
       // back to caller order
-      launch_scatter_state(n, c->ids[c->ci], (const double* const*)(dtab + tlam + 7 * cur),
+      launch_scatter_state(n, sten.ids, (const double* const*)(dtab + tlam + 7 * cur),
                            dtab + tlam + 7 * (1 - cur), 7, st);
       cur = 1 - cur;
     }

@@ -86,6 +86,49 @@ def test_adjoint_matches_oracle_tangent_small(dev, orc):
             assert abs(fd - a) <= 1e-5 * abs(a) + 1e-6, (i, k, fd, a)
 
 
+@pytest.mark.parametrize("ghosts", [False, True])
+def test_adjoint_keeps_whole_run_or_reruns_segments_alike(dev, orc, ghosts):
+    """lp_step_adjoint with room for the whole run's data (the forward sweep
+    keeps every segment; nothing is recomputed) and with none
+    (lp_ctx_set_adjoint_memory(0): each segment re-run from its checkpoint),
+    on the sheared 8^3 cube, 13 FP64 steps with stencils rebuilt every 4 (a
+    last segment of one step), without and with ghosts: both equal the
+    oracle's tangent-linear run, and each other to rounding (the reverse
+    sweep's scattered sums are FP64 atomics, so not bit for bit)."""
+    from paper_2206_14061_gb300 import capi
+    wl = W.cube(8)
+    s0 = dict(wl.state)
+    s0["u"] = 20.0 * s0["z"]
+    pd = W.param_dict(wl)
+    mui, eos, prm = _split(pd)
+    if ghosts:
+        prm = dict(prm, free_surface=1)
+        pd = dict(pd, free_surface=1)
+    nsteps, C = 13, 4
+    rng = np.random.default_rng(8)
+    w = {k: rng.standard_normal(wl.n) for k in capi.FIELDS}
+    init = {k: torch.tensor(s0[k], device=dev) for k in capi.FIELDS}
+    seed = {k: torch.tensor(w[k], device=dev) for k in capi.FIELDS}
+    _, tan = orc.step_tangent(s0, orc.params(**pd), nsteps, rebuild_every=C)
+    ref = np.array([sum((w[k] * tan[t, f]).sum() for f, k in enumerate(capi.FIELDS))
+                    for t in range(3)])
+    out = {}
+    for mode, limit in (("keep", -1), ("rerun", 0)):
+        ctx = capi.Context(wl.n, cap=64)
+        ctx.set_adjoint_memory(limit)
+        dmui, gi = capi.lp_step_adjoint(ctx, init, mui, eos, prm, pd["dt"], nsteps, C, seed,
+                                        want_initial=True)
+        got = dmui.cpu().numpy()
+        print(mode, "adjoint", got, "tangent", ref)
+        assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max(), (mode, got, ref)
+        out[mode] = (got, {k: gi[k].cpu().numpy() for k in capi.FIELDS})
+    (a, ga), (b, gb) = out["keep"], out["rerun"]
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max(), (a, b)
+    for k in capi.FIELDS:
+        scale = np.abs(ga[k]).max()
+        assert np.abs(ga[k] - gb[k]).max() <= 1e-12 * scale + 1e-300, k
+
+
 def test_adjoint_across_all_three_regimes(dev, orc):
     """The adjoint on a sheared cube that spans the gas, inertial and
     quasi-static regimes (solid fraction 0.47 + 0.14 sin(2 pi x/L)
