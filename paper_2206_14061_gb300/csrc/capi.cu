@@ -35,12 +35,12 @@ void launch_neighbors(int keep, int n, const double* x, const double* y, const d
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
                       int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs = kBlock,
                       const int* search = nullptr, double* xref = nullptr,
-                      bool periodic = false);
+                      bool periodic = false, VerletSkip vs = VerletSkip{});
 void launch_filter(int n, const double* x, const double* y, const double* z, const float4* pf,
                    const int32_t* cand, const int32_t* ccnt, int capc, const GridCol* grids,
                    const int32_t* colid, double r, double floor_z, int cap, int32_t* nbr,
                    int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs,
-                   bool periodic = false);
+                   bool periodic = false, VerletSkip vs = VerletSkip{});
 void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,
                    const int32_t* cnt, int32_t* gcnt, const StepConsts& K, DevDiag* dg,
@@ -52,7 +52,7 @@ void launch_wrap_positions(int n, double* x, double* y, double Lx, double Ly, cu
 void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
 void launch_need_search(int n, const double* x, const double* y, const double* z,
                         const double* xref, double half_skin2, double Lx, double Ly, int* flag,
-                        cudaStream_t st);
+                        VerletSkip vs, cudaStream_t st);
 void launch_nbr_to_caller(int n, int cap, const int32_t* ids, const int32_t* nbr_s,
                           const int32_t* cnt_s, int32_t* nbr_o, int32_t* cnt_o, cudaStream_t st);
 // fit.cu
@@ -120,6 +120,7 @@ struct lp_ctx {
   // last call stay valid for the same particle count, columns and search
   // parameters until another entry point uses the context
   bool lists_valid = false;
+  bool marg_valid = false;   // with lists_valid: the filter margins (vmarg) still hold
   int64_t lists_n = 0;
   std::vector<int32_t> lists_offs;
   double lists_sig[6] = {};
@@ -146,6 +147,9 @@ struct lp_ctx {
   int32_t* ccnt = nullptr;
   int capc = 0;
   double* xref = nullptr;    // positions at the last search, 3 x n
+  float* vmarg = nullptr;    // filter skipping (VerletSkip): margins, n
+  float* vdmax = nullptr;    // running maximum displacements since the search, n
+  unsigned* vdall = nullptr; // their maximum
   int* d_search = nullptr;   // device flag: search at the next step
   int32_t* iota = nullptr;   // 0..n-1 (identity gather)
   double skin = 0.0;         // skin of the current lp_step call (0: off)
@@ -390,6 +394,13 @@ void sort_particles(lp_ctx* c, int n, int kind, int nsrc, cudaStream_t st,
   c->launches += 7;
 }
 
+// Filter skipping between searches (VerletSkip); off with free-surface ghosts,
+// whose kernel rewrites the stencils after the filter
+VerletSkip verlet_skip(lp_ctx* c, const StepConsts& K) {
+  if (K.free_surface || !c->vmarg) return VerletSkip{};
+  return VerletSkip{c->vmarg, c->vdmax, c->vdall};
+}
+
 StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
   StepArgs A{};
   A.n = n;
@@ -417,6 +428,7 @@ StepArgs step_args(lp_ctx* c, int n, const StepConsts& K) {
     const double hs = 0.5 * c->skin;
     A.half_skin2 = hs * hs * (1.0 - 0x1p-20);
     A.need_search = c->d_search;
+    A.vskip = verlet_skip(c, K);
   }
   return A;
 }
@@ -448,10 +460,11 @@ void run_step(lp_ctx* c, int n, const StepConsts& K, int prec, bool rebuild, cud
     launch_neighbors(false, n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf, c->colid[c->ci],
                      c->ids[c->ci], c->d_grids, c->cells + 2 * c->cell_capacity, nullptr,
                      K.radius + c->skin, K.mirror_mode, K.floor_z, c->capc, c->cand, c->ccnt,
-                     c->dg, st, c->bs_nbr, c->d_search, c->xref, K.periodic != 0);
+                     c->dg, st, c->bs_nbr, c->d_search, c->xref, K.periodic != 0,
+                     verlet_skip(c, K));
     launch_filter(n, c->X[e][0], c->X[e][1], c->X[e][2], c->pf, c->cand, c->ccnt, c->capc,
                   c->d_grids, c->colid[c->ci], K.radius, K.floor_z, c->cap, c->nbr, c->cnt,
-                  c->dg, c->d_search, st, c->bs_nbr, K.periodic != 0);
+                  c->dg, c->d_search, st, c->bs_nbr, K.periodic != 0, verlet_skip(c, K));
     if (K.free_surface) {
       launch_ghosts(n, c->X[e][0], c->X[e][1], c->X[e][2], c->colid[c->ci], c->d_grids, c->Xfix,
                     c->nbr, c->cnt, c->gcnt, K, c->dg, st, c->bs_nbr, c->glist, c->gcount, c->olist);
@@ -726,6 +739,9 @@ lp_status lp_ctx_create(const lp_ctx_desc* desc, lp_ctx** out) {
   if (s == LP_OK) s = dalloc(c, &c->cand, n * c->capc);
   if (s == LP_OK) s = dalloc(c, &c->ccnt, n);
   if (s == LP_OK) s = dalloc(c, &c->xref, 3 * n);
+  if (s == LP_OK) s = dalloc(c, &c->vmarg, n);
+  if (s == LP_OK) s = dalloc(c, &c->vdmax, n);
+  if (s == LP_OK) s = dalloc(c, &c->vdall, 1);
   if (s == LP_OK) s = dalloc(c, &c->d_search, 1);
   if (s == LP_OK) s = dalloc(c, &c->iota, n);
   if (s == LP_OK) {
@@ -1194,10 +1210,19 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
     if (cudaMemcpyAsync(c->d_search, &first, sizeof(int), cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
       return LP_ERR_CUDA;
+    // filter margins carry over only with the kept lists of a call that kept
+    // them up to date (no ghosts, no persistent launch): nothing else has
+    // written the stencils since, and the need-search test below adds the
+    // caller's new state to the displacement bounds; otherwise NaN margins,
+    // so that every particle is filtered on the first step
+    if (!(reuse && c->marg_valid) &&
+        cudaMemsetAsync(c->vmarg, 0xff, sizeof(float) * n, st) != cudaSuccess)
+      return LP_ERR_CUDA;
     if (reuse) {
       const double hs = 0.5 * skin;
       launch_need_search(n, c->X[d][0], c->X[d][1], c->X[d][2], c->xref,
-                         hs * hs * (1.0 - 0x1p-20), q->period_x, q->period_y, c->d_search, st);
+                         hs * hs * (1.0 - 0x1p-20), q->period_x, q->period_y, c->d_search,
+                         VerletSkip{c->vmarg, c->vdmax, c->vdall}, st);
       c->launches += 2;  // gather, displacement test
     }
   }
@@ -1219,6 +1244,7 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, const lp_mui* mui, const lp_eos* e
   }
   if (keep && skin > 0.0) {  // lists, reference positions and order stay for the next call
     c->lists_valid = true;
+    c->marg_valid = !K.free_surface && q->launch_mode != LP_LAUNCH_PERSISTENT;
     c->lists_n = n;
     c->lists_offs = offs;
     std::memcpy(c->lists_sig, sig, sizeof(sig));

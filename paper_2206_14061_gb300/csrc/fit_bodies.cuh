@@ -995,6 +995,7 @@ template <int PREC, bool PER = false>
 __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) {
   int regime = 1;
   bool overc = false, nonfin = false, below = false;
+  float disp = 0.f;  // displacement from the search positions (filter skipping)
   if (live) {
     const int n = A.n;
     const double xi = A.x[s], yi = A.y[s], zi = A.z[s];
@@ -1212,7 +1213,12 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
       const double ex = per_off<PER>(x1 - A.xref[s], A.K.Lx);
       const double ey = per_off<PER>(y1 - A.xref[A.n + s], A.K.Ly);
       const double ez = z1 - A.xref[2 * A.n + s];
-      if (!(((ex * ex) + (ey * ey)) + (ez * ez) <= A.half_skin2)) *A.need_search = 1;
+      const double e2 = ((ex * ex) + (ey * ey)) + (ez * ez);
+      if (!(e2 <= A.half_skin2)) *A.need_search = 1;
+      if (A.vskip.dmax) {  // rounded up: the conversion and sqrtf err by at most 2 ulp
+        disp = fmaxf(A.vskip.dmax[s], sqrtf(__double2float_ru(e2)) * (1.f + 0x1p-21f));
+        A.vskip.dmax[s] = disp;
+      }
     }
     below = A.K.mirror_mode != LP_MIRROR_NONE && z1 < A.K.floor_z;
   }
@@ -1221,6 +1227,10 @@ __device__ __forceinline__ void pass2_body(const StepArgs& A, int s, bool live) 
   warp_count(&A.dg->n_over_c, live && overc);
   warp_count(&A.dg->n_nonfinite, live && nonfin);
   warp_count(&A.dg->n_below_floor, live && below);
+  if (A.vskip.dmax_all) {  // one atomic per warp (floats >= 0 order as their bits)
+    const unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(live ? disp : 0.f));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(A.vskip.dmax_all, v);
+  }
   if (live && nonfin) atomicOr(&A.dg->flags, (unsigned)LP_FLAG_NONFINITE);
   if (live && below) atomicOr(&A.dg->flags, (unsigned)LP_FLAG_BELOW_FLOOR);
 }

@@ -239,6 +239,21 @@ __device__ __forceinline__ void warp_count(unsigned long long* ctr, bool pred) {
 // indices of the per-particle pass-1 outputs in the SoA block p1[k*n + s]
 enum { P1_GD = 0, P1_GN = 6, P1_LD = 7, P1_VN = 10, P1_DIV = 11, P1_N = 12 };
 
+// Filter skipping between Verlet searches. A particle whose stencil was
+// computed at step t_c keeps it while every candidate stays on the same side
+// of the radius: the pair distance moves by at most the two particles'
+// displacements since t_c, each at most twice the running maximum of their
+// displacement from the search positions. So with marg_i the smallest
+// distance of a candidate of i from the radius at t_c (a lower bound, net of
+// the FP32 rounding) and dmax the running maxima since the search,
+// 2 (dmax_i + max_j dmax_j) < marg_i means the exact test would keep the same
+// candidates, in the same order. All members NULL: the filter always runs.
+struct VerletSkip {
+  float* marg;          // per particle, at its last filter; < 0 forces the filter
+  float* dmax;          // per particle, running maximum displacement since the search
+  unsigned* dmax_all;   // maximum of dmax over all particles (bits of a float >= 0)
+};
+
 struct StepArgs {
   int n, cap;
   const double *x, *y, *z, *u, *v, *w, *V;  // state at time n (sorted order)
@@ -282,6 +297,7 @@ struct StepArgs {
   const double* xref;  // 3 * n, or NULL when candidate lists are off
   double half_skin2;
   int* need_search;
+  VerletSkip vskip;    // running maximum displacements for filter skipping
 };
 
 struct FitArgs {

@@ -73,20 +73,34 @@ void launch_heun_combine(int n, double* const* y, double* const* y0, double Lx, 
   k_heun_combine<<<(n + 255) / 256, 256, 0, st>>>(n, a, b, Lx, Ly);
 }
 // Verlet lists kept across calls: flag a search if some particle moved more
-// than skin/2 (squared: half_skin2) since the last one, or is not finite
+// than skin/2 (squared: half_skin2) since the last one, or is not finite; the
+// caller's state enters the running maximum displacements of filter skipping
+// as every step's new state does (the pass-2 epilogue)
 __global__ void k_need_search(int n, const double* __restrict__ x, const double* __restrict__ y,
                               const double* __restrict__ z, const double* __restrict__ xref,
-                              double half_skin2, double Lx, double Ly, int* __restrict__ flag) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const double ex = min_image(x[s] - xref[s], Lx), ey = min_image(y[s] - xref[n + s], Ly);
-  const double ez = z[s] - xref[2 * n + s];
-  if (!(((ex * ex) + (ey * ey)) + (ez * ez) <= half_skin2)) *flag = 1;
+                              double half_skin2, double Lx, double Ly, int* __restrict__ flag,
+                              VerletSkip vs) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  float disp = 0.f;
+  if (s < n) {
+    const double ex = min_image(x[s] - xref[s], Lx), ey = min_image(y[s] - xref[n + s], Ly);
+    const double ez = z[s] - xref[2 * n + s];
+    const double e2 = ((ex * ex) + (ey * ey)) + (ez * ez);
+    if (!(e2 <= half_skin2)) *flag = 1;
+    if (vs.dmax) {
+      disp = fmaxf(vs.dmax[s], sqrtf(__double2float_ru(e2)) * (1.f + 0x1p-21f));
+      vs.dmax[s] = disp;
+    }
+  }
+  if (vs.dmax_all) {  // (the whole warp is here: no early exit above)
+    const unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(disp));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(vs.dmax_all, v);
+  }
 }
 void launch_need_search(int n, const double* x, const double* y, const double* z,
                         const double* xref, double half_skin2, double Lx, double Ly, int* flag,
-                        cudaStream_t st) {
-  k_need_search<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, z, xref, half_skin2, Lx, Ly, flag);
+                        VerletSkip vs, cudaStream_t st) {
+  k_need_search<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, z, xref, half_skin2, Lx, Ly, flag, vs);
 }
 void launch_wrap_positions(int n, double* x, double* y, double Lx, double Ly, cudaStream_t st) {
   k_wrap_positions<<<(n + 255) / 256, 256, 0, st>>>(n, x, y, Lx, Ly);

@@ -375,17 +375,38 @@ __device__ __forceinline__ void stencil_stats(bool live, int c, int cap, DevDiag
 // (found within radius + skin at the last search) that passes the exact
 // radius test, in candidate order. Same FP32 prefilter and uncontracted FP64
 // test as the search. Every lane of the warp must call it (live or not).
-template <bool PER = false>
+// With vs.marg set, a particle whose candidates provably all kept their side
+// of the radius since its last filter (VerletSkip) keeps its stencil, and a
+// filtered particle records its margin, a lower bound of min |d - r| over its
+// candidates: with m a lower bound of |d^2 - r^2|, |d - r| = m / (d + r) >=
+// m r / (2 r^2 + m), increasing in m, so the smallest m bounds every
+// candidate (one beyond 2r has |d - r| > r, above any such bound). m is the
+// exact FP64 |d^2 - r^2| where the filter computes it (the prefilter band),
+// else the FP32 one net of its error bound e2f: each FP32 offset is within
+// ec = 2^-24 (6 cmax + 6 r) of the exact one (rounded positions, the
+// difference, the mirror height or the period), so the FP32 d^2 of a pair
+// within 2r is within ec (7 r + 3 ec) plus 16 roundings of r^2 (the sums,
+// r^2 itself and the subtractions that form m).
+// (TRACK: vs is set; without it the kernel is the plain filter)
+template <bool PER = false, bool TRACK = false>
 __device__ __forceinline__ void filter_body(
     int s, bool live, int n, const double* __restrict__ x, const double* __restrict__ y,
     const double* __restrict__ z, const float4* __restrict__ pf,
     const int32_t* __restrict__ cand, const int32_t* __restrict__ ccnt, int capc,
     const GridCol* __restrict__ grids, const int32_t* __restrict__ colid, double r,
     double floor_z, int cap, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt,
-    DevDiag* __restrict__ dg) {
+    DevDiag* __restrict__ dg, VerletSkip vs = VerletSkip{}) {
   int c = 0;
-  bool over = false;
-  if (live) {
+  bool over = false, built = live;
+  if (TRACK && live) {
+    const float mg = vs.marg[s];
+    if (mg > 0.f && 2.f * (vs.dmax[s] + __uint_as_float(*vs.dmax_all)) < mg) {  // (no NaN)
+      c = cnt[s];
+      over = c > cap || ccnt[s] > capc;
+      built = false;
+    }
+  }
+  if (built) {
     const GridCol g = grids[colid[s]];
     const double xi = x[s], yi = y[s], zi = z[s];
     const double r2 = r * r;
@@ -402,6 +423,9 @@ __device__ __forceinline__ void filter_body(
     const float lo = r2f * (1.0f - band), hi = r2f * (1.0f + band);
     const bool exact_only = !(band < 0.25f);  // far from the origin: FP64 for every pair
     const int m = min(ccnt[s], capc);
+    float m2 = 3.f * r2f;  // lower bound of min |d^2 - r^2| (at most 3 r^2: see above)
+    const float ec = 0x1p-24f * (6.f * cmax + 6.f * rf);
+    const float e2f = (ec * (7.f * rf + 3.f * ec) + 16.f * 0x1p-24f * r2f) * (1.f + 0x1p-10f);
     // Candidates in chunks of kFilterChunk: the chunk's position gathers are
     // issued together and the next chunk's codes load while this one is
     // tested, so each thread keeps several gathers in flight. The stencil
@@ -435,14 +459,20 @@ __device__ __forceinline__ void filter_body(
         }
         const float dzf = (mir ? fz2 - pj[t].z : pj[t].z) - pi.z;
         const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
-        if (!exact_only && d2f > hi) continue;
+        if (!exact_only && d2f > hi) {
+          if (TRACK) m2 = fminf(m2, (d2f - r2f) - e2f);
+          continue;
+        }
         bool in;
         if (!exact_only && d2f < lo) {
           in = true;
+          if (TRACK) m2 = fminf(m2, (r2f - d2f) - e2f);
         } else {
           double d2;
           const double zj = mir ? __dsub_rn(2.0 * floor_z, z[j]) : z[j];
           in = exact_in(xi, yi, zi, x[j], y[j], zj, r2, &d2, PER ? g.Lx : 0.0, PER ? g.Ly : 0.0);
+          // (the FP64 d^2 errs by far less than 2^-40 r^2)
+          if (TRACK) m2 = fminf(m2, __double2float_rd(fabs(d2 - r2) - 0x1p-40 * r2));
         }
         if (!in) continue;
         if (c < cap) nbr[(int64_t)c * n + s] = (int32_t)cd;
@@ -453,10 +483,14 @@ __device__ __forceinline__ void filter_body(
     }
     over = c > cap || ccnt[s] > capc;
     cnt[s] = c;
+    if (TRACK) {  // rounded down (1 - 2^-20: the FP32 evaluation and rf, r2f)
+      const float mm = fmaxf(0.f, m2);
+      vs.marg[s] = mm * rf / (2.f * r2f + mm) * (1.f - 0x1p-20f);
+    }
   }
   warp_count(&dg->n_overflow, live && over);
   if (live && over) atomicOr(&dg->flags, (unsigned)LP_FLAG_OVERFLOW);
-  stencil_stats(live, c, cap, dg);
+  stencil_stats(built, c, cap, dg);  // (stencils built this step)
 }
 
 // ------------------------------------------------------- free boundary

@@ -201,13 +201,18 @@ k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
             const double* __restrict__ radius, double r_const, int mirror_mode, double floor_z,
             int cap, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt,
             DevDiag* __restrict__ dg, const int* search, double* __restrict__ xref,
-            int keep_mode) {
+            int keep_mode, VerletSkip vs) {
   if (!searching(search)) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (xref && s < n) {  // positions of this search, for the displacement test
     xref[s] = x[s];
     xref[n + s] = y[s];
     xref[2 * n + s] = z[s];
+    if (vs.marg) {  // new candidates: filter every particle, displacements from here
+      vs.marg[s] = -1.f;
+      vs.dmax[s] = 0.f;
+      if (s == 0) *vs.dmax_all = 0u;
+    }
   }
   neighbors_body<KEEP, PER>(s, s < n, n, x, y, z, pf, colid, ids, grids, start, radius, r_const,
                             mirror_mode, floor_z, cap, nbr, cnt, dg, xref == nullptr, keep_mode);
@@ -215,18 +220,18 @@ k_neighbors(int n, const double* __restrict__ x, const double* __restrict__ y,
 
 // Verlet filter (filter_body). Thread 0 clears the search flag for the
 // displacement test of this step's update.
-template <bool PER>
+template <bool PER, bool TRACK>
 __global__ void __launch_bounds__(kMaxBlock)
 k_filter(int n, const double* __restrict__ x, const double* __restrict__ y,
          const double* __restrict__ z, const float4* __restrict__ pf,
          const int32_t* __restrict__ cand, const int32_t* __restrict__ ccnt, int capc,
          const GridCol* __restrict__ grids, const int32_t* __restrict__ colid, double r,
          double floor_z, int cap, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt,
-         DevDiag* __restrict__ dg, int* search) {
+         DevDiag* __restrict__ dg, int* search, VerletSkip vs) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s == 0) *search = 0;
-  filter_body<PER>(s, s < n, n, x, y, z, pf, cand, ccnt, capc, grids, colid, r, floor_z, cap,
-                   nbr, cnt, dg);
+  filter_body<PER, TRACK>(s, s < n, n, x, y, z, pf, cand, ccnt, capc, grids, colid, r, floor_z,
+                          cap, nbr, cnt, dg, vs);
 }
 
 // Free-surface ghosts (ghost_body): fixed-point positions, then completion of
@@ -322,33 +327,40 @@ void launch_neighbors(int keep, int n, const double* x, const double* y, const d
                       const GridCol* grids, const uint32_t* start, const double* radius,
                       double r_const, int mirror_mode, double floor_z, int cap, int32_t* nbr,
                       int32_t* cnt, DevDiag* dg, cudaStream_t st, int bs, const int* search,
-                      double* xref, bool periodic) {
+                      double* xref, bool periodic, VerletSkip vs) {
   const int nb = (n + bs - 1) / bs;
   if (keep)  // (stencils for callers: never periodic)
     k_neighbors<true, false><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
                                                  r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
-                                                 search, xref, keep);
+                                                 search, xref, keep, vs);
   else if (periodic)
     k_neighbors<false, true><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start, radius,
                                                  r_const, mirror_mode, floor_z, cap, nbr, cnt, dg,
-                                                 search, xref, 0);
+                                                 search, xref, 0, vs);
   else
     k_neighbors<false, false><<<nb, bs, 0, st>>>(n, x, y, z, pf, colid, ids, grids, start,
                                                   radius, r_const, mirror_mode, floor_z, cap, nbr,
-                                                  cnt, dg, search, xref, 0);
+                                                  cnt, dg, search, xref, 0, vs);
 }
 void launch_filter(int n, const double* x, const double* y, const double* z, const float4* pf,
                    const int32_t* cand, const int32_t* ccnt, int capc, const GridCol* grids,
                    const int32_t* colid, double r, double floor_z, int cap, int32_t* nbr,
                    int32_t* cnt, DevDiag* dg, int* search, cudaStream_t st, int bs,
-                   bool periodic) {
+                   bool periodic, VerletSkip vs) {
   const int nb = (n + bs - 1) / bs;
-  if (periodic)
-    k_filter<true><<<nb, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r, floor_z,
-                                      cap, nbr, cnt, dg, search);
+  const bool track = vs.marg != nullptr;
+  if (periodic && track)
+    k_filter<true, true><<<nb, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
+                                            floor_z, cap, nbr, cnt, dg, search, vs);
+  else if (periodic)
+    k_filter<true, false><<<nb, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
+                                             floor_z, cap, nbr, cnt, dg, search, vs);
+  else if (track)
+    k_filter<false, true><<<nb, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
+                                             floor_z, cap, nbr, cnt, dg, search, vs);
   else
-    k_filter<false><<<nb, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
-                                       floor_z, cap, nbr, cnt, dg, search);
+    k_filter<false, false><<<nb, bs, 0, st>>>(n, x, y, z, pf, cand, ccnt, capc, grids, colid, r,
+                                              floor_z, cap, nbr, cnt, dg, search, vs);
 }
 void launch_ghosts(int n, const double* x, const double* y, const double* z,
                    const int32_t* colid, const GridCol* grids, int4* X, int32_t* nbr,

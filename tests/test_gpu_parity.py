@@ -564,6 +564,60 @@ def test_step_verlet_skin_under_shear_drift(dev, capi):
                           stream=torch.cuda.Stream())
         e = _state_err(got, ref, s)
         assert max(e.values()) <= 1e-12, (mode, e)
+        # stencils built by the filter (the persistent launch filters every step)
+        print("mode", mode, "stencils built per particle-step:", d["n_stencils"] / (40 * wl.n))
+        assert wl.n <= d["n_stencils"] <= 40 * wl.n
+        if mode == 2:
+            assert d["n_stencils"] == 40 * wl.n
+
+
+def test_step_verlet_filter_skipping_under_slow_shear(dev, capi, orc):
+    """Slow gas-regime shear u = G z over 200 steps: particles keep their
+    stencils while their candidates provably stay on one side of the radius,
+    and are filtered again before any pair can cross it; pairs do cross (the
+    oracle's stencils of the first and last states differ), and the state
+    equals the full-search run's."""
+    wl = W.cube(14)
+    s = dict(wl.state)
+    s["u"] = 1.0 * s["z"]  # 0.003h relative drift of pairs 1.5h apart over the run
+    s["V"] = np.full(wl.n, 1.0 / 0.3)  # gas: a = g
+    wl.state = s
+    pd = dict(W.param_dict(wl), mirror_mode=0, gz=0.0)
+    nsteps = 200
+    ref, _ = _run_gpu(capi, dev, wl, pd, nsteps, launch_mode=0)
+    p = orc.params(**pd)
+    n0, c0, _ = orc.step_stencils(s["x"], s["y"], s["z"], p, brute=False)
+    n1, c1, _ = orc.step_stencils(ref["x"], ref["y"], ref["z"], p, brute=False)
+    changed = sum(set(n0[i, :c0[i]].tolist()) != set(n1[i, :c1[i]].tolist())
+                  for i in range(wl.n))
+    print("particles whose stencil changed over the run:", changed)
+    assert changed > 0.03 * wl.n
+    for mode in (0, 1):
+        got, d = _run_gpu(capi, dev, wl, pd, nsteps, launch_mode=mode, skin=0.1 * pd["h"],
+                          stream=torch.cuda.Stream())
+        e = _state_err(got, ref, s)
+        built = d["n_stencils"] / (nsteps * wl.n)
+        print("mode", mode, "stencils built per particle-step:", built, "errors:", e)
+        assert max(e.values()) <= 1e-12, (mode, e)
+        assert built < 0.99, built
+
+
+def test_step_verlet_filter_skipped_at_rest(dev, capi):
+    """A lattice at rest without gravity stays bitwise at rest; with candidate
+    lists the first step filters every particle and the later steps keep the
+    stencils (no particle moved), with the same state as the full search."""
+    wl = W.cube(12)
+    s = dict(wl.state)
+    s["u"] = np.zeros(wl.n)
+    wl.state = s
+    pd = dict(W.param_dict(wl), gz=0.0)
+    ref, _ = _run_gpu(capi, dev, wl, pd, 10, launch_mode=0)
+    for mode in (0, 1):
+        got, d = _run_gpu(capi, dev, wl, pd, 10, launch_mode=mode, skin=0.1 * pd["h"],
+                          stream=torch.cuda.Stream())
+        for k in capi.FIELDS:
+            assert np.array_equal(got[k], ref[k]) and np.array_equal(got[k], s[k]), (mode, k)
+        assert wl.n <= d["n_stencils"] <= 1.01 * wl.n, (mode, d["n_stencils"])
 
 
 def test_persistent_bounded_wait_reports_timeout(dev, capi):
