@@ -51,6 +51,8 @@ def test_invalid_arguments_fail_on_host(L):
                            None) == capi.LP_ERR_INVALID_ARG
     assert L.lp_step_adjoint(None, None, None, None, None, 1e-5, 1, 1, None, None, None,
                              None) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_ctx_set_adjoint_memory(None, 0) == capi.LP_ERR_INVALID_ARG
+    assert L.lp_ctx_set_wait_limit(None, 1, 0) == capi.LP_ERR_INVALID_ARG
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
